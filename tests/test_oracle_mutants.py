@@ -1,0 +1,50 @@
+"""Plants one plausible mistake at a time in a copy of the oracle source
+(compiled on the CPU into a temporary library) and checks that at least one
+pin fails on it, so that the pins would notice such a mistake in the oracle."""
+import pytest
+
+import oracle
+from tests import _pins
+
+# (name, text in cg_oracle.c, replacement)
+MUTANTS = [
+    ("suffix_complement", "out[k].contrib = suf[x];", "out[k].contrib = len[w] - suf[x];"),
+    ("entry_end_from_own_bit", "o = (code[x] >> 1) & 1;", "o = code[x] & 1;"),
+    ("leave_through_entry_end", "edge_at_end(rp, col, code, is_branch, cur, 1 - o)", "edge_at_end(rp, col, code, is_branch, cur, o)"),
+    ("rc_without_complement", "3 - stored_base(packed, off, L - 1 - k)", "stored_base(packed, off, L - 1 - k)"),
+    ("rc_without_reversal", "3 - stored_base(packed, off, L - 1 - k)", "3 - stored_base(packed, off, k)"),
+    ("prefix_not_suffix", "for (int64_t k = L - contrib, t = 0; k < L; ++k, ++t)", "for (int64_t k = 0, t = 0; k < contrib; ++k, ++t)"),
+    ("degree_threshold_4", "b1[v] = (uint8_t)(d >= 3);", "b1[v] = (uint8_t)(d >= 4);"),
+    ("degree_threshold_2", "b1[v] = (uint8_t)(d >= 3);", "b1[v] = (uint8_t)(d >= 2);"),
+    ("no_same_end_rule", "if (cnt == 2 && ends[0] == ends[1]) br = 1;", "if (0) br = 1;"),
+    ("same_end_rule_inverted", "if (cnt == 2 && ends[0] == ends[1]) br = 1;", "if (cnt == 2 && ends[0] != ends[1]) br = 1;"),
+    ("same_end_counts_masked_nbrs", "if (b1[col[x]]) continue;\n        if (cnt < 2)", "if (0) continue;\n        if (cnt < 2)"),
+    ("root_orientation_flipped", "o_root = 1 - e;", "o_root = e;"),
+    ("larger_root_first", "          o_root = 0;\n        }\n        break;", "          o_root = 0;\n        }\n        continue;"),
+    ("cycle_starts_reverse", "if (root < 0) { root = c; o_root = 0; cycle = 1; }", "if (root < 0) { root = c; o_root = 1; cycle = 1; }"),
+    ("no_min_chain_filter", "if (q < min_chain_reads) continue;", "if (0) continue;"),
+    ("ascii_table_swapped", "{'A', 'C', 'G', 'T'}", "{'A', 'G', 'C', 'T'}"),
+    ("packed_bit_order", "return (packed[q >> 2] >> (2 * (q & 3))) & 3;", "return (packed[q >> 2] >> (6 - 2 * (q & 3))) & 3;"),
+    ("validate_skips_mirror_code", "if (code[y] != swapped) BAD", "if (0) BAD"),
+    ("validate_allows_full_suffix", "suf[x] > len[v] - 1", "suf[x] > len[v]"),
+    ("lpt_most_loaded", "if (loads[b] < loads[best]) best = b;", "if (loads[b] > loads[best]) best = b;"),
+    ("lpt_ascending", "while (j > 0 && sizes[order[j - 1]] < sizes[t])", "while (j > 0 && sizes[order[j - 1]] > sizes[t])"),
+    ("uf_ignores_mask", "int64_t v = col[x];\n      if (is_branch[v]) continue;\n      int64_t a = uf_find",
+     "int64_t v = col[x];\n      int64_t a = uf_find"),
+    ("contigs_in_root_order", "r->chain_id[s->read] = (int32_t)c;", "r->chain_id[s->read] = (int32_t)root;"),
+    ("rank_off_by_one", "r->rank[s->read] = (int32_t)i;", "r->rank[s->read] = (int32_t)(i + 1);"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_catch_planted_mistake(name, old, new, tmp_path):
+    src = oracle.source()
+    assert src.count(old) == 1, f"mutation site for {name} must be unique"
+    mut = oracle.compile_variant(src.replace(old, new), str(tmp_path / f"mut_{name}.so"))
+    caught = []
+    for pin in _pins.ALL_PINS:
+        try:
+            pin(mut)
+        except Exception as e:  # an assertion or a crash-free error report both count
+            caught.append(f"{pin.__name__}: {type(e).__name__}")
+    assert caught, f"no pin notices the planted mistake {name}"
