@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""Contig-generation benchmark on GB300: contig Gbases/s of the plain path.
+
+One step = one pass of the whole path over one string graph: branch masking,
+successor table, list ranking, contig sizes and order, compaction by chain,
+piece offsets and spelling (cg_mask_branches -> cg_chains -> cg_emit_contigs),
+with the graph and the reads resident in HBM. The default workload is the
+3.1 Gb genome-shaped graph (6.2M reads, 23 GB of 2-bit packed reads).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+Prints one JSON line (rank 0). With --gpus N > 1 under torchrun every rank
+runs an independent replica of the workload (the path needs no cross-GPU
+exchange) and the time is the maximum over ranks. --impl reference times the
+CPU oracle instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "contig Gbases/s & ms per graph (plain vs batched) vs HBM roofline; p50/p99 latency"
+UNIT = "Gbases/s"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=30)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--workload", default="genome-3.1Gb")
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU budget of the oracle baseline sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--min-chain-reads", type=int, default=2)
+    p.add_argument("--threads", type=int, default=0, help="generator threads (0 = all cores)")
+    return p.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"])}, "measured"
+    except Exception:
+        return PEAKS_FALLBACK, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples (SM clock, reasons) taken while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append((time.time(), [x.strip() for x in line.split(",")]))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+
+    def summary(self, t0, t1):
+        rows = [r for t, r in self.rows if t0 <= t <= t1 and len(r) >= 9]
+        window = "timed region"
+        if not rows:
+            rows = [r for _, r in self.rows if len(r) >= 9]
+            window = "whole run (timed region shorter than the 100 ms sampling period)"
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "window": window}
+
+
+# -------------------------------------------------------------- workload
+def workload_cfg(name):
+    import gen
+    if name not in gen.WORKLOADS:
+        raise SystemExit(f"unknown workload {name}; one of {sorted(gen.WORKLOADS)}")
+    return gen.WORKLOADS[name]()
+
+
+def generate_pinned(cfg, threads):
+    import torch
+
+    import gen
+    keep = []
+
+    def alloc(shape, dt):
+        t = torch.empty(shape, dtype=getattr(torch, dt.__name__ if hasattr(dt, "__name__") else str(dt)),
+                        pin_memory=True)
+        keep.append(t)
+        return t.numpy()
+    G = gen.generate(cfg, threads=threads or None, alloc=alloc, keep_genome=False)
+    G._pinned = keep
+    return G
+
+
+def bmin_bytes(G, W, total, C):
+    """Least bytes any implementation moves: row_ptr, every CSR entry once,
+    len+off of the spelled reads, the 2-bit bases spelled, the ASCII output
+    and the contig offsets."""
+    rp = G.row_ptr.dtype.itemsize
+    return (G.n + 1) * rp + 9 * G.m + 12 * W + (total + 3) // 4 + total + 8 * (C + 1)
+
+
+# --------------------------------------------------------------- ours
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_2207_04350_gb300 import cg
+
+    torch.cuda.set_device(local_rank)
+    pk, pk_kind = peaks()
+    cfg = workload_cfg(args.workload)
+    t_gen = time.time()
+    G = generate_pinned(cfg, args.threads)
+    t_gen = time.time() - t_gen
+
+    stream = torch.cuda.Stream()
+    ctx = cg.cg_create(local_rank, stream=stream)
+    names = ("row_ptr", "col", "code", "suf", "len", "off", "packed")
+    with torch.cuda.stream(stream):
+        dev = {k: torch.from_numpy(getattr(G, k)).to("cuda", non_blocking=True) for k in names}
+    stream.synchronize()
+
+    class D:
+        pass
+    dg = D()
+    for k, v in dev.items():
+        setattr(dg, k, v)
+    g = cg.cg_load_graph(ctx, dg, flags=cg.BORROW_DEVICE, min_chain_reads=args.min_chain_reads)
+    # sizes (untimed): walk positions, contigs, bases
+    cid = np.empty(G.n, np.int32)
+    cg.cg_chains(g, cid, None, None)
+    W = int((cid >= 0).sum())
+    n_contigs, total = cg.cg_emit_contigs(g)
+    bases = torch.empty(max(16, (total + 15) // 16 * 16), dtype=torch.uint8, device="cuda")
+    contig_off = torch.empty(n_contigs + 1, dtype=torch.int64, device="cuda")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB of L2
+    cg.cg_set_timing(ctx, True)
+
+    def step():
+        cg.cg_mask_branches(g, want_count=False)
+        cg.cg_chains(g, want_counts=False)
+        cg.cg_emit_contigs(g, contig_off, bases, want_counts=False)
+
+    for _ in range(args.warmup):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+        step()
+    cg.cg_sync(ctx)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = cg.cg_get_stats(ctx)["kernels_launched"]
+    step_ms, emit_ms, stage = [], [], []
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    t0 = time.time()
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(2)
+        ev0.record(stream)
+        step()
+        ev1.record(stream)
+        st = cg.cg_get_stats(ctx)          # waits for the step
+        step_ms.append(ev0.elapsed_time(ev1))
+        emit_ms.append(st["stage_ms"][3])
+        stage.append(st["stage_ms"])
+    cg.cg_sync(ctx)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    launches = cg.cg_get_stats(ctx)["kernels_launched"] - launches0
+    if world > 1:
+        torch.distributed.barrier()
+    time.sleep(0.2)
+    clocks.stop()
+    ms = statistics.mean(step_ms)
+    ms_emit = statistics.mean(emit_ms)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * total / (ms * 1e-3) / 1e9
+
+    # end to end through the public API with host buffers (pinned inputs / outputs)
+    e2e = None
+    if not args.no_e2e and args.e2e_steps > 0:
+        h_bases = torch.empty(max(total, 1), dtype=torch.uint8, pin_memory=True).numpy()
+        h_off = torch.empty(n_contigs + 1, dtype=torch.int64, pin_memory=True).numpy()
+        h2d = sum(getattr(G, k).nbytes for k in names)
+        d2h = total + (n_contigs + 1) * 8
+        times = []
+        for i in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            gh = cg.cg_load_graph(ctx, G, min_chain_reads=args.min_chain_reads)
+            cg.cg_mask_branches(gh, want_count=False)
+            cg.cg_chains(gh, want_counts=False)
+            cg.cg_emit_contigs(gh, h_off, h_bases)
+            gh.close()
+            b = time.perf_counter()
+            if i > 0:                      # the first one warms the context's buffer pool
+                times.append(b - a)
+        te = statistics.mean(times)
+        e2e = {"value": world * total / te / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": te * 1e3, "steps": len(times), "path": "cg_load_graph(host, validated) -> "
+               "cg_mask_branches -> cg_chains -> cg_emit_contigs(host) -> cg_free_graph"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args, cfg)
+
+    B = bmin_bytes(G, W, total, n_contigs)
+    emit_bytes = total + (total + 3) // 4
+    ach = emit_bytes / (ms_emit * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "ms_per_graph": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic (seeded generator, workload recipe in DESIGN.md)",
+        "config": {
+            "workload": args.workload, "n_reads": G.n, "n_entries": G.m, "walk_reads": W, "n_contigs": n_contigs,
+            "contig_bases": total, "packed_read_bytes": int(G.packed.nbytes), "min_chain_reads": args.min_chain_reads,
+            "row_ptr_bytes": int(G.row_ptr.dtype.itemsize), "replicas": world,
+            "l2": "flushed between steps (512 MiB write, outside the timed events)",
+            "inputs": "resident in HBM (CG_BORROW_DEVICE)", "reads_per_s": G.n / (ms * 1e-3),
+            "stage_ms_mean": [statistics.mean(s[k] for s in stage) for k in range(4)],
+            "stage_names": ["mask", "chains", "offsets", "emit"],
+            "B_min_bytes": B, "path_achieved_gbs": B / (ms * 1e-3) / 1e9,
+            "path_roofline_frac": B / (ms * 1e-3) / 1e9 / pk["hbm_gbs"],
+            "path_roofline_frac_8tbs": B / (ms * 1e-3) / 1e9 / 8000.0,
+            "generate_s": round(t_gen, 1), "wall_s_timed": t1 - t0,
+        },
+        "roofline": {"kernel": "k_emit (contig spelling)", "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"],
+                     "unit": "GB/s", "frac": ach / pk["hbm_gbs"], "traffic": None,
+                     "algorithmic_bytes_per_launch": emit_bytes, "bytes_per_unit": 1.25,
+                     "units_per_launch": total, "ms_per_launch": ms_emit, "peak_kind": pk_kind + " (hbm_gbs, copy)"},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clocks.summary(t0, t1),
+        "gpu_launches": launches,
+    }
+    g.close()
+    ctx.close()
+    return line
+
+
+def cpu_baseline(args, cfg, steps=None, warmup=0):
+    """The oracle as it stands (single thread) on a bounded sample of the same
+    workload: the workload's recipe on a genome scaled down so that the oracle
+    runs for about `cpu_seconds`."""
+    import gen
+    import oracle
+    G0 = cfg["genome_len"]
+    scale = min(G0, 20_000_000)
+    d = dict(cfg, genome_len=scale)
+    G = gen.generate(d, threads=args.threads or None, keep_genome=False)
+    a = time.perf_counter()
+    r = oracle.run(G, min_chain_reads=args.min_chain_reads)
+    once = time.perf_counter() - a
+    if steps is None:
+        steps = max(1, int(args.cpu_seconds / max(once, 1e-3)))
+    for _ in range(warmup):
+        oracle.run(G, min_chain_reads=args.min_chain_reads)
+    times = []
+    for _ in range(steps):
+        a = time.perf_counter()
+        r = oracle.run(G, min_chain_reads=args.min_chain_reads)
+        times.append(time.perf_counter() - a)
+    t = statistics.mean(times)
+    return {"value": r.total_bases / t / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{args.workload} recipe on a {scale/1e6:.0f} Mb genome ({G.n} reads, {r.total_bases} contig "
+                      f"bases), full oracle pipeline, mean of {len(times)} runs, {t:.2f} s each, 1 thread",
+            "ms_per_step": t * 1e3, "host_cores_available": os.cpu_count()}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    cfg = workload_cfg(args.workload)
+    cpu = cpu_baseline(args, cfg, steps=args.steps, warmup=args.warmup)
+    return {"impl": "reference", "metric": METRIC, "value": cpu["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": cpu["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": args.workload, "min_chain_reads": args.min_chain_reads},
+            "cpu_baseline": {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": cpu["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
+    import torch
+    if world > 1:
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    import __graft_entry__
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        torch.distributed.barrier()
+        __graft_entry__.build()
+    line = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

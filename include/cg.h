@@ -1,0 +1,158 @@
+/*
+ * cg.h - contig generation on one GPU (GB300, sm_103a): the C ABI.
+ *
+ * The problem these calls solve is ContigGeneration(S, sequences) -> cset of
+ * Guidi et al., "Distributed-Memory Parallel Contig Generation for De Novo
+ * Long-Read Genome Assembly", ICPP'22 (Alg. 2): mask the branch reads of a
+ * bidirected string graph S, group the remaining reads into linear chains,
+ * walk each chain and concatenate the oriented read suffixes into contigs.
+ *
+ * Input format (cg_graph_desc):
+ *   - reads 0..n-1; len[r] >= 1 bases; off[r] = first base of read r in one
+ *     2-bit stream `packed` (A=0 C=1 G=2 T=3; base i is in byte i>>2 at bits
+ *     2*(i&3)); reads may start at any base offset;
+ *   - S as CSR: row_ptr[n+1] (int32 or int64), col[m] (int32), and per entry
+ *     (u->v) code[m] = E_u | (E_v << 1), where E = 0 names the 5' end (first
+ *     stored base) and E = 1 the 3' end of the stored read touched by the
+ *     overlap (the bidirected arrows of Sec. 2), and suf[m] = number of bases
+ *     of v, in walk orientation, beyond the overlap (the overhang weight of
+ *     Sec. 2). The mirror entry (v->u) carries the swapped code.
+ *   A read with orientation o (0 forward, 1 reverse complement) is entered
+ *   through end o and left through end 1-o (a valid walk, Sec. 2).
+ *
+ * Output (canonical, identical to the CPU oracle byte for byte):
+ *   - branch reads: degree >= 3 in S (Sec. 4.2), or exactly two overlaps to
+ *     reads of degree <= 2 that touch the same end of the read;
+ *   - one contig per linear chain of at least `min_chain_reads` reads, listed
+ *     by the smallest read id of the chain; each is spelled from its
+ *     smaller-id end read (oriented to leave through its one overlap), the
+ *     first read whole, every later read by the suffix of the overlap used
+ *     (Sec. 4.4); a closed chain starts at its smallest read, forward;
+ *   - contig i occupies bases[contig_off[i], contig_off[i+1]) as ASCII A/C/G/T.
+ *
+ * Ownership and ordering: the caller owns every buffer it passes. Calls on
+ * one context are ordered on the context's CUDA stream; a context is not
+ * thread-safe. A call whose count pointers are all NULL does not wait for the
+ * GPU: errors found by its kernels are reported by the next call that waits
+ * (cg_sync or any call given a count pointer). After CG_ETIMEOUT or
+ * CG_EKERNEL every call on that context fails until cg_destroy.
+ * Limits: n_reads < 2^30, n_entries < 2^31, a read shorter than 2^31 bases.
+ */
+#ifndef CG_H
+#define CG_H
+#include <stddef.h>
+#include <stdint.h>
+#if defined(__GNUC__)
+#define CG_API __attribute__((visibility("default")))
+#else
+#define CG_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CG_OK = 0,
+  CG_EINVAL = 1,    /* bad argument: null, size, alignment, capacity too small */
+  CG_ENOMEM = 2,    /* device memory or the context's HBM budget exhausted */
+  CG_ECUDA = 3,     /* a CUDA runtime call failed */
+  CG_EGRAPH = 4,    /* the input is not a valid string graph (see cg_load_graph) */
+  CG_ETIMEOUT = 5,  /* a device-side wait ran past its iteration limit */
+  CG_EBUSY = 6,     /* no room: admission refused (server) */
+  CG_EKERNEL = 7    /* a kernel found an inconsistency it cannot continue from */
+} cg_status;
+
+enum { CG_MEM_HOST = 0, CG_MEM_DEVICE = 1 };
+
+/* cg_load_graph flags */
+enum {
+  CG_BORROW_DEVICE = 1u, /* desc pointers are device memory used in place (must outlive the graph) */
+  CG_NO_VALIDATE = 2u    /* skip the input checks (only for graphs known to be valid) */
+};
+
+typedef struct cg_ctx cg_ctx;
+typedef struct cg_graph cg_graph;
+
+typedef struct {
+  int64_t n_reads;         /* n */
+  int64_t n_entries;       /* m = row_ptr[n] */
+  const void* row_ptr;     /* n+1 entries of row_ptr_bytes each */
+  int32_t row_ptr_bytes;   /* 4 or 8 */
+  int32_t mem;             /* CG_MEM_HOST or CG_MEM_DEVICE: where all pointers below live */
+  const int32_t* col;      /* m */
+  const uint8_t* code;     /* m, values 0..3 */
+  const int32_t* suf;      /* m */
+  const int32_t* len;      /* n */
+  const int64_t* off;      /* n, base offsets into packed */
+  const uint8_t* packed;   /* packed_bytes */
+  int64_t packed_bytes;
+  int32_t min_chain_reads; /* chains with fewer reads are not contigs; <= 0 means 2 (Sec. 4.4) */
+  int32_t reserved;
+} cg_graph_desc;
+
+/* Create a context on CUDA device `device`. hbm_budget_bytes caps the device
+ * memory the context allocates for graphs and scratch (0 = no cap).
+ * cuda_stream: a cudaStream_t to order all work on, or NULL for a private
+ * non-blocking stream. */
+CG_API cg_status cg_create(cg_ctx** ctx, int device, uint64_t hbm_budget_bytes, void* cuda_stream);
+CG_API cg_status cg_destroy(cg_ctx* ctx);
+
+/* Load one string graph (Alg. 2 input S, sequences). Copies host or device
+ * inputs into context-owned device memory, or with CG_BORROW_DEVICE uses the
+ * caller's device buffers in place (16-byte aligned `packed`). Unless
+ * CG_NO_VALIDATE is given, checks on the GPU that: row_ptr starts at 0, never
+ * decreases and ends at m; 0 <= col < n and col != row; code <= 3; no pair
+ * appears twice in a row; every entry has exactly one mirror entry with the
+ * swapped code; 1 <= suf(u->v) <= len[v]-1; len >= 1; each read lies inside
+ * the packed stream. A failed check returns CG_EGRAPH and no graph. Waits for
+ * the GPU. */
+CG_API cg_status cg_load_graph(cg_ctx* ctx, const cg_graph_desc* desc, uint32_t flags, cg_graph** out);
+CG_API cg_status cg_free_graph(cg_graph* g);
+
+/* BranchRemoval (Alg. 2; Sec. 4.2). is_branch: NULL or n bytes (1 = branch),
+ * in `mem`. n_branch: NULL or receives the count (waits for the GPU). */
+CG_API cg_status cg_mask_branches(cg_graph* g, uint8_t* is_branch, int mem, int64_t* n_branch);
+
+/* ConnectedComponent + the walk order of every chain (Alg. 2; Sec. 4.2, 4.4).
+ * Runs the mask first. Per read, in `mem`, each optional: chain_id = smallest
+ * read id of its chain, rank = position in the contig's walk, orient = 0
+ * forward / 1 reverse complement; reads in no contig get -1, -1, 255.
+ * n_contigs and n_cycles (closed chains) are optional and make the call wait. */
+CG_API cg_status cg_chains(cg_graph* g, int32_t* chain_id, int32_t* rank, uint8_t* orient, int mem,
+                    int64_t* n_contigs, int64_t* n_cycles);
+
+/* LocalAssembly (Alg. 2; Sec. 4.4): spells every contig. Runs the earlier
+ * steps first. contig_off: NULL or contig_off_cap >= n_contigs+1 entries.
+ * bases: NULL or bases_cap >= total bases, 16-byte aligned when in device
+ * memory. With both NULL only the sizes are computed (two-call size query).
+ * A capacity that is too small gives CG_EINVAL and nothing is written; with
+ * device outputs and no count pointers that check happens on the GPU and is
+ * reported by the next waiting call. */
+CG_API cg_status cg_emit_contigs(cg_graph* g, int64_t* contig_off, int64_t contig_off_cap, uint8_t* bases,
+                          int64_t bases_cap, int mem, int64_t* n_contigs, int64_t* total_bases);
+
+/* Counters of a context, for measurement. */
+typedef struct {
+  uint64_t kernels_launched; /* CUDA kernels this context has launched so far */
+  float stage_ms[4];         /* last mask, chain, offset and emission stage, in ms of GPU time
+                                (CUDA events on the context stream; 0 unless timing is on) */
+} cg_stats;
+
+/* Turns per-stage CUDA-event timing on (1) or off (0). Events are recorded
+ * around each stage on the context stream; the work itself is unchanged. */
+CG_API cg_status cg_set_timing(cg_ctx* ctx, int enable);
+/* Fills *out; with timing on it waits for the last stages to finish. */
+CG_API cg_status cg_get_stats(cg_ctx* ctx, cg_stats* out);
+
+/* Waits for all work of the context; returns the first error its kernels found. */
+CG_API cg_status cg_sync(cg_ctx* ctx);
+
+CG_API const char* cg_status_str(cg_status s);
+/* Copies the context's last error message (NUL-terminated) into buf. */
+CG_API cg_status cg_last_error(cg_ctx* ctx, char* buf, size_t buflen);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,264 @@
+"""Thin Python binding of include/cg.h (ctypes; argument marshalling only).
+
+Every step of contig generation runs in the CUDA library libcg.so; this module
+only turns numpy arrays / torch tensors into pointers and sizes. Buffers that
+are torch CUDA tensors are passed as device memory, numpy arrays and CPU
+tensors as host memory. If libcg.so has not been built the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcg.so")
+
+CG_OK, CG_EINVAL, CG_ENOMEM, CG_ECUDA, CG_EGRAPH, CG_ETIMEOUT, CG_EBUSY, CG_EKERNEL = range(8)
+MEM_HOST, MEM_DEVICE = 0, 1
+BORROW_DEVICE, NO_VALIDATE = 1, 2
+
+_lock = threading.Lock()
+_lib = None
+
+
+class CgError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_status_name(status)}: {msg}")
+        self.status = status
+
+
+def _status_name(s):
+    return ["CG_OK", "CG_EINVAL", "CG_ENOMEM", "CG_ECUDA", "CG_EGRAPH", "CG_ETIMEOUT", "CG_EBUSY",
+            "CG_EKERNEL"][s] if 0 <= s < 8 else f"status {s}"
+
+
+class GraphDesc(ctypes.Structure):
+    _fields_ = [("n_reads", ctypes.c_int64), ("n_entries", ctypes.c_int64), ("row_ptr", ctypes.c_void_p),
+                ("row_ptr_bytes", ctypes.c_int32), ("mem", ctypes.c_int32), ("col", ctypes.c_void_p),
+                ("code", ctypes.c_void_p), ("suf", ctypes.c_void_p), ("len", ctypes.c_void_p),
+                ("off", ctypes.c_void_p), ("packed", ctypes.c_void_p), ("packed_bytes", ctypes.c_int64),
+                ("min_chain_reads", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+API = {
+    "cg_create": [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_uint64, ctypes.c_void_p],
+    "cg_destroy": [ctypes.c_void_p],
+    "cg_load_graph": [ctypes.c_void_p, ctypes.POINTER(GraphDesc), ctypes.c_uint32, ctypes.POINTER(ctypes.c_void_p)],
+    "cg_free_graph": [ctypes.c_void_p],
+    "cg_mask_branches": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)],
+    "cg_chains": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                  ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
+    "cg_emit_contigs": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                        ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
+    "cg_sync": [ctypes.c_void_p],
+    "cg_set_timing": [ctypes.c_void_p, ctypes.c_int],
+    "cg_get_stats": [ctypes.c_void_p, ctypes.c_void_p],
+    "cg_status_str": [ctypes.c_int],
+    "cg_last_error": [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t],
+}
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first "
+                                   "(python -c 'import __graft_entry__ as g; g.build()')")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, args in API.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = ctypes.c_char_p if name == "cg_status_str" else ctypes.c_int
+            _lib = L
+    return _lib
+
+
+# ---------------------------------------------------------------- marshal
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _mem_of(a) -> int:
+    if _is_torch(a):
+        return MEM_DEVICE if a.is_cuda else MEM_HOST
+    return MEM_HOST
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if _is_torch(a):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    if not isinstance(a, np.ndarray) or not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("buffers must be C-contiguous numpy arrays or torch tensors")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _nbytes(a) -> int:
+    return a.numel() * a.element_size() if _is_torch(a) else a.nbytes
+
+
+def _check(ctx_ptr, st: int):
+    if st != CG_OK:
+        buf = ctypes.create_string_buffer(512)
+        if ctx_ptr:
+            lib().cg_last_error(ctx_ptr, buf, 512)
+        raise CgError(st, buf.value.decode(errors="replace"))
+
+
+def _mem_of_all(arrays):
+    mems = {_mem_of(a) for a in arrays if a is not None}
+    if len(mems) > 1:
+        raise ValueError("all buffers of one call must be in the same memory (host or device)")
+    return mems.pop() if mems else MEM_HOST
+
+
+class Context:
+    """A cg_ctx: one device, one stream."""
+
+    def __init__(self, ptr):
+        self.ptr = ptr
+
+    def close(self):
+        if self.ptr:
+            lib().cg_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Graph:
+    """A loaded cg_graph (keeps borrowed inputs alive)."""
+
+    def __init__(self, ctx: Context, ptr, keep, n: int):
+        self.ctx, self.ptr, self._keep, self.n = ctx, ptr, keep, n
+
+    def close(self):
+        if self.ptr:
+            lib().cg_free_graph(self.ptr)
+            self.ptr = None
+            self._keep = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------ the C ABI
+def cg_create(device: int = 0, hbm_budget_bytes: int = 0, stream=None) -> Context:
+    """cg_create: stream may be a torch.cuda.Stream, a raw cudaStream_t int, or None."""
+    handle = None
+    if stream is not None:
+        handle = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    out = ctypes.c_void_p()
+    st = lib().cg_create(ctypes.byref(out), int(device), int(hbm_budget_bytes), handle)
+    if st != CG_OK:
+        raise CgError(st, "cg_create failed")
+    return Context(out)
+
+
+def cg_destroy(ctx: Context):
+    ctx.close()
+
+
+def cg_load_graph(ctx: Context, graph, flags: int = 0, min_chain_reads: int = 2) -> Graph:
+    """cg_load_graph from any object with row_ptr, col, code, suf, len, off, packed."""
+    arrs = [graph.row_ptr, graph.col, graph.code, graph.suf, graph.len, graph.off, graph.packed]
+    mem = _mem_of_all(arrs)
+    rp = graph.row_ptr
+    rp_bytes = rp.element_size() if _is_torch(rp) else rp.dtype.itemsize
+    d = GraphDesc()
+    d.n_reads = len(graph.len)
+    d.n_entries = len(graph.col)
+    d.row_ptr, d.row_ptr_bytes, d.mem = _ptr(rp), rp_bytes, mem
+    d.col, d.code, d.suf = _ptr(graph.col), _ptr(graph.code), _ptr(graph.suf)
+    d.len, d.off, d.packed = _ptr(graph.len), _ptr(graph.off), _ptr(graph.packed)
+    d.packed_bytes = _nbytes(graph.packed)
+    d.min_chain_reads = int(min_chain_reads)
+    out = ctypes.c_void_p()
+    _check(ctx.ptr, lib().cg_load_graph(ctx.ptr, ctypes.byref(d), int(flags), ctypes.byref(out)))
+    return Graph(ctx, out, arrs if flags & BORROW_DEVICE else None, d.n_reads)
+
+
+def cg_free_graph(g: Graph):
+    g.close()
+
+
+def cg_mask_branches(g: Graph, is_branch=None, want_count: bool = True):
+    nb = ctypes.c_int64(-1)
+    _check(g.ctx.ptr, lib().cg_mask_branches(g.ptr, _ptr(is_branch), _mem_of_all([is_branch]),
+                                             ctypes.byref(nb) if want_count else None))
+    return nb.value if want_count else None
+
+
+def cg_chains(g: Graph, chain_id=None, rank=None, orient=None, want_counts: bool = True):
+    nc, ncy = ctypes.c_int64(-1), ctypes.c_int64(-1)
+    mem = _mem_of_all([chain_id, rank, orient])
+    _check(g.ctx.ptr, lib().cg_chains(g.ptr, _ptr(chain_id), _ptr(rank), _ptr(orient), mem,
+                                      ctypes.byref(nc) if want_counts else None,
+                                      ctypes.byref(ncy) if want_counts else None))
+    return (nc.value, ncy.value) if want_counts else None
+
+
+def cg_emit_contigs(g: Graph, contig_off=None, bases=None, want_counts: bool = True):
+    nc, tot = ctypes.c_int64(-1), ctypes.c_int64(-1)
+    mem = _mem_of_all([contig_off, bases])
+    ocap = len(contig_off) if contig_off is not None else 0
+    bcap = _nbytes(bases) if bases is not None else 0
+    _check(g.ctx.ptr, lib().cg_emit_contigs(g.ptr, _ptr(contig_off), ocap, _ptr(bases), bcap, mem,
+                                            ctypes.byref(nc) if want_counts else None,
+                                            ctypes.byref(tot) if want_counts else None))
+    return (nc.value, tot.value) if want_counts else None
+
+
+def cg_sync(ctx: Context):
+    _check(ctx.ptr, lib().cg_sync(ctx.ptr))
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("kernels_launched", ctypes.c_uint64), ("stage_ms", ctypes.c_float * 4)]
+
+
+def cg_set_timing(ctx: Context, enable: bool):
+    _check(ctx.ptr, lib().cg_set_timing(ctx.ptr, 1 if enable else 0))
+
+
+def cg_get_stats(ctx: Context) -> dict:
+    """kernels launched so far and the last mask / chain / offset / emission stage times (ms)."""
+    s = Stats()
+    _check(ctx.ptr, lib().cg_get_stats(ctx.ptr, ctypes.byref(s)))
+    return {"kernels_launched": int(s.kernels_launched), "stage_ms": [float(x) for x in s.stage_ms]}
+
+
+def cg_status_str(s: int) -> str:
+    return lib().cg_status_str(int(s)).decode()
+
+
+# ------------------------------------------------------- convenience
+def contigs_host(g: Graph):
+    """Two-call size query, then every output into host numpy arrays."""
+    n_contigs, total = cg_emit_contigs(g)
+    off = np.empty(n_contigs + 1, dtype=np.int64)
+    bases = np.empty(max(total, 1), dtype=np.uint8)
+    cg_emit_contigs(g, off, bases)
+    return off, bases[:total]
+
+
+def chains_host(g: Graph):
+    cid = np.empty(g.n, dtype=np.int32)
+    rank = np.empty(g.n, dtype=np.int32)
+    orient = np.empty(g.n, dtype=np.uint8)
+    n_contigs, n_cycles = cg_chains(g, cid, rank, orient)
+    return cid, rank, orient, n_contigs, n_cycles

@@ -1,0 +1,560 @@
+// cg_api.cu - the C ABI of include/cg.h: contexts, graph loading, and the
+// stage sequence mask -> chains -> offsets -> emission on one CUDA stream.
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "cg.h"
+#include "cg_internal.cuh"
+
+struct cg_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  uint64_t budget = 0, used = 0;
+  cg::LaunchEnv env{};
+  cg::Tuning tune{};
+  cg::DevError* derr = nullptr;   // device
+  cg::DevError* h_err = nullptr;  // pinned host mirror
+  cg::Counters* h_ctr = nullptr;  // pinned host mirror of one graph's counters
+  unsigned long long* h_u64 = nullptr;  // pinned host word
+  cg_status sticky = CG_OK;
+  std::string last_error;
+  std::multimap<size_t, void*> pool;   // freed device buffers kept for reuse
+  std::map<void*, size_t> sizes;       // every live or pooled buffer of this context
+  unsigned long long launches = 0;
+  bool timing = false;
+  cudaEvent_t ev[8] = {};              // start/end of mask, chains, offsets, emission
+  bool recorded[4] = {false, false, false, false};
+};
+
+struct cg_graph {
+  cg_ctx* ctx = nullptr;
+  cg::DevGraph g{};
+  cg::Scratch s{};
+  std::vector<void*> owned;
+  int stage = 0;                  // 0 loaded, 1 masked, 2 chained, 3 offsets
+  int64_t sum_len = 0;
+  uint8_t* stage_bases = nullptr; // device staging for host outputs
+  int64_t stage_bases_cap = 0;
+  void* stage_reads = nullptr;
+  unsigned long long* d_sum = nullptr;
+};
+
+namespace {
+
+cg_status fail(cg_ctx* c, cg_status s, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    c->last_error = buf;
+    if (s == CG_ETIMEOUT || s == CG_EKERNEL || s == CG_ECUDA) c->sticky = s;
+  }
+  return s;
+}
+
+cg_status cuda_fail(cg_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, CG_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                 \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+  } while (0)
+
+// Device allocation through the context pool (reuses a freed buffer whose
+// size is within 2x of the request) under the context's HBM budget.
+void* dalloc(cg_ctx* c, size_t bytes, cg_status* st) {
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~size_t(255);
+  auto it = c->pool.lower_bound(bytes);
+  if (it != c->pool.end() && it->first <= 2 * bytes) {
+    void* p = it->second;
+    c->pool.erase(it);
+    return p;
+  }
+  if (c->budget && c->used + bytes > c->budget) {
+    // give pooled memory back before refusing
+    for (auto& kv : c->pool) { cudaFree(kv.second); c->used -= kv.first; c->sizes.erase(kv.second); }
+    c->pool.clear();
+    if (c->used + bytes > c->budget) {
+      *st = fail(c, CG_ENOMEM, "HBM budget: %zu bytes in use, %zu more requested, budget %llu", (size_t)c->used,
+                 bytes, (unsigned long long)c->budget);
+      return nullptr;
+    }
+  }
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    for (auto& kv : c->pool) { cudaFree(kv.second); c->used -= kv.first; c->sizes.erase(kv.second); }
+    c->pool.clear();
+    e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      *st = fail(c, CG_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+      return nullptr;
+    }
+  }
+  c->used += bytes;
+  c->sizes[p] = bytes;
+  return p;
+}
+
+void dfree(cg_ctx* c, void* p) {
+  if (!p) return;
+  auto it = c->sizes.find(p);
+  if (it == c->sizes.end()) return;
+  c->pool.emplace(it->second, p);
+}
+
+template <class T>
+T* galloc(cg_graph* g, size_t count, cg_status* st) {
+  void* p = dalloc(g->ctx, count * sizeof(T), st);
+  if (p) g->owned.push_back(p);
+  return reinterpret_cast<T*>(p);
+}
+
+// Reads the context error word and the graph counters (waits for the stream).
+cg_status wait_and_read(cg_graph* g) {
+  cg_ctx* c = g->ctx;
+  CK(cudaMemcpyAsync(c->h_err, c->derr, sizeof(cg::DevError), cudaMemcpyDeviceToHost, c->stream), "read error word");
+  if (g->s.ctr)
+    CK(cudaMemcpyAsync(c->h_ctr, g->s.ctr, sizeof(cg::Counters), cudaMemcpyDeviceToHost, c->stream), "read counters");
+  CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+  cg::DevError e = *c->h_err;
+  if (e.err == cg::DERR_NONE) return CG_OK;
+  if (e.err == cg::DERR_CAPACITY || e.err == cg::DERR_GRAPH) {
+    CK(cudaMemsetAsync(c->derr, 0, sizeof(cg::DevError), c->stream), "clear error word");
+    CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+    if (e.err == cg::DERR_CAPACITY)
+      return fail(c, CG_EINVAL, "output buffer too small: %lld needed (kernel %d)", e.index, e.where);
+    return fail(c, CG_EGRAPH, "invalid string graph: check %d failed at index %lld", e.where, e.index);
+  }
+  if (e.err == cg::DERR_TIMEOUT) return fail(c, CG_ETIMEOUT, "device wait timed out in kernel %d", e.where);
+  return fail(c, CG_EKERNEL, "kernel %d found an inconsistency at index %lld", e.where, e.index);
+}
+
+cg_status check_ctx(cg_ctx* c) {
+  if (!c) return CG_EINVAL;
+  if (c->sticky != CG_OK) return c->sticky;
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  return CG_OK;
+}
+
+// Brackets one stage with CUDA events when timing is on.
+struct StageTimer {
+  cg_ctx* c;
+  int k;
+  StageTimer(cg_ctx* c_, int k_) : c(c_), k(k_) {
+    if (c->timing) cudaEventRecord(c->ev[2 * k], c->stream);
+  }
+  ~StageTimer() {
+    if (c->timing) {
+      cudaEventRecord(c->ev[2 * k + 1], c->stream);
+      c->recorded[k] = true;
+    }
+  }
+};
+
+cg_status run_mask(cg_graph* g) {
+  cg_ctx* c = g->ctx;
+  StageTimer tm(c, 0);
+  CK(cg::launch_mask(g->g, g->s, c->env), "mask kernels");
+  g->stage = 1;
+  return CG_OK;
+}
+
+cg_status run_chains(cg_graph* g) {
+  cg_ctx* c = g->ctx;
+  if (g->stage < 1) {
+    cg_status st = run_mask(g);
+    if (st != CG_OK) return st;
+  }
+  StageTimer tm(c, 1);
+  CK(cg::launch_chains(g->g, g->s, c->tune, c->env), "chain kernels");
+  g->stage = 2;
+  return CG_OK;
+}
+
+cg_status run_offsets(cg_graph* g) {
+  cg_ctx* c = g->ctx;
+  if (g->stage < 2) {
+    cg_status st = run_chains(g);
+    if (st != CG_OK) return st;
+  }
+  StageTimer tm(c, 2);
+  CK(cg::launch_offsets(g->g, g->s, c->tune, c->env), "offset kernels");
+  g->stage = 3;
+  return CG_OK;
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+const char* cg_status_str(cg_status s) {
+  switch (s) {
+    case CG_OK: return "CG_OK";
+    case CG_EINVAL: return "CG_EINVAL";
+    case CG_ENOMEM: return "CG_ENOMEM";
+    case CG_ECUDA: return "CG_ECUDA";
+    case CG_EGRAPH: return "CG_EGRAPH";
+    case CG_ETIMEOUT: return "CG_ETIMEOUT";
+    case CG_EBUSY: return "CG_EBUSY";
+    case CG_EKERNEL: return "CG_EKERNEL";
+  }
+  return "CG_UNKNOWN";
+}
+
+cg_status cg_last_error(cg_ctx* c, char* buf, size_t buflen) {
+  if (!c || !buf || buflen == 0) return CG_EINVAL;
+  snprintf(buf, buflen, "%s", c->last_error.c_str());
+  return CG_OK;
+}
+
+cg_status cg_create(cg_ctx** out, int device, uint64_t hbm_budget_bytes, void* cuda_stream) {
+  if (!out) return CG_EINVAL;
+  *out = nullptr;
+  cg_ctx* c = new (std::nothrow) cg_ctx();
+  if (!c) return CG_ENOMEM;
+  c->device = device;
+  c->budget = hbm_budget_bytes;
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) { delete c; return CG_ECUDA; }
+  if (cuda_stream) {
+    c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { delete c; return CG_ECUDA; }
+    c->own_stream = true;
+  }
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  c->env.stream = c->stream;
+  c->env.num_sms = sms > 0 ? sms : 1;
+  c->env.coop_blocks = cg::coop_blocks_for_grid_kernels(c->env.num_sms);
+  c->env.launches = &c->launches;
+  if (cudaMalloc(&c->derr, sizeof(cg::DevError)) != cudaSuccess ||
+      cudaMallocHost(&c->h_err, sizeof(cg::DevError)) != cudaSuccess ||
+      cudaMallocHost(&c->h_ctr, sizeof(cg::Counters)) != cudaSuccess ||
+      cudaMallocHost(&c->h_u64, sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError();
+    cg_destroy(c);
+    return CG_ENOMEM;
+  }
+  cudaMemsetAsync(c->derr, 0, sizeof(cg::DevError), c->stream);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) { cudaGetLastError(); cg_destroy(c); return CG_ECUDA; }
+  *out = c;
+  return CG_OK;
+}
+
+cg_status cg_destroy(cg_ctx* c) {
+  if (!c) return CG_EINVAL;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (auto& kv : c->sizes) cudaFree(kv.first);
+  if (c->derr) cudaFree(c->derr);
+  if (c->h_err) cudaFreeHost(c->h_err);
+  if (c->h_ctr) cudaFreeHost(c->h_ctr);
+  if (c->h_u64) cudaFreeHost(c->h_u64);
+  for (cudaEvent_t e : c->ev)
+    if (e) cudaEventDestroy(e);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  cudaGetLastError();
+  delete c;
+  return CG_OK;
+}
+
+cg_status cg_set_timing(cg_ctx* c, int enable) {
+  cg_status st = check_ctx(c);
+  if (st != CG_OK) return st;
+  if (enable && !c->ev[0])
+    for (cudaEvent_t& e : c->ev) CK(cudaEventCreate(&e), "cudaEventCreate");
+  c->timing = enable != 0;
+  for (bool& r : c->recorded) r = false;
+  return CG_OK;
+}
+
+cg_status cg_get_stats(cg_ctx* c, cg_stats* out) {
+  cg_status st = check_ctx(c);
+  if (st != CG_OK) return st;
+  if (!out) return CG_EINVAL;
+  out->kernels_launched = c->launches;
+  for (int k = 0; k < 4; ++k) out->stage_ms[k] = 0.f;
+  if (c->timing) {
+    CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+    for (int k = 0; k < 4; ++k)
+      if (c->recorded[k]) CK(cudaEventElapsedTime(&out->stage_ms[k], c->ev[2 * k], c->ev[2 * k + 1]), "event time");
+  }
+  return CG_OK;
+}
+
+cg_status cg_sync(cg_ctx* c) {
+  if (!c) return CG_EINVAL;
+  if (c->sticky != CG_OK) return c->sticky;
+  cg_graph tmp;
+  tmp.ctx = c;
+  return wait_and_read(&tmp);
+}
+
+cg_status cg_free_graph(cg_graph* g) {
+  if (!g) return CG_EINVAL;
+  cg_ctx* c = g->ctx;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);   // buffers may still be in use by queued work
+  for (void* p : g->owned) dfree(c, p);
+  dfree(c, g->stage_bases);
+  delete g;
+  return CG_OK;
+}
+
+cg_status cg_load_graph(cg_ctx* c, const cg_graph_desc* d, uint32_t flags, cg_graph** out) {
+  cg_status st = check_ctx(c);
+  if (st != CG_OK) return st;
+  if (!d || !out) return fail(c, CG_EINVAL, "null argument");
+  *out = nullptr;
+  const int64_t n = d->n_reads, m = d->n_entries;
+  if (n < 0 || n >= (1ll << 30)) return fail(c, CG_EINVAL, "n_reads out of range");
+  if (m < 0 || m >= (1ll << 31)) return fail(c, CG_EINVAL, "n_entries out of range");
+  if (d->row_ptr_bytes != 4 && d->row_ptr_bytes != 8) return fail(c, CG_EINVAL, "row_ptr_bytes must be 4 or 8");
+  if (d->mem != CG_MEM_HOST && d->mem != CG_MEM_DEVICE) return fail(c, CG_EINVAL, "bad mem");
+  if (!d->row_ptr || (m > 0 && (!d->col || !d->code || !d->suf)) || (n > 0 && (!d->len || !d->off)) ||
+      d->packed_bytes < 0 || (d->packed_bytes > 0 && !d->packed))
+    return fail(c, CG_EINVAL, "missing input array");
+  const bool borrow = (flags & CG_BORROW_DEVICE) != 0;
+  if (borrow && d->mem != CG_MEM_DEVICE) return fail(c, CG_EINVAL, "CG_BORROW_DEVICE needs device inputs");
+  if (borrow && (!aligned(d->packed, 16) || !aligned(d->row_ptr, d->row_ptr_bytes) || !aligned(d->col, 4) ||
+                 !aligned(d->suf, 4) || !aligned(d->len, 4) || !aligned(d->off, 8)))
+    return fail(c, CG_EINVAL, "borrowed device inputs are misaligned");
+
+  cg_graph* g = new (std::nothrow) cg_graph();
+  if (!g) return fail(c, CG_ENOMEM, "host allocation");
+  g->ctx = c;
+  auto bail = [&](cg_status s) {
+    cg_free_graph(g);
+    return s;
+  };
+  st = CG_OK;
+  const cudaMemcpyKind kind = d->mem == CG_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  cg::DevGraph& G = g->g;
+  G.n = n;
+  G.m = m;
+  G.rp64 = d->row_ptr_bytes == 8;
+  G.min_chain = d->min_chain_reads <= 0 ? 2 : d->min_chain_reads;
+  G.packed_bytes = d->packed_bytes;
+  if (borrow) {
+    G.row_ptr = d->row_ptr;
+    G.col = d->col;
+    G.code = d->code;
+    G.suf = d->suf;
+    G.len = d->len;
+    G.off = d->off;
+    G.packed = d->packed;
+  } else {
+    auto copy_in = [&](const void* src, size_t bytes, size_t pad) -> const void* {
+      void* p = dalloc(c, bytes + pad, &st);
+      if (!p) return nullptr;
+      g->owned.push_back(p);
+      if (bytes) {
+        cudaError_t e = cudaMemcpyAsync(p, src, bytes, kind, c->stream);
+        if (e != cudaSuccess) { st = cuda_fail(c, e, "copy graph input"); return nullptr; }
+      }
+      if (pad) cudaMemsetAsync((char*)p + bytes, 0, pad, c->stream);
+      return p;
+    };
+    G.row_ptr = copy_in(d->row_ptr, (size_t)(n + 1) * d->row_ptr_bytes, 0);
+    if (st == CG_OK) G.col = (const int32_t*)copy_in(d->col, (size_t)m * 4, 0);
+    if (st == CG_OK) G.code = (const uint8_t*)copy_in(d->code, (size_t)m, 0);
+    if (st == CG_OK) G.suf = (const int32_t*)copy_in(d->suf, (size_t)m * 4, 0);
+    if (st == CG_OK) G.len = (const int32_t*)copy_in(d->len, (size_t)n * 4, 0);
+    if (st == CG_OK) G.off = (const int64_t*)copy_in(d->off, (size_t)n * 8, 0);
+    if (st == CG_OK) G.packed = (const uint8_t*)copy_in(d->packed, (size_t)d->packed_bytes, 16);
+    if (st != CG_OK) return bail(st);
+  }
+
+  // scratch
+  cg::Scratch& S = g->s;
+  const size_t N = (size_t)(n > 0 ? n : 1), N2 = 2 * N;
+  S.branch = galloc<uint8_t>(g, N, &st);
+  S.cand = galloc<int32_t>(g, N, &st);
+  S.chain = galloc<int32_t>(g, N, &st);
+  S.emit = galloc<int32_t>(g, N, &st);
+  S.succ = galloc<int2>(g, N, &st);
+  S.sufin = galloc<int32_t>(g, N2, &st);
+  S.rid = galloc<int32_t>(g, N2, &st);
+  S.roff = galloc<int32_t>(g, N2, &st);
+  S.r_next_node = galloc<int32_t>(g, N2, &st);
+  S.r_len = galloc<int32_t>(g, N2, &st);
+  S.r_min = galloc<int32_t>(g, N2, &st);
+  S.r_last = galloc<int32_t>(g, N2, &st);
+  for (int b = 0; b < 2; ++b) {
+    S.pj_next[b] = galloc<int32_t>(g, N2, &st);
+    S.pj_acc[b] = galloc<int32_t>(g, N2, &st);
+    S.pj_min[b] = galloc<int32_t>(g, N2, &st);
+    S.pj_tail[b] = galloc<int32_t>(g, N2, &st);
+    S.c_ptr[b] = galloc<int32_t>(g, N2, &st);
+    S.c_val[b] = galloc<int32_t>(g, N2, &st);
+  }
+  S.c_head = galloc<int32_t>(g, N2, &st);
+  S.cid = galloc<int32_t>(g, N, &st);
+  S.rank = galloc<int32_t>(g, N, &st);
+  S.orient = galloc<uint8_t>(g, N, &st);
+  S.contrib = galloc<int32_t>(g, N, &st);
+  S.headq = galloc<int32_t>(g, N, &st);
+  S.rb = galloc<unsigned long long>(g, N + 1, &st);
+  S.cyc = galloc<int32_t>(g, N, &st);
+  S.wsrc = galloc<unsigned long long>(g, N, &st);
+  S.wlen = galloc<int32_t>(g, N, &st);
+  S.out_off = galloc<int64_t>(g, N + 1, &st);
+  S.cstart = galloc<int32_t>(g, N, &st);
+  S.contig_off = galloc<int64_t>(g, N + 1, &st);
+  S.scan_tiles_cap = (int64_t)(N + 2047) / 2048 + 1;
+  S.scan_state = galloc<unsigned long long>(g, (size_t)S.scan_tiles_cap + 1, &st);
+  S.ctr = galloc<cg::Counters>(g, 1, &st);
+  g->d_sum = galloc<unsigned long long>(g, 1, &st);
+  S.derr = c->derr;
+  if (st != CG_OK) return bail(st);
+  CK(cudaMemsetAsync(S.ctr, 0, sizeof(cg::Counters), c->stream), "clear counters");
+  CK(cudaMemsetAsync(g->d_sum, 0, 8, c->stream), "clear sum");
+
+  if (!(flags & CG_NO_VALIDATE) && n > 0) CK(cg::launch_validate(G, c->derr, c->env), "validation kernels");
+  CK(cg::launch_sum_len(G, g->d_sum, c->env), "length sum");
+  CK(cudaMemcpyAsync(c->h_u64, g->d_sum, 8, cudaMemcpyDeviceToHost, c->stream), "read sum");
+  st = wait_and_read(g);
+  if (st != CG_OK) return bail(st);
+  g->sum_len = (int64_t)*c->h_u64;
+  // the longest possible output is every read spelled whole; tiles of at least 4 KiB
+  S.tiles_cap = g->sum_len / 4096 + 2;
+  S.tile_seg = galloc<int32_t>(g, (size_t)S.tiles_cap + 1, &st);
+  if (st != CG_OK) return bail(st);
+  if (c->tune.tile_bytes < 4096) c->tune.tile_bytes = 4096;
+  *out = g;
+  return CG_OK;
+}
+
+cg_status cg_mask_branches(cg_graph* g, uint8_t* is_branch, int mem, int64_t* n_branch) {
+  if (!g) return CG_EINVAL;
+  cg_ctx* c = g->ctx;
+  cg_status st = check_ctx(c);
+  if (st != CG_OK) return st;
+  if (mem != CG_MEM_HOST && mem != CG_MEM_DEVICE) return fail(c, CG_EINVAL, "bad mem");
+  st = run_mask(g);
+  if (st != CG_OK) return st;
+  if (is_branch && g->g.n > 0)
+    CK(cudaMemcpyAsync(is_branch, g->s.branch, (size_t)g->g.n,
+                       mem == CG_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream),
+       "copy is_branch");
+  if (n_branch || (is_branch && mem == CG_MEM_HOST)) {
+    st = wait_and_read(g);
+    if (st != CG_OK) return st;
+    if (n_branch) *n_branch = (int64_t)c->h_ctr->n_branch;
+  }
+  return CG_OK;
+}
+
+cg_status cg_chains(cg_graph* g, int32_t* chain_id, int32_t* rank, uint8_t* orient, int mem, int64_t* n_contigs,
+                    int64_t* n_cycles) {
+  if (!g) return CG_EINVAL;
+  cg_ctx* c = g->ctx;
+  cg_status st = check_ctx(c);
+  if (st != CG_OK) return st;
+  if (mem != CG_MEM_HOST && mem != CG_MEM_DEVICE) return fail(c, CG_EINVAL, "bad mem");
+  st = run_chains(g);
+  if (st != CG_OK) return st;
+  const int64_t n = g->g.n;
+  const bool want_reads = chain_id || rank || orient;
+  if (want_reads && n > 0) {
+    if (mem == CG_MEM_DEVICE) {
+      CK(cg::launch_export_reads(g->g, g->s, chain_id, rank, orient, c->env), "export reads");
+    } else {
+      if (!g->stage_reads) {
+        g->stage_reads = dalloc(c, (size_t)n * 9, &st);
+        if (!g->stage_reads) return st;
+        g->owned.push_back(g->stage_reads);
+      }
+      int32_t* dc = (int32_t*)g->stage_reads;
+      int32_t* dr = dc + n;
+      uint8_t* dor = (uint8_t*)(dr + n);
+      CK(cg::launch_export_reads(g->g, g->s, dc, dr, dor, c->env), "export reads");
+      if (chain_id) CK(cudaMemcpyAsync(chain_id, dc, (size_t)n * 4, cudaMemcpyDeviceToHost, c->stream), "copy chain_id");
+      if (rank) CK(cudaMemcpyAsync(rank, dr, (size_t)n * 4, cudaMemcpyDeviceToHost, c->stream), "copy rank");
+      if (orient) CK(cudaMemcpyAsync(orient, dor, (size_t)n, cudaMemcpyDeviceToHost, c->stream), "copy orient");
+    }
+  }
+  if (n_contigs || n_cycles || (want_reads && mem == CG_MEM_HOST)) {
+    st = wait_and_read(g);
+    if (st != CG_OK) return st;
+    if (n_contigs) *n_contigs = (int64_t)c->h_ctr->n_lone + (int64_t)c->h_ctr->n_heads;
+    if (n_cycles) *n_cycles = (int64_t)c->h_ctr->n_cycles;
+  }
+  return CG_OK;
+}
+
+cg_status cg_emit_contigs(cg_graph* g, int64_t* contig_off, int64_t contig_off_cap, uint8_t* bases,
+                          int64_t bases_cap, int mem, int64_t* n_contigs, int64_t* total_bases) {
+  if (!g) return CG_EINVAL;
+  cg_ctx* c = g->ctx;
+  cg_status st = check_ctx(c);
+  if (st != CG_OK) return st;
+  if (mem != CG_MEM_HOST && mem != CG_MEM_DEVICE) return fail(c, CG_EINVAL, "bad mem");
+  if ((bases && bases_cap < 0) || (contig_off && contig_off_cap < 1)) return fail(c, CG_EINVAL, "bad capacity");
+  st = run_offsets(g);
+  if (st != CG_OK) return st;
+  if (mem == CG_MEM_DEVICE) {
+    if (bases) {
+      if (!aligned(bases, 16)) return fail(c, CG_EINVAL, "device bases buffer must be 16-byte aligned");
+      StageTimer tm(c, 3);
+      CK(cg::launch_emit(g->g, g->s, c->tune, bases, bases_cap, c->env), "emission kernel");
+    }
+    if (contig_off) CK(cg::launch_export_contig_off(g->s, contig_off, contig_off_cap, c->env), "export contig_off");
+    if (n_contigs || total_bases) {
+      st = wait_and_read(g);
+      if (st != CG_OK) return st;
+    }
+  } else {
+    st = wait_and_read(g);
+    if (st != CG_OK) return st;
+    const int64_t total = c->h_ctr->total_bases, C = c->h_ctr->n_contigs;
+    if (bases && bases_cap < total) return fail(c, CG_EINVAL, "bases capacity %lld < %lld", (long long)bases_cap, (long long)total);
+    if (contig_off && contig_off_cap < C + 1) return fail(c, CG_EINVAL, "contig_off capacity too small");
+    if (bases && total > 0) {
+      if (g->stage_bases_cap < total) {
+        if (g->stage_bases) dfree(c, g->stage_bases);
+        g->stage_bases = (uint8_t*)dalloc(c, (size_t)total, &st);
+        if (!g->stage_bases) { g->stage_bases_cap = 0; return st; }
+        g->stage_bases_cap = total;
+      }
+      {
+        StageTimer tm(c, 3);
+        CK(cg::launch_emit(g->g, g->s, c->tune, g->stage_bases, g->stage_bases_cap, c->env), "emission kernel");
+      }
+      CK(cudaMemcpyAsync(bases, g->stage_bases, (size_t)total, cudaMemcpyDeviceToHost, c->stream), "copy bases");
+    }
+    if (contig_off)
+      CK(cudaMemcpyAsync(contig_off, g->s.contig_off, (size_t)(C + 1) * 8, cudaMemcpyDeviceToHost, c->stream),
+         "copy contig_off");
+    if (bases || contig_off) {
+      st = wait_and_read(g);
+      if (st != CG_OK) return st;
+    }
+  }
+  if (n_contigs) *n_contigs = (int64_t)c->h_ctr->n_contigs;
+  if (total_bases) *total_bases = c->h_ctr->total_bases;
+  return CG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,183 @@
+// cg_internal.cuh - device data layout and kernel launchers shared by the
+// translation units of the contig-generation library (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace cg {
+
+constexpr int kBlock = 256;
+
+// First device-side error wins (atomicCAS from 0).
+enum : int32_t {
+  DERR_NONE = 0,
+  DERR_GRAPH = 1,     // input check failed
+  DERR_TIMEOUT = 2,   // a bounded wait gave up
+  DERR_KERNEL = 3,    // an internal consistency check failed
+  DERR_CAPACITY = 4   // an output buffer is too small
+};
+
+// Device-side error word of a context: the first error a kernel finds stays
+// until the host reads and clears it.
+// Per-graph counters of one run: each stage zeroes its own part.
+struct DevError {
+  int err;                     // DERR_*
+  int where;                   // kernel id of the first error
+  long long index;             // element index of the first error
+};
+
+struct Counters {
+  // mask stage
+  unsigned long long n_branch;
+  unsigned int n_cand;         // unmasked reads with at least one overlap
+  unsigned int n_lone;         // reads with no overlap spelled as one-read contigs
+  // chain stage
+  unsigned int n_chain;        // unmasked reads with at least one surviving overlap
+  unsigned int n_rulers;       // sublist starts of the list ranking
+  unsigned int n_cycle_reads;  // reads on closed chains
+  unsigned int n_emit;         // reads spelled into some contig (= walk positions)
+  unsigned int n_cycles;
+  unsigned int n_heads;        // contigs found by the chain stage (lone reads of the mask stage excluded)
+  unsigned int final_buf;      // which pointer-jumping buffer holds the result
+  unsigned int bar_count;      // grid barrier arrival counter
+  unsigned int bar_gen;        // grid barrier generation
+  unsigned int round_flag[64]; // "some pointer still moves" per jumping round
+  // offsets stage
+  unsigned int n_contigs;
+  unsigned int n_tiles;        // emission tiles
+  long long total_bases;
+};
+
+// The graph as kernels see it (all device pointers).
+struct DevGraph {
+  int64_t n, m;
+  const void* row_ptr;
+  int rp64;                    // 1: int64 row_ptr, 0: int32
+  int min_chain;               // >= 1
+  const int32_t* col;
+  const uint8_t* code;
+  const int32_t* suf;
+  const int32_t* len;
+  const int64_t* off;
+  const uint8_t* packed;
+  int64_t packed_bytes;
+};
+
+// Scratch owned by a loaded graph. Sizes in elements.
+struct Scratch {
+  uint8_t* branch;      // n
+  int32_t* cand;        // n: reads to build successors for
+  int32_t* chain;       // n: reads to rank
+  int32_t* emit;        // n: reads spelled into a contig
+  int2* succ;           // n: (successor of (v,fwd), successor of (v,rc)) as oriented ids 2w+o, or -1
+  int32_t* sufin;       // 2n: suffix of the overlap entering oriented read x
+  int32_t* rid;         // 2n: sublist of oriented read x (-1: not reached)
+  int32_t* roff;        // 2n: position of x inside its sublist
+  // sublists (capacity 2n)
+  int32_t* r_next_node; // first oriented read of the next sublist, -1 at the list end
+  int32_t* r_len;
+  int32_t* r_min;       // smallest read id inside the sublist
+  int32_t* r_last;      // last oriented read of the sublist
+  int32_t* pj_next[2];  // pointer jumping over sublists, double buffered
+  int32_t* pj_acc[2];
+  int32_t* pj_min[2];
+  int32_t* pj_tail[2];
+  // per read
+  int32_t* cid;         // smallest read id of the chain
+  int32_t* rank;        // walk position
+  uint8_t* orient;
+  int32_t* contrib;     // bases this read adds to its contig
+  int32_t* headq;       // reads of the chain at its smallest read, else 0
+  unsigned long long* rb;   // n+1: exclusive prefix of (1<<32 | headq) over read ids
+  // closed chains
+  int32_t* cyc;         // n: reads on closed chains
+  int32_t* c_ptr[2];    // 2n
+  int32_t* c_val[2];    // 2n
+  int32_t* c_head;      // 2n
+  // walk order
+  unsigned long long* wsrc; // n: first stored base of the piece | reverse flag << 63
+  int32_t* wlen;        // n: piece length
+  int64_t* out_off;     // n+1
+  int32_t* cstart;      // n: contig -> first walk position
+  int64_t* contig_off;  // n+1
+  int32_t* tile_seg;    // tiles_cap+1: walk position holding the first byte of each emission tile
+  int64_t tiles_cap;
+  unsigned long long* scan_state;  // scan tile descriptors (+1 ticket word)
+  int64_t scan_tiles_cap;
+  Counters* ctr;
+  DevError* derr;
+};
+
+// Tuning knobs (chosen by the autotuner per size class).
+struct Tuning {
+  int ruler_log2 = 4;      // a read starts a sublist with probability 2^-ruler_log2
+  int tile_bytes = 8192;   // emission tile (multiple of 16)
+  int emit_blocks_per_sm = 8;
+  int grid_blocks_per_sm = 8;
+};
+
+struct LaunchEnv {
+  cudaStream_t stream;
+  int num_sms;
+  int coop_blocks;         // co-resident blocks for the grid-synchronised kernels
+  unsigned long long* launches;  // host counter of kernel launches
+};
+
+// ---- launchers (each returns cudaGetLastError()) ----
+cudaError_t launch_validate(const DevGraph& g, DevError* derr, const LaunchEnv& env);
+cudaError_t launch_mask(const DevGraph& g, const Scratch& s, const LaunchEnv& env);
+cudaError_t launch_chains(const DevGraph& g, const Scratch& s, const Tuning& t, const LaunchEnv& env);
+cudaError_t launch_offsets(const DevGraph& g, const Scratch& s, const Tuning& t, const LaunchEnv& env);
+cudaError_t launch_emit(const DevGraph& g, const Scratch& s, const Tuning& t, uint8_t* out, int64_t cap,
+                        const LaunchEnv& env);
+cudaError_t launch_export_reads(const DevGraph& g, const Scratch& s, int32_t* cid, int32_t* rank, uint8_t* orient,
+                                const LaunchEnv& env);
+cudaError_t launch_export_contig_off(const Scratch& s, int64_t* out, int64_t cap, const LaunchEnv& env);
+cudaError_t launch_sum_len(const DevGraph& g, unsigned long long* out, const LaunchEnv& env);
+int coop_blocks_for_grid_kernels(int num_sms);
+
+// ---- device helpers ----
+__device__ __forceinline__ void set_error(DevError* e, int code, int where, long long index) {
+  if (atomicCAS(&e->err, 0, code) == 0) {
+    e->where = where;
+    e->index = index;
+  }
+}
+
+__device__ __forceinline__ long long grid_tid() { return (long long)blockIdx.x * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ long long grid_threads() { return (long long)gridDim.x * blockDim.x; }
+// Rounded-up trip count so that whole warps iterate together (for warp_append).
+__device__ __forceinline__ long long warp_round(long long n) { return (n + 31) & ~31ll; }
+
+enum KernelId {
+  K_VALIDATE1 = 1, K_VALIDATE2, K_MASK, K_SUCC, K_WALK, K_JUMP, K_FINAL, K_CYCLE, K_EXPORT,
+  K_SCAN_HEADS, K_SCATTER, K_SCAN_OFFSETS, K_CONTIG_OFF, K_EMIT
+};
+
+inline int grid_for(long long n, const LaunchEnv& env, int per_sm = 8) {
+  long long b = (n + kBlock - 1) / kBlock;
+  long long cap = (long long)env.num_sms * per_sm;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+__device__ __forceinline__ int64_t rowp(const DevGraph& g, int64_t v) {
+  return g.rp64 ? reinterpret_cast<const int64_t*>(g.row_ptr)[v]
+                : (int64_t)reinterpret_cast<const int32_t*>(g.row_ptr)[v];
+}
+
+// Warp-aggregated append to a list; returns the slot.
+__device__ __forceinline__ unsigned warp_append(unsigned* counter, bool want) {
+  unsigned mask = __ballot_sync(0xffffffffu, want);
+  if (!want) return 0;
+  int lane = threadIdx.x & 31;
+  int leader = __ffs(mask) - 1;
+  unsigned base = 0;
+  if (lane == leader) base = atomicAdd(counter, (unsigned)__popc(mask));
+  base = __shfl_sync(mask, base, leader);
+  return base + (unsigned)__popc(mask & ((1u << lane) - 1u));
+}
+
+}  // namespace cg
