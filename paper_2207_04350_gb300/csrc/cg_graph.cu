@@ -198,6 +198,10 @@ __global__ void k_succ(DevGraph g, Scratch s) {
         if (lone) atomicAdd(&c->n_heads, 1u);
       } else {
         chain = true;
+        // not yet reached by a sublist walk (closed chains without a
+        // sampled read are never reached, and are found by this mark)
+        s.rid[2 * v] = -1;
+        s.rid[2 * v + 1] = -1;
       }
     }
     unsigned slot = warp_append(&c->n_chain, chain);
