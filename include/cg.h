@@ -145,6 +145,29 @@ CG_API cg_status cg_set_timing(cg_ctx* ctx, int enable);
 /* Fills *out; with timing on it waits for the last stages to finish. */
 CG_API cg_status cg_get_stats(cg_ctx* ctx, cg_stats* out);
 
+/* Exclusive prefix offsets without any device allocation, for callers that
+ * cannot call cudaMalloc: code running while another allocator owns the
+ * device memory (a caching allocator, or a hard HBM budget the caller must
+ * not exceed), or a latency-critical loop where an allocation would stall or
+ * synchronise the device. The paper has no counterpart: this is the offset
+ * scan that places contigs and read pieces in the output (the one behind
+ * contig_off of cg_emit_contigs), with its scratch in a fixed device array.
+ *   lengths: device memory, count values >= 0; offsets: device memory,
+ *   count + 1 entries; offsets[i] = lengths[0] + ... + lengths[i-1] and
+ *   offsets[count] = the total. count <= CG_NOALLOC_MAX_COUNT, else CG_EINVAL.
+ * Work is queued on cuda_stream (NULL = the legacy default stream) of the
+ * current device; the call then waits for that stream so that it can return
+ * CG_ETIMEOUT if the kernel's bounded wait gave up (else CG_OK / CG_ECUDA).
+ * The scratch is one file-scope device array of 8 * (CG_NOALLOC_MAX_COUNT /
+ * 2048 + 2) bytes (64 KiB + 16) that every GPU which loads the library holds
+ * until the process exits. The first call on a device, with that device
+ * current, looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture. Every call shares the array and
+ * clears the part it uses first, so calls that overlap on the GPU (other
+ * streams, other threads) race and must be serialised by the caller. */
+#define CG_NOALLOC_MAX_COUNT 16777216
+CG_API cg_status cg_offsets_noalloc(const int32_t* lengths, int64_t count, int64_t* offsets, void* cuda_stream);
+
 /* Waits for all work of the context; returns the first error its kernels found. */
 CG_API cg_status cg_sync(cg_ctx* ctx);
 

@@ -56,6 +56,7 @@ API = {
     "cg_sync": [ctypes.c_void_p],
     "cg_set_timing": [ctypes.c_void_p, ctypes.c_int],
     "cg_get_stats": [ctypes.c_void_p, ctypes.c_void_p],
+    "cg_offsets_noalloc": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p],
     "cg_status_str": [ctypes.c_int],
     "cg_last_error": [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t],
 }
@@ -240,6 +241,20 @@ def cg_get_stats(ctx: Context) -> dict:
     s = Stats()
     _check(ctx.ptr, lib().cg_get_stats(ctx.ptr, ctypes.byref(s)))
     return {"kernels_launched": int(s.kernels_launched), "stage_ms": [float(x) for x in s.stage_ms]}
+
+
+NOALLOC_MAX_COUNT = 16777216
+
+
+def cg_offsets_noalloc(lengths, offsets, stream=None):
+    """cg_offsets_noalloc on device tensors: offsets[i] = sum(lengths[:i]), offsets[-1] = total."""
+    handle = None
+    if stream is not None:
+        handle = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    count = len(lengths)
+    if len(offsets) < count + 1:
+        raise ValueError("offsets needs count + 1 entries")
+    _check(None, lib().cg_offsets_noalloc(_ptr(lengths), count, _ptr(offsets), handle))
 
 
 def cg_status_str(s: int) -> str:
