@@ -46,6 +46,11 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--min-chain-reads", type=int, default=2)
     p.add_argument("--threads", type=int, default=0, help="generator threads (0 = all cores)")
+    p.add_argument("--scale-genome", type=int, default=0,
+                   help="profiling only: the workload's recipe on a genome of this many bases")
+    p.add_argument("--ruler-log2", type=int, default=0)
+    p.add_argument("--tile-bytes", type=int, default=0)
+    p.add_argument("--emit-blocks-per-sm", type=int, default=0)
     return p.parse_args()
 
 
@@ -160,12 +165,15 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     pk, pk_kind = peaks()
     cfg = workload_cfg(args.workload)
+    if args.scale_genome:
+        cfg = dict(cfg, genome_len=int(args.scale_genome))
     t_gen = time.time()
     G = generate_pinned(cfg, args.threads)
     t_gen = time.time() - t_gen
 
     stream = torch.cuda.Stream()
     ctx = cg.cg_create(local_rank, stream=stream)
+    cg.cg_set_tuning(ctx, args.ruler_log2, args.tile_bytes, args.emit_blocks_per_sm)
     names = ("row_ptr", "col", "code", "suf", "len", "off", "packed")
     with torch.cuda.stream(stream):
         dev = {k: torch.from_numpy(getattr(G, k)).to("cuda", non_blocking=True) for k in names}
@@ -270,7 +278,8 @@ def run_ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": ms, "ms_per_graph": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8", "data": "synthetic (seeded generator, workload recipe in DESIGN.md)",
         "config": {
-            "workload": args.workload, "n_reads": G.n, "n_entries": G.m, "walk_reads": W, "n_contigs": n_contigs,
+            "workload": args.workload + (f" (recipe scaled to {args.scale_genome} bases)" if args.scale_genome else ""),
+            "tuning": cg.cg_get_tuning(ctx), "n_reads": G.n, "n_entries": G.m, "walk_reads": W, "n_contigs": n_contigs,
             "contig_bases": total, "packed_read_bytes": int(G.packed.nbytes), "min_chain_reads": args.min_chain_reads,
             "row_ptr_bytes": int(G.row_ptr.dtype.itemsize), "replicas": world,
             "l2": "flushed between steps (512 MiB write, outside the timed events)",

@@ -132,6 +132,19 @@ CG_API cg_status cg_chains(cg_graph* g, int32_t* chain_id, int32_t* rank, uint8_
 CG_API cg_status cg_emit_contigs(cg_graph* g, int64_t* contig_off, int64_t contig_off_cap, uint8_t* bases,
                           int64_t bases_cap, int mem, int64_t* n_contigs, int64_t* total_bases);
 
+/* Launch parameters of a context's kernels. None changes any output. */
+typedef struct {
+  int32_t ruler_log2;         /* list ranking: a read starts a sublist with probability 2^-ruler_log2, 1..12 */
+  int32_t tile_bytes;         /* spelling: output tile per block iteration, 4096, 8192, 16384 or 32768 */
+  int32_t emit_blocks_per_sm; /* spelling: resident blocks per SM, 1..8 */
+  int32_t reserved;
+} cg_tuning;
+
+/* Sets the launch parameters (a field <= 0 keeps its value); CG_EINVAL for
+ * values out of range. Applies to the next calls. */
+CG_API cg_status cg_set_tuning(cg_ctx* ctx, const cg_tuning* t);
+CG_API cg_status cg_get_tuning(cg_ctx* ctx, cg_tuning* out);
+
 /* Counters of a context, for measurement. */
 typedef struct {
   uint64_t kernels_launched; /* CUDA kernels this context has launched so far */

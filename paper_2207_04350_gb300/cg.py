@@ -55,6 +55,8 @@ API = {
                         ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
     "cg_sync": [ctypes.c_void_p],
     "cg_set_timing": [ctypes.c_void_p, ctypes.c_int],
+    "cg_set_tuning": [ctypes.c_void_p, ctypes.c_void_p],
+    "cg_get_tuning": [ctypes.c_void_p, ctypes.c_void_p],
     "cg_get_stats": [ctypes.c_void_p, ctypes.c_void_p],
     "cg_offsets_noalloc": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p],
     "cg_status_str": [ctypes.c_int],
@@ -226,6 +228,22 @@ def cg_emit_contigs(g: Graph, contig_off=None, bases=None, want_counts: bool = T
 
 def cg_sync(ctx: Context):
     _check(ctx.ptr, lib().cg_sync(ctx.ptr))
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("ruler_log2", ctypes.c_int32), ("tile_bytes", ctypes.c_int32), ("emit_blocks_per_sm", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+def cg_set_tuning(ctx: Context, ruler_log2: int = 0, tile_bytes: int = 0, emit_blocks_per_sm: int = 0):
+    t = Tuning(int(ruler_log2), int(tile_bytes), int(emit_blocks_per_sm), 0)
+    _check(ctx.ptr, lib().cg_set_tuning(ctx.ptr, ctypes.byref(t)))
+
+
+def cg_get_tuning(ctx: Context) -> dict:
+    t = Tuning()
+    _check(ctx.ptr, lib().cg_get_tuning(ctx.ptr, ctypes.byref(t)))
+    return {"ruler_log2": t.ruler_log2, "tile_bytes": t.tile_bytes, "emit_blocks_per_sm": t.emit_blocks_per_sm}
 
 
 class Stats(ctypes.Structure):

@@ -279,6 +279,35 @@ cg_status cg_destroy(cg_ctx* c) {
   return CG_OK;
 }
 
+cg_status cg_set_tuning(cg_ctx* c, const cg_tuning* t) {
+  if (!c || !t) return CG_EINVAL;
+  cg::Tuning n = c->tune;
+  if (t->ruler_log2 > 0) {
+    if (t->ruler_log2 > 12) return fail(c, CG_EINVAL, "ruler_log2 must be in 1..12");
+    n.ruler_log2 = t->ruler_log2;
+  }
+  if (t->tile_bytes > 0) {
+    if (t->tile_bytes != 4096 && t->tile_bytes != 8192 && t->tile_bytes != 16384 && t->tile_bytes != 32768)
+      return fail(c, CG_EINVAL, "tile_bytes must be 4096, 8192, 16384 or 32768");
+    n.tile_bytes = t->tile_bytes;
+  }
+  if (t->emit_blocks_per_sm > 0) {
+    if (t->emit_blocks_per_sm > 8) return fail(c, CG_EINVAL, "emit_blocks_per_sm must be in 1..8");
+    n.emit_blocks_per_sm = t->emit_blocks_per_sm;
+  }
+  c->tune = n;
+  return CG_OK;
+}
+
+cg_status cg_get_tuning(cg_ctx* c, cg_tuning* out) {
+  if (!c || !out) return CG_EINVAL;
+  out->ruler_log2 = c->tune.ruler_log2;
+  out->tile_bytes = c->tune.tile_bytes;
+  out->emit_blocks_per_sm = c->tune.emit_blocks_per_sm;
+  out->reserved = 0;
+  return CG_OK;
+}
+
 cg_status cg_set_timing(cg_ctx* c, int enable) {
   cg_status st = check_ctx(c);
   if (st != CG_OK) return st;
@@ -441,7 +470,6 @@ cg_status cg_load_graph(cg_ctx* c, const cg_graph_desc* d, uint32_t flags, cg_gr
   S.tiles_cap = g->sum_len / 4096 + 2;
   S.tile_seg = galloc<int32_t>(g, (size_t)S.tiles_cap + 1, &st);
   if (st != CG_OK) return bail(st);
-  if (c->tune.tile_bytes < 4096) c->tune.tile_bytes = 4096;
   *out = g;
   return CG_OK;
 }

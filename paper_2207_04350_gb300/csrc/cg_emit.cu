@@ -34,103 +34,114 @@ __device__ __forceinline__ uint32_t load_word(const uint32_t* words, const uint8
   return r;
 }
 
-// 16 bases starting at stored base p (p >= 0); base k at bits 2k.
-__device__ __forceinline__ uint32_t get16(const uint32_t* words, const uint8_t* bytes, long long full_words,
-                                          long long packed_bytes, long long p) {
-  long long w = p >> 4;
-  uint32_t lo = load_word(words, bytes, full_words, packed_bytes, w);
-  uint32_t hi = load_word(words, bytes, full_words, packed_bytes, w + 1);
-  return __funnelshift_r(lo, hi, (unsigned)(2 * (p & 15)));
-}
-
 // Reverse the order of the sixteen 2-bit groups.
 __device__ __forceinline__ uint32_t rev2(uint32_t x) {
   x = __brev(x);
   return ((x >> 1) & 0x55555555u) | ((x & 0x55555555u) << 1);
 }
 
+// Eight 2-bit codes (bits 0..15) spread to one code per nibble.
+__device__ __forceinline__ uint32_t spread8(uint32_t t) {
+  t &= 0xFFFFu;
+  t = (t | (t << 8)) & 0x00FF00FFu;
+  t = (t | (t << 4)) & 0x0F0F0F0Fu;
+  t = (t | (t << 2)) & 0x33333333u;
+  return t;
+}
+
+// 16 codes -> 16 ASCII bytes: each nibble selects a byte of "ACGT".
+__device__ __forceinline__ uint4 ascii16(uint32_t bits) {
+  const uint32_t acgt = 0x54474341u;   // 'T' 'G' 'C' 'A' from the high byte down
+  uint32_t lo = spread8(bits), hi = spread8(bits >> 16);
+  return make_uint4(__byte_perm(acgt, 0u, lo & 0xFFFFu), __byte_perm(acgt, 0u, lo >> 16),
+                    __byte_perm(acgt, 0u, hi & 0xFFFFu), __byte_perm(acgt, 0u, hi >> 16));
+}
+
 __device__ __forceinline__ int stored_base(const uint8_t* bytes, long long i) {
   return (__ldg(bytes + (i >> 2)) >> (2 * (i & 3))) & 3;
 }
 
+__device__ __forceinline__ long long shfl64(long long v, int src) {
+  int lo = __shfl_sync(0xffffffffu, (int)(v & 0xffffffffll), src);
+  int hi = __shfl_sync(0xffffffffu, (int)(v >> 32), src);
+  return ((long long)hi << 32) | (unsigned)lo;
+}
+
+// One ASCII base at output position X of a piece: source word w (first stored
+// base | reverse flag << 63), piece starts at output offset oj.
+__device__ __forceinline__ uint8_t base_at(const uint8_t* packed, unsigned long long w, long long oj, long long X) {
+  const long long src = (long long)(w & ~(1ull << 63));
+  const long long k = X - oj;
+  const int b = (w >> 63) ? (stored_base(packed, src - k) ^ 3) : stored_base(packed, src + k);
+  return (uint8_t)(0x54474341u >> (8 * b));
+}
+
+// One warp per output tile (persistent grid). The warp takes the pieces of its
+// tile, [tile_seg[t], tile_seg[t+1]], in order; of each piece it writes the
+// 16-byte-aligned interior inside the tile with full chunks (U chunks per lane
+// whose packed words are loaded together before any is used), and the at most
+// 30 bytes at its two ragged ends byte by byte. Chunks shared by two pieces
+// are thus written as disjoint bytes by each piece; no search per chunk.
+template <int U>
 __global__ void __launch_bounds__(kBlock) k_emit(Scratch s, const uint8_t* packed, long long packed_bytes,
                                                  uint8_t* out, long long cap, int tile_bytes) {
-  __shared__ uint32_t lut[256];
-  for (int i = threadIdx.x; i < 256; i += blockDim.x) {
-    uint32_t v = 0;
-    for (int k = 0; k < 4; ++k) v |= (uint32_t)("ACGT"[(i >> (2 * k)) & 3]) << (8 * k);
-    lut[i] = v;
-  }
-  __syncthreads();
   const Counters* c = s.ctr;
-  long long total = *(const volatile long long*)&c->total_bases;
+  const long long total = *(const volatile long long*)&c->total_bases;
   if (total > cap) {
     if (grid_tid() == 0) set_error(s.derr, DERR_CAPACITY, K_EMIT, total);
     return;
   }
-  long long ntiles = (total + tile_bytes - 1) / tile_bytes;
+  const int lane = threadIdx.x & 31;
+  const long long ntiles = (total + tile_bytes - 1) / tile_bytes;
   const uint32_t* words = reinterpret_cast<const uint32_t*>(packed);
-  long long full_words = packed_bytes >> 2;
+  const long long full_words = packed_bytes >> 2;
   const int64_t* oo = s.out_off;
   const unsigned long long* ws = s.wsrc;
-  int chunks = tile_bytes >> 4;
-  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    int lo = s.tile_seg[t], hi = s.tile_seg[t + 1];
-    long long tbase = t * (long long)tile_bytes;
-    for (int k = threadIdx.x; k < chunks; k += blockDim.x) {
-      long long X = tbase + 16ll * k;
-      if (X >= total) break;
-      int a = lo, b = hi;                       // last piece starting at or before X
-      while (a < b) {
-        int mid = (a + b + 1) >> 1;
-        if (oo[mid] <= X) a = mid; else b = mid - 1;
-      }
-      int j = a;
-      long long oj = oo[j], oe = oo[j + 1];
-      uint32_t r0, r1, r2, r3;
-      bool fast = X + 16 <= oe;
-      if (fast) {
-        unsigned long long w = ws[j];
-        long long src = (long long)(w & ~(1ull << 63));
-        long long k0 = X - oj;
-        uint32_t bits;
-        if (!(w >> 63)) {
-          bits = get16(words, packed, full_words, packed_bytes, src + k0);
-        } else {
-          long long q = src - k0 - 15;
-          if (q < 0) {
-            fast = false;
-          } else {
-            bits = ~rev2(get16(words, packed, full_words, packed_bytes, q));
+  for (long long t = grid_tid() >> 5; t < ntiles; t += grid_threads() >> 5) {
+    const int lo = s.tile_seg[t], hi = s.tile_seg[t + 1];
+    const long long tbase = t * (long long)tile_bytes;
+    const long long tend = min(tbase + (long long)tile_bytes, total);
+    for (int jb = lo; jb <= hi; jb += 32) {
+      const int jl = jb + lane;
+      const long long my_o = jl <= hi ? oo[jl] : 0, my_e = jl <= hi ? oo[jl + 1] : 0;
+      const long long my_w = jl <= hi ? (long long)ws[jl] : 0;
+      const int cnt = min(32, hi - jb + 1);
+      for (int q = 0; q < cnt; ++q) {
+        const long long oj = shfl64(my_o, q), oe = shfl64(my_e, q);
+        const unsigned long long w = (unsigned long long)shfl64(my_w, q);
+        const long long a = max(oj, tbase), b = min(oe, tend);   // the piece's bytes in this tile
+        if (a >= b) continue;
+        const long long A = (a + 15) & ~15ll, B = b & ~15ll;     // aligned interior [A, B)
+        const bool rc = (w >> 63) != 0;
+        const long long src = (long long)(w & ~(1ull << 63));
+        for (long long X0 = A + 16ll * lane; X0 < B; X0 += 512ll * U) {
+          uint32_t wlo[U], whi[U];
+          int sh[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const long long X = X0 + 512ll * u;
+            wlo[u] = whi[u] = 0u;
+            sh[u] = 0;
+            if (X >= B) continue;
+            const long long k0 = X - oj;
+            const long long p = rc ? src - k0 - 15 : src + k0;   // lowest stored base of the 16
+            sh[u] = (int)(2 * (p & 15));
+            wlo[u] = load_word(words, packed, full_words, packed_bytes, p >> 4);
+            whi[u] = load_word(words, packed, full_words, packed_bytes, (p >> 4) + 1);
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const long long X = X0 + 512ll * u;
+            if (X >= B) continue;
+            uint32_t bits = __funnelshift_r(wlo[u], whi[u], (unsigned)sh[u]);
+            if (rc) bits = ~rev2(bits);
+            __stcs(reinterpret_cast<uint4*>(out + X), ascii16(bits));
           }
         }
-        if (fast) {
-          r0 = lut[bits & 255u];
-          r1 = lut[(bits >> 8) & 255u];
-          r2 = lut[(bits >> 16) & 255u];
-          r3 = lut[bits >> 24];
-        }
-      }
-      if (!fast) {
-        uint32_t r[4] = {0u, 0u, 0u, 0u};
-        int jj = j;
-        for (int bb = 0; bb < 16; ++bb) {
-          long long Xb = X + bb;
-          if (Xb >= total) break;
-          while (jj < hi && Xb >= oo[jj + 1]) ++jj;
-          unsigned long long w = ws[jj];
-          long long src = (long long)(w & ~(1ull << 63));
-          long long kk = Xb - oo[jj];
-          int base = (w >> 63) ? (stored_base(packed, src - kk) ^ 3) : stored_base(packed, src + kk);
-          r[bb >> 2] |= (uint32_t)("ACGT"[base]) << (8 * (bb & 3));
-        }
-        r0 = r[0]; r1 = r[1]; r2 = r[2]; r3 = r[3];
-      }
-      if (X + 16 <= total) {
-        *reinterpret_cast<uint4*>(out + X) = make_uint4(r0, r1, r2, r3);
-      } else {
-        uint32_t r[4] = {r0, r1, r2, r3};
-        for (long long bb = 0; X + bb < total; ++bb) out[X + bb] = (uint8_t)(r[bb >> 2] >> (8 * (bb & 3)));
+        // ragged ends: [a, head_end) and, when there is an interior, [B, b)
+        const long long head_end = A < B ? A : b;
+        if (a + lane < head_end) out[a + lane] = base_at(packed, w, oj, a + lane);
+        if (A < B && B + lane < b) out[B + lane] = base_at(packed, w, oj, B + lane);
       }
     }
   }
@@ -140,8 +151,16 @@ __global__ void __launch_bounds__(kBlock) k_emit(Scratch s, const uint8_t* packe
 
 cudaError_t launch_emit(const DevGraph& g, const Scratch& s, const Tuning& t, uint8_t* out, int64_t cap,
                         const LaunchEnv& env) {
-  int blocks = env.num_sms * t.emit_blocks_per_sm;
-  k_emit<<<blocks, kBlock, 0, env.stream>>>(s, g.packed, g.packed_bytes, out, cap, t.tile_bytes);
+  // a persistent grid: never more blocks than can be resident at once
+  static int resident = 0;
+  if (resident == 0) {
+    int r = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_emit<4>, kBlock, 0);
+    resident = r > 0 ? r : 1;
+  }
+  int per_sm = t.emit_blocks_per_sm < resident ? t.emit_blocks_per_sm : resident;
+  int blocks = env.num_sms * per_sm;
+  k_emit<4><<<blocks, kBlock, 0, env.stream>>>(s, g.packed, g.packed_bytes, out, cap, t.tile_bytes);
   ++*env.launches;
   return cudaGetLastError();
 }

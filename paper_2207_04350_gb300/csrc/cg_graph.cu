@@ -117,14 +117,17 @@ __global__ void k_validate_entries(DevGraph g, DevError* c) {
 // <= 2 whose overlaps to reads of degree <= 2 are exactly two, both on the
 // same end, cannot be passed by a valid walk and is a branch too. Reads with
 // no overlap are lone reads: a one-read contig when min_chain <= 1.
-__global__ void k_mask(DevGraph g, Scratch s) {
+constexpr int kMaskItems = 4;
+
+__global__ void __launch_bounds__(kBlock) k_mask(DevGraph g, Scratch s) {
   Counters* c = s.ctr;
-  long long nn = warp_round(g.n);
   unsigned long long nb = 0;
-  for (long long v = grid_tid(); v < nn; v += grid_threads()) {
-    bool valid = v < g.n;
-    bool cand = false, lone = false;
-    if (valid) {
+  const long long step = (long long)gridDim.x * kBlock * kMaskItems;
+  for (long long base = (long long)blockIdx.x * kBlock * kMaskItems; base < g.n; base += step) {  // block-uniform
+    unsigned candm = 0, lonem = 0;
+    for (int k = 0; k < kMaskItems; ++k) {
+      long long v = base + (long long)k * kBlock + threadIdx.x;
+      if (v >= g.n) continue;
       int64_t a = rowp(g, v), b = rowp(g, v + 1);
       int64_t d = b - a;
       uint8_t br = 0;
@@ -147,17 +150,23 @@ __global__ void k_mask(DevGraph g, Scratch s) {
       if (br) {
         s.headq[v] = 0;
       } else if (d == 0) {
-        lone = g.min_chain <= 1;
+        bool lone = g.min_chain <= 1;
         s.headq[v] = lone ? 1 : 0;
-        if (lone) { s.cid[v] = (int32_t)v; s.rank[v] = 0; s.orient[v] = 0; s.contrib[v] = g.len[v]; }
+        if (lone) {
+          s.cid[v] = (int32_t)v; s.rank[v] = 0; s.orient[v] = 0; s.contrib[v] = g.len[v];
+          lonem |= 1u << k;
+        }
       } else {
-        cand = true;
+        candm |= 1u << k;
       }
     }
-    unsigned slot = warp_append(&c->n_cand, cand);
-    if (cand) s.cand[slot] = (int32_t)v;
-    unsigned eslot = warp_append(&c->n_lone, lone);
-    if (lone) s.emit[eslot] = (int32_t)v;
+    unsigned cs = block_reserve(&c->n_cand, __popc(candm));
+    unsigned ls = block_reserve(&c->n_lone, __popc(lonem));
+    for (int k = 0; k < kMaskItems; ++k) {
+      int32_t v = (int32_t)(base + (long long)k * kBlock + threadIdx.x);
+      if ((candm >> k) & 1u) s.cand[cs++] = v;
+      if ((lonem >> k) & 1u) s.emit[ls++] = v;
+    }
   }
   for (int o = 16; o > 0; o >>= 1) nb += __shfl_down_sync(0xffffffffu, nb, o);
   if ((threadIdx.x & 31) == 0 && nb) atomicAdd(&c->n_branch, nb);
@@ -169,7 +178,7 @@ __global__ void k_mask(DevGraph g, Scratch s) {
 // incoming suffix is suf(v->w).
 __global__ void k_succ(DevGraph g, Scratch s) {
   Counters* c = s.ctr;
-  long long n = warp_round(*(volatile unsigned*)&c->n_cand);
+  long long n = block_round(*(volatile unsigned*)&c->n_cand);
   for (long long i = grid_tid(); i < n; i += grid_threads()) {
     bool valid = i < c->n_cand;
     bool chain = false, lone = false;
@@ -204,9 +213,9 @@ __global__ void k_succ(DevGraph g, Scratch s) {
         s.rid[2 * v + 1] = -1;
       }
     }
-    unsigned slot = warp_append(&c->n_chain, chain);
+    unsigned slot = block_reserve(&c->n_chain, chain ? 1u : 0u);
     if (chain) s.chain[slot] = v;
-    unsigned eslot = warp_append(&c->n_emit, lone);
+    unsigned eslot = block_reserve(&c->n_emit, lone ? 1u : 0u);
     if (lone) s.emit[eslot] = v;
   }
 }
@@ -214,7 +223,7 @@ __global__ void k_succ(DevGraph g, Scratch s) {
 // One thread per sublist start: walk to the next start or the list end.
 __global__ void k_walk(Scratch s, int ruler_log2, int64_t limit) {
   Counters* c = s.ctr;
-  long long nodes = warp_round(2ll * *(volatile unsigned*)&c->n_chain);
+  long long nodes = block_round(2ll * *(volatile unsigned*)&c->n_chain);
   for (long long i = grid_tid(); i < nodes; i += grid_threads()) {
     bool valid = i < 2ll * c->n_chain;
     bool ruler = false;
@@ -227,7 +236,7 @@ __global__ void k_walk(Scratch s, int ruler_log2, int64_t limit) {
       nx = o == 0 ? sv.x : sv.y;
       ruler = pred < 0 || sampled(v, ruler_log2);
     }
-    unsigned r = warp_append(&c->n_rulers, ruler);
+    unsigned r = block_reserve(&c->n_rulers, ruler ? 1u : 0u);
     if (!ruler) continue;
     int32_t y = 2 * v + o, z = nx, mn = v, last = y, next_start = -1;
     int32_t cnt = 0;
@@ -306,7 +315,7 @@ __global__ void k_jump(Scratch s) {
 __global__ void k_final(DevGraph g, Scratch s) {
   Counters* c = s.ctr;
   int fb = (int)*(volatile unsigned*)&c->final_buf;
-  long long n = warp_round(*(volatile unsigned*)&c->n_chain);
+  long long n = block_round(*(volatile unsigned*)&c->n_chain);
   const int32_t* nx = s.pj_next[fb];
   const int32_t* acc = s.pj_acc[fb];
   const int32_t* mnv = s.pj_min[fb];
@@ -349,9 +358,9 @@ __global__ void k_final(DevGraph g, Scratch s) {
         }
       }
     }
-    unsigned slot = warp_append(&c->n_cycle_reads, cyc);
+    unsigned slot = block_reserve(&c->n_cycle_reads, cyc ? 1u : 0u);
     if (cyc) s.cyc[slot] = v;
-    unsigned eslot = warp_append(&c->n_emit, emit);
+    unsigned eslot = block_reserve(&c->n_emit, emit ? 1u : 0u);
     if (emit) s.emit[eslot] = v;
   }
 }
@@ -422,7 +431,7 @@ __global__ void k_cycles(DevGraph g, Scratch s) {
     cur = nxt;
     if (!grid_sync(c, s.derr)) return;
   }
-  long long NN = warp_round(N);
+  long long NN = block_round(N);
   for (long long i = grid_tid(); i < NN; i += grid_threads()) {
     bool emit = false;
     int32_t v = 0;
@@ -451,7 +460,7 @@ __global__ void k_cycles(DevGraph g, Scratch s) {
         if (rk == 0) atomicAdd(&c->n_cycles, 1u);
       }
     }
-    unsigned eslot = warp_append(&c->n_emit, emit);
+    unsigned eslot = block_reserve(&c->n_emit, emit ? 1u : 0u);
     if (emit) s.emit[eslot] = v;
   }
 }

@@ -112,7 +112,7 @@ struct Scratch {
 // Tuning knobs (chosen by the autotuner per size class).
 struct Tuning {
   int ruler_log2 = 4;      // a read starts a sublist with probability 2^-ruler_log2
-  int tile_bytes = 8192;   // emission tile (multiple of 16)
+  int tile_bytes = 32768;  // emission tile: 4, 8, 16 or 32 KiB
   int emit_blocks_per_sm = 8;
   int grid_blocks_per_sm = 8;
 };
@@ -147,8 +147,9 @@ __device__ __forceinline__ void set_error(DevError* e, int code, int where, long
 
 __device__ __forceinline__ long long grid_tid() { return (long long)blockIdx.x * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ long long grid_threads() { return (long long)gridDim.x * blockDim.x; }
-// Rounded-up trip count so that whole warps iterate together (for warp_append).
-__device__ __forceinline__ long long warp_round(long long n) { return (n + 31) & ~31ll; }
+// Rounded-up trip count so that whole blocks iterate together (block_reserve
+// synchronises the block).
+__device__ __forceinline__ long long block_round(long long n) { return (n + kBlock - 1) / kBlock * kBlock; }
 
 enum KernelId {
   K_VALIDATE1 = 1, K_VALIDATE2, K_MASK, K_SUCC, K_WALK, K_JUMP, K_FINAL, K_CYCLE, K_EXPORT,
@@ -178,6 +179,34 @@ __device__ __forceinline__ unsigned warp_append(unsigned* counter, bool want) {
   if (lane == leader) base = atomicAdd(counter, (unsigned)__popc(mask));
   base = __shfl_sync(mask, base, leader);
   return base + (unsigned)__popc(mask & ((1u << lane) - 1u));
+}
+
+// Block-wide reservation of `count` list slots per thread with one atomic per
+// block: every thread of the block must call it (block-uniform control flow).
+// Returns the first slot of this thread's items.
+__device__ __forceinline__ unsigned block_reserve(unsigned* counter, unsigned count) {
+  __shared__ unsigned s_w[kBlock / 32 + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned inc = count;
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) s_w[warp] = inc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned tot = 0;
+    for (int w = 0; w < kBlock / 32; ++w) {
+      unsigned c = s_w[w];
+      s_w[w] = tot;
+      tot += c;
+    }
+    s_w[kBlock / 32] = tot ? atomicAdd(counter, tot) : 0u;
+  }
+  __syncthreads();
+  unsigned base = s_w[kBlock / 32] + s_w[warp] + inc - count;
+  __syncthreads();
+  return base;
 }
 
 }  // namespace cg

@@ -66,6 +66,7 @@ def test_struct_layouts_match_header(tmp_path):
     for f in fields:
         assert int(out[f]) == getattr(cg.GraphDesc, f).offset, f
     s, o = out["stats"].split()
+    assert ctypes.sizeof(cg.Tuning) == 16
     assert int(s) == ctypes.sizeof(cg.Stats) and int(o) == cg.Stats.stage_ms.offset
 
 

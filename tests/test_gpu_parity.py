@@ -169,6 +169,21 @@ def test_small_capacity_rejected(ctx):
     assert np.array_equal(bases, orc.bases)
 
 
+@pytest.mark.parametrize("ruler_log2,tile_bytes,bps", [(1, 4096, 1), (2, 8192, 2), (4, 16384, 8), (7, 32768, 4),
+                                                       (12, 32768, 3)])
+def test_tuning_does_not_change_output(ruler_log2, tile_bytes, bps):
+    """Launch parameters chosen by the autotuner never change a byte."""
+    c = cg.cg_create(0)
+    try:
+        cg.cg_set_tuning(c, ruler_log2=ruler_log2, tile_bytes=tile_bytes, emit_blocks_per_sm=bps)
+        assert cg.cg_get_tuning(c) == {"ruler_log2": ruler_log2, "tile_bytes": tile_bytes, "emit_blocks_per_sm": bps}
+        check(c, structured(21, [50_000, 3, 4, 17] + [2] * 40 + [6] * 30, [False, True, True, True] + [False] * 70,
+                            lone=50, align=1), 1)
+        check(c, gen.generate(gen.batched_graph(11), threads=8), 2)
+    finally:
+        c.close()
+
+
 def test_repeat_runs_are_identical(ctx):
     G = gen.generate(gen.batched_graph(3), threads=8)
     g = cg.cg_load_graph(ctx, G)
