@@ -212,7 +212,7 @@ def run_ours(args, rank, world, local_rank):
     clocks.start()
     time.sleep(0.3)
     launches0 = cg.cg_get_stats(ctx)["kernels_launched"]
-    step_ms, emit_ms, stage = [], [], []
+    step_ms, emit_ms, stage, kern = [], [], [], {}
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     t0 = time.time()
@@ -230,6 +230,15 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     t1 = time.time()
     launches = cg.cg_get_stats(ctx)["kernels_launched"] - launches0
+    # per-kernel breakdown: separate untimed steps with an event after every kernel
+    cg.cg_set_timing(ctx, 2)
+    for _ in range(3):
+        with torch.cuda.stream(stream):
+            flush.fill_(3)
+        step()
+        for name, kms in cg.cg_kernel_times(ctx):
+            kern.setdefault(name, []).append(kms)
+    cg.cg_set_timing(ctx, 1)
     if world > 1:
         torch.distributed.barrier()
     time.sleep(0.2)
@@ -286,6 +295,8 @@ def run_ours(args, rank, world, local_rank):
             "inputs": "resident in HBM (CG_BORROW_DEVICE)", "reads_per_s": G.n / (ms * 1e-3),
             "stage_ms_mean": [statistics.mean(s[k] for s in stage) for k in range(4)],
             "stage_names": ["mask", "chains", "offsets", "emit"],
+            "kernel_ms_mean": {k: statistics.mean(v) for k, v in kern.items()},
+            "kernel_ms_note": "3 extra untimed steps with a CUDA event after every kernel",
             "B_min_bytes": B, "path_achieved_gbs": B / (ms * 1e-3) / 1e9,
             "path_roofline_frac": B / (ms * 1e-3) / 1e9 / pk["hbm_gbs"],
             "path_roofline_frac_8tbs": B / (ms * 1e-3) / 1e9 / 8000.0,

@@ -202,8 +202,9 @@ class _Handle:
 
 
 def generate(d: dict | str, threads: int | None = None, rp_bytes: int | None = None, off_align: int = 32,
-             shuffle_ids: bool = True, keep_genome: bool = True, alloc=None) -> Graph:
-    """Build one graph. `alloc(shape, dtype)` may supply (e.g. pinned) host buffers."""
+             shuffle_ids: bool = True, keep_genome: bool = True, alloc=None, with_packed: bool = True) -> Graph:
+    """Build one graph. `alloc(shape, dtype)` may supply (e.g. pinned) host buffers;
+    with_packed=False leaves the read sequences out (graph statistics only)."""
     if isinstance(d, str):
         d = WORKLOADS[d]()
     lib = _load()
@@ -225,14 +226,15 @@ def generate(d: dict | str, threads: int | None = None, rp_bytes: int | None = N
     rp = mk((n + 1,), np.int64 if rp_bytes == 8 else np.int32)
     col, code, suf = mk((m,), np.int32), mk((m,), np.uint8), mk((m,), np.int32)
     ln, off = mk((n,), np.int32), mk((n,), np.int64)
-    packed = mk((info["packed_bytes"],), np.uint8)
+    packed = mk((info["packed_bytes"],), np.uint8) if with_packed else np.zeros(1, np.uint8)
     is_true, gstart, strand = np.empty(m, np.uint8), np.empty(n, np.int64), np.empty(n, np.uint8)
     contained = np.empty(n, np.uint8)
 
     def p(a):
         return ctypes.c_void_p(a.ctypes.data if isinstance(a, np.ndarray) else a.data_ptr())
 
-    rc = lib.cg_gen_fill(h.ptr, p(rp), rp_bytes, p(col), p(code), p(suf), p(ln), p(off), p(packed),
+    rc = lib.cg_gen_fill(h.ptr, p(rp), rp_bytes, p(col), p(code), p(suf), p(ln), p(off),
+                         p(packed) if with_packed else None,
                          p(is_true), p(gstart), p(strand), p(contained))
     if rc != 0:
         h.close()

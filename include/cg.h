@@ -145,6 +145,12 @@ typedef struct {
 CG_API cg_status cg_set_tuning(cg_ctx* ctx, const cg_tuning* t);
 CG_API cg_status cg_get_tuning(cg_ctx* ctx, cg_tuning* out);
 
+/* With graphs on (the default), each stage's kernel launches are captured
+ * once into a CUDA graph per graph and set of buffers, sizes and launch
+ * parameters, and replayed with one launch afterwards. Off: launched one by
+ * one. Outputs are the same either way. */
+CG_API cg_status cg_set_graphs(cg_ctx* ctx, int enable);
+
 /* Counters of a context, for measurement. */
 typedef struct {
   uint64_t kernels_launched; /* CUDA kernels this context has launched so far */
@@ -152,11 +158,17 @@ typedef struct {
                                 (CUDA events on the context stream; 0 unless timing is on) */
 } cg_stats;
 
-/* Turns per-stage CUDA-event timing on (1) or off (0). Events are recorded
- * around each stage on the context stream; the work itself is unchanged. */
+/* Timing: 0 off, 1 CUDA events around each stage, 2 also after every
+ * kernel (for cg_kernel_time; the extra events cost some GPU time). Events
+ * are recorded on the context stream; the work itself is unchanged. */
 CG_API cg_status cg_set_timing(cg_ctx* ctx, int enable);
 /* Fills *out; with timing on it waits for the last stages to finish. */
 CG_API cg_status cg_get_stats(cg_ctx* ctx, cg_stats* out);
+/* With timing 2: the name (static string) and GPU time in ms of the k-th
+ * kernel (k from 0) launched since the last mask stage began; each time runs
+ * from the previous kernel's end mark, so it includes the small memsets
+ * queued between kernels. Waits for the GPU. CG_EINVAL past the last one. */
+CG_API cg_status cg_kernel_time(cg_ctx* ctx, int k, const char** name, float* ms);
 
 /* Exclusive prefix offsets without any device allocation, for callers that
  * cannot call cudaMalloc: code running while another allocator owns the

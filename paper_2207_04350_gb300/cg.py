@@ -55,8 +55,10 @@ API = {
                         ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
     "cg_sync": [ctypes.c_void_p],
     "cg_set_timing": [ctypes.c_void_p, ctypes.c_int],
+    "cg_set_graphs": [ctypes.c_void_p, ctypes.c_int],
     "cg_set_tuning": [ctypes.c_void_p, ctypes.c_void_p],
     "cg_get_tuning": [ctypes.c_void_p, ctypes.c_void_p],
+    "cg_kernel_time": [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_float)],
     "cg_get_stats": [ctypes.c_void_p, ctypes.c_void_p],
     "cg_offsets_noalloc": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p],
     "cg_status_str": [ctypes.c_int],
@@ -250,8 +252,13 @@ class Stats(ctypes.Structure):
     _fields_ = [("kernels_launched", ctypes.c_uint64), ("stage_ms", ctypes.c_float * 4)]
 
 
-def cg_set_timing(ctx: Context, enable: bool):
-    _check(ctx.ptr, lib().cg_set_timing(ctx.ptr, 1 if enable else 0))
+def cg_set_graphs(ctx: Context, enable: bool):
+    _check(ctx.ptr, lib().cg_set_graphs(ctx.ptr, 1 if enable else 0))
+
+
+def cg_set_timing(ctx: Context, level):
+    """0 off, 1 (or True) stage events, 2 stage and per-kernel events."""
+    _check(ctx.ptr, lib().cg_set_timing(ctx.ptr, int(level)))
 
 
 def cg_get_stats(ctx: Context) -> dict:
@@ -273,6 +280,18 @@ def cg_offsets_noalloc(lengths, offsets, stream=None):
     if len(offsets) < count + 1:
         raise ValueError("offsets needs count + 1 entries")
     _check(None, lib().cg_offsets_noalloc(_ptr(lengths), count, _ptr(offsets), handle))
+
+
+def cg_kernel_times(ctx: Context) -> list:
+    """[(kernel name, ms)] of the last run, with timing level 2 (cg_set_timing)."""
+    out = []
+    k = 0
+    while True:
+        name, ms = ctypes.c_char_p(), ctypes.c_float()
+        if lib().cg_kernel_time(ctx.ptr, k, ctypes.byref(name), ctypes.byref(ms)) != CG_OK:
+            return out
+        out.append((name.value.decode(), float(ms.value)))
+        k += 1
 
 
 def cg_status_str(s: int) -> str:

@@ -33,6 +33,16 @@ struct cg_ctx {
   bool timing = false;
   cudaEvent_t ev[8] = {};              // start/end of mask, chains, offsets, emission
   bool recorded[4] = {false, false, false, false};
+  cg::KernelMarks marks;               // per-kernel events of the last run (timing on)
+  bool graphs = true;                  // replay each stage from a captured CUDA graph
+};
+
+// A captured stage: the instantiated graph and what its capture recorded.
+struct StageExec {
+  cudaGraphExec_t exec = nullptr;
+  uint64_t key = 0;
+  unsigned long long kernels = 0;      // kernels in the graph
+  int mark_end = 0;                    // per-kernel timing marks after the stage
 };
 
 struct cg_graph {
@@ -46,6 +56,7 @@ struct cg_graph {
   int64_t stage_bases_cap = 0;
   void* stage_reads = nullptr;
   unsigned long long* d_sum = nullptr;
+  StageExec execs[5];                  // mask, chains, offsets, emission, contig_off export
 };
 
 namespace {
@@ -169,10 +180,64 @@ struct StageTimer {
   }
 };
 
+uint64_t mix_key(uint64_t h, uint64_t v) { return (h ^ (v + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2))); }
+
+// Runs one stage's launches. With graphs on, the launches are captured once
+// into a CUDA graph per (stage, key) and replayed with a single launch; the
+// key covers every host-side value the launches bake in (buffers, sizes,
+// tuning, timing marks).
+template <class F>
+cg_status run_stage(cg_graph* g, int slot, uint64_t key, F&& launch) {
+  cg_ctx* c = g->ctx;
+  if (!c->graphs) return launch();
+  StageExec& e = g->execs[slot];
+  key = mix_key(key, c->marks.on ? 1 : 2);
+  if (e.exec && e.key == key) {
+    c->launches += e.kernels;
+    if (c->marks.on) c->marks.n = e.mark_end;
+    CK(cudaGraphLaunch(e.exec, c->stream), "cudaGraphLaunch");
+    return CG_OK;
+  }
+  if (e.exec) {
+    cudaGraphExecDestroy(e.exec);
+    e.exec = nullptr;
+  }
+  const unsigned long long l0 = c->launches;
+  CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+  cg_status st = launch();
+  cudaGraph_t graph = nullptr;
+  cudaError_t ee = cudaStreamEndCapture(c->stream, &graph);
+  if (st != CG_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return st;
+  }
+  if (ee != cudaSuccess) return cuda_fail(c, ee, "cudaStreamEndCapture");
+  ee = cudaGraphInstantiate(&e.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ee != cudaSuccess) {
+    e.exec = nullptr;
+    return cuda_fail(c, ee, "cudaGraphInstantiate");
+  }
+  e.key = key;
+  e.kernels = c->launches - l0;
+  e.mark_end = c->marks.n;
+  CK(cudaGraphLaunch(e.exec, c->stream), "cudaGraphLaunch");
+  return CG_OK;
+}
+
 cg_status run_mask(cg_graph* g) {
   cg_ctx* c = g->ctx;
+  if (c->marks.on) {                   // a new run: per-kernel marks start over
+    c->marks.n = 0;
+    cudaEventRecord(c->marks.ev[0], c->stream);
+  }
   StageTimer tm(c, 0);
-  CK(cg::launch_mask(g->g, g->s, c->env), "mask kernels");
+  cg_status st = run_stage(g, 0, 1, [&]() -> cg_status {
+    CK(cg::launch_mask(g->g, g->s, c->env), "mask kernels");
+    return CG_OK;
+  });
+  if (st != CG_OK) return st;
   g->stage = 1;
   return CG_OK;
 }
@@ -180,11 +245,15 @@ cg_status run_mask(cg_graph* g) {
 cg_status run_chains(cg_graph* g) {
   cg_ctx* c = g->ctx;
   if (g->stage < 1) {
-    cg_status st = run_mask(g);
-    if (st != CG_OK) return st;
+    cg_status st0 = run_mask(g);
+    if (st0 != CG_OK) return st0;
   }
   StageTimer tm(c, 1);
-  CK(cg::launch_chains(g->g, g->s, c->tune, c->env), "chain kernels");
+  cg_status st = run_stage(g, 1, (uint64_t)c->tune.ruler_log2, [&]() -> cg_status {
+    CK(cg::launch_chains(g->g, g->s, c->tune, c->env), "chain kernels");
+    return CG_OK;
+  });
+  if (st != CG_OK) return st;
   g->stage = 2;
   return CG_OK;
 }
@@ -192,11 +261,15 @@ cg_status run_chains(cg_graph* g) {
 cg_status run_offsets(cg_graph* g) {
   cg_ctx* c = g->ctx;
   if (g->stage < 2) {
-    cg_status st = run_chains(g);
-    if (st != CG_OK) return st;
+    cg_status st0 = run_chains(g);
+    if (st0 != CG_OK) return st0;
   }
   StageTimer tm(c, 2);
-  CK(cg::launch_offsets(g->g, g->s, c->tune, c->env), "offset kernels");
+  cg_status st = run_stage(g, 2, (uint64_t)c->tune.tile_bytes, [&]() -> cg_status {
+    CK(cg::launch_offsets(g->g, g->s, c->tune, c->env), "offset kernels");
+    return CG_OK;
+  });
+  if (st != CG_OK) return st;
   g->stage = 3;
   return CG_OK;
 }
@@ -248,6 +321,7 @@ cg_status cg_create(cg_ctx** out, int device, uint64_t hbm_budget_bytes, void* c
   c->env.num_sms = sms > 0 ? sms : 1;
   c->env.coop_blocks = cg::coop_blocks_for_grid_kernels(c->env.num_sms);
   c->env.launches = &c->launches;
+  c->env.marks = &c->marks;
   if (cudaMalloc(&c->derr, sizeof(cg::DevError)) != cudaSuccess ||
       cudaMallocHost(&c->h_err, sizeof(cg::DevError)) != cudaSuccess ||
       cudaMallocHost(&c->h_ctr, sizeof(cg::Counters)) != cudaSuccess ||
@@ -272,6 +346,8 @@ cg_status cg_destroy(cg_ctx* c) {
   if (c->h_ctr) cudaFreeHost(c->h_ctr);
   if (c->h_u64) cudaFreeHost(c->h_u64);
   for (cudaEvent_t e : c->ev)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->marks.ev)
     if (e) cudaEventDestroy(e);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   cudaGetLastError();
@@ -308,12 +384,23 @@ cg_status cg_get_tuning(cg_ctx* c, cg_tuning* out) {
   return CG_OK;
 }
 
+cg_status cg_set_graphs(cg_ctx* c, int enable) {
+  cg_status st = check_ctx(c);
+  if (st != CG_OK) return st;
+  c->graphs = enable != 0;
+  return CG_OK;
+}
+
 cg_status cg_set_timing(cg_ctx* c, int enable) {
   cg_status st = check_ctx(c);
   if (st != CG_OK) return st;
-  if (enable && !c->ev[0])
+  if (enable && !c->ev[0]) {
     for (cudaEvent_t& e : c->ev) CK(cudaEventCreate(&e), "cudaEventCreate");
+    for (cudaEvent_t& e : c->marks.ev) CK(cudaEventCreate(&e), "cudaEventCreate");
+  }
   c->timing = enable != 0;
+  c->marks.on = enable >= 2;
+  c->marks.n = 0;
   for (bool& r : c->recorded) r = false;
   return CG_OK;
 }
@@ -332,6 +419,19 @@ cg_status cg_get_stats(cg_ctx* c, cg_stats* out) {
   return CG_OK;
 }
 
+cg_status cg_kernel_time(cg_ctx* c, int k, const char** name, float* ms) {
+  cg_status st = check_ctx(c);
+  if (st != CG_OK) return st;
+  if (!c->marks.on || k < 0 || k >= c->marks.n) return CG_EINVAL;
+  CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+  if (name) *name = c->marks.name[k + 1];
+  if (ms && cudaEventElapsedTime(ms, c->marks.ev[k], c->marks.ev[k + 1]) != cudaSuccess) {
+    cudaGetLastError();                // a measurement gap is not a failure of the context
+    *ms = -1.f;
+  }
+  return CG_OK;
+}
+
 cg_status cg_sync(cg_ctx* c) {
   if (!c) return CG_EINVAL;
   if (c->sticky != CG_OK) return c->sticky;
@@ -345,6 +445,8 @@ cg_status cg_free_graph(cg_graph* g) {
   cg_ctx* c = g->ctx;
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);   // buffers may still be in use by queued work
+  for (StageExec& e : g->execs)
+    if (e.exec) cudaGraphExecDestroy(e.exec);
   for (void* p : g->owned) dfree(c, p);
   dfree(c, g->stage_bases);
   delete g;
@@ -385,6 +487,7 @@ cg_status cg_load_graph(cg_ctx* c, const cg_graph_desc* d, uint32_t flags, cg_gr
   G.rp64 = d->row_ptr_bytes == 8;
   G.min_chain = d->min_chain_reads <= 0 ? 2 : d->min_chain_reads;
   G.packed_bytes = d->packed_bytes;
+  G.packed_readable = borrow ? d->packed_bytes : d->packed_bytes + 16;   // owned copies carry 16 zero bytes
   if (borrow) {
     G.row_ptr = d->row_ptr;
     G.col = d->col;
@@ -417,15 +520,21 @@ cg_status cg_load_graph(cg_ctx* c, const cg_graph_desc* d, uint32_t flags, cg_gr
 
   // scratch
   cg::Scratch& S = g->s;
-  const size_t N = (size_t)(n > 0 ? n : 1), N2 = 2 * N;
+  const size_t N = (size_t)(n > 0 ? n : 1), N2 = 2 * N, NW = N / 32 + 2;
   S.branch = galloc<uint8_t>(g, N, &st);
   S.cand = galloc<int32_t>(g, N, &st);
   S.chain = galloc<int32_t>(g, N, &st);
-  S.emit = galloc<int32_t>(g, N, &st);
+  S.lone = galloc<int32_t>(g, N, &st);
+  S.lone2 = galloc<int32_t>(g, N, &st);
+  S.hb_mask = galloc<unsigned>(g, NW, &st);
+  S.hb = galloc<unsigned>(g, NW, &st);
+  S.wp = galloc<unsigned>(g, NW, &st);
   S.succ = galloc<int2>(g, N, &st);
   S.sufin = galloc<int32_t>(g, N2, &st);
   S.rid = galloc<int32_t>(g, N2, &st);
   S.roff = galloc<int32_t>(g, N2, &st);
+  S.rlist = galloc<int32_t>(g, N2, &st);
+  S.hlist = galloc<int32_t>(g, N2, &st);
   S.r_next_node = galloc<int32_t>(g, N2, &st);
   S.r_len = galloc<int32_t>(g, N2, &st);
   S.r_min = galloc<int32_t>(g, N2, &st);
@@ -444,15 +553,20 @@ cg_status cg_load_graph(cg_ctx* c, const cg_graph_desc* d, uint32_t flags, cg_gr
   S.orient = galloc<uint8_t>(g, N, &st);
   S.contrib = galloc<int32_t>(g, N, &st);
   S.headq = galloc<int32_t>(g, N, &st);
-  S.rb = galloc<unsigned long long>(g, N + 1, &st);
   S.cyc = galloc<int32_t>(g, N, &st);
+  S.qd = galloc<int32_t>(g, N, &st);
+  S.cbase = galloc<unsigned long long>(g, N + 1, &st);
   S.wsrc = galloc<unsigned long long>(g, N, &st);
   S.wlen = galloc<int32_t>(g, N, &st);
   S.out_off = galloc<int64_t>(g, N + 1, &st);
   S.cstart = galloc<int32_t>(g, N, &st);
   S.contig_off = galloc<int64_t>(g, N + 1, &st);
   S.scan_tiles_cap = (int64_t)(N + 2047) / 2048 + 1;
-  S.scan_state = galloc<unsigned long long>(g, (size_t)S.scan_tiles_cap + 1, &st);
+  S.scan_state[0] = galloc<unsigned long long>(g, 3 * ((size_t)S.scan_tiles_cap + 1), &st);
+  if (S.scan_state[0]) {
+    S.scan_state[1] = S.scan_state[0] + (S.scan_tiles_cap + 1);
+    S.scan_state[2] = S.scan_state[1] + (S.scan_tiles_cap + 1);
+  }
   S.ctr = galloc<cg::Counters>(g, 1, &st);
   g->d_sum = galloc<unsigned long long>(g, 1, &st);
   S.derr = c->derr;
@@ -546,9 +660,21 @@ cg_status cg_emit_contigs(cg_graph* g, int64_t* contig_off, int64_t contig_off_c
     if (bases) {
       if (!aligned(bases, 16)) return fail(c, CG_EINVAL, "device bases buffer must be 16-byte aligned");
       StageTimer tm(c, 3);
-      CK(cg::launch_emit(g->g, g->s, c->tune, bases, bases_cap, c->env), "emission kernel");
+      uint64_t key = mix_key(mix_key(mix_key((uint64_t)(uintptr_t)bases, (uint64_t)bases_cap), (uint64_t)c->tune.tile_bytes),
+                             (uint64_t)c->tune.emit_blocks_per_sm);
+      st = run_stage(g, 3, key, [&]() -> cg_status {
+        CK(cg::launch_emit(g->g, g->s, c->tune, bases, bases_cap, c->env), "emission kernel");
+        return CG_OK;
+      });
+      if (st != CG_OK) return st;
     }
-    if (contig_off) CK(cg::launch_export_contig_off(g->s, contig_off, contig_off_cap, c->env), "export contig_off");
+    if (contig_off) {
+      st = run_stage(g, 4, mix_key((uint64_t)(uintptr_t)contig_off, (uint64_t)contig_off_cap), [&]() -> cg_status {
+        CK(cg::launch_export_contig_off(g->s, contig_off, contig_off_cap, c->env), "export contig_off");
+        return CG_OK;
+      });
+      if (st != CG_OK) return st;
+    }
     if (n_contigs || total_bases) {
       st = wait_and_read(g);
       if (st != CG_OK) return st;
@@ -568,7 +694,13 @@ cg_status cg_emit_contigs(cg_graph* g, int64_t* contig_off, int64_t contig_off_c
       }
       {
         StageTimer tm(c, 3);
-        CK(cg::launch_emit(g->g, g->s, c->tune, g->stage_bases, g->stage_bases_cap, c->env), "emission kernel");
+        uint64_t key = mix_key(mix_key(mix_key((uint64_t)(uintptr_t)g->stage_bases, (uint64_t)g->stage_bases_cap),
+                                       (uint64_t)c->tune.tile_bytes), (uint64_t)c->tune.emit_blocks_per_sm);
+        st = run_stage(g, 3, key, [&]() -> cg_status {
+          CK(cg::launch_emit(g->g, g->s, c->tune, g->stage_bases, g->stage_bases_cap, c->env), "emission kernel");
+          return CG_OK;
+        });
+        if (st != CG_OK) return st;
       }
       CK(cudaMemcpyAsync(bases, g->stage_bases, (size_t)total, cudaMemcpyDeviceToHost, c->stream), "copy bases");
     }

@@ -10,11 +10,9 @@
 //
 // A chunk inside one piece is read with two 32-bit words of the packed
 // stream and one funnel shift (16 bases); a reverse-complement piece takes
-// the 16 bases below it, reverses the 2-bit groups and complements them
-// (complement of b is 3-b = b^3, i.e. bitwise NOT). Four lookups in a
-// shared-memory table turn 4 bases (one byte) into 4 ASCII characters.
-// Chunks that straddle pieces, or sit at the very start of the stream, take
-// the base-by-base path.
+// the 16 bases below it. Four lookups in a shared-memory table turn 4 bases
+// (one byte) into 4 ASCII characters; the reverse-complement table holds
+// the complemented characters in reverse order (complement of b is 3-b).
 #include <cuda_runtime.h>
 
 #include "cg_internal.cuh"
@@ -32,29 +30,6 @@ __device__ __forceinline__ uint32_t load_word(const uint32_t* words, const uint8
     if (i < packed_bytes) r |= (uint32_t)__ldg(bytes + i) << (8 * b);
   }
   return r;
-}
-
-// Reverse the order of the sixteen 2-bit groups.
-__device__ __forceinline__ uint32_t rev2(uint32_t x) {
-  x = __brev(x);
-  return ((x >> 1) & 0x55555555u) | ((x & 0x55555555u) << 1);
-}
-
-// Eight 2-bit codes (bits 0..15) spread to one code per nibble.
-__device__ __forceinline__ uint32_t spread8(uint32_t t) {
-  t &= 0xFFFFu;
-  t = (t | (t << 8)) & 0x00FF00FFu;
-  t = (t | (t << 4)) & 0x0F0F0F0Fu;
-  t = (t | (t << 2)) & 0x33333333u;
-  return t;
-}
-
-// 16 codes -> 16 ASCII bytes: each nibble selects a byte of "ACGT".
-__device__ __forceinline__ uint4 ascii16(uint32_t bits) {
-  const uint32_t acgt = 0x54474341u;   // 'T' 'G' 'C' 'A' from the high byte down
-  uint32_t lo = spread8(bits), hi = spread8(bits >> 16);
-  return make_uint4(__byte_perm(acgt, 0u, lo & 0xFFFFu), __byte_perm(acgt, 0u, lo >> 16),
-                    __byte_perm(acgt, 0u, hi & 0xFFFFu), __byte_perm(acgt, 0u, hi >> 16));
 }
 
 __device__ __forceinline__ int stored_base(const uint8_t* bytes, long long i) {
@@ -78,13 +53,30 @@ __device__ __forceinline__ uint8_t base_at(const uint8_t* packed, unsigned long 
 
 // One warp per output tile (persistent grid). The warp takes the pieces of its
 // tile, [tile_seg[t], tile_seg[t+1]], in order; of each piece it writes the
-// 16-byte-aligned interior inside the tile with full chunks (U chunks per lane
-// whose packed words are loaded together before any is used), and the at most
-// 30 bytes at its two ragged ends byte by byte. Chunks shared by two pieces
-// are thus written as disjoint bytes by each piece; no search per chunk.
+// 16-byte-aligned interior inside the tile with full chunks, and the at most
+// 30 bytes at its two ragged ends byte by byte (chunks shared by two pieces
+// are thus written as disjoint bytes by each piece). Inside one piece every
+// chunk starts 16 bases after the previous one, so the funnel-shift amount
+// is the same for the whole piece and the packed word index moves by one per
+// chunk (up for a forward piece, down for a reverse-complement one): all
+// address arithmetic is done once per piece. Each chunk is two word loads,
+// one funnel shift and four lookups in a shared table that maps a byte (four
+// bases) to four ASCII characters, forward or reverse-complemented.
 template <int U>
 __global__ void __launch_bounds__(kBlock) k_emit(Scratch s, const uint8_t* packed, long long packed_bytes,
-                                                 uint8_t* out, long long cap, int tile_bytes) {
+                                                 long long readable_words, uint8_t* out, long long cap,
+                                                 int tile_bytes) {
+  __shared__ uint32_t lut[2][256];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+    uint32_t f = 0, r = 0;
+    for (int k = 0; k < 4; ++k) {
+      f |= (0x54474341u >> (8 * ((i >> (2 * k)) & 3)) & 255u) << (8 * k);             // base k -> byte k
+      r |= (0x54474341u >> (8 * (3 - ((i >> (2 * (3 - k))) & 3))) & 255u) << (8 * k);  // complement of base 3-k
+    }
+    lut[0][i] = f;
+    lut[1][i] = r;
+  }
+  __syncthreads();
   const Counters* c = s.ctr;
   const long long total = *(const volatile long long*)&c->total_bases;
   if (total > cap) {
@@ -112,30 +104,53 @@ __global__ void __launch_bounds__(kBlock) k_emit(Scratch s, const uint8_t* packe
         const long long a = max(oj, tbase), b = min(oe, tend);   // the piece's bytes in this tile
         if (a >= b) continue;
         const long long A = (a + 15) & ~15ll, B = b & ~15ll;     // aligned interior [A, B)
-        const bool rc = (w >> 63) != 0;
-        const long long src = (long long)(w & ~(1ull << 63));
-        for (long long X0 = A + 16ll * lane; X0 < B; X0 += 512ll * U) {
-          uint32_t wlo[U], whi[U];
-          int sh[U];
+        if (A < B) {
+          const int rc = (int)(w >> 63);
+          const long long src = (long long)(w & ~(1ull << 63));
+          const long long p0 = rc ? src - (A - oj) - 15 : src + (A - oj);   // lowest stored base of chunk 0
+          const unsigned sh = (unsigned)(2 * (p0 & 15));
+          const int nch = (int)((B - A) >> 4);
+          const long long w0 = p0 >> 4;
+          const long long wmax = rc ? w0 + 1 : w0 + nch;             // highest word the piece reads
+          const uint32_t* tab = lut[rc];
+          uint4* dst = reinterpret_cast<uint4*>(out + A);
+          if (wmax < readable_words) {
+            const int step = rc ? -1 : 1;
+            const uint32_t* wp = words + w0;
+            for (int c0 = lane; c0 < nch; c0 += 32 * U) {
+              uint32_t lo4[U], hi4[U];
 #pragma unroll
-          for (int u = 0; u < U; ++u) {
-            const long long X = X0 + 512ll * u;
-            wlo[u] = whi[u] = 0u;
-            sh[u] = 0;
-            if (X >= B) continue;
-            const long long k0 = X - oj;
-            const long long p = rc ? src - k0 - 15 : src + k0;   // lowest stored base of the 16
-            sh[u] = (int)(2 * (p & 15));
-            wlo[u] = load_word(words, packed, full_words, packed_bytes, p >> 4);
-            whi[u] = load_word(words, packed, full_words, packed_bytes, (p >> 4) + 1);
-          }
+              for (int u = 0; u < U; ++u) {
+                const int ci = c0 + 32 * u;
+                const int wi = ci < nch ? ci * step : 0;
+                lo4[u] = __ldg(wp + wi);
+                hi4[u] = __ldg(wp + wi + 1);
+              }
 #pragma unroll
-          for (int u = 0; u < U; ++u) {
-            const long long X = X0 + 512ll * u;
-            if (X >= B) continue;
-            uint32_t bits = __funnelshift_r(wlo[u], whi[u], (unsigned)sh[u]);
-            if (rc) bits = ~rev2(bits);
-            __stcs(reinterpret_cast<uint4*>(out + X), ascii16(bits));
+              for (int u = 0; u < U; ++u) {
+                const int ci = c0 + 32 * u;
+                if (ci >= nch) continue;
+                const uint32_t bits = __funnelshift_r(lo4[u], hi4[u], sh);
+                uint4 v;
+                if (rc) {
+                  v = make_uint4(tab[bits >> 24], tab[(bits >> 16) & 255u], tab[(bits >> 8) & 255u], tab[bits & 255u]);
+                } else {
+                  v = make_uint4(tab[bits & 255u], tab[(bits >> 8) & 255u], tab[(bits >> 16) & 255u], tab[bits >> 24]);
+                }
+                __stcs(dst + ci, v);
+              }
+            }
+          } else {                                                     // piece ends at the stream's end
+            for (int ci = lane; ci < nch; ci += 32) {
+              const long long wi = rc ? w0 - ci : w0 + ci;
+              const uint32_t bits = __funnelshift_r(load_word(words, packed, full_words, packed_bytes, wi),
+                                                    load_word(words, packed, full_words, packed_bytes, wi + 1), sh);
+              const uint4 v = rc ? make_uint4(tab[bits >> 24], tab[(bits >> 16) & 255u], tab[(bits >> 8) & 255u],
+                                              tab[bits & 255u])
+                                 : make_uint4(tab[bits & 255u], tab[(bits >> 8) & 255u], tab[(bits >> 16) & 255u],
+                                              tab[bits >> 24]);
+              __stcs(dst + ci, v);
+            }
           }
         }
         // ragged ends: [a, head_end) and, when there is an interior, [B, b)
@@ -160,8 +175,9 @@ cudaError_t launch_emit(const DevGraph& g, const Scratch& s, const Tuning& t, ui
   }
   int per_sm = t.emit_blocks_per_sm < resident ? t.emit_blocks_per_sm : resident;
   int blocks = env.num_sms * per_sm;
-  k_emit<4><<<blocks, kBlock, 0, env.stream>>>(s, g.packed, g.packed_bytes, out, cap, t.tile_bytes);
-  ++*env.launches;
+  k_emit<4><<<blocks, kBlock, 0, env.stream>>>(s, g.packed, g.packed_bytes, g.packed_readable / 4, out, cap,
+                                               t.tile_bytes);
+  mark(env, "k_emit");
   return cudaGetLastError();
 }
 

@@ -14,12 +14,14 @@
 //
 // List ranking (Helman-JaJa style sublists): every list head and every read
 // whose hash falls in a 2^-k sample starts a sublist; one thread walks each
-// sublist to the next sublist start, then pointer jumping over the (few)
-// sublists gives each one its distance to the list tail, the tail itself and
-// the smallest read id up to the tail. A read then knows, from its two
-// oriented copies, the chain's length, both end reads, its position from
-// either end, and the chain's smallest read id. Closed chains (no tail) are
-// detected after the jumping and ranked separately from their smallest read.
+// sublist to the next sublist start. Each list head then walks its (short)
+// list of sublists twice -- once for the length, the tail and the smallest
+// read, once to hand every sublist its distance to the tail. Lists with more
+// sublists than that walk follows are left to grid-synchronised pointer
+// jumping, which only runs when needed; closed chains (no head) go to their
+// own kernel. A read then knows, from its two oriented copies, the chain's
+// length, both end reads, its position from either end, and the chain's
+// smallest read id.
 #include <cuda_runtime.h>
 
 #include "cg_internal.cuh"
@@ -29,6 +31,8 @@ namespace cg {
 namespace {
 
 constexpr long long kSpinLimit = 1ll << 22;   // barrier polls before giving up (~1 s with backoff)
+constexpr int kListWalkMax = 64;              // sublists a list head follows before leaving it to jumping
+constexpr int kUnresolved = -2;               // pj_next value of a sublist no list walk has finished
 
 __device__ __forceinline__ int sampled(int v, int ruler_log2) {
   unsigned h = (unsigned)v * 0x9E3779B1u;
@@ -36,6 +40,12 @@ __device__ __forceinline__ int sampled(int v, int ruler_log2) {
   h *= 0x85EBCA77u;
   h ^= h >> 13;
   return (h & ((1u << ruler_log2) - 1u)) == 0u;
+}
+
+// Read m is the smallest read of a contig of q reads.
+__device__ __forceinline__ void mark_head(const Scratch& s, int32_t m, int32_t q) {
+  atomicOr(&s.hb[m >> 5], 1u << (m & 31));
+  s.headq[m] = q;
 }
 
 // Software grid barrier for kernels launched cooperatively (all blocks
@@ -116,56 +126,62 @@ __global__ void k_validate_entries(DevGraph g, DevError* c) {
 // d[v] = row length of S (Sec. 4.2); d >= 3 is a branch. A read of degree
 // <= 2 whose overlaps to reads of degree <= 2 are exactly two, both on the
 // same end, cannot be passed by a valid walk and is a branch too. Reads with
-// no overlap are lone reads: a one-read contig when min_chain <= 1.
+// no overlap are lone reads: a one-read contig when min_chain <= 1. Every
+// word of the mask-stage bitmap of contig heads is written here (the lone
+// reads' bits); the chain stage adds the other heads to a copy of it.
 constexpr int kMaskItems = 4;
 
 __global__ void __launch_bounds__(kBlock) k_mask(DevGraph g, Scratch s) {
   Counters* c = s.ctr;
   unsigned long long nb = 0;
+  const int lane = threadIdx.x & 31;
   const long long step = (long long)gridDim.x * kBlock * kMaskItems;
   for (long long base = (long long)blockIdx.x * kBlock * kMaskItems; base < g.n; base += step) {  // block-uniform
     unsigned candm = 0, lonem = 0;
     for (int k = 0; k < kMaskItems; ++k) {
-      long long v = base + (long long)k * kBlock + threadIdx.x;
-      if (v >= g.n) continue;
-      int64_t a = rowp(g, v), b = rowp(g, v + 1);
-      int64_t d = b - a;
-      uint8_t br = 0;
-      if (d >= 3) {
-        br = 1;
-      } else if (d > 0) {
-        int cnt = 0, e0 = -1, e1 = -1;
-        for (int64_t x = a; x < b; ++x) {
-          int32_t w = g.col[x];
-          int64_t dw = rowp(g, w + 1) - rowp(g, w);
-          if (dw >= 3) continue;
-          int e = g.code[x] & 1;
-          if (cnt == 0) e0 = e; else e1 = e;
-          ++cnt;
+      const long long v = base + (long long)k * kBlock + threadIdx.x;
+      bool lone = false;
+      if (v < g.n) {
+        int64_t a = rowp(g, v), b = rowp(g, v + 1);
+        int64_t d = b - a;
+        uint8_t br = 0;
+        if (d >= 3) {
+          br = 1;
+        } else if (d > 0) {
+          int cnt = 0, e0 = -1, e1 = -1;
+          for (int64_t x = a; x < b; ++x) {
+            int32_t w = g.col[x];
+            int64_t dw = rowp(g, w + 1) - rowp(g, w);
+            if (dw >= 3) continue;
+            int e = g.code[x] & 1;
+            if (cnt == 0) e0 = e; else e1 = e;
+            ++cnt;
+          }
+          br = (cnt == 2 && e0 == e1) ? 1 : 0;
         }
-        br = (cnt == 2 && e0 == e1) ? 1 : 0;
-      }
-      s.branch[v] = br;
-      nb += br;
-      if (br) {
-        s.headq[v] = 0;
-      } else if (d == 0) {
-        bool lone = g.min_chain <= 1;
-        s.headq[v] = lone ? 1 : 0;
-        if (lone) {
-          s.cid[v] = (int32_t)v; s.rank[v] = 0; s.orient[v] = 0; s.contrib[v] = g.len[v];
-          lonem |= 1u << k;
+        s.branch[v] = br;
+        nb += br;
+        if (!br && d == 0) {
+          lone = g.min_chain <= 1;
+          if (lone) {
+            s.cid[v] = (int32_t)v; s.rank[v] = 0; s.orient[v] = 0; s.contrib[v] = g.len[v]; s.headq[v] = 1;
+            lonem |= 1u << k;
+          }
+        } else if (!br) {
+          candm |= 1u << k;
         }
-      } else {
-        candm |= 1u << k;
       }
+      // a warp holds 32 consecutive reads: one bitmap word
+      const unsigned word = __ballot_sync(0xffffffffu, lone);
+      const long long v0 = base + (long long)k * kBlock + (threadIdx.x & ~31);
+      if (lane == 0 && v0 < g.n) s.hb_mask[v0 >> 5] = word;
     }
     unsigned cs = block_reserve(&c->n_cand, __popc(candm));
     unsigned ls = block_reserve(&c->n_lone, __popc(lonem));
     for (int k = 0; k < kMaskItems; ++k) {
       int32_t v = (int32_t)(base + (long long)k * kBlock + threadIdx.x);
       if ((candm >> k) & 1u) s.cand[cs++] = v;
-      if ((lonem >> k) & 1u) s.emit[ls++] = v;
+      if ((lonem >> k) & 1u) s.lone[ls++] = v;
     }
   }
   for (int o = 16; o > 0; o >>= 1) nb += __shfl_down_sync(0xffffffffu, nb, o);
@@ -175,18 +191,20 @@ __global__ void __launch_bounds__(kBlock) k_mask(DevGraph g, Scratch s) {
 // Successor table of L for the unmasked reads that have overlaps:
 // succ[v] = (successor of (v,0), successor of (v,1)); the overlap (v->w)
 // on end E_v is the way out of (v, 1-E_v) and enters (w, E_w), whose
-// incoming suffix is suf(v->w).
-__global__ void k_succ(DevGraph g, Scratch s) {
+// incoming suffix is suf(v->w). Also lists the chain reads, the sublist
+// starts (list heads and sampled reads) and, among them, the list heads.
+__global__ void __launch_bounds__(kBlock) k_succ(DevGraph g, Scratch s, int ruler_log2) {
   Counters* c = s.ctr;
-  long long n = block_round(*(volatile unsigned*)&c->n_cand);
-  for (long long i = grid_tid(); i < n; i += grid_threads()) {
-    bool valid = i < c->n_cand;
-    bool chain = false, lone = false;
+  const long long N = *(volatile unsigned*)&c->n_cand;
+  const long long n = block_round(N);
+  unsigned* const ctrs[4] = {&c->n_chain, &c->n_lone2, &c->n_rulers, &c->n_hlist};
+  for (long long i = grid_tid(); i < n; i += grid_threads()) {   // block-uniform trip count
     int32_t v = 0;
-    if (valid) {
+    int s0 = -1, s1 = -1;
+    bool chain = false, lone = false, r0 = false, r1 = false;
+    if (i < N) {
       v = s.cand[i];
       int64_t a = rowp(g, v), b = rowp(g, v + 1);
-      int s0 = -1, s1 = -1;
       for (int64_t x = a; x < b; ++x) {
         int32_t w = g.col[x];
         if (s.branch[w]) continue;
@@ -197,58 +215,61 @@ __global__ void k_succ(DevGraph g, Scratch s) {
         s.sufin[to] = g.suf[x];
       }
       s.succ[v] = make_int2(s0, s1);
-      if (s0 < 0 && s1 < 0) {
+      if (s0 < 0 && s1 < 0) {            // every overlap leads to a branch read
         lone = g.min_chain <= 1;
-        s.headq[v] = lone ? 1 : 0;
         s.cid[v] = lone ? v : -1;
         s.rank[v] = lone ? 0 : -1;
         s.orient[v] = lone ? 0 : 255;
         s.contrib[v] = g.len[v];
-        if (lone) atomicAdd(&c->n_heads, 1u);
+        if (lone) {
+          mark_head(s, v, 1);
+          atomicAdd(&c->n_heads, 1u);
+        }
       } else {
         chain = true;
-        // not yet reached by a sublist walk (closed chains without a
-        // sampled read are never reached, and are found by this mark)
-        s.rid[2 * v] = -1;
+        s.rid[2 * v] = -1;               // not yet reached by a sublist walk
         s.rid[2 * v + 1] = -1;
+        const bool smp = sampled(v, ruler_log2) != 0;
+        r0 = s1 < 0 || smp;              // (v,0) has no predecessor when (v,1) has no successor
+        r1 = s0 < 0 || smp;
       }
     }
-    unsigned slot = block_reserve(&c->n_chain, chain ? 1u : 0u);
-    if (chain) s.chain[slot] = v;
-    unsigned eslot = block_reserve(&c->n_emit, lone ? 1u : 0u);
-    if (lone) s.emit[eslot] = v;
+    const bool h0 = chain && s1 < 0, h1 = chain && s0 < 0;
+    const unsigned long long cnt = (unsigned long long)chain | ((unsigned long long)lone << 16) |
+                                   ((unsigned long long)(r0 + r1) << 32) | ((unsigned long long)(h0 + h1) << 48);
+    unsigned base[4];
+    block_reserve4(ctrs, cnt, base);
+    if (chain) s.chain[base[0]] = v;
+    if (lone) s.lone2[base[1]] = v;
+    if (r0) {
+      s.rlist[base[2]] = 2 * v;
+      if (h0) s.hlist[base[3]++] = (int32_t)base[2];
+      ++base[2];
+    }
+    if (r1) {
+      s.rlist[base[2]] = 2 * v + 1;
+      if (h1) s.hlist[base[3]] = (int32_t)base[2];
+    }
   }
 }
 
 // One thread per sublist start: walk to the next start or the list end.
 __global__ void k_walk(Scratch s, int ruler_log2, int64_t limit) {
   Counters* c = s.ctr;
-  long long nodes = block_round(2ll * *(volatile unsigned*)&c->n_chain);
-  for (long long i = grid_tid(); i < nodes; i += grid_threads()) {
-    bool valid = i < 2ll * c->n_chain;
-    bool ruler = false;
-    int32_t v = 0, o = 0, nx = -1;
-    if (valid) {
-      v = s.chain[i >> 1];
-      o = (int)(i & 1);
-      int2 sv = s.succ[v];
-      int pred = o == 0 ? sv.y : sv.x;  // (v,o) has a predecessor iff (v,1-o) has a successor
-      nx = o == 0 ? sv.x : sv.y;
-      ruler = pred < 0 || sampled(v, ruler_log2);
-    }
-    unsigned r = block_reserve(&c->n_rulers, ruler ? 1u : 0u);
-    if (!ruler) continue;
-    int32_t y = 2 * v + o, z = nx, mn = v, last = y, next_start = -1;
+  const long long R = *(volatile unsigned*)&c->n_rulers;
+  for (long long r = grid_tid(); r < R; r += grid_threads()) {
+    const int32_t x = s.rlist[r];
+    const int2 sv = s.succ[x >> 1];
+    int32_t y = x, z = (x & 1) ? sv.y : sv.x, mn = x >> 1, next_start = -1;
     int32_t cnt = 0;
     for (;;) {
       s.rid[y] = (int32_t)r;
       s.roff[y] = cnt;
       ++cnt;
       mn = min(mn, y >> 1);
-      last = y;
       if (z < 0) break;
       if (sampled(z >> 1, ruler_log2)) { next_start = z; break; }
-      int2 sz = s.succ[z >> 1];
+      const int2 sz = s.succ[z >> 1];
       y = z;
       z = (z & 1) ? sz.y : sz.x;
       if (cnt > limit) { set_error(s.derr, DERR_KERNEL, K_WALK, y); break; }
@@ -256,16 +277,58 @@ __global__ void k_walk(Scratch s, int ruler_log2, int64_t limit) {
     s.r_next_node[r] = next_start;
     s.r_len[r] = cnt;
     s.r_min[r] = mn;
-    s.r_last[r] = last;
+    s.r_last[r] = y;
+    s.pj_next[0][r] = kUnresolved;
   }
 }
 
-// Pointer jumping over the sublists (grid-synchronised rounds). After it,
-// for a sublist on an open list: acc = oriented reads from its start to the
-// list tail, mn = smallest read id over that span, tail = last sublist.
-// Sublists on directed cycles keep next >= 0.
+// One thread per list head: walk the list of sublists for the total length,
+// the tail and the smallest read, then again to give each sublist its
+// distance to the tail. Longer lists are left to pointer jumping.
+__global__ void k_listwalk(Scratch s) {
+  Counters* c = s.ctr;
+  const long long H = *(volatile unsigned*)&c->n_hlist;
+  for (long long h = grid_tid(); h < H; h += grid_threads()) {
+    const int32_t r0 = s.hlist[h];
+    int32_t r = r0, mn = 0x7fffffff, steps = 0;
+    long long total = 0;
+    bool ok = true;
+    for (;;) {
+      total += s.r_len[r];
+      mn = min(mn, s.r_min[r]);
+      const int32_t nn = s.r_next_node[r];
+      if (nn < 0) break;
+      if (++steps >= kListWalkMax) { ok = false; break; }
+      r = s.rid[nn];
+    }
+    if (!ok || total > 0x7fffffffll) {
+      atomicOr(&c->need_jump, 1u);
+      continue;
+    }
+    const int32_t tail = r;
+    long long acc = total;
+    r = r0;
+    for (;;) {
+      s.pj_acc[0][r] = (int32_t)acc;
+      s.pj_min[0][r] = mn;
+      s.pj_tail[0][r] = tail;
+      s.pj_next[0][r] = -1;
+      acc -= s.r_len[r];
+      const int32_t nn = s.r_next_node[r];
+      if (nn < 0) break;
+      r = s.rid[nn];
+    }
+  }
+}
+
+// Pointer jumping over all sublists (grid-synchronised rounds), only when a
+// list walk gave up (very long chains). After it, for a sublist on an open
+// list: acc = oriented reads from its start to the list tail, mn = smallest
+// read id over that span, tail = last sublist. Sublists on directed cycles
+// keep next >= 0.
 __global__ void k_jump(Scratch s) {
   Counters* c = s.ctr;
+  if (*(volatile unsigned*)&c->need_jump == 0) return;   // the same for every block: written by the kernel before
   unsigned R = *(volatile unsigned*)&c->n_rulers;
   for (long long i = grid_tid(); i < R; i += grid_threads()) {
     int32_t nn = s.r_next_node[i];
@@ -311,57 +374,56 @@ __global__ void k_jump(Scratch s) {
 // Per chain read: combine its two oriented copies. head(list of (v,0)) is
 // the reverse of tail(list of (v,1)). The contig starts at the smaller-id
 // end read, so (v,0) is the walk orientation when that end heads the list
-// of (v,0).
+// of (v,0). Reads of closed chains (no list head reached them) are listed
+// for the cycle kernel.
 __global__ void k_final(DevGraph g, Scratch s) {
   Counters* c = s.ctr;
-  int fb = (int)*(volatile unsigned*)&c->final_buf;
-  long long n = block_round(*(volatile unsigned*)&c->n_chain);
+  const int fb = (int)*(volatile unsigned*)&c->final_buf;
+  const long long N = *(volatile unsigned*)&c->n_chain;
+  const long long n = (N + 31) & ~31ll;
   const int32_t* nx = s.pj_next[fb];
   const int32_t* acc = s.pj_acc[fb];
   const int32_t* mnv = s.pj_min[fb];
   const int32_t* tl = s.pj_tail[fb];
-  for (long long k = grid_tid(); k < n; k += grid_threads()) {
-    bool valid = k < c->n_chain;
-    bool cyc = false, emit = false;
+  for (long long k = grid_tid(); k < n; k += grid_threads()) {   // warp-uniform trip count
+    bool cyc = false;
     int32_t v = 0;
-    if (valid) {
+    if (k < N) {
       v = s.chain[k];
-      int32_t x0 = 2 * v, x1 = x0 + 1;
-      int32_t i0 = s.rid[x0], i1 = s.rid[x1];
-      if (i0 < 0 || i1 < 0 || nx[i0] >= 0 || nx[i1] >= 0) {
+      const int32_t x0 = 2 * v, x1 = x0 + 1;
+      const int32_t i0 = s.rid[x0], i1 = s.rid[x1];
+      if (i0 < 0 || i1 < 0 || nx[i0] != -1 || nx[i1] != -1) {
         cyc = true;
       } else {
-        int32_t d0 = acc[i0] - s.roff[x0] - 1;
-        int32_t d1 = acc[i1] - s.roff[x1] - 1;
-        int32_t t0 = s.r_last[tl[i0]];
-        int32_t t1 = s.r_last[tl[i1]];
-        int32_t h0 = t1 >> 1, h1 = t0 >> 1;       // first read of the list of (v,0) / (v,1)
-        int32_t hr = s.rid[t1 ^ 1];                // the head of (v,0)'s list starts a sublist
-        int32_t m = hr >= 0 ? mnv[hr] : -1;
-        int32_t q = d0 + d1 + 1;
-        int o = h0 < h1 ? 0 : 1;
-        int32_t rk = o == 0 ? d1 : d0;
+        const int32_t d0 = acc[i0] - s.roff[x0] - 1;
+        const int32_t d1 = acc[i1] - s.roff[x1] - 1;
+        const int32_t t0 = s.r_last[tl[i0]];
+        const int32_t t1 = s.r_last[tl[i1]];
+        const int32_t h0 = t1 >> 1, h1 = t0 >> 1;       // first read of the list of (v,0) / (v,1)
+        const int32_t hr = s.rid[t1 ^ 1];               // the head of (v,0)'s list starts a sublist
+        const int32_t m = hr >= 0 ? mnv[hr] : -1;
+        const int32_t q = d0 + d1 + 1;
+        const int o = h0 < h1 ? 0 : 1;
+        const int32_t rk = o == 0 ? d1 : d0;
         if (m < 0 || h0 == h1) set_error(s.derr, DERR_KERNEL, K_FINAL, v);
         if (q >= g.min_chain) {
-          emit = true;
           s.cid[v] = m;
           s.rank[v] = rk;
           s.orient[v] = (uint8_t)o;
           s.contrib[v] = rk == 0 ? g.len[v] : s.sufin[x0 + o];
-          s.headq[v] = (v == m) ? q : 0;
-          if (v == m) atomicAdd(&c->n_heads, 1u);
+          if (v == m) {
+            mark_head(s, m, q);
+            atomicAdd(&c->n_heads, 1u);
+          }
         } else {
           s.cid[v] = -1;
           s.rank[v] = -1;
           s.orient[v] = 255;
-          s.headq[v] = 0;
         }
       }
     }
-    unsigned slot = block_reserve(&c->n_cycle_reads, cyc ? 1u : 0u);
+    const unsigned slot = warp_append(&c->n_cycle_reads, cyc);
     if (cyc) s.cyc[slot] = v;
-    unsigned eslot = block_reserve(&c->n_emit, emit ? 1u : 0u);
-    if (emit) s.emit[eslot] = v;
   }
 }
 
@@ -431,37 +493,29 @@ __global__ void k_cycles(DevGraph g, Scratch s) {
     cur = nxt;
     if (!grid_sync(c, s.derr)) return;
   }
-  long long NN = block_round(N);
-  for (long long i = grid_tid(); i < NN; i += grid_threads()) {
-    bool emit = false;
-    int32_t v = 0;
-    if (i < N) {
-      v = s.cyc[i >> 1];
-      int32_t y = 2 * v + (int)(i & 1);
-      int32_t head = s.c_head[y];
-      if ((head & 1) == 0) {
-        int32_t L = s.c_val[cur][head] + 1;       // distance from the start to the cut, plus one
-        int32_t rk = L - 1 - s.c_val[cur][y];
-        int32_t m = head >> 1;
-        if (L >= g.min_chain) {
-          emit = true;
-          s.cid[v] = m;
-          s.rank[v] = rk;
-          s.orient[v] = (uint8_t)(y & 1);
-          s.contrib[v] = rk == 0 ? g.len[v] : s.sufin[y];
-          s.headq[v] = rk == 0 ? L : 0;
-          if (rk == 0) atomicAdd(&c->n_heads, 1u);
-        } else {
-          s.cid[v] = -1;
-          s.rank[v] = -1;
-          s.orient[v] = 255;
-          s.headq[v] = 0;
-        }
-        if (rk == 0) atomicAdd(&c->n_cycles, 1u);
+  for (long long i = grid_tid(); i < N; i += grid_threads()) {
+    int32_t v = s.cyc[i >> 1];
+    int32_t y = 2 * v + (int)(i & 1);
+    int32_t head = s.c_head[y];
+    if (head & 1) continue;
+    int32_t L = s.c_val[cur][head] + 1;       // distance from the start to the cut, plus one
+    int32_t rk = L - 1 - s.c_val[cur][y];
+    int32_t m = head >> 1;
+    if (L >= g.min_chain) {
+      s.cid[v] = m;
+      s.rank[v] = rk;
+      s.orient[v] = (uint8_t)(y & 1);
+      s.contrib[v] = rk == 0 ? g.len[v] : s.sufin[y];
+      if (rk == 0) {
+        mark_head(s, m, L);
+        atomicAdd(&c->n_heads, 1u);
       }
+    } else {
+      s.cid[v] = -1;
+      s.rank[v] = -1;
+      s.orient[v] = 255;
     }
-    unsigned eslot = block_reserve(&c->n_emit, emit ? 1u : 0u);
-    if (emit) s.emit[eslot] = v;
+    if (rk == 0) atomicAdd(&c->n_cycles, 1u);
   }
 }
 
@@ -488,9 +542,20 @@ __global__ void k_sum_len(DevGraph g, unsigned long long* out) {
   if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
 }
 
+// Cooperative launch (all blocks co-resident, as the grid barrier needs);
+// expressed as a launch attribute so that stream capture can record it.
 cudaError_t coop(const void* fn, int blocks, void** args, const LaunchEnv& env) {
-  ++*env.launches;
-  return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(kBlock), args, 0, env.stream);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(kBlock);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = env.stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
 }  // namespace
@@ -500,58 +565,63 @@ int coop_blocks_for_grid_kernels(int num_sms) {
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_jump, kBlock, 0);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cycles, kBlock, 0);
   int per = a < b ? a : b;
-  if (per > 4) per = 4;
+  if (per > 2) per = 2;
   if (per < 1) per = 1;
   return per * num_sms;
 }
 
 cudaError_t launch_validate(const DevGraph& g, DevError* derr, const LaunchEnv& env) {
   k_validate_reads<<<grid_for(g.n, env), kBlock, 0, env.stream>>>(g, derr);
-  ++*env.launches;
+  mark(env, "k_validate_reads");
   k_validate_entries<<<grid_for(g.n, env), kBlock, 0, env.stream>>>(g, derr);
-  ++*env.launches;
+  mark(env, "k_validate_entries");
   return cudaGetLastError();
 }
 
 cudaError_t launch_sum_len(const DevGraph& g, unsigned long long* out, const LaunchEnv& env) {
   k_sum_len<<<grid_for(g.n, env), kBlock, 0, env.stream>>>(g, out);
-  ++*env.launches;
+  mark(env, "k_sum_len");
   return cudaGetLastError();
 }
 
 cudaError_t launch_mask(const DevGraph& g, const Scratch& s, const LaunchEnv& env) {
   cudaMemsetAsync(&s.ctr->n_branch, 0, sizeof(Counters) - offsetof(Counters, n_branch), env.stream);
-  k_mask<<<grid_for(g.n, env), kBlock, 0, env.stream>>>(g, s);
-  ++*env.launches;
+  k_mask<<<grid_for((g.n + kMaskItems - 1) / kMaskItems, env), kBlock, 0, env.stream>>>(g, s);
+  mark(env, "k_mask");
   return cudaGetLastError();
 }
 
 cudaError_t launch_chains(const DevGraph& g, const Scratch& s, const Tuning& t, const LaunchEnv& env) {
-  // restart the chain-stage counters; the walk list starts after the lone
-  // reads the mask stage already placed in it
+  // restart the chain-stage counters; the head bitmap restarts from the mask
+  // stage's words (lone reads) and gains the chain heads below
   cudaMemsetAsync(&s.ctr->n_chain, 0, offsetof(Counters, n_contigs) - offsetof(Counters, n_chain), env.stream);
-  cudaMemcpyAsync(&s.ctr->n_emit, &s.ctr->n_lone, sizeof(unsigned), cudaMemcpyDeviceToDevice, env.stream);
-  k_succ<<<grid_for(g.n, env), kBlock, 0, env.stream>>>(g, s);
-  ++*env.launches;
+  cudaMemcpyAsync(s.hb, s.hb_mask, (size_t)((g.n + 31) / 32) * sizeof(unsigned), cudaMemcpyDeviceToDevice,
+                  env.stream);
+  k_succ<<<grid_for(g.n, env), kBlock, 0, env.stream>>>(g, s, t.ruler_log2);
+  mark(env, "k_succ");
   k_walk<<<grid_for(2 * g.n, env), kBlock, 0, env.stream>>>(s, t.ruler_log2, 2 * g.n + 1);
-  ++*env.launches;
+  mark(env, "k_walk");
+  k_listwalk<<<grid_for(2 * g.n, env), kBlock, 0, env.stream>>>(s);
+  mark(env, "k_listwalk");
   Scratch sc = s;
   void* args[] = {&sc};
   cudaError_t e = coop((const void*)k_jump, env.coop_blocks, args, env);
   if (e != cudaSuccess) return e;
+  mark(env, "k_jump");
   DevGraph gg = g;
   k_final<<<grid_for(g.n, env), kBlock, 0, env.stream>>>(gg, s);
-  ++*env.launches;
+  mark(env, "k_final");
   void* args2[] = {&gg, &sc};
   e = coop((const void*)k_cycles, env.coop_blocks, args2, env);
   if (e != cudaSuccess) return e;
+  mark(env, "k_cycles");
   return cudaGetLastError();
 }
 
 cudaError_t launch_export_reads(const DevGraph& g, const Scratch& s, int32_t* cid, int32_t* rank, uint8_t* orient,
                                 const LaunchEnv& env) {
   k_export_reads<<<grid_for(g.n, env), kBlock, 0, env.stream>>>(g, s, cid, rank, orient);
-  ++*env.launches;
+  mark(env, "k_export_reads");
   return cudaGetLastError();
 }
 

@@ -31,21 +31,25 @@ struct Counters {
   // mask stage
   unsigned long long n_branch;
   unsigned int n_cand;         // unmasked reads with at least one overlap
-  unsigned int n_lone;         // reads with no overlap spelled as one-read contigs
+  unsigned int n_lone;         // reads without overlaps spelled as one-read contigs (min_chain <= 1)
   // chain stage
   unsigned int n_chain;        // unmasked reads with at least one surviving overlap
+  unsigned int n_lone2;        // reads whose overlaps all lead to branch reads, spelled alone (min_chain <= 1)
   unsigned int n_rulers;       // sublist starts of the list ranking
+  unsigned int n_hlist;        // sublists that start a list
   unsigned int n_cycle_reads;  // reads on closed chains
-  unsigned int n_emit;         // reads spelled into some contig (= walk positions)
   unsigned int n_cycles;
-  unsigned int n_heads;        // contigs found by the chain stage (lone reads of the mask stage excluded)
+  unsigned int n_heads;        // contigs found by the chain stage
+  unsigned int need_jump;      // a list had more sublists than the list walk follows
   unsigned int final_buf;      // which pointer-jumping buffer holds the result
   unsigned int bar_count;      // grid barrier arrival counter
   unsigned int bar_gen;        // grid barrier generation
   unsigned int round_flag[64]; // "some pointer still moves" per jumping round
   // offsets stage
   unsigned int n_contigs;
+  unsigned int n_walk;         // walk positions = reads spelled
   unsigned int n_tiles;        // emission tiles
+  unsigned int pad;
   long long total_bases;
 };
 
@@ -62,24 +66,30 @@ struct DevGraph {
   const int64_t* off;
   const uint8_t* packed;
   int64_t packed_bytes;
+  int64_t packed_readable;     // bytes of `packed` that may be read (>= packed_bytes: padding of owned copies)
 };
 
-// Scratch owned by a loaded graph. Sizes in elements.
+// Scratch owned by a loaded graph. Sizes in elements (n reads).
 struct Scratch {
   uint8_t* branch;      // n
   int32_t* cand;        // n: reads to build successors for
   int32_t* chain;       // n: reads to rank
-  int32_t* emit;        // n: reads spelled into a contig
+  int32_t* lone;        // n: reads without overlaps spelled alone
+  int32_t* lone2;       // n: reads cut off by branch reads spelled alone
+  unsigned* hb_mask;    // n/32+1: heads bitmap words of the mask stage
+  unsigned* hb;         // n/32+1: bit m set when read m is the smallest read of a contig
   int2* succ;           // n: (successor of (v,fwd), successor of (v,rc)) as oriented ids 2w+o, or -1
   int32_t* sufin;       // 2n: suffix of the overlap entering oriented read x
   int32_t* rid;         // 2n: sublist of oriented read x (-1: not reached)
   int32_t* roff;        // 2n: position of x inside its sublist
   // sublists (capacity 2n)
+  int32_t* rlist;       // first oriented read of each sublist
+  int32_t* hlist;       // sublists that start a list
   int32_t* r_next_node; // first oriented read of the next sublist, -1 at the list end
   int32_t* r_len;
   int32_t* r_min;       // smallest read id inside the sublist
   int32_t* r_last;      // last oriented read of the sublist
-  int32_t* pj_next[2];  // pointer jumping over sublists, double buffered
+  int32_t* pj_next[2];  // per sublist: -1 resolved, -2 unresolved; pointer jumping double buffers
   int32_t* pj_acc[2];
   int32_t* pj_min[2];
   int32_t* pj_tail[2];
@@ -88,22 +98,24 @@ struct Scratch {
   int32_t* rank;        // walk position
   uint8_t* orient;
   int32_t* contrib;     // bases this read adds to its contig
-  int32_t* headq;       // reads of the chain at its smallest read, else 0
-  unsigned long long* rb;   // n+1: exclusive prefix of (1<<32 | headq) over read ids
+  int32_t* headq;       // at a contig's smallest read: its number of reads
   // closed chains
   int32_t* cyc;         // n: reads on closed chains
   int32_t* c_ptr[2];    // 2n
   int32_t* c_val[2];    // 2n
   int32_t* c_head;      // 2n
-  // walk order
-  unsigned long long* wsrc; // n: first stored base of the piece | reverse flag << 63
+  // contig order and walk order
+  unsigned* wp;         // n/32+1: heads before each bitmap word
+  int32_t* qd;          // n: reads per contig, in contig order
+  unsigned long long* cbase; // n+1: first walk position of each contig
+  unsigned long long* wsrc;  // n: first stored base of the piece | reverse flag << 63
   int32_t* wlen;        // n: piece length
   int64_t* out_off;     // n+1
   int32_t* cstart;      // n: contig -> first walk position
   int64_t* contig_off;  // n+1
   int32_t* tile_seg;    // tiles_cap+1: walk position holding the first byte of each emission tile
   int64_t tiles_cap;
-  unsigned long long* scan_state;  // scan tile descriptors (+1 ticket word)
+  unsigned long long* scan_state[3];  // look-back tile descriptors (+1 ticket word) of the three scans
   int64_t scan_tiles_cap;
   Counters* ctr;
   DevError* derr;
@@ -117,12 +129,34 @@ struct Tuning {
   int grid_blocks_per_sm = 8;
 };
 
+// CUDA events recorded after each kernel when timing is on.
+struct KernelMarks {
+  static constexpr int kMax = 64;
+  bool on = false;
+  int n = 0;
+  cudaEvent_t ev[kMax + 1] = {};
+  const char* name[kMax + 1] = {};
+};
+
 struct LaunchEnv {
   cudaStream_t stream;
   int num_sms;
   int coop_blocks;         // co-resident blocks for the grid-synchronised kernels
   unsigned long long* launches;  // host counter of kernel launches
+  KernelMarks* marks;
 };
+
+// Counts the kernel just launched and, with timing on, records an event after it.
+inline void mark(const LaunchEnv& env, const char* name) {
+  ++*env.launches;
+  KernelMarks* m = env.marks;
+  if (m && m->on && m->n < KernelMarks::kMax) {
+    // external: inside a stream capture this becomes an event-record node
+    cudaEventRecordWithFlags(m->ev[m->n + 1], env.stream, cudaEventRecordExternal);
+    m->name[m->n + 1] = name;
+    ++m->n;
+  }
+}
 
 // ---- launchers (each returns cudaGetLastError()) ----
 cudaError_t launch_validate(const DevGraph& g, DevError* derr, const LaunchEnv& env);
@@ -207,6 +241,40 @@ __device__ __forceinline__ unsigned block_reserve(unsigned* counter, unsigned co
   unsigned base = s_w[kBlock / 32] + s_w[warp] + inc - count;
   __syncthreads();
   return base;
+}
+
+// Reserves slots in up to four lists with one block-wide scan: 16-bit field f
+// of `counts` is this thread's count for *counters[f] (at most 255 per
+// thread). base[f] receives the thread's first slot in list f. Every thread
+// of the block must call it (block-uniform control flow).
+__device__ __forceinline__ void block_reserve4(unsigned* const counters[4], unsigned long long counts,
+                                               unsigned base[4]) {
+  __shared__ unsigned long long s_w[kBlock / 32];
+  __shared__ unsigned s_g[4];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long inc = counts;
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned long long t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) s_w[warp] = inc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long tot = 0;
+    for (int w = 0; w < kBlock / 32; ++w) {
+      unsigned long long c = s_w[w];
+      s_w[w] = tot;
+      tot += c;
+    }
+    for (int f = 0; f < 4; ++f) {
+      unsigned tf = (unsigned)((tot >> (16 * f)) & 0xFFFFu);
+      s_g[f] = tf ? atomicAdd(counters[f], tf) : 0u;
+    }
+  }
+  __syncthreads();
+  const unsigned long long ex = s_w[warp] + inc - counts;
+  for (int f = 0; f < 4; ++f) base[f] = s_g[f] + (unsigned)((ex >> (16 * f)) & 0xFFFFu);
+  __syncthreads();
 }
 
 }  // namespace cg

@@ -2,19 +2,21 @@
 // the contig-size estimate, the redistribution by contig and the offsets of
 // the concatenation (Alg. 2, Sec. 4.2-4.4).
 //
-//   1. scan over read ids of (1<<32 | q) at each chain's smallest read: the
-//      contig index (high word) and the chain's first walk position (low word)
-//      in contig order (contigs are listed by smallest read id);
-//   2. scatter every spelled read to walk position first(chain) + rank: the
+//   1. scan over the words of the heads bitmap (bit m set when read m is the
+//      smallest read of a contig) of their popcounts: the contig index of
+//      every head, listing contigs by smallest read id; each word's store
+//      step lays the heads' read counts out in contig order;
+//   2. scan of those read counts: every contig's first walk position;
+//   3. scatter every spelled read to walk position first(contig) + rank: the
 //      on-device compaction that replaces the induced-subgraph exchange;
-//   3. scan over walk positions of the bases each read adds: the output
+//   4. scan over walk positions of the bases each read adds: the output
 //      offset of every piece, the contig offsets and the map from output
 //      tiles to the piece holding each tile's first byte.
 //
-// Both scans are single-pass decoupled look-back scans: tiles take tickets
-// in order, publish their aggregate, then look back over predecessors with
-// one warp (32 descriptors at a time) until an inclusive prefix is found.
-// The wait on a predecessor is bounded; on timeout the kernel records
+// The scans are single-pass decoupled look-back scans: tiles take tickets in
+// order, publish their aggregate, then look back over predecessors with one
+// warp (32 descriptors at a time) until an inclusive prefix is found. The
+// wait on a predecessor is bounded; on timeout the kernel records
 // DERR_TIMEOUT and stops.
 #include <cuda_runtime.h>
 
@@ -126,27 +128,46 @@ __global__ void __launch_bounds__(kBlock) k_scan(Load ld, Store st, long long co
   }
 }
 
-// ---- scan 1: chains in contig order ----
-struct HeadsLoad {
-  const int32_t* headq;
-  __device__ unsigned long long operator()(long long i) const {
-    int32_t q = headq[i];
-    return q > 0 ? ((1ull << 32) | (unsigned)q) : 0ull;
-  }
+// ---- scan 1: contig index of every head (bitmap popcounts) ----
+struct HeadWordLoad {
+  const unsigned* hb;
+  __device__ unsigned long long operator()(long long w) const { return (unsigned long long)__popc(hb[w]); }
 };
-struct HeadsStore {
-  unsigned long long* rb;
+struct HeadWordStore {
+  const unsigned* hb;
+  unsigned* wp;
+  const int32_t* headq;
+  int32_t* qd;
   Counters* c;
-  DevError* derr;
-  __device__ void item(long long i, unsigned long long e) const { rb[i] = e; }
+  __device__ void item(long long w, unsigned long long e) const {
+    wp[w] = (unsigned)e;
+    unsigned bits = hb[w];
+    unsigned k = (unsigned)e;
+    while (bits) {
+      int b = __ffs(bits) - 1;
+      bits &= bits - 1;
+      qd[k++] = headq[32 * w + b];     // contigs in order of their smallest read
+    }
+  }
+  __device__ void last(long long, unsigned long long total) const { c->n_contigs = (unsigned)total; }
+};
+
+// ---- scan 2: first walk position of every contig ----
+struct ContigLoad {
+  const int32_t* qd;
+  __device__ unsigned long long operator()(long long i) const { return (unsigned long long)(unsigned)qd[i]; }
+};
+struct ContigStore {
+  unsigned long long* cbase;
+  Counters* c;
+  __device__ void item(long long i, unsigned long long e) const { cbase[i] = e; }
   __device__ void last(long long count, unsigned long long total) const {
-    rb[count] = total;
-    c->n_contigs = (unsigned)(total >> 32);
-    if ((unsigned)(total & 0xffffffffull) != c->n_emit) set_error(derr, DERR_KERNEL, K_SCAN_HEADS, count);
+    cbase[count] = total;
+    c->n_walk = (unsigned)total;
   }
 };
 
-// ---- scan 2: piece offsets over walk positions ----
+// ---- scan 4: piece offsets over walk positions ----
 struct PieceLoad {
   const int32_t* wlen;
   __device__ unsigned long long operator()(long long j) const { return (unsigned long long)(unsigned)wlen[j]; }
@@ -178,26 +199,31 @@ struct PieceStore {
   }
 };
 
-// Every spelled read goes to walk position first(chain) + rank, with the
+// Every spelled read goes to walk position first(contig) + rank, with the
 // stored-base address of its piece: forward reads add stored bases
 // [len-contrib, len), reverse-complement reads the complement of stored
-// bases contrib-1 down to 0.
+// bases contrib-1 down to 0. The spelled reads are the lone reads of the
+// mask stage, those cut off by branch reads, and the chain reads of chains
+// long enough to be contigs.
 __global__ void k_scatter(DevGraph g, Scratch s) {
   Counters* c = s.ctr;
-  long long W = *(volatile unsigned*)&c->n_emit;
-  for (long long k = grid_tid(); k < W; k += grid_threads()) {
-    int32_t v = s.emit[k];
-    int32_t ch = s.cid[v];
-    unsigned long long pb = s.rb[ch];
-    long long first = (long long)(pb & 0xffffffffull), cidx = (long long)(pb >> 32);
-    int32_t rk = s.rank[v];
-    long long pos = first + rk;
-    if (ch < 0 || pos >= W) { set_error(s.derr, DERR_KERNEL, K_SCATTER, v); continue; }
-    int o = s.orient[v];
-    int32_t L = g.len[v], cb = s.contrib[v];
-    int64_t base = g.off[v];
-    unsigned long long src = o == 0 ? (unsigned long long)(base + L - cb)
-                                    : ((unsigned long long)(base + cb - 1) | (1ull << 63));
+  const long long L1 = *(volatile unsigned*)&c->n_lone, L2 = *(volatile unsigned*)&c->n_lone2;
+  const long long NC = *(volatile unsigned*)&c->n_chain, W = *(volatile unsigned*)&c->n_walk;
+  const long long total = L1 + L2 + NC;
+  for (long long k = grid_tid(); k < total; k += grid_threads()) {
+    const int32_t v = k < L1 ? s.lone[k] : (k < L1 + L2 ? s.lone2[k - L1] : s.chain[k - L1 - L2]);
+    const int32_t m = s.cid[v];
+    if (m < 0) continue;                 // a chain shorter than min_chain
+    const unsigned word = s.hb[m >> 5];
+    const long long cidx = (long long)s.wp[m >> 5] + __popc(word & ((1u << (m & 31)) - 1u));
+    const int32_t rk = s.rank[v];
+    const long long pos = (long long)s.cbase[cidx] + rk;
+    if (!((word >> (m & 31)) & 1u) || pos >= W) { set_error(s.derr, DERR_KERNEL, K_SCATTER, v); continue; }
+    const int o = s.orient[v];
+    const int32_t L = g.len[v], cb = s.contrib[v];
+    const int64_t base = g.off[v];
+    const unsigned long long src = o == 0 ? (unsigned long long)(base + L - cb)
+                                          : ((unsigned long long)(base + cb - 1) | (1ull << 63));
     s.wsrc[pos] = src;
     s.wlen[pos] = cb;
     if (rk == 0) s.cstart[cidx] = (int32_t)pos;
@@ -225,34 +251,42 @@ __global__ void k_export_contig_off(Scratch s, int64_t* out, long long cap) {
 
 cudaError_t launch_offsets(const DevGraph& g, const Scratch& s, const Tuning& t, const LaunchEnv& env) {
   cudaMemsetAsync(&s.ctr->n_contigs, 0, sizeof(Counters) - offsetof(Counters, n_contigs), env.stream);
-  long long tiles_n = (g.n + kTileItems - 1) / kTileItems;
-  if (tiles_n > s.scan_tiles_cap) return cudaErrorInvalidValue;
-  // scan 1 (count = n, host known)
-  cudaMemsetAsync(s.scan_state, 0, (size_t)(s.scan_tiles_cap + 1) * sizeof(unsigned long long), env.stream);
-  HeadsLoad hl{s.headq};
-  HeadsStore hs{s.rb, s.ctr, s.derr};
-  if (g.n > 0)
-    k_scan<<<(unsigned)tiles_n, kBlock, 0, env.stream>>>(hl, hs, (long long)g.n, nullptr, s.scan_state,
-                                                        s.scan_tiles_cap, s.derr, K_SCAN_HEADS);
-  ++*env.launches;
+  const long long words = (g.n + 31) / 32;
+  const long long tiles_w = (words + kTileItems - 1) / kTileItems;
+  const long long tiles_n = (g.n + kTileItems - 1) / kTileItems;
+  if (tiles_n > s.scan_tiles_cap || tiles_w > s.scan_tiles_cap) return cudaErrorInvalidValue;
+  // the three scans' tile descriptors and tickets are contiguous: one memset
+  cudaMemsetAsync(s.scan_state[0], 0, (size_t)3 * (s.scan_tiles_cap + 1) * sizeof(unsigned long long), env.stream);
+  if (g.n == 0) {
+    k_contig_off<<<1, kBlock, 0, env.stream>>>(s);
+    mark(env, "k_contig_off");
+    return cudaGetLastError();
+  }
+  HeadWordLoad hl{s.hb};
+  HeadWordStore hs{s.hb, s.wp, s.headq, s.qd, s.ctr};
+  k_scan<<<(unsigned)tiles_w, kBlock, 0, env.stream>>>(hl, hs, words, nullptr, s.scan_state[0], s.scan_tiles_cap,
+                                                       s.derr, K_SCAN_HEADS);
+  mark(env, "k_scan_heads");
+  ContigLoad cl{s.qd};
+  ContigStore cs{s.cbase, s.ctr};
+  k_scan<<<(unsigned)tiles_n, kBlock, 0, env.stream>>>(cl, cs, 0, &s.ctr->n_contigs, s.scan_state[1],
+                                                       s.scan_tiles_cap, s.derr, K_SCAN_HEADS);
+  mark(env, "k_scan_contigs");
   k_scatter<<<grid_for(g.n, env), kBlock, 0, env.stream>>>(g, s);
-  ++*env.launches;
-  // scan 2 (count = walk positions, known on the device only; bounded by n)
-  cudaMemsetAsync(s.scan_state, 0, (size_t)(s.scan_tiles_cap + 1) * sizeof(unsigned long long), env.stream);
+  mark(env, "k_scatter");
   PieceLoad pl{s.wlen};
   PieceStore ps{s.wlen, s.out_off, s.tile_seg, s.tiles_cap, t.tile_bytes, s.ctr, s.derr};
-  if (g.n > 0)
-    k_scan<<<(unsigned)tiles_n, kBlock, 0, env.stream>>>(pl, ps, 0, &s.ctr->n_emit, s.scan_state, s.scan_tiles_cap,
-                                                        s.derr, K_SCAN_OFFSETS);
-  ++*env.launches;
+  k_scan<<<(unsigned)tiles_n, kBlock, 0, env.stream>>>(pl, ps, 0, &s.ctr->n_walk, s.scan_state[2], s.scan_tiles_cap,
+                                                       s.derr, K_SCAN_OFFSETS);
+  mark(env, "k_scan_pieces");
   k_contig_off<<<grid_for(g.n + 1, env), kBlock, 0, env.stream>>>(s);
-  ++*env.launches;
+  mark(env, "k_contig_off");
   return cudaGetLastError();
 }
 
 cudaError_t launch_export_contig_off(const Scratch& s, int64_t* out, int64_t cap, const LaunchEnv& env) {
   k_export_contig_off<<<env.num_sms, kBlock, 0, env.stream>>>(s, out, cap);
-  ++*env.launches;
+  mark(env, "k_export_contig_off");
   return cudaGetLastError();
 }
 

@@ -184,6 +184,33 @@ def test_tuning_does_not_change_output(ruler_log2, tile_bytes, bps):
         c.close()
 
 
+def test_graphs_off_and_replay_with_new_buffers():
+    """Stages launched one by one give the same bytes as replayed CUDA graphs,
+    also when the output buffers change between replays."""
+    import torch
+    G = structured(31, [20_000, 5, 9] + [2] * 300 + [7] * 50, [False, True, True] + [False] * 350, lone=100)
+    orc = oracle.run(G, min_chain_reads=1)
+    for graphs in (False, True):
+        c = cg.cg_create(0)
+        try:
+            cg.cg_set_graphs(c, graphs)
+            assert_parity(run_gpu(c, G, 1), orc)
+            g = cg.cg_load_graph(c, G, min_chain_reads=1)
+            n_contigs, total = cg.cg_emit_contigs(g)
+            for rep in range(3):
+                off = torch.empty(n_contigs + 1 + rep, dtype=torch.int64, device="cuda")
+                bases = torch.empty(total + 16 * rep + 16, dtype=torch.uint8, device="cuda")
+                cg.cg_mask_branches(g, want_count=False)
+                cg.cg_chains(g, want_counts=False)
+                cg.cg_emit_contigs(g, off, bases, want_counts=False)
+                cg.cg_sync(c)
+                assert np.array_equal(off.cpu().numpy()[:n_contigs + 1], orc.contig_off)
+                assert np.array_equal(bases.cpu().numpy()[:total], orc.bases)
+            g.close()
+        finally:
+            c.close()
+
+
 def test_repeat_runs_are_identical(ctx):
     G = gen.generate(gen.batched_graph(3), threads=8)
     g = cg.cg_load_graph(ctx, G)
