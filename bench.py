@@ -31,6 +31,10 @@ sys.path.insert(0, ROOT)
 METRIC = "contig Gbases/s & ms per graph (plain vs batched) vs HBM roofline; p50/p99 latency"
 UNIT = "Gbases/s"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+# DRAM bytes (read + write) per contig base of k_emit from one ncu capture
+# (--set full, the 3.1 Gb recipe on a 450 Mb genome: 551.5 MB for 481,446,585
+# bases), valid only for the emission source it was taken on.
+EMIT_TRAFFIC = {"bytes_per_base": 551.5e6 / 481446585, "source_sha256_16": "c863d26b78abdb32"}
 
 
 def parse():
@@ -280,6 +284,10 @@ def run_ours(args, rank, world, local_rank):
         cpu = cpu_baseline(args, cfg)
 
     B = bmin_bytes(G, W, total, n_contigs)
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2207_04350_gb300", "csrc", "cg_emit.cu"), "rb") as f:
+        same_kernel = hashlib.sha256(f.read()).hexdigest()[:16] == EMIT_TRAFFIC["source_sha256_16"]
+    traffic = EMIT_TRAFFIC["bytes_per_base"] * total if same_kernel else None
     emit_bytes = total + (total + 3) // 4
     ach = emit_bytes / (ms_emit * 1e-3) / 1e9
     line = {
@@ -303,7 +311,9 @@ def run_ours(args, rank, world, local_rank):
             "generate_s": round(t_gen, 1), "wall_s_timed": t1 - t0,
         },
         "roofline": {"kernel": "k_emit (contig spelling)", "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"],
-                     "unit": "GB/s", "frac": ach / pk["hbm_gbs"], "traffic": None,
+                     "unit": "GB/s", "frac": ach / pk["hbm_gbs"], "traffic": traffic,
+                     "traffic_note": "ncu dram bytes of a scaled capture (450 Mb recipe) x contig bases; null when "
+                                     "the kernel changed since",
                      "algorithmic_bytes_per_launch": emit_bytes, "bytes_per_unit": 1.25,
                      "units_per_launch": total, "ms_per_launch": ms_emit, "peak_kind": pk_kind + " (hbm_gbs, copy)"},
         "cpu_baseline": cpu,
