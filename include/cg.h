@@ -110,6 +110,21 @@ CG_API cg_status cg_destroy(cg_ctx* ctx);
 CG_API cg_status cg_load_graph(cg_ctx* ctx, const cg_graph_desc* desc, uint32_t flags, cg_graph** out);
 CG_API cg_status cg_free_graph(cg_graph* g);
 
+/* The batched form: k string graphs loaded as one disjoint union (reads,
+ * entries and packed bases of graph j follow those of graphs 0..j-1), so
+ * that each stage below runs as one launch over every graph. All descs must
+ * share mem, row_ptr_bytes and min_chain_reads; inputs are always copied
+ * (CG_BORROW_DEVICE is refused). Chains never cross graphs, so the union's
+ * contigs are those of graph 0, then graph 1, ... in each graph's own order,
+ * and read r of graph j is read R_j + r of the union (R_j = reads of graphs
+ * before j). Waits for the GPU. */
+CG_API cg_status cg_load_batch(cg_ctx* ctx, const cg_graph_desc* descs, int k, uint32_t flags, cg_graph** out);
+/* For a batch: first_contig[j] / first_base[j] = index of graph j's first
+ * contig / its first base in the union's contig_off / bases; entry k holds
+ * the totals. Each optional (k+1 entries in `mem`). Runs the earlier stages
+ * if needed; waits for the GPU with host outputs. */
+CG_API cg_status cg_batch_ranges(cg_graph* g, int64_t* first_contig, int64_t* first_base, int mem);
+
 /* BranchRemoval (Alg. 2; Sec. 4.2). is_branch: NULL or n bytes (1 = branch),
  * in `mem`. n_branch: NULL or receives the count (waits for the GPU). */
 CG_API cg_status cg_mask_branches(cg_graph* g, uint8_t* is_branch, int mem, int64_t* n_branch);

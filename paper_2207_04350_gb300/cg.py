@@ -48,6 +48,9 @@ API = {
     "cg_destroy": [ctypes.c_void_p],
     "cg_load_graph": [ctypes.c_void_p, ctypes.POINTER(GraphDesc), ctypes.c_uint32, ctypes.POINTER(ctypes.c_void_p)],
     "cg_free_graph": [ctypes.c_void_p],
+    "cg_load_batch": [ctypes.c_void_p, ctypes.POINTER(GraphDesc), ctypes.c_int, ctypes.c_uint32,
+                      ctypes.POINTER(ctypes.c_void_p)],
+    "cg_batch_ranges": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int],
     "cg_mask_branches": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)],
     "cg_chains": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                   ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
@@ -195,6 +198,42 @@ def cg_load_graph(ctx: Context, graph, flags: int = 0, min_chain_reads: int = 2)
     out = ctypes.c_void_p()
     _check(ctx.ptr, lib().cg_load_graph(ctx.ptr, ctypes.byref(d), int(flags), ctypes.byref(out)))
     return Graph(ctx, out, arrs if flags & BORROW_DEVICE else None, d.n_reads)
+
+
+def _desc(graph, min_chain_reads):
+    arrs = [graph.row_ptr, graph.col, graph.code, graph.suf, graph.len, graph.off, graph.packed]
+    mem = _mem_of_all(arrs)
+    rp = graph.row_ptr
+    d = GraphDesc()
+    d.n_reads = len(graph.len)
+    d.n_entries = len(graph.col)
+    d.row_ptr, d.row_ptr_bytes, d.mem = _ptr(rp), (rp.element_size() if _is_torch(rp) else rp.dtype.itemsize), mem
+    d.col, d.code, d.suf = _ptr(graph.col), _ptr(graph.code), _ptr(graph.suf)
+    d.len, d.off, d.packed = _ptr(graph.len), _ptr(graph.off), _ptr(graph.packed)
+    d.packed_bytes = _nbytes(graph.packed)
+    d.min_chain_reads = int(min_chain_reads)
+    return d
+
+
+def cg_load_batch(ctx: Context, graphs, flags: int = 0, min_chain_reads: int = 2) -> Graph:
+    """cg_load_batch: the graphs as one union graph (see cg_batch_ranges)."""
+    k = len(graphs)
+    descs = (GraphDesc * k)(*[_desc(gr, min_chain_reads) for gr in graphs])
+    out = ctypes.c_void_p()
+    _check(ctx.ptr, lib().cg_load_batch(ctx.ptr, descs, k, int(flags), ctypes.byref(out)))
+    g = Graph(ctx, out, None, int(sum(len(gr.len) for gr in graphs)))
+    g.batch_k = k
+    return g
+
+
+def cg_batch_ranges(g: Graph, first_contig=None, first_base=None):
+    """Per graph of a batch: first contig and first base in the union outputs (k+1 entries)."""
+    if first_contig is None and first_base is None:
+        first_contig = np.empty(g.batch_k + 1, np.int64)
+        first_base = np.empty(g.batch_k + 1, np.int64)
+    mem = _mem_of_all([first_contig, first_base])
+    _check(g.ctx.ptr, lib().cg_batch_ranges(g.ptr, _ptr(first_contig), _ptr(first_base), mem))
+    return first_contig, first_base
 
 
 def cg_free_graph(g: Graph):

@@ -57,6 +57,8 @@ struct cg_graph {
   void* stage_reads = nullptr;
   unsigned long long* d_sum = nullptr;
   StageExec execs[5];                  // mask, chains, offsets, emission, contig_off export
+  int batch_k = 0;                     // graphs of a batch (0: a single graph)
+  int64_t* batch_R = nullptr;          // device: first read of each graph, batch_k + 1 entries
 };
 
 namespace {
@@ -275,6 +277,81 @@ cg_status run_offsets(cg_graph* g) {
 }
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
+
+// Scratch, input checks and output bounds of a graph whose inputs are in place.
+cg_status finish_load(cg_graph* g, uint32_t flags) {
+  cg_ctx* c = g->ctx;
+  cg::DevGraph& G = g->g;
+  const int64_t n = G.n;
+  cg_status st = CG_OK;
+  // scratch
+  cg::Scratch& S = g->s;
+  const size_t N = (size_t)(n > 0 ? n : 1), N2 = 2 * N, NW = N / 32 + 2;
+  S.branch = galloc<uint8_t>(g, N, &st);
+  S.cand = galloc<int32_t>(g, N, &st);
+  S.chain = galloc<int32_t>(g, N, &st);
+  S.lone = galloc<int32_t>(g, N, &st);
+  S.lone2 = galloc<int32_t>(g, N, &st);
+  S.hb_mask = galloc<unsigned>(g, NW, &st);
+  S.hb = galloc<unsigned>(g, NW, &st);
+  S.wp = galloc<unsigned>(g, NW, &st);
+  S.succ = galloc<int2>(g, N, &st);
+  S.sufin = galloc<int32_t>(g, N2, &st);
+  S.rid = galloc<int32_t>(g, N2, &st);
+  S.roff = galloc<int32_t>(g, N2, &st);
+  S.rlist = galloc<int32_t>(g, N2, &st);
+  S.hlist = galloc<int32_t>(g, N2, &st);
+  S.r_next_node = galloc<int32_t>(g, N2, &st);
+  S.r_len = galloc<int32_t>(g, N2, &st);
+  S.r_min = galloc<int32_t>(g, N2, &st);
+  S.r_last = galloc<int32_t>(g, N2, &st);
+  for (int b = 0; b < 2; ++b) {
+    S.pj_next[b] = galloc<int32_t>(g, N2, &st);
+    S.pj_acc[b] = galloc<int32_t>(g, N2, &st);
+    S.pj_min[b] = galloc<int32_t>(g, N2, &st);
+    S.pj_tail[b] = galloc<int32_t>(g, N2, &st);
+    S.c_ptr[b] = galloc<int32_t>(g, N2, &st);
+    S.c_val[b] = galloc<int32_t>(g, N2, &st);
+  }
+  S.c_head = galloc<int32_t>(g, N2, &st);
+  S.cid = galloc<int32_t>(g, N, &st);
+  S.rank = galloc<int32_t>(g, N, &st);
+  S.orient = galloc<uint8_t>(g, N, &st);
+  S.contrib = galloc<int32_t>(g, N, &st);
+  S.headq = galloc<int32_t>(g, N, &st);
+  S.cyc = galloc<int32_t>(g, N, &st);
+  S.qd = galloc<int32_t>(g, N, &st);
+  S.cbase = galloc<unsigned long long>(g, N + 1, &st);
+  S.wsrc = galloc<unsigned long long>(g, N, &st);
+  S.wlen = galloc<int32_t>(g, N, &st);
+  S.out_off = galloc<int64_t>(g, N + 1, &st);
+  S.cstart = galloc<int32_t>(g, N, &st);
+  S.contig_off = galloc<int64_t>(g, N + 1, &st);
+  S.scan_tiles_cap = (int64_t)(N + 2047) / 2048 + 1;
+  S.scan_state[0] = galloc<unsigned long long>(g, 3 * ((size_t)S.scan_tiles_cap + 1), &st);
+  if (S.scan_state[0]) {
+    S.scan_state[1] = S.scan_state[0] + (S.scan_tiles_cap + 1);
+    S.scan_state[2] = S.scan_state[1] + (S.scan_tiles_cap + 1);
+  }
+  S.ctr = galloc<cg::Counters>(g, 1, &st);
+  g->d_sum = galloc<unsigned long long>(g, 1, &st);
+  S.derr = c->derr;
+  if (st != CG_OK) return st;
+  CK(cudaMemsetAsync(S.ctr, 0, sizeof(cg::Counters), c->stream), "clear counters");
+  CK(cudaMemsetAsync(g->d_sum, 0, 8, c->stream), "clear sum");
+
+  if (!(flags & CG_NO_VALIDATE) && n > 0) CK(cg::launch_validate(G, c->derr, c->env), "validation kernels");
+  CK(cg::launch_sum_len(G, g->d_sum, c->env), "length sum");
+  CK(cudaMemcpyAsync(c->h_u64, g->d_sum, 8, cudaMemcpyDeviceToHost, c->stream), "read sum");
+  st = wait_and_read(g);
+  if (st != CG_OK) return st;
+  g->sum_len = (int64_t)*c->h_u64;
+  // the longest possible output is every read spelled whole; tiles of at least 4 KiB
+  S.tiles_cap = g->sum_len / 4096 + 2;
+  S.tile_seg = galloc<int32_t>(g, (size_t)S.tiles_cap + 1, &st);
+  return st;
+}
+
 
 }  // namespace
 
@@ -518,74 +595,128 @@ cg_status cg_load_graph(cg_ctx* c, const cg_graph_desc* d, uint32_t flags, cg_gr
     if (st != CG_OK) return bail(st);
   }
 
-  // scratch
-  cg::Scratch& S = g->s;
-  const size_t N = (size_t)(n > 0 ? n : 1), N2 = 2 * N, NW = N / 32 + 2;
-  S.branch = galloc<uint8_t>(g, N, &st);
-  S.cand = galloc<int32_t>(g, N, &st);
-  S.chain = galloc<int32_t>(g, N, &st);
-  S.lone = galloc<int32_t>(g, N, &st);
-  S.lone2 = galloc<int32_t>(g, N, &st);
-  S.hb_mask = galloc<unsigned>(g, NW, &st);
-  S.hb = galloc<unsigned>(g, NW, &st);
-  S.wp = galloc<unsigned>(g, NW, &st);
-  S.succ = galloc<int2>(g, N, &st);
-  S.sufin = galloc<int32_t>(g, N2, &st);
-  S.rid = galloc<int32_t>(g, N2, &st);
-  S.roff = galloc<int32_t>(g, N2, &st);
-  S.rlist = galloc<int32_t>(g, N2, &st);
-  S.hlist = galloc<int32_t>(g, N2, &st);
-  S.r_next_node = galloc<int32_t>(g, N2, &st);
-  S.r_len = galloc<int32_t>(g, N2, &st);
-  S.r_min = galloc<int32_t>(g, N2, &st);
-  S.r_last = galloc<int32_t>(g, N2, &st);
-  for (int b = 0; b < 2; ++b) {
-    S.pj_next[b] = galloc<int32_t>(g, N2, &st);
-    S.pj_acc[b] = galloc<int32_t>(g, N2, &st);
-    S.pj_min[b] = galloc<int32_t>(g, N2, &st);
-    S.pj_tail[b] = galloc<int32_t>(g, N2, &st);
-    S.c_ptr[b] = galloc<int32_t>(g, N2, &st);
-    S.c_val[b] = galloc<int32_t>(g, N2, &st);
-  }
-  S.c_head = galloc<int32_t>(g, N2, &st);
-  S.cid = galloc<int32_t>(g, N, &st);
-  S.rank = galloc<int32_t>(g, N, &st);
-  S.orient = galloc<uint8_t>(g, N, &st);
-  S.contrib = galloc<int32_t>(g, N, &st);
-  S.headq = galloc<int32_t>(g, N, &st);
-  S.cyc = galloc<int32_t>(g, N, &st);
-  S.qd = galloc<int32_t>(g, N, &st);
-  S.cbase = galloc<unsigned long long>(g, N + 1, &st);
-  S.wsrc = galloc<unsigned long long>(g, N, &st);
-  S.wlen = galloc<int32_t>(g, N, &st);
-  S.out_off = galloc<int64_t>(g, N + 1, &st);
-  S.cstart = galloc<int32_t>(g, N, &st);
-  S.contig_off = galloc<int64_t>(g, N + 1, &st);
-  S.scan_tiles_cap = (int64_t)(N + 2047) / 2048 + 1;
-  S.scan_state[0] = galloc<unsigned long long>(g, 3 * ((size_t)S.scan_tiles_cap + 1), &st);
-  if (S.scan_state[0]) {
-    S.scan_state[1] = S.scan_state[0] + (S.scan_tiles_cap + 1);
-    S.scan_state[2] = S.scan_state[1] + (S.scan_tiles_cap + 1);
-  }
-  S.ctr = galloc<cg::Counters>(g, 1, &st);
-  g->d_sum = galloc<unsigned long long>(g, 1, &st);
-  S.derr = c->derr;
-  if (st != CG_OK) return bail(st);
-  CK(cudaMemsetAsync(S.ctr, 0, sizeof(cg::Counters), c->stream), "clear counters");
-  CK(cudaMemsetAsync(g->d_sum, 0, 8, c->stream), "clear sum");
-
-  if (!(flags & CG_NO_VALIDATE) && n > 0) CK(cg::launch_validate(G, c->derr, c->env), "validation kernels");
-  CK(cg::launch_sum_len(G, g->d_sum, c->env), "length sum");
-  CK(cudaMemcpyAsync(c->h_u64, g->d_sum, 8, cudaMemcpyDeviceToHost, c->stream), "read sum");
-  st = wait_and_read(g);
-  if (st != CG_OK) return bail(st);
-  g->sum_len = (int64_t)*c->h_u64;
-  // the longest possible output is every read spelled whole; tiles of at least 4 KiB
-  S.tiles_cap = g->sum_len / 4096 + 2;
-  S.tile_seg = galloc<int32_t>(g, (size_t)S.tiles_cap + 1, &st);
+  st = finish_load(g, flags);
   if (st != CG_OK) return bail(st);
   *out = g;
   return CG_OK;
+}
+
+cg_status cg_load_batch(cg_ctx* c, const cg_graph_desc* d, int k, uint32_t flags, cg_graph** out) {
+  cg_status st = check_ctx(c);
+  if (st != CG_OK) return st;
+  if (!d || !out || k < 1) return fail(c, CG_EINVAL, "null argument or empty batch");
+  *out = nullptr;
+  if (flags & CG_BORROW_DEVICE) return fail(c, CG_EINVAL, "a batch is always copied into one union graph");
+  const int mem = d[0].mem, rpb = d[0].row_ptr_bytes, mcr = d[0].min_chain_reads;
+  std::vector<int64_t> R(k + 1, 0), E(k + 1, 0), PB(k + 1, 0), SR(k + 1, 0);
+  for (int j = 0; j < k; ++j) {
+    const cg_graph_desc& q = d[j];
+    if (q.mem != mem || q.row_ptr_bytes != rpb || q.min_chain_reads != mcr)
+      return fail(c, CG_EINVAL, "graph %d: mem, row_ptr_bytes and min_chain_reads must match the batch", j);
+    if ((rpb != 4 && rpb != 8) || (mem != CG_MEM_HOST && mem != CG_MEM_DEVICE)) return fail(c, CG_EINVAL, "bad desc");
+    if (q.n_reads < 0 || q.n_entries < 0 || q.packed_bytes < 0 || !q.row_ptr ||
+        (q.n_entries > 0 && (!q.col || !q.code || !q.suf)) || (q.n_reads > 0 && (!q.len || !q.off)) ||
+        (q.packed_bytes > 0 && !q.packed))
+      return fail(c, CG_EINVAL, "graph %d: missing input array", j);
+    R[j + 1] = R[j] + q.n_reads;
+    E[j + 1] = E[j] + q.n_entries;
+    PB[j + 1] = PB[j] + (q.packed_bytes + 15) / 16 * 16;   // each graph's bases start 16-byte aligned
+    SR[j + 1] = SR[j] + q.n_reads + 1;
+  }
+  const int64_t n = R[k], m = E[k];
+  if (n >= (1ll << 30) || m >= (1ll << 31)) return fail(c, CG_EINVAL, "batch too large");
+  cg_graph* g = new (std::nothrow) cg_graph();
+  if (!g) return fail(c, CG_ENOMEM, "host allocation");
+  g->ctx = c;
+  auto bail = [&](cg_status s2) {
+    cg_free_graph(g);
+    return s2;
+  };
+  const cudaMemcpyKind kind = mem == CG_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  cg::DevGraph& G = g->g;
+  G.n = n;
+  G.m = m;
+  G.rp64 = 1;
+  G.min_chain = mcr <= 0 ? 2 : mcr;
+  G.packed_bytes = PB[k];
+  G.packed_readable = PB[k] + 16;
+  int64_t* rp = galloc<int64_t>(g, (size_t)n + 1, &st);
+  int32_t* col = galloc<int32_t>(g, (size_t)(m > 0 ? m : 1), &st);
+  uint8_t* code = galloc<uint8_t>(g, (size_t)(m > 0 ? m : 1), &st);
+  int32_t* suf = galloc<int32_t>(g, (size_t)(m > 0 ? m : 1), &st);
+  int32_t* len = galloc<int32_t>(g, (size_t)(n > 0 ? n : 1), &st);
+  int64_t* off = galloc<int64_t>(g, (size_t)(n > 0 ? n : 1), &st);
+  uint8_t* packed = galloc<uint8_t>(g, (size_t)PB[k] + 16, &st);
+  void* stage_rp = dalloc(c, (size_t)SR[k] * rpb, &st);
+  int64_t* tab = galloc<int64_t>(g, 4 * (size_t)(k + 1), &st);
+  if (st != CG_OK) { dfree(c, stage_rp); return bail(st); }
+  g->batch_k = k;
+  g->batch_R = tab;
+  CK(cudaMemsetAsync(packed, 0, (size_t)PB[k] + 16, c->stream), "clear packed");
+  for (int j = 0; j < k; ++j) {
+    const cg_graph_desc& q = d[j];
+    auto cp = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+      return bytes ? cudaMemcpyAsync(dst, src, bytes, kind, c->stream) : cudaSuccess;
+    };
+    cudaError_t e = cp((char*)stage_rp + (size_t)SR[j] * rpb, q.row_ptr, (size_t)(q.n_reads + 1) * rpb);
+    if (e == cudaSuccess) e = cp(col + E[j], q.col, (size_t)q.n_entries * 4);
+    if (e == cudaSuccess) e = cp(code + E[j], q.code, (size_t)q.n_entries);
+    if (e == cudaSuccess) e = cp(suf + E[j], q.suf, (size_t)q.n_entries * 4);
+    if (e == cudaSuccess) e = cp(len + R[j], q.len, (size_t)q.n_reads * 4);
+    if (e == cudaSuccess) e = cp(off + R[j], q.off, (size_t)q.n_reads * 8);
+    if (e == cudaSuccess) e = cp(packed + PB[j], q.packed, (size_t)q.packed_bytes);
+    if (e != cudaSuccess) { dfree(c, stage_rp); return bail(cuda_fail(c, e, "copy batch input")); }
+  }
+  std::vector<int64_t> host_tab;
+  host_tab.insert(host_tab.end(), R.begin(), R.end());
+  host_tab.insert(host_tab.end(), E.begin(), E.end());
+  host_tab.insert(host_tab.end(), PB.begin(), PB.end());
+  host_tab.insert(host_tab.end(), SR.begin(), SR.end());
+  CK(cudaMemcpyAsync(tab, host_tab.data(), host_tab.size() * 8, cudaMemcpyHostToDevice, c->stream), "copy tables");
+  CK(cg::launch_batch_fixup(k, tab, tab + (k + 1), tab + 2 * (k + 1), tab + 3 * (k + 1), stage_rp, rpb, rp, col, off,
+                            n, m, c->env), "batch fixup");
+  CK(cudaStreamSynchronize(c->stream), "stream synchronize");   // host_tab and stage_rp are done with
+  dfree(c, stage_rp);
+  G.row_ptr = rp;
+  G.col = col;
+  G.code = code;
+  G.suf = suf;
+  G.len = len;
+  G.off = off;
+  G.packed = packed;
+  st = finish_load(g, flags);
+  if (st != CG_OK) return bail(st);
+  *out = g;
+  return CG_OK;
+}
+
+cg_status cg_batch_ranges(cg_graph* g, int64_t* first_contig, int64_t* first_base, int mem) {
+  if (!g) return CG_EINVAL;
+  cg_ctx* c = g->ctx;
+  cg_status st = check_ctx(c);
+  if (st != CG_OK) return st;
+  if (g->batch_k < 1) return fail(c, CG_EINVAL, "not a batch");
+  if (mem != CG_MEM_HOST && mem != CG_MEM_DEVICE) return fail(c, CG_EINVAL, "bad mem");
+  if (g->stage < 3) {
+    st = run_offsets(g);
+    if (st != CG_OK) return st;
+  }
+  const int k = g->batch_k;
+  if (mem == CG_MEM_DEVICE) {
+    CK(cg::launch_batch_ranges(g->s, k, g->batch_R, g->g.n, first_contig, first_base, c->env), "batch ranges");
+    return CG_OK;
+  }
+  int64_t* tmp = (int64_t*)dalloc(c, 16 * (size_t)(k + 1), &st);
+  if (!tmp) return st;
+  cudaError_t e = cg::launch_batch_ranges(g->s, k, g->batch_R, g->g.n, tmp, tmp + (k + 1), c->env);
+  if (e == cudaSuccess && first_contig)
+    e = cudaMemcpyAsync(first_contig, tmp, 8 * (size_t)(k + 1), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess && first_base)
+    e = cudaMemcpyAsync(first_base, tmp + (k + 1), 8 * (size_t)(k + 1), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  dfree(c, tmp);
+  if (e != cudaSuccess) return cuda_fail(c, e, "batch ranges");
+  return wait_and_read(g);
 }
 
 cg_status cg_mask_branches(cg_graph* g, uint8_t* is_branch, int mem, int64_t* n_branch) {

@@ -169,6 +169,11 @@ cudaError_t launch_export_reads(const DevGraph& g, const Scratch& s, int32_t* ci
                                 const LaunchEnv& env);
 cudaError_t launch_export_contig_off(const Scratch& s, int64_t* out, int64_t cap, const LaunchEnv& env);
 cudaError_t launch_sum_len(const DevGraph& g, unsigned long long* out, const LaunchEnv& env);
+cudaError_t launch_batch_fixup(int k, const int64_t* R, const int64_t* E, const int64_t* PB, const int64_t* SR,
+                               const void* stage_rp, int rp_bytes, int64_t* rp, int32_t* col, int64_t* off,
+                               long long N, long long M, const LaunchEnv& env);
+cudaError_t launch_batch_ranges(const Scratch& s, int k, const int64_t* R, long long N, int64_t* first_contig,
+                                int64_t* first_base, const LaunchEnv& env);
 int coop_blocks_for_grid_kernels(int num_sms);
 
 // ---- device helpers ----
