@@ -43,8 +43,13 @@ def parse():
     p.add_argument("--steps", type=int, default=30)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--workload", default="genome-3.1Gb",
-                   help="tiny-1Mb | genome-100Mb | genome-3.1Gb | batched-512")
+                   help="tiny-1Mb | genome-100Mb | genome-3.1Gb | batched-512 | served-2000")
     p.add_argument("--batch-graphs", type=int, default=512, help="graphs of the batched workload")
+    p.add_argument("--serve-requests", type=int, default=2000)
+    p.add_argument("--serve-pool", type=int, default=48, help="pre-generated graphs the requests draw from")
+    p.add_argument("--serve-budget-gb", type=float, default=150.0)
+    p.add_argument("--serve-max-batch", type=int, default=64)
+    p.add_argument("--serve-load", type=float, default=0.8, help="offered load / plain one-at-a-time throughput")
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU budget of the oracle baseline sample")
@@ -311,6 +316,121 @@ def run_batched(args, rank, world, local_rank):
     return line
 
 
+def run_served(args, rank, world, local_rank):
+    """A seeded Poisson stream of graph requests (drawn from a pool of
+    pre-generated graphs, no result caching) at a fixed offered load, served
+    by continuous batching, against the plain path one request at a time."""
+    import threading as th
+
+    import numpy as np
+    import torch
+
+    import gen
+    from paper_2207_04350_gb300 import cg
+
+    torch.cuda.set_device(local_rank)
+    P, R = args.serve_pool, args.serve_requests
+    t_gen = time.time()
+    pool = [generate_pinned(gen.served_graph(j), args.threads) for j in range(P)]
+    t_gen = time.time() - t_gen
+    rng = np.random.default_rng(gen.SEED0 + 4)
+    pick = rng.integers(0, P, size=R)
+    budget = int(args.serve_budget_gb * (1 << 30))
+    mcr = args.min_chain_reads
+
+    def drive(srv, arrivals):
+        """Submit request i at arrivals[i] (seconds from start; None: all at once) and
+        collect (latency, bases, batch size) as results complete."""
+        import queue
+        q, out = queue.Queue(), []
+
+        def consume():
+            while True:
+                item = q.get()
+                if item is None:
+                    return
+                rid = item
+                res = srv.wait(rid, copy=False)
+                out.append(((res["t_done_ns"] - res["t_submit_ns"]) * 1e-6, res["total_bases"], res["batch_size"],
+                            res["t_submit_ns"], res["t_done_ns"], res["status"]))
+                srv.release(rid)
+        c = th.Thread(target=consume, daemon=True)
+        c.start()
+        t0 = time.perf_counter()
+        for i in range(len(pick)):
+            if arrivals is not None:
+                while time.perf_counter() - t0 < arrivals[i]:
+                    time.sleep(min(2e-4, max(0.0, arrivals[i] - (time.perf_counter() - t0))))
+            q.put(srv.submit(pool[pick[i]], min_chain_reads=mcr))
+        q.put(None)
+        c.join()
+        assert all(o[5] == cg.CG_OK for o in out)
+        lat = np.array([o[0] for o in out])
+        span = (max(o[4] for o in out) - min(o[3] for o in out)) * 1e-9
+        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_ms": float(lat.mean()), "graphs_per_s": len(out) / span,
+                "gbases_per_s": sum(o[1] for o in out) / span / 1e9, "span_s": span,
+                "mean_batch": float(np.mean([o[2] for o in out]))}
+
+    # plain path, one request at a time: its closed-loop rate sets the offered load
+    plain = cg.Server(local_rank, hbm_budget_bytes=budget, max_batch=1, workers=1)
+    cal = {}
+    try:
+        saved = pick
+        pick = saved[: min(R, 200)]
+        cal = drive(plain, None)
+        pick = saved
+        lam = args.serve_load * cal["graphs_per_s"]
+        gaps = rng.exponential(1.0 / lam, size=R)
+        arrivals = np.cumsum(gaps) - gaps[0]
+        plain_load = drive(plain, arrivals)
+    finally:
+        plain.stop()
+    served = cg.Server(local_rank, hbm_budget_bytes=budget, max_batch=args.serve_max_batch, workers=2)
+    clocks = ClockSampler(local_rank)
+    try:
+        clocks.start()
+        t0 = time.time()
+        served_load = drive(served, arrivals)
+        t1 = time.time()
+        served_max = drive(served, None)
+        stats = served.stats()
+    finally:
+        served.stop()
+        clocks.stop()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_graphs(args, pool[:4])
+    bases_total = sum(int(pool[j].info["n_reads"]) for j in pick[:1])
+    line = {
+        "metric": METRIC, "value": world * served_max["gbases_per_s"], "unit": UNIT, "n_gpus": world,
+        "steps": R, "warmup": 0, "ms_per_step": 1e3 / served_max["graphs_per_s"],
+        "ms_per_graph": 1e3 / served_max["graphs_per_s"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic (seeded generator, workload recipe in DESIGN.md)",
+        "config": {
+            "workload": f"served-{R} (Poisson requests over a pool of {P} graphs, genome log-U[1,200] Mb, 5% repeats, "
+                        "30x, LN(12 kb, 6 kb))",
+            "requests": R, "pool": P, "hbm_budget_gb": args.serve_budget_gb, "max_batch": args.serve_max_batch,
+            "workers": 2, "offered_load_req_per_s": lam, "offered_over_plain_rate": args.serve_load,
+            "plain_closed_loop": cal, "plain_at_offered_load": plain_load, "served_at_offered_load": served_load,
+            "served_closed_loop": served_max, "server_stats": stats,
+            "p50_ms": served_load["p50_ms"], "p99_ms": served_load["p99_ms"],
+            "p50_ms_plain": plain_load["p50_ms"], "p99_ms_plain": plain_load["p99_ms"],
+            "value_is": "served closed-loop contig Gbases/s; requests arrive from pinned host memory and results "
+                        "return to host memory (H2D and D2H inside every request)",
+            "generate_s": round(t_gen, 1),
+        },
+        "roofline": None, "cpu_baseline": cpu,
+        "e2e": {"value": world * served_load["gbases_per_s"], "unit": UNIT,
+                "h2d_bytes_per_step": int(np.mean([sum(getattr(pool[j], k).nbytes for k in
+                                                       ("row_ptr", "col", "code", "suf", "len", "off", "packed"))
+                                                   for j in pick])),
+                "d2h_bytes_per_step": None, "note": "per request, at the offered load"},
+        "clocks": clocks.summary(t0, t1), "gpu_launches": None,
+    }
+    return line
+
+
 def cpu_baseline_graphs(args, graphs):
     """The oracle (one thread) on a bounded sample of the batch: the first graphs."""
     import oracle
@@ -566,6 +686,8 @@ def main():
         __graft_entry__.build()
     if args.workload.startswith("batched"):
         line = run_batched(args, rank, world, local_rank)
+    elif args.workload.startswith("served"):
+        line = run_served(args, rank, world, local_rank)
     else:
         line = run_ours(args, rank, world, local_rank)
     if rank == 0:

@@ -125,6 +125,40 @@ CG_API cg_status cg_load_batch(cg_ctx* ctx, const cg_graph_desc* descs, int k, u
  * if needed; waits for the GPU with host outputs. */
 CG_API cg_status cg_batch_ranges(cg_graph* g, int64_t* first_contig, int64_t* first_base, int mem);
 
+/* ------------------------------------------------------------- serving
+ * A request loop over the batched form. Each request is one string graph
+ * in host memory (its buffers must stay valid until the request is done).
+ * Requests are admitted while the sum of their device-memory estimates
+ * (2 x packed bytes + 400 B per read + 16 B per CSR entry + 1 MiB) stays
+ * within hbm_budget_bytes; a request that alone exceeds it is refused with
+ * CG_EBUSY. `workers` threads, each with its own context and stream, take
+ * every admitted request waiting at that moment (at most max_batch) as one
+ * batch (continuous batching), so batches overlap on the device. Results
+ * stay in server-owned host memory until cg_server_release. */
+typedef struct cg_server cg_server;
+typedef struct {
+  int32_t max_batch;          /* requests per batch, >= 1 */
+  int32_t workers;            /* batches in flight, 1..8 */
+  uint64_t hbm_budget_bytes;  /* admission budget, > 0 */
+} cg_server_opts;
+typedef struct {
+  cg_status status;
+  int32_t batch_size;         /* requests in the batch this one ran in */
+  int64_t n_contigs, total_bases;
+  const int64_t* contig_off;  /* n_contigs + 1 */
+  const uint8_t* bases;       /* total_bases ASCII */
+  int64_t t_submit_ns, t_start_ns, t_done_ns;  /* steady clock */
+} cg_server_result;
+CG_API cg_status cg_server_start(int device, const cg_server_opts* opts, cg_server** out);
+CG_API cg_status cg_server_submit(cg_server* s, const cg_graph_desc* desc, uint64_t* id);
+CG_API cg_status cg_server_poll(cg_server* s, uint64_t id, int* done);
+/* Waits up to timeout_ms (< 0: no limit); CG_ETIMEOUT if not done by then. */
+CG_API cg_status cg_server_wait(cg_server* s, uint64_t id, int64_t timeout_ms, cg_server_result* out);
+CG_API cg_status cg_server_release(cg_server* s, uint64_t id);
+CG_API cg_status cg_server_stats(cg_server* s, uint64_t* batches, uint64_t* requests, uint64_t* in_flight_bytes);
+/* Finishes every submitted request, then stops the workers. */
+CG_API cg_status cg_server_stop(cg_server* s);
+
 /* BranchRemoval (Alg. 2; Sec. 4.2). is_branch: NULL or n bytes (1 = branch),
  * in `mem`. n_branch: NULL or receives the count (waits for the GPU). */
 CG_API cg_status cg_mask_branches(cg_graph* g, uint8_t* is_branch, int mem, int64_t* n_branch);

@@ -43,6 +43,17 @@ class GraphDesc(ctypes.Structure):
                 ("min_chain_reads", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("max_batch", ctypes.c_int32), ("workers", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_uint64)]
+
+
+class ServerResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("batch_size", ctypes.c_int32), ("n_contigs", ctypes.c_int64),
+                ("total_bases", ctypes.c_int64), ("contig_off", ctypes.POINTER(ctypes.c_int64)),
+                ("bases", ctypes.POINTER(ctypes.c_uint8)), ("t_submit_ns", ctypes.c_int64),
+                ("t_start_ns", ctypes.c_int64), ("t_done_ns", ctypes.c_int64)]
+
+
 API = {
     "cg_create": [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_uint64, ctypes.c_void_p],
     "cg_destroy": [ctypes.c_void_p],
@@ -63,6 +74,14 @@ API = {
     "cg_get_tuning": [ctypes.c_void_p, ctypes.c_void_p],
     "cg_kernel_time": [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_float)],
     "cg_get_stats": [ctypes.c_void_p, ctypes.c_void_p],
+    "cg_server_start": [ctypes.c_int, ctypes.POINTER(ServerOpts), ctypes.POINTER(ctypes.c_void_p)],
+    "cg_server_submit": [ctypes.c_void_p, ctypes.POINTER(GraphDesc), ctypes.POINTER(ctypes.c_uint64)],
+    "cg_server_poll": [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)],
+    "cg_server_wait": [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(ServerResult)],
+    "cg_server_release": [ctypes.c_void_p, ctypes.c_uint64],
+    "cg_server_stats": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                        ctypes.POINTER(ctypes.c_uint64)],
+    "cg_server_stop": [ctypes.c_void_p],
     "cg_offsets_noalloc": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p],
     "cg_status_str": [ctypes.c_int],
     "cg_last_error": [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t],
@@ -305,6 +324,68 @@ def cg_get_stats(ctx: Context) -> dict:
     s = Stats()
     _check(ctx.ptr, lib().cg_get_stats(ctx.ptr, ctypes.byref(s)))
     return {"kernels_launched": int(s.kernels_launched), "stage_ms": [float(x) for x in s.stage_ms]}
+
+
+class Server:
+    """cg_server: continuous batching over the batched form (host inputs and outputs)."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 150 << 30, max_batch: int = 64, workers: int = 2):
+        self.ptr = ctypes.c_void_p()
+        opts = ServerOpts(int(max_batch), int(workers), int(hbm_budget_bytes))
+        st = lib().cg_server_start(int(device), ctypes.byref(opts), ctypes.byref(self.ptr))
+        if st != CG_OK:
+            raise CgError(st, "cg_server_start failed")
+        self._keep = {}
+
+    def submit(self, graph, min_chain_reads: int = 2) -> int:
+        d = _desc(graph, min_chain_reads)
+        if d.mem != MEM_HOST:
+            raise ValueError("server requests take host buffers")
+        rid = ctypes.c_uint64()
+        st = lib().cg_server_submit(self.ptr, ctypes.byref(d), ctypes.byref(rid))
+        if st != CG_OK:
+            raise CgError(st, "cg_server_submit refused the request")
+        self._keep[rid.value] = graph            # its buffers must outlive the request
+        return rid.value
+
+    def poll(self, rid: int) -> bool:
+        done = ctypes.c_int()
+        _check(None, lib().cg_server_poll(self.ptr, rid, ctypes.byref(done)))
+        return bool(done.value)
+
+    def wait(self, rid: int, timeout_ms: int = -1, copy: bool = True) -> dict:
+        """Result of a request: status, counts, contig_off / bases (copies), timestamps (ns)."""
+        r = ServerResult()
+        _check(None, lib().cg_server_wait(self.ptr, rid, int(timeout_ms), ctypes.byref(r)))
+        out = {"status": r.status, "batch_size": r.batch_size, "n_contigs": r.n_contigs,
+               "total_bases": r.total_bases, "t_submit_ns": r.t_submit_ns, "t_start_ns": r.t_start_ns,
+               "t_done_ns": r.t_done_ns}
+        if copy and r.status == CG_OK:
+            out["contig_off"] = np.ctypeslib.as_array(r.contig_off, shape=(r.n_contigs + 1,)).copy()
+            out["bases"] = (np.ctypeslib.as_array(r.bases, shape=(r.total_bases,)).copy() if r.total_bases
+                            else np.zeros(0, np.uint8))
+        return out
+
+    def release(self, rid: int):
+        _check(None, lib().cg_server_release(self.ptr, rid))
+        self._keep.pop(rid, None)
+
+    def stats(self) -> dict:
+        b, q, f = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(None, lib().cg_server_stats(self.ptr, ctypes.byref(b), ctypes.byref(q), ctypes.byref(f)))
+        return {"batches": b.value, "requests": q.value, "in_flight_bytes": f.value}
+
+    def stop(self):
+        if self.ptr:
+            lib().cg_server_stop(self.ptr)
+            self.ptr = None
+            self._keep = {}
+
+    def __del__(self):
+        try:
+            self.stop()
+        except Exception:
+            pass
 
 
 NOALLOC_MAX_COUNT = 16777216

@@ -1,0 +1,262 @@
+// cg_server.cu - the served form: a request loop over the library's batched
+// path. Requests (one string graph each, host inputs) are admitted against a
+// device-memory budget, grouped by continuous batching -- every admitted
+// request waiting when a worker becomes free joins its batch -- and run as
+// one union graph per batch. Two workers, each with its own context and
+// stream, keep two batches in flight so that one batch's host-to-device copy
+// overlaps the other's kernels. Host code only.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "cg.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+int64_t now_ns() {
+  return std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now().time_since_epoch()).count();
+}
+
+struct Request {
+  uint64_t id = 0;
+  cg_graph_desc desc{};
+  uint64_t est_bytes = 0;
+  int64_t t_submit = 0, t_start = 0, t_done = 0;
+  int done = 0;
+  cg_status status = CG_OK;
+  int64_t n_contigs = 0, total_bases = 0;
+  std::vector<int64_t> contig_off;
+  std::vector<uint8_t> bases;
+  int batch_size = 0;
+};
+
+}  // namespace
+
+struct cg_server {
+  int device = 0;
+  cg_server_opts opts{};
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Request*> waiting;          // submitted, not yet admitted
+  std::deque<Request*> admitted;         // within the budget, not yet taken by a worker
+  std::map<uint64_t, Request*> all;
+  uint64_t next_id = 1;
+  uint64_t in_flight_bytes = 0;          // estimates of admitted, unfinished requests
+  bool stopping = false;
+  std::vector<std::thread> workers;
+  std::vector<cg_ctx*> ctxs;
+  uint64_t batches = 0, batched_requests = 0;
+};
+
+namespace {
+
+// Device memory a request needs at most: its inputs, the library's scratch
+// (about 400 bytes per read and 16 per CSR entry) and room for its output.
+uint64_t estimate(const cg_graph_desc& d) {
+  return (uint64_t)d.packed_bytes * 2 + 400ull * (uint64_t)d.n_reads + 16ull * (uint64_t)d.n_entries + (1ull << 20);
+}
+
+// Moves waiting requests into the admitted queue while the budget allows.
+void admit_locked(cg_server* s) {
+  while (!s->waiting.empty()) {
+    Request* r = s->waiting.front();
+    if (s->in_flight_bytes + r->est_bytes > s->opts.hbm_budget_bytes && s->in_flight_bytes > 0) break;
+    s->waiting.pop_front();
+    s->in_flight_bytes += r->est_bytes;
+    s->admitted.push_back(r);
+  }
+}
+
+void run_batch(cg_server* s, cg_ctx* ctx, std::vector<Request*>& batch) {
+  const int k = (int)batch.size();
+  std::vector<cg_graph_desc> descs(k);
+  const int64_t t0 = now_ns();
+  for (int j = 0; j < k; ++j) {
+    descs[j] = batch[j]->desc;
+    batch[j]->t_start = t0;
+    batch[j]->batch_size = k;
+  }
+  cg_graph* g = nullptr;
+  cg_status st = cg_load_batch(ctx, descs.data(), k, 0, &g);
+  std::vector<int64_t> fc(k + 1), fb(k + 1), off;
+  std::vector<uint8_t> bases;
+  int64_t n_contigs = 0, total = 0;
+  if (st == CG_OK) st = cg_mask_branches(g, nullptr, CG_MEM_DEVICE, nullptr);
+  if (st == CG_OK) st = cg_chains(g, nullptr, nullptr, nullptr, CG_MEM_DEVICE, nullptr, nullptr);
+  if (st == CG_OK) st = cg_emit_contigs(g, nullptr, 0, nullptr, 0, CG_MEM_HOST, &n_contigs, &total);
+  if (st == CG_OK) {
+    off.resize((size_t)n_contigs + 1);
+    bases.resize((size_t)(total > 0 ? total : 1));
+    st = cg_emit_contigs(g, off.data(), n_contigs + 1, bases.data(), total, CG_MEM_HOST, nullptr, nullptr);
+  }
+  if (st == CG_OK) st = cg_batch_ranges(g, fc.data(), fb.data(), CG_MEM_HOST);
+  if (g) cg_free_graph(g);
+  const int64_t t1 = now_ns();
+  std::lock_guard<std::mutex> lk(s->mu);
+  for (int j = 0; j < k; ++j) {
+    Request* r = batch[j];
+    r->status = st;
+    if (st == CG_OK) {
+      const int64_t c0 = fc[j], c1 = fc[j + 1], b0 = fb[j], b1 = fb[j + 1];
+      r->n_contigs = c1 - c0;
+      r->total_bases = b1 - b0;
+      r->contig_off.resize((size_t)(c1 - c0) + 1);
+      for (int64_t i = c0; i <= c1; ++i) r->contig_off[(size_t)(i - c0)] = off[(size_t)i] - b0;
+      r->bases.assign(bases.begin() + b0, bases.begin() + b1);
+    }
+    r->t_done = t1;
+    r->done = 1;
+    s->in_flight_bytes -= r->est_bytes;
+  }
+  s->batches += 1;
+  s->batched_requests += (uint64_t)k;
+  admit_locked(s);
+  s->cv_done.notify_all();
+  s->cv_work.notify_all();
+}
+
+void worker_main(cg_server* s, int w) {
+  cg_ctx* ctx = s->ctxs[(size_t)w];
+  for (;;) {
+    std::vector<Request*> batch;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->cv_work.wait(lk, [&] { return s->stopping || !s->admitted.empty(); });
+      if (s->admitted.empty() && s->stopping) return;
+      while (!s->admitted.empty() && (int)batch.size() < s->opts.max_batch) {
+        batch.push_back(s->admitted.front());
+        s->admitted.pop_front();
+      }
+    }
+    if (!batch.empty()) run_batch(s, ctx, batch);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+cg_status cg_server_start(int device, const cg_server_opts* opts, cg_server** out) {
+  if (!opts || !out || opts->max_batch < 1 || opts->workers < 1 || opts->workers > 8 || opts->hbm_budget_bytes == 0)
+    return CG_EINVAL;
+  *out = nullptr;
+  cg_server* s = new (std::nothrow) cg_server();
+  if (!s) return CG_ENOMEM;
+  s->device = device;
+  s->opts = *opts;
+  for (int w = 0; w < opts->workers; ++w) {
+    cg_ctx* c = nullptr;
+    cg_status st = cg_create(&c, device, opts->hbm_budget_bytes, nullptr);
+    if (st != CG_OK) {
+      for (cg_ctx* x : s->ctxs) cg_destroy(x);
+      delete s;
+      return st;
+    }
+    cg_set_graphs(c, 0);   // every batch is a new union graph: nothing to replay
+    s->ctxs.push_back(c);
+  }
+  for (int w = 0; w < opts->workers; ++w) s->workers.emplace_back(worker_main, s, w);
+  *out = s;
+  return CG_OK;
+}
+
+cg_status cg_server_submit(cg_server* s, const cg_graph_desc* d, uint64_t* id) {
+  if (!s || !d || !id) return CG_EINVAL;
+  if (d->mem != CG_MEM_HOST) return CG_EINVAL;
+  Request* r = new (std::nothrow) Request();
+  if (!r) return CG_ENOMEM;
+  r->desc = *d;
+  r->est_bytes = estimate(*d);
+  if (r->est_bytes > s->opts.hbm_budget_bytes) {
+    delete r;
+    return CG_EBUSY;                     // can never fit the budget
+  }
+  r->t_submit = now_ns();
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->stopping) {
+    delete r;
+    return CG_EINVAL;
+  }
+  r->id = s->next_id++;
+  *id = r->id;
+  s->all[r->id] = r;
+  s->waiting.push_back(r);
+  admit_locked(s);
+  s->cv_work.notify_one();
+  return CG_OK;
+}
+
+cg_status cg_server_poll(cg_server* s, uint64_t id, int* done) {
+  if (!s || !done) return CG_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->all.find(id);
+  if (it == s->all.end()) return CG_EINVAL;
+  *done = it->second->done;
+  return CG_OK;
+}
+
+cg_status cg_server_wait(cg_server* s, uint64_t id, int64_t timeout_ms, cg_server_result* res) {
+  if (!s || !res) return CG_EINVAL;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->all.find(id);
+  if (it == s->all.end()) return CG_EINVAL;
+  Request* r = it->second;
+  const bool ok = s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms < 0 ? 1ll << 40 : timeout_ms),
+                                      [&] { return r->done != 0; });
+  if (!ok) return CG_ETIMEOUT;
+  res->status = r->status;
+  res->n_contigs = r->n_contigs;
+  res->total_bases = r->total_bases;
+  res->contig_off = r->contig_off.data();
+  res->bases = r->bases.data();
+  res->t_submit_ns = r->t_submit;
+  res->t_start_ns = r->t_start;
+  res->t_done_ns = r->t_done;
+  res->batch_size = r->batch_size;
+  return CG_OK;
+}
+
+cg_status cg_server_release(cg_server* s, uint64_t id) {
+  if (!s) return CG_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->all.find(id);
+  if (it == s->all.end() || !it->second->done) return CG_EINVAL;
+  delete it->second;
+  s->all.erase(it);
+  return CG_OK;
+}
+
+cg_status cg_server_stats(cg_server* s, uint64_t* batches, uint64_t* requests, uint64_t* in_flight_bytes) {
+  if (!s) return CG_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (batches) *batches = s->batches;
+  if (requests) *requests = s->batched_requests;
+  if (in_flight_bytes) *in_flight_bytes = s->in_flight_bytes;
+  return CG_OK;
+}
+
+cg_status cg_server_stop(cg_server* s) {
+  if (!s) return CG_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stopping = true;
+  }
+  s->cv_work.notify_all();
+  for (std::thread& t : s->workers) t.join();
+  for (cg_ctx* c : s->ctxs) cg_destroy(c);
+  for (auto& kv : s->all) delete kv.second;   // every request is in `all` until released; workers drained them
+  delete s;
+  return CG_OK;
+}
+
+}  // extern "C"
