@@ -27,8 +27,8 @@ struct cg_ctx {
   unsigned long long* h_u64 = nullptr;  // pinned host word
   cg_status sticky = CG_OK;
   std::string last_error;
-  std::multimap<size_t, void*> pool;   // freed device buffers kept for reuse
-  std::map<void*, size_t> sizes;       // every live or pooled buffer of this context
+  cudaMemPool_t mempool = nullptr;     // device memory of this context's graphs and scratch
+  std::map<void*, size_t> sizes;       // every live allocation of this context
   unsigned long long launches = 0;
   bool timing = false;
   cudaEvent_t ev[8] = {};              // start/end of mask, chains, offsets, emission
@@ -86,39 +86,23 @@ cg_status cuda_fail(cg_ctx* c, cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
   } while (0)
 
-// Device allocation through the context pool (reuses a freed buffer whose
-// size is within 2x of the request) under the context's HBM budget.
+// Device allocation: stream-ordered suballocation from the context's CUDA
+// memory pool (which keeps freed memory for reuse, up to the budget), under
+// the context's HBM budget.
 void* dalloc(cg_ctx* c, size_t bytes, cg_status* st) {
   if (bytes == 0) bytes = 16;
   bytes = (bytes + 255) & ~size_t(255);
-  auto it = c->pool.lower_bound(bytes);
-  if (it != c->pool.end() && it->first <= 2 * bytes) {
-    void* p = it->second;
-    c->pool.erase(it);
-    return p;
-  }
   if (c->budget && c->used + bytes > c->budget) {
-    // give pooled memory back before refusing
-    for (auto& kv : c->pool) { cudaFree(kv.second); c->used -= kv.first; c->sizes.erase(kv.second); }
-    c->pool.clear();
-    if (c->used + bytes > c->budget) {
-      *st = fail(c, CG_ENOMEM, "HBM budget: %zu bytes in use, %zu more requested, budget %llu", (size_t)c->used,
-                 bytes, (unsigned long long)c->budget);
-      return nullptr;
-    }
+    *st = fail(c, CG_ENOMEM, "HBM budget: %zu bytes in use, %zu more requested, budget %llu", (size_t)c->used,
+               bytes, (unsigned long long)c->budget);
+    return nullptr;
   }
   void* p = nullptr;
-  cudaError_t e = cudaMalloc(&p, bytes);
+  cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, c->mempool, c->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    for (auto& kv : c->pool) { cudaFree(kv.second); c->used -= kv.first; c->sizes.erase(kv.second); }
-    c->pool.clear();
-    e = cudaMalloc(&p, bytes);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      *st = fail(c, CG_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
-      return nullptr;
-    }
+    *st = fail(c, CG_ENOMEM, "device allocation of %zu bytes: %s", bytes, cudaGetErrorString(e));
+    return nullptr;
   }
   c->used += bytes;
   c->sizes[p] = bytes;
@@ -129,7 +113,9 @@ void dfree(cg_ctx* c, void* p) {
   if (!p) return;
   auto it = c->sizes.find(p);
   if (it == c->sizes.end()) return;
-  c->pool.emplace(it->second, p);
+  cudaFreeAsync(p, c->stream);
+  c->used -= it->second;
+  c->sizes.erase(it);
 }
 
 template <class T>
@@ -397,6 +383,20 @@ cg_status cg_create(cg_ctx** out, int device, uint64_t hbm_budget_bytes, void* c
   c->env.stream = c->stream;
   c->env.num_sms = sms > 0 ? sms : 1;
   c->env.coop_blocks = cg::coop_blocks_for_grid_kernels(c->env.num_sms);
+  {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    if (cudaMemPoolCreate(&c->mempool, &props) != cudaSuccess) {
+      cudaGetLastError();
+      c->mempool = nullptr;
+      cg_destroy(c);
+      return CG_ECUDA;
+    }
+    uint64_t keep = c->budget ? c->budget : ~0ull;   // freed memory stays in the pool up to this much
+    cudaMemPoolSetAttribute(c->mempool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
   c->env.launches = &c->launches;
   c->env.marks = &c->marks;
   if (cudaMalloc(&c->derr, sizeof(cg::DevError)) != cudaSuccess ||
@@ -417,7 +417,9 @@ cg_status cg_destroy(cg_ctx* c) {
   if (!c) return CG_EINVAL;
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
-  for (auto& kv : c->sizes) cudaFree(kv.first);
+  for (auto& kv : c->sizes) cudaFreeAsync(kv.first, c->stream);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->mempool) cudaMemPoolDestroy(c->mempool);
   if (c->derr) cudaFree(c->derr);
   if (c->h_err) cudaFreeHost(c->h_err);
   if (c->h_ctr) cudaFreeHost(c->h_ctr);
@@ -675,7 +677,7 @@ cg_status cg_load_batch(cg_ctx* c, const cg_graph_desc* d, int k, uint32_t flags
   CK(cudaMemcpyAsync(tab, host_tab.data(), host_tab.size() * 8, cudaMemcpyHostToDevice, c->stream), "copy tables");
   CK(cg::launch_batch_fixup(k, tab, tab + (k + 1), tab + 2 * (k + 1), tab + 3 * (k + 1), stage_rp, rpb, rp, col, off,
                             n, m, c->env), "batch fixup");
-  CK(cudaStreamSynchronize(c->stream), "stream synchronize");   // host_tab and stage_rp are done with
+  CK(cudaStreamSynchronize(c->stream), "stream synchronize");   // host_tab is read by the copy above
   dfree(c, stage_rp);
   G.row_ptr = rp;
   G.col = col;

@@ -4,7 +4,8 @@
 // request waiting when a worker becomes free joins its batch -- and run as
 // one union graph per batch. Two workers, each with its own context and
 // stream, keep two batches in flight so that one batch's host-to-device copy
-// overlaps the other's kernels. Host code only.
+// overlaps the other's kernels; each request's contigs are copied from the
+// batch's device output straight into the request's result. Host code only.
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -55,6 +56,7 @@ struct cg_server {
   bool stopping = false;
   std::vector<std::thread> workers;
   std::vector<cg_ctx*> ctxs;
+  std::vector<cudaStream_t> streams;
   uint64_t batches = 0, batched_requests = 0;
 };
 
@@ -77,7 +79,36 @@ void admit_locked(cg_server* s) {
   }
 }
 
-void run_batch(cg_server* s, cg_ctx* ctx, std::vector<Request*>& batch) {
+// A worker's device output buffers, grown when a batch needs more.
+struct WorkerBuffers {
+  uint8_t* bases = nullptr;
+  int64_t bases_cap = 0;
+  int64_t* off = nullptr;
+  int64_t off_cap = 0;
+  void release() {
+    if (bases) cudaFree(bases);
+    if (off) cudaFree(off);
+    bases = nullptr;
+    off = nullptr;
+    bases_cap = off_cap = 0;
+  }
+};
+
+cg_status grow(WorkerBuffers& wb, int64_t total, int64_t contigs) {
+  if (total > wb.bases_cap) {
+    if (wb.bases) cudaFree(wb.bases);
+    wb.bases_cap = total + total / 4 + 4096;
+    if (cudaMalloc(&wb.bases, (size_t)wb.bases_cap) != cudaSuccess) { cudaGetLastError(); wb.bases = nullptr; wb.bases_cap = 0; return CG_ENOMEM; }
+  }
+  if (contigs + 1 > wb.off_cap) {
+    if (wb.off) cudaFree(wb.off);
+    wb.off_cap = contigs + contigs / 4 + 1024;
+    if (cudaMalloc(&wb.off, (size_t)wb.off_cap * 8) != cudaSuccess) { cudaGetLastError(); wb.off = nullptr; wb.off_cap = 0; return CG_ENOMEM; }
+  }
+  return CG_OK;
+}
+
+void run_batch(cg_server* s, cg_ctx* ctx, cudaStream_t stream, WorkerBuffers& wb, std::vector<Request*>& batch) {
   const int k = (int)batch.size();
   std::vector<cg_graph_desc> descs(k);
   const int64_t t0 = now_ns();
@@ -88,32 +119,41 @@ void run_batch(cg_server* s, cg_ctx* ctx, std::vector<Request*>& batch) {
   }
   cg_graph* g = nullptr;
   cg_status st = cg_load_batch(ctx, descs.data(), k, 0, &g);
-  std::vector<int64_t> fc(k + 1), fb(k + 1), off;
-  std::vector<uint8_t> bases;
+  std::vector<int64_t> fc(k + 1), fb(k + 1);
   int64_t n_contigs = 0, total = 0;
   if (st == CG_OK) st = cg_mask_branches(g, nullptr, CG_MEM_DEVICE, nullptr);
   if (st == CG_OK) st = cg_chains(g, nullptr, nullptr, nullptr, CG_MEM_DEVICE, nullptr, nullptr);
-  if (st == CG_OK) st = cg_emit_contigs(g, nullptr, 0, nullptr, 0, CG_MEM_HOST, &n_contigs, &total);
+  if (st == CG_OK) st = cg_emit_contigs(g, nullptr, 0, nullptr, 0, CG_MEM_DEVICE, &n_contigs, &total);
+  if (st == CG_OK) st = grow(wb, total, n_contigs);
+  if (st == CG_OK)
+    st = cg_emit_contigs(g, wb.off, wb.off_cap, wb.bases, wb.bases_cap, CG_MEM_DEVICE, nullptr, nullptr);
+  if (st == CG_OK) st = cg_batch_ranges(g, fc.data(), fb.data(), CG_MEM_HOST);   // waits for the stream
   if (st == CG_OK) {
-    off.resize((size_t)n_contigs + 1);
-    bases.resize((size_t)(total > 0 ? total : 1));
-    st = cg_emit_contigs(g, off.data(), n_contigs + 1, bases.data(), total, CG_MEM_HOST, nullptr, nullptr);
+    // each request's slice goes straight from device memory into its result
+    for (int j = 0; j < k && st == CG_OK; ++j) {
+      Request* r = batch[j];
+      const int64_t c0 = fc[j], c1 = fc[j + 1], b0 = fb[j], b1 = fb[j + 1];
+      r->n_contigs = c1 - c0;
+      r->total_bases = b1 - b0;
+      r->contig_off.resize((size_t)(c1 - c0) + 1);
+      r->bases.resize((size_t)(b1 - b0));
+      if (cudaMemcpyAsync(r->contig_off.data(), wb.off + c0, (size_t)(c1 - c0 + 1) * 8, cudaMemcpyDeviceToHost,
+                          stream) != cudaSuccess ||
+          (b1 > b0 && cudaMemcpyAsync(r->bases.data(), wb.bases + b0, (size_t)(b1 - b0), cudaMemcpyDeviceToHost,
+                                      stream) != cudaSuccess))
+        st = CG_ECUDA;
+    }
+    if (cudaStreamSynchronize(stream) != cudaSuccess) st = CG_ECUDA;
+    for (int j = 0; j < k; ++j)
+      for (int64_t& o : batch[j]->contig_off) o -= fb[j];
   }
-  if (st == CG_OK) st = cg_batch_ranges(g, fc.data(), fb.data(), CG_MEM_HOST);
   if (g) cg_free_graph(g);
+  cudaGetLastError();
   const int64_t t1 = now_ns();
   std::lock_guard<std::mutex> lk(s->mu);
   for (int j = 0; j < k; ++j) {
     Request* r = batch[j];
     r->status = st;
-    if (st == CG_OK) {
-      const int64_t c0 = fc[j], c1 = fc[j + 1], b0 = fb[j], b1 = fb[j + 1];
-      r->n_contigs = c1 - c0;
-      r->total_bases = b1 - b0;
-      r->contig_off.resize((size_t)(c1 - c0) + 1);
-      for (int64_t i = c0; i <= c1; ++i) r->contig_off[(size_t)(i - c0)] = off[(size_t)i] - b0;
-      r->bases.assign(bases.begin() + b0, bases.begin() + b1);
-    }
     r->t_done = t1;
     r->done = 1;
     s->in_flight_bytes -= r->est_bytes;
@@ -127,18 +167,24 @@ void run_batch(cg_server* s, cg_ctx* ctx, std::vector<Request*>& batch) {
 
 void worker_main(cg_server* s, int w) {
   cg_ctx* ctx = s->ctxs[(size_t)w];
+  cudaStream_t stream = s->streams[(size_t)w];
+  cudaSetDevice(s->device);
+  WorkerBuffers wb;
   for (;;) {
     std::vector<Request*> batch;
     {
       std::unique_lock<std::mutex> lk(s->mu);
       s->cv_work.wait(lk, [&] { return s->stopping || !s->admitted.empty(); });
-      if (s->admitted.empty() && s->stopping) return;
+      if (s->admitted.empty() && s->stopping) {
+        wb.release();
+        return;
+      }
       while (!s->admitted.empty() && (int)batch.size() < s->opts.max_batch) {
         batch.push_back(s->admitted.front());
         s->admitted.pop_front();
       }
     }
-    if (!batch.empty()) run_batch(s, ctx, batch);
+    if (!batch.empty()) run_batch(s, ctx, stream, wb, batch);
   }
 }
 
@@ -154,14 +200,24 @@ cg_status cg_server_start(int device, const cg_server_opts* opts, cg_server** ou
   if (!s) return CG_ENOMEM;
   s->device = device;
   s->opts = *opts;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    cudaGetLastError();
+    delete s;
+    return CG_ECUDA;
+  }
   for (int w = 0; w < opts->workers; ++w) {
     cg_ctx* c = nullptr;
-    cg_status st = cg_create(&c, device, opts->hbm_budget_bytes, nullptr);
+    cudaStream_t st_w = nullptr;
+    cg_status st = cudaStreamCreateWithFlags(&st_w, cudaStreamNonBlocking) == cudaSuccess ? CG_OK : CG_ECUDA;
+    if (st == CG_OK) st = cg_create(&c, device, opts->hbm_budget_bytes, st_w);
     if (st != CG_OK) {
+      if (st_w) cudaStreamDestroy(st_w);
       for (cg_ctx* x : s->ctxs) cg_destroy(x);
+      for (cudaStream_t y : s->streams) cudaStreamDestroy(y);
       delete s;
       return st;
     }
+    s->streams.push_back(st_w);
     cg_set_graphs(c, 0);   // every batch is a new union graph: nothing to replay
     s->ctxs.push_back(c);
   }
@@ -254,6 +310,7 @@ cg_status cg_server_stop(cg_server* s) {
   s->cv_work.notify_all();
   for (std::thread& t : s->workers) t.join();
   for (cg_ctx* c : s->ctxs) cg_destroy(c);
+  for (cudaStream_t y : s->streams) cudaStreamDestroy(y);
   for (auto& kv : s->all) delete kv.second;   // every request is in `all` until released; workers drained them
   delete s;
   return CG_OK;
