@@ -62,6 +62,8 @@ def parse():
     p.add_argument("--ruler-log2", type=int, default=0)
     p.add_argument("--tile-bytes", type=int, default=0)
     p.add_argument("--emit-blocks-per-sm", type=int, default=0)
+    p.add_argument("--partition-parts", type=int, nargs="*", default=[8, 18, 72, 128],
+                   help="part counts for the GreedyPartitioning measurement (none: skip)")
     return p.parse_args()
 
 
@@ -532,6 +534,21 @@ def run_ours(args, rank, world, local_rank):
         step()
         for name, kms in cg.cg_kernel_times(ctx):
             kern.setdefault(name, []).append(kms)
+    # GreedyPartitioning of the contigs (Sec. 4.3) into parts, outside the timed steps
+    part_d = torch.empty(max(n_contigs, 1), dtype=torch.int32, device="cuda")
+    psum_d = torch.empty(cg.MAX_PARTS, dtype=torch.int64, device="cuda")
+    partition = {"weight": "reads per contig", "n_contigs": n_contigs, "by_parts": {}}
+    for P in args.partition_parts:
+        kms, wall = [], []
+        for _ in range(4):
+            a = time.perf_counter()
+            cg.cg_partition_contigs(g, P, cg.WEIGHT_READS, part_d, psum_d[:P])
+            wall.append((time.perf_counter() - a) * 1e3)
+            kms.append(sum(t for _, t in cg.cg_kernel_times(ctx)))
+        psum = psum_d[:P].cpu().numpy()
+        partition["by_parts"][str(P)] = {
+            "kernel_ms": statistics.mean(kms[1:]), "call_ms": statistics.mean(wall[1:]),
+            "max_over_mean_part": float(psum.max() / max(psum.mean(), 1e-9))}
     cg.cg_set_timing(ctx, 1)
     if world > 1:
         torch.distributed.barrier()
@@ -595,6 +612,7 @@ def run_ours(args, rank, world, local_rank):
             "stage_names": ["mask", "chains", "offsets", "emit"],
             "kernel_ms_mean": {k: statistics.mean(v) for k, v in kern.items()},
             "kernel_ms_note": "3 extra untimed steps with a CUDA event after every kernel",
+            "partition": partition,
             "B_min_bytes": B, "path_achieved_gbs": B / (ms * 1e-3) / 1e9,
             "path_roofline_frac": B / (ms * 1e-3) / 1e9 / pk["hbm_gbs"],
             "path_roofline_frac_8tbs": B / (ms * 1e-3) / 1e9 / 8000.0,

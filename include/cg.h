@@ -181,6 +181,23 @@ CG_API cg_status cg_chains(cg_graph* g, int32_t* chain_id, int32_t* rank, uint8_
 CG_API cg_status cg_emit_contigs(cg_graph* g, int64_t* contig_off, int64_t contig_off_cap, uint8_t* bases,
                           int64_t bases_cap, int mem, int64_t* n_contigs, int64_t* total_bases);
 
+/* GreedyPartitioning (Alg. 2; Sec. 4.3): splits the contigs among n_parts
+ * parts (processes, GPUs) with the longest-processing-time rule. Each contig
+ * weighs its number of reads (weight CG_WEIGHT_READS, the size estimate of
+ * Sec. 4.3) or its spelled bases (CG_WEIGHT_BASES). Contigs are taken by
+ * weight, heaviest first, equal weights in contig order (the order of
+ * cg_emit_contigs), and each goes to the part whose weight sum is smallest so
+ * far, the lowest part index on ties. Runs the earlier steps first and waits
+ * for the GPU. part: part_cap >= n_contigs entries, part[c] = part of contig
+ * c; part_weight: n_parts entries, the weight sum of each part; both in `mem`.
+ * n_parts in [1, CG_MAX_PARTS]; CG_EINVAL otherwise or when part_cap is too
+ * small (nothing is written then). */
+#define CG_WEIGHT_READS 0
+#define CG_WEIGHT_BASES 1
+#define CG_MAX_PARTS 1024
+CG_API cg_status cg_partition_contigs(cg_graph* g, int32_t n_parts, int32_t weight, int32_t* part, int64_t part_cap,
+                               int64_t* part_weight, int mem, int64_t* n_contigs);
+
 /* Launch parameters of a context's kernels. None changes any output. */
 typedef struct {
   int32_t ruler_log2;         /* list ranking: a read starts a sublist with probability 2^-ruler_log2, 1..12 */

@@ -3,13 +3,14 @@
 The compute lives in libcg.so (hand-written CUDA for sm_103a behind the C ABI
 of include/cg.h); `cg` is its thin Python binding.
 """
-from .cg import (BORROW_DEVICE, MEM_DEVICE, MEM_HOST, NO_VALIDATE, CgError, Context, Graph, Server, cg_batch_ranges,
-                 cg_chains, cg_create, cg_load_batch,
-                 cg_destroy, cg_emit_contigs, cg_free_graph, cg_get_stats, cg_get_tuning, cg_kernel_times, cg_load_graph, cg_mask_branches, cg_offsets_noalloc,
-                 cg_set_graphs, cg_set_timing, cg_set_tuning,
-                 cg_status_str, cg_sync, chains_host, contigs_host)
+from .cg import (BORROW_DEVICE, MAX_PARTS, MEM_DEVICE, MEM_HOST, NO_VALIDATE, WEIGHT_BASES, WEIGHT_READS, CgError,
+                 Context, Graph, Server, cg_batch_ranges, cg_chains, cg_create, cg_destroy, cg_emit_contigs,
+                 cg_free_graph, cg_get_stats, cg_get_tuning, cg_kernel_times, cg_load_batch, cg_load_graph,
+                 cg_mask_branches, cg_offsets_noalloc, cg_partition_contigs, cg_set_graphs, cg_set_timing,
+                 cg_set_tuning, cg_status_str, cg_sync, chains_host, contigs_host)
 
-__all__ = ["BORROW_DEVICE", "MEM_DEVICE", "MEM_HOST", "NO_VALIDATE", "CgError", "Context", "Graph", "Server",
-           "cg_batch_ranges", "cg_chains", "cg_load_batch",
-           "cg_create", "cg_destroy", "cg_emit_contigs", "cg_free_graph", "cg_get_stats", "cg_get_tuning", "cg_kernel_times", "cg_load_graph", "cg_offsets_noalloc",
-           "cg_mask_branches", "cg_set_graphs", "cg_set_timing", "cg_set_tuning", "cg_status_str", "cg_sync", "chains_host", "contigs_host"]
+__all__ = ["BORROW_DEVICE", "MAX_PARTS", "MEM_DEVICE", "MEM_HOST", "NO_VALIDATE", "WEIGHT_BASES", "WEIGHT_READS",
+           "CgError", "Context", "Graph", "Server", "cg_batch_ranges", "cg_chains", "cg_create", "cg_destroy",
+           "cg_emit_contigs", "cg_free_graph", "cg_get_stats", "cg_get_tuning", "cg_kernel_times", "cg_load_batch",
+           "cg_load_graph", "cg_mask_branches", "cg_offsets_noalloc", "cg_partition_contigs", "cg_set_graphs",
+           "cg_set_timing", "cg_set_tuning", "cg_status_str", "cg_sync", "chains_host", "contigs_host"]

@@ -67,6 +67,8 @@ API = {
                   ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
     "cg_emit_contigs": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
                         ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
+    "cg_partition_contigs": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64,
+                             ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)],
     "cg_sync": [ctypes.c_void_p],
     "cg_set_timing": [ctypes.c_void_p, ctypes.c_int],
     "cg_set_graphs": [ctypes.c_void_p, ctypes.c_int],
@@ -284,6 +286,33 @@ def cg_emit_contigs(g: Graph, contig_off=None, bases=None, want_counts: bool = T
                                             ctypes.byref(nc) if want_counts else None,
                                             ctypes.byref(tot) if want_counts else None))
     return (nc.value, tot.value) if want_counts else None
+
+
+WEIGHT_READS, WEIGHT_BASES = 0, 1
+MAX_PARTS = 1024
+
+
+def cg_partition_contigs(g: Graph, n_parts: int, weight: int = WEIGHT_READS, part=None, part_weight=None):
+    """GreedyPartitioning of the contigs into n_parts parts (Sec. 4.3).
+
+    With no buffers given, returns host arrays (part per contig, weight sum per
+    part); otherwise fills `part` (>= n_contigs entries) and `part_weight`
+    (n_parts entries), both host or both device, and returns n_contigs.
+    """
+    if part is None and part_weight is None:
+        nc, _ = cg_emit_contigs(g)
+        part = np.empty(max(nc, 1), dtype=np.int32)
+        part_weight = np.empty(max(int(n_parts), 1), dtype=np.int64)
+        out = ctypes.c_int64(-1)
+        _check(g.ctx.ptr, lib().cg_partition_contigs(g.ptr, int(n_parts), int(weight), _ptr(part), len(part),
+                                                     _ptr(part_weight), MEM_HOST, ctypes.byref(out)))
+        return part[:out.value], part_weight[:n_parts]
+    mem = _mem_of_all([part, part_weight])
+    out = ctypes.c_int64(-1)
+    _check(g.ctx.ptr, lib().cg_partition_contigs(g.ptr, int(n_parts), int(weight), _ptr(part),
+                                                 len(part) if part is not None else 0, _ptr(part_weight), mem,
+                                                 ctypes.byref(out)))
+    return out.value
 
 
 def cg_sync(ctx: Context):

@@ -850,4 +850,69 @@ cg_status cg_emit_contigs(cg_graph* g, int64_t* contig_off, int64_t contig_off_c
   return CG_OK;
 }
 
+static_assert(cg::kMaxParts == CG_MAX_PARTS, "part limit");
+
+cg_status cg_partition_contigs(cg_graph* g, int32_t n_parts, int32_t weight, int32_t* part, int64_t part_cap,
+                               int64_t* part_weight, int mem, int64_t* n_contigs) {
+  if (!g) return CG_EINVAL;
+  cg_ctx* c = g->ctx;
+  cg_status st = check_ctx(c);
+  if (st != CG_OK) return st;
+  if (mem != CG_MEM_HOST && mem != CG_MEM_DEVICE) return fail(c, CG_EINVAL, "bad mem");
+  if (n_parts < 1 || n_parts > CG_MAX_PARTS) return fail(c, CG_EINVAL, "n_parts %d not in [1, %d]", n_parts, CG_MAX_PARTS);
+  if (weight != CG_WEIGHT_READS && weight != CG_WEIGHT_BASES) return fail(c, CG_EINVAL, "bad weight");
+  if (!part_weight) return fail(c, CG_EINVAL, "part_weight is required");
+  if (g->stage < 3) {
+    st = run_offsets(g);
+    if (st != CG_OK) return st;
+  }
+  st = wait_and_read(g);
+  if (st != CG_OK) return st;
+  const long long C = c->h_ctr->n_contigs;
+  const long long max_w = weight == CG_WEIGHT_READS ? (long long)c->h_ctr->n_walk : (long long)c->h_ctr->total_bases;
+  if (C > 0 && (!part || part_cap < C)) return fail(c, CG_EINVAL, "part capacity %lld < %lld", (long long)part_cap, C);
+  // temporaries: the sort buffers, and staging for host outputs
+  const size_t N = (size_t)(C > 0 ? C : 1);
+  const long long tiles = (long long)(N + 2047) / 2048;
+  cg::SortBuffers b{};
+  b.tiles_cap = tiles;
+  b.state_cap = (256 * tiles + 2047) / 2048 + 1;
+  const size_t bytes[8] = {8 * N, 8 * N, 4 * N, 4 * N, 4 * 256 * (size_t)tiles, 8 * 256 * (size_t)tiles,
+                           8 * ((size_t)b.state_cap + 1), mem == CG_MEM_HOST ? 4 * N + 8 * (size_t)n_parts : 0};
+  void* p[8] = {};
+  for (int k = 0; k < 8 && st == CG_OK; ++k)
+    if (bytes[k]) p[k] = dalloc(c, bytes[k], &st);
+  auto release = [&]() {
+    for (int k = 0; k < 8; ++k) dfree(c, p[k]);
+  };
+  if (st != CG_OK) {
+    release();
+    return st;
+  }
+  b.key[0] = (unsigned long long*)p[0];
+  b.key[1] = (unsigned long long*)p[1];
+  b.val[0] = (int32_t*)p[2];
+  b.val[1] = (int32_t*)p[3];
+  b.hist = (unsigned*)p[4];
+  b.base = (unsigned long long*)p[5];
+  b.state = (unsigned long long*)p[6];
+  int64_t* d_w = mem == CG_MEM_HOST ? (int64_t*)p[7] : part_weight;
+  int32_t* d_part = mem == CG_MEM_HOST ? (int32_t*)((char*)p[7] + 8 * (size_t)n_parts) : part;
+  if (c->marks.on) {                   // per-kernel marks cover the partition alone
+    c->marks.n = 0;
+    cudaEventRecord(c->marks.ev[0], c->stream);
+  }
+  cudaError_t e = cg::launch_partition(g->s, C, weight, max_w, n_parts, b, d_part, d_w, c->env);
+  if (e == cudaSuccess && mem == CG_MEM_HOST) {
+    e = cudaMemcpyAsync(part_weight, d_w, 8 * (size_t)n_parts, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && C > 0) e = cudaMemcpyAsync(part, d_part, 4 * (size_t)C, cudaMemcpyDeviceToHost, c->stream);
+  }
+  if (e == cudaSuccess) st = wait_and_read(g);
+  release();
+  if (e != cudaSuccess) return cuda_fail(c, e, "partition kernels");
+  if (st != CG_OK) return st;
+  if (n_contigs) *n_contigs = C;
+  return CG_OK;
+}
+
 }  // extern "C"

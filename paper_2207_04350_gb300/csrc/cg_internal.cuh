@@ -151,8 +151,13 @@ inline void mark(const LaunchEnv& env, const char* name) {
   ++*env.launches;
   KernelMarks* m = env.marks;
   if (m && m->on && m->n < KernelMarks::kMax) {
-    // external: inside a stream capture this becomes an event-record node
-    cudaEventRecordWithFlags(m->ev[m->n + 1], env.stream, cudaEventRecordExternal);
+    // inside a stream capture an external record becomes an event-record node
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(env.stream, &cs);
+    if (cs == cudaStreamCaptureStatusActive)
+      cudaEventRecordWithFlags(m->ev[m->n + 1], env.stream, cudaEventRecordExternal);
+    else
+      cudaEventRecord(m->ev[m->n + 1], env.stream);
     m->name[m->n + 1] = name;
     ++m->n;
   }
@@ -174,6 +179,20 @@ cudaError_t launch_batch_fixup(int k, const int64_t* R, const int64_t* E, const 
                                long long N, long long M, const LaunchEnv& env);
 cudaError_t launch_batch_ranges(const Scratch& s, int k, const int64_t* R, long long N, int64_t* first_contig,
                                 int64_t* first_base, const LaunchEnv& env);
+// Buffers of the contig-weight sort (capacity: the number of contigs).
+struct SortBuffers {
+  unsigned long long* key[2];
+  int32_t* val[2];
+  unsigned* hist;              // 256 x tiles_cap digit counts
+  unsigned long long* base;    // 256 x tiles_cap scatter bases
+  unsigned long long* state;   // look-back descriptors of the digit scan, + 1 ticket
+  long long tiles_cap, state_cap;
+};
+constexpr int kMaxParts = 1024;
+// GreedyPartitioning of the C contigs of the last offsets stage into P parts
+// (weight 0: reads per contig, 1: bases); max_weight bounds every part sum.
+cudaError_t launch_partition(const Scratch& s, long long C, int weight, long long max_weight, int P,
+                             const SortBuffers& b, int32_t* part, int64_t* psum, const LaunchEnv& env);
 int coop_blocks_for_grid_kernels(int num_sms);
 
 // ---- device helpers ----
@@ -192,7 +211,7 @@ __device__ __forceinline__ long long block_round(long long n) { return (n + kBlo
 
 enum KernelId {
   K_VALIDATE1 = 1, K_VALIDATE2, K_MASK, K_SUCC, K_WALK, K_JUMP, K_FINAL, K_CYCLE, K_EXPORT,
-  K_SCAN_HEADS, K_SCATTER, K_SCAN_OFFSETS, K_CONTIG_OFF, K_EMIT
+  K_SCAN_HEADS, K_SCATTER, K_SCAN_OFFSETS, K_CONTIG_OFF, K_EMIT, K_SORT
 };
 
 inline int grid_for(long long n, const LaunchEnv& env, int per_sm = 8) {

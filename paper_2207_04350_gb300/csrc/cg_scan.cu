@@ -20,6 +20,8 @@
 // DERR_TIMEOUT and stops.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "cg_internal.cuh"
 
 namespace cg {
@@ -287,6 +289,205 @@ cudaError_t launch_offsets(const DevGraph& g, const Scratch& s, const Tuning& t,
 cudaError_t launch_export_contig_off(const Scratch& s, int64_t* out, int64_t cap, const LaunchEnv& env) {
   k_export_contig_off<<<env.num_sms, kBlock, 0, env.stream>>>(s, out, cap);
   mark(env, "k_export_contig_off");
+  return cudaGetLastError();
+}
+
+}  // namespace cg
+
+// ------------------------------------------------------------------------
+// GreedyPartitioning (LPT, Sec. 4.3). Contigs are weighted by their number of
+// reads (the size estimate of Sec. 4.3) or by their spelled bases, sorted by
+// weight, largest first, equal weights in contig order, and each in turn goes
+// to the part whose weight sum is smallest so far, the lowest part on ties.
+// The sort is a stable LSD radix sort, 8-bit digits, of kmax - weight; the
+// assignment is sequential by definition and runs in one warp.
+namespace cg {
+
+namespace {
+
+constexpr int kSortItems = 8;
+constexpr long long kSortTile = (long long)kSortItems * kBlock;     // 2048 keys per tile
+
+__device__ __forceinline__ unsigned digit_of(unsigned long long key, int pass) {
+  return (unsigned)((key >> (8 * pass)) & 255ull);
+}
+
+__global__ void k_sort_keys(const Scratch s, long long C, int weight, unsigned long long kmax, unsigned long long* key,
+                            int32_t* val) {
+  for (long long i = grid_tid(); i < C; i += grid_threads()) {
+    const long long w = weight == 0 ? (long long)s.qd[i] : s.contig_off[i + 1] - s.contig_off[i];
+    key[i] = kmax - (unsigned long long)w;
+    val[i] = (int32_t)i;
+  }
+}
+
+// Per tile and digit, the keys of the tile with that digit, stored digit-major
+// (hist[d * tiles + t]) so that one exclusive scan gives every scatter base.
+__global__ void k_sort_hist(const unsigned long long* key, long long C, int pass, unsigned* hist, long long tiles) {
+  __shared__ unsigned cnt[256];
+  for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
+    for (int d = threadIdx.x; d < 256; d += blockDim.x) cnt[d] = 0;
+    __syncthreads();
+    for (int k = 0; k < kSortItems; ++k) {
+      const long long i = t * kSortTile + k * kBlock + threadIdx.x;
+      if (i < C) atomicAdd(&cnt[digit_of(key[i], pass)], 1u);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < 256; d += blockDim.x) hist[(long long)d * tiles + t] = cnt[d];
+    __syncthreads();
+  }
+}
+
+struct HistLoad {
+  const unsigned* h;
+  __device__ unsigned long long operator()(long long i) const { return h[i]; }
+};
+struct HistStore {
+  unsigned long long* base;
+  __device__ void item(long long i, unsigned long long e) const { base[i] = e; }
+  __device__ void last(long long, unsigned long long) const {}
+};
+
+// Stable scatter. A tile's keys are taken in index order, 256 per round; a
+// key's place is its digit's base for the tile, plus the keys with that digit
+// in earlier rounds, in earlier warps of this round and in earlier lanes.
+__global__ void k_sort_scatter(const unsigned long long* key_in, const int32_t* val_in, unsigned long long* key_out,
+                               int32_t* val_out, long long C, int pass, const unsigned long long* base,
+                               long long tiles) {
+  __shared__ unsigned running[256];
+  __shared__ unsigned wcnt[kBlock / 32][256];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
+    for (int d = threadIdx.x; d < 256; d += blockDim.x) running[d] = 0;
+    for (int k = 0; k < kSortItems; ++k) {
+      const long long i = t * kSortTile + k * kBlock + threadIdx.x;
+      const bool valid = i < C;
+      const unsigned long long kk = valid ? key_in[i] : 0ull;
+      const unsigned d = valid ? digit_of(kk, pass) : 256u + lane;   // no two invalid lanes match
+      const unsigned peers = __match_any_sync(0xffffffffu, d);
+      const unsigned before_lane = __popc(peers & ((1u << lane) - 1u));
+      for (int x = threadIdx.x; x < (kBlock / 32) * 256; x += blockDim.x) (&wcnt[0][0])[x] = 0;
+      __syncthreads();
+      if (valid && before_lane == 0) wcnt[warp][d] = __popc(peers);
+      __syncthreads();
+      if (valid) {
+        unsigned before_warp = 0;
+        for (int w = 0; w < warp; ++w) before_warp += wcnt[w][d];
+        const unsigned long long pos = base[(long long)d * tiles + t] + running[d] + before_warp + before_lane;
+        key_out[pos] = kk;
+        val_out[pos] = val_in[i];
+      }
+      __syncthreads();
+      for (int dd = threadIdx.x; dd < 256; dd += blockDim.x) {
+        unsigned sum = 0;
+        for (int w = 0; w < kBlock / 32; ++w) sum += wcnt[w][dd];
+        running[dd] += sum;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// One warp. A part is the key (weight sum << part_bits) | part index, so that
+// the smallest key is the least-loaded part, the lowest index on ties, and no
+// two keys are equal. Lane l holds the keys of parts l + 32 j, j < KPL, in
+// registers. Per contig the warp takes the smallest key overall with the
+// redux unit (one 32-bit minimum when every key fits in 32 bits, else the
+// high halves, then the low halves at that high half) and the part holding
+// it adds the contig's weight; no branch depends on the data.
+template <int KPL, bool Narrow>
+__global__ void __launch_bounds__(32) k_lpt_assign(const unsigned long long* key, const int32_t* val, long long C,
+                                                   unsigned long long kmax, int P, int part_bits, int32_t* part,
+                                                   int64_t* psum) {
+  const unsigned full = 0xffffffffu;
+  const unsigned long long idx_mask = (1ull << part_bits) - 1;
+  const int lane = threadIdx.x;
+  unsigned long long K[KPL];
+#pragma unroll
+  for (int j = 0; j < KPL; ++j) K[j] = lane + 32 * j < P ? (unsigned long long)(lane + 32 * j) : ~0ull;
+  for (long long i0 = 0; i0 < C; i0 += 32) {
+    const long long ii = i0 + lane;
+    const int32_t ci = ii < C ? val[ii] : -1;
+    const unsigned long long w = ii < C ? (kmax - key[ii]) << part_bits : 0ull;
+    unsigned long long mine = 0;
+    const int cnt = (int)min(32ll, C - i0);
+    for (int q = 0; q < cnt; ++q) {
+      const unsigned long long wq = __shfl_sync(full, w, q);
+      unsigned long long my = K[0];
+#pragma unroll
+      for (int j = 1; j < KPL; ++j) my = min(my, K[j]);
+      unsigned long long m;
+      if (Narrow) {
+        m = __reduce_min_sync(full, (unsigned)min(my, 0xffffffffull));
+      } else {
+        const unsigned hi = (unsigned)(my >> 32);
+        const unsigned mhi = __reduce_min_sync(full, hi);
+        const unsigned mlo = __reduce_min_sync(full, hi == mhi ? (unsigned)my : 0xffffffffu);
+        m = ((unsigned long long)mhi << 32) | mlo;
+      }
+      mine = lane == q ? m : mine;
+#pragma unroll
+      for (int j = 0; j < KPL; ++j) K[j] += K[j] == m ? wq : 0ull;
+    }
+    if (ii < C) part[ci] = (int32_t)(mine & idx_mask);
+  }
+#pragma unroll
+  for (int j = 0; j < KPL; ++j)
+    if (lane + 32 * j < P) psum[lane + 32 * j] = (int64_t)(K[j] >> part_bits);
+}
+
+template <int KPL>
+void lpt_launch(bool narrow, const unsigned long long* key, const int32_t* val, long long C, unsigned long long kmax,
+                int P, int part_bits, int32_t* part, int64_t* psum, cudaStream_t st) {
+  if (narrow) k_lpt_assign<KPL, true><<<1, 32, 0, st>>>(key, val, C, kmax, P, part_bits, part, psum);
+  else k_lpt_assign<KPL, false><<<1, 32, 0, st>>>(key, val, C, kmax, P, part_bits, part, psum);
+}
+
+}  // namespace
+
+cudaError_t launch_partition(const Scratch& s, long long C, int weight, long long max_weight, int P,
+                             const SortBuffers& b, int32_t* part, int64_t* psum, const LaunchEnv& env) {
+  int bits = 8;
+  while (bits < 63 && (max_weight >> bits) != 0) bits += 8;
+  const unsigned long long kmax = bits >= 64 ? ~0ull : (1ull << bits) - 1;
+  if (C > 0) {
+    const long long tiles = (C + kSortTile - 1) / kSortTile;
+    const long long nh = 256 * tiles;
+    const long long scan_tiles = (nh + kTileItems - 1) / kTileItems;
+    if (scan_tiles > b.state_cap || tiles > b.tiles_cap) return cudaErrorInvalidValue;
+    k_sort_keys<<<grid_for(C, env), kBlock, 0, env.stream>>>(s, C, weight, kmax, b.key[0], b.val[0]);
+    mark(env, "k_sort_keys");
+    const int grid = (int)std::min<long long>(tiles, (long long)env.num_sms * 4);
+    int cur = 0;
+    for (int pass = 0; pass < bits / 8; ++pass) {
+      k_sort_hist<<<grid, kBlock, 0, env.stream>>>(b.key[cur], C, pass, b.hist, tiles);
+      mark(env, "k_sort_hist");
+      cudaMemsetAsync(b.state, 0, (size_t)(b.state_cap + 1) * sizeof(unsigned long long), env.stream);
+      k_scan<<<(unsigned)scan_tiles, kBlock, 0, env.stream>>>(HistLoad{b.hist}, HistStore{b.base}, nh, nullptr,
+                                                              b.state, b.state_cap, s.derr, K_SORT);
+      mark(env, "k_scan_digits");
+      k_sort_scatter<<<grid, kBlock, 0, env.stream>>>(b.key[cur], b.val[cur], b.key[cur ^ 1], b.val[cur ^ 1], C,
+                                                      pass, b.base, tiles);
+      mark(env, "k_sort_scatter");
+      cur ^= 1;
+    }
+    int part_bits = 0;
+    while ((1 << part_bits) < P) ++part_bits;
+    if (part_bits + bits > 63) return cudaErrorInvalidValue;
+    // narrow: the largest key, max_weight << part_bits | (P - 1), stays below 2^32 - 1
+    const bool narrow = (((unsigned long long)max_weight << part_bits) | (unsigned long long)(P - 1)) < 0xffffffffull;
+    const unsigned long long* kk = b.key[cur];
+    const int32_t* vv = b.val[cur];
+    if (P <= 32) lpt_launch<1>(narrow, kk, vv, C, kmax, P, part_bits, part, psum, env.stream);
+    else if (P <= 64) lpt_launch<2>(narrow, kk, vv, C, kmax, P, part_bits, part, psum, env.stream);
+    else if (P <= 128) lpt_launch<4>(narrow, kk, vv, C, kmax, P, part_bits, part, psum, env.stream);
+    else if (P <= 256) lpt_launch<8>(narrow, kk, vv, C, kmax, P, part_bits, part, psum, env.stream);
+    else if (P <= 512) lpt_launch<16>(narrow, kk, vv, C, kmax, P, part_bits, part, psum, env.stream);
+    else lpt_launch<32>(narrow, kk, vv, C, kmax, P, part_bits, part, psum, env.stream);
+    mark(env, "k_lpt_assign");
+  } else {
+    cudaMemsetAsync(psum, 0, (size_t)P * sizeof(int64_t), env.stream);
+  }
   return cudaGetLastError();
 }
 
