@@ -37,6 +37,38 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 EMIT_TRAFFIC = {"bytes_per_base": 551.5e6 / 481446585, "source_sha256_16": "c863d26b78abdb32"}
 
 
+def _reduce(x: float, world: int, op: str) -> float:
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    """The largest x over all ranks (the slowest replica's time); x on one rank."""
+    return _reduce(x, world, "max")
+
+
+def sum_over_ranks(x: float, world: int) -> float:
+    """The sum of x over all ranks (units every replica processed); x on one rank."""
+    return _reduce(x, world, "sum")
+
+
+def rank_barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def job_rate(units_per_rank: float, seconds_per_rank: float, world: int) -> float:
+    """Whole-job throughput: units of all ranks over the slowest rank's time."""
+    return sum_over_ranks(units_per_rank, world) / max_over_ranks(seconds_per_rank, world)
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -243,9 +275,13 @@ def run_batched(args, rank, world, local_rank):
     time.sleep(0.3)
     launches0 = cg.cg_get_stats(ctx)["kernels_launched"]
     emit_ms = []
+    rank_barrier(world)
     t0 = time.time()
-    ms = timed(run_union, args.steps, args.warmup, emit_ms)
+    ms_rank = timed(run_union, args.steps, args.warmup, emit_ms)
+    rank_barrier(world)
     t1 = time.time()
+    value = job_rate(total, ms_rank * 1e-3, world) / 1e9
+    ms = max_over_ranks(ms_rank, world)
     launches = cg.cg_get_stats(ctx)["kernels_launched"] - launches0
     time.sleep(0.2)
     clocks.stop()
@@ -278,7 +314,7 @@ def run_batched(args, rank, world, local_rank):
             if i > 0:
                 times.append(b - a)
         te = statistics.mean(times)
-        e2e = {"value": total / te / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        e2e = {"value": job_rate(total, te, world) / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": total + 8 * (n_contigs + 1) + 16 * (k + 1), "ms_per_step": te * 1e3,
                "graphs_per_s": k / te, "steps": len(times),
                "path": "cg_load_batch(host, validated) -> mask -> chains -> cg_emit_contigs(host) -> cg_batch_ranges"}
@@ -289,7 +325,7 @@ def run_batched(args, rank, world, local_rank):
     ach = emit_bytes / (ms_emit * 1e-3) / 1e9
     n_reads = sum(G.n for G in graphs)
     line = {
-        "metric": METRIC, "value": world * total / (ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": world,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "ms_per_graph": ms / k,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic (seeded generator, workload recipe in DESIGN.md)",
@@ -392,10 +428,13 @@ def run_served(args, rank, world, local_rank):
     clocks = ClockSampler(local_rank)
     try:
         clocks.start()
+        rank_barrier(world)
         t0 = time.time()
         served_load = drive(served, arrivals)
         t1 = time.time()
+        rank_barrier(world)
         served_max = drive(served, None)
+        rank_barrier(world)
         stats = served.stats()
     finally:
         served.stop()
@@ -405,7 +444,9 @@ def run_served(args, rank, world, local_rank):
         cpu = cpu_baseline_graphs(args, pool[:4])
     bases_total = sum(int(pool[j].info["n_reads"]) for j in pick[:1])
     line = {
-        "metric": METRIC, "value": world * served_max["gbases_per_s"], "unit": UNIT, "n_gpus": world,
+        "metric": METRIC,
+        "value": job_rate(served_max["gbases_per_s"] * served_max["span_s"], served_max["span_s"], world) / 1e9,
+        "unit": UNIT, "n_gpus": world,
         "steps": R, "warmup": 0, "ms_per_step": 1e3 / served_max["graphs_per_s"],
         "ms_per_graph": 1e3 / served_max["graphs_per_s"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8", "data": "synthetic (seeded generator, workload recipe in DESIGN.md)",
@@ -423,7 +464,8 @@ def run_served(args, rank, world, local_rank):
             "generate_s": round(t_gen, 1),
         },
         "roofline": None, "cpu_baseline": cpu,
-        "e2e": {"value": world * served_load["gbases_per_s"], "unit": UNIT,
+        "e2e": {"value": job_rate(served_load["gbases_per_s"] * served_load["span_s"], served_load["span_s"], world) / 1e9,
+                "unit": UNIT,
                 "h2d_bytes_per_step": int(np.mean([sum(getattr(pool[j], k).nbytes for k in
                                                        ("row_ptr", "col", "code", "suf", "len", "off", "packed"))
                                                    for j in pick])),
@@ -554,13 +596,10 @@ def run_ours(args, rank, world, local_rank):
         torch.distributed.barrier()
     time.sleep(0.2)
     clocks.stop()
-    ms = statistics.mean(step_ms)
+    ms_rank = statistics.mean(step_ms)
     ms_emit = statistics.mean(emit_ms)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * total / (ms * 1e-3) / 1e9
+    value = job_rate(total, ms_rank * 1e-3, world) / 1e9
+    ms = max_over_ranks(ms_rank, world)
 
     # end to end through the public API with host buffers (pinned inputs / outputs)
     e2e = None
@@ -582,7 +621,7 @@ def run_ours(args, rank, world, local_rank):
             if i > 0:                      # the first one warms the context's buffer pool
                 times.append(b - a)
         te = statistics.mean(times)
-        e2e = {"value": world * total / te / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+        e2e = {"value": job_rate(total, te, world) / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": te * 1e3, "steps": len(times), "path": "cg_load_graph(host, validated) -> "
                "cg_mask_branches -> cg_chains -> cg_emit_contigs(host) -> cg_free_graph"}
 
