@@ -181,6 +181,16 @@ CG_API cg_status cg_chains(cg_graph* g, int32_t* chain_id, int32_t* rank, uint8_
 CG_API cg_status cg_emit_contigs(cg_graph* g, int64_t* contig_off, int64_t contig_off_cap, uint8_t* bases,
                           int64_t bases_cap, int mem, int64_t* n_contigs, int64_t* total_bases);
 
+/* LocalAssembly (Alg. 2; Sec. 4.4) into a 2-bit stream: the same contigs as
+ * cg_emit_contigs, base i of the stream at byte i >> 2, bits 2 (i & 3),
+ * A=0 C=1 G=2 T=3 (the convention of the packed reads); contig c is bases
+ * [contig_off[c], contig_off[c+1]). packed_out: NULL or packed_cap >=
+ * 16 * ceil(total_bases / 64) bytes (whole 16-byte chunks; bits past the last
+ * base are 0), 16-byte aligned when in device memory. Sizes, capacities and
+ * errors as for cg_emit_contigs. */
+CG_API cg_status cg_emit_contigs_2bit(cg_graph* g, int64_t* contig_off, int64_t contig_off_cap, uint8_t* packed_out,
+                               int64_t packed_cap, int mem, int64_t* n_contigs, int64_t* total_bases);
+
 /* GreedyPartitioning (Alg. 2; Sec. 4.3): splits the contigs among n_parts
  * parts (processes, GPUs) with the longest-processing-time rule. Each contig
  * weighs its number of reads (weight CG_WEIGHT_READS, the size estimate of

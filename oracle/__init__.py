@@ -205,3 +205,23 @@ def revcomp(s: str) -> str:
 
 def lpt(sizes, P: int):
     return default().lpt(sizes, P)
+
+
+_CODE2 = np.full(256, 255, dtype=np.uint8)
+for _i, _ch in enumerate(b"ACGT"):
+    _CODE2[_ch] = _i
+
+
+def pack2(ascii_bases) -> np.ndarray:
+    """The 2-bit form of an ASCII base stream, by definition: base i goes to
+    byte i >> 2, bits 2 (i & 3), with A=0 C=1 G=2 T=3 -- the layout of the
+    packed read buffers that Sec. 4.4 concatenates from. ceil(len / 4) bytes."""
+    a = np.frombuffer(bytes(ascii_bases), dtype=np.uint8) if not isinstance(ascii_bases, np.ndarray) else ascii_bases
+    code = _CODE2[a]
+    if code.size and code.max() == 255:
+        raise ValueError("not an A/C/G/T stream")
+    out = np.zeros((code.size + 3) // 4, dtype=np.uint8)
+    for k in range(4):
+        part = code[k::4]
+        out[: part.size] |= (part << (2 * k)).astype(np.uint8)
+    return out

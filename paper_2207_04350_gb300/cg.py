@@ -67,6 +67,8 @@ API = {
                   ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
     "cg_emit_contigs": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
                         ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
+    "cg_emit_contigs_2bit": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                             ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
     "cg_partition_contigs": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64,
                              ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)],
     "cg_sync": [ctypes.c_void_p],
@@ -288,6 +290,24 @@ def cg_emit_contigs(g: Graph, contig_off=None, bases=None, want_counts: bool = T
     return (nc.value, tot.value) if want_counts else None
 
 
+def cg_emit_contigs_2bit(g: Graph, contig_off=None, packed=None, want_counts: bool = True):
+    """Contigs in the 2-bit layout (base i at byte i >> 2, bits 2 (i & 3)); `packed`
+    holds at least packed_bytes_2bit(total_bases) bytes. NULL outputs: sizes only."""
+    nc, tot = ctypes.c_int64(-1), ctypes.c_int64(-1)
+    mem = _mem_of_all([contig_off, packed])
+    ocap = len(contig_off) if contig_off is not None else 0
+    pcap = _nbytes(packed) if packed is not None else 0
+    _check(g.ctx.ptr, lib().cg_emit_contigs_2bit(g.ptr, _ptr(contig_off), ocap, _ptr(packed), pcap, mem,
+                                                 ctypes.byref(nc) if want_counts else None,
+                                                 ctypes.byref(tot) if want_counts else None))
+    return (nc.value, tot.value) if want_counts else None
+
+
+def packed_bytes_2bit(total_bases: int) -> int:
+    """Output bytes of the 2-bit form: whole 16-byte chunks of 64 bases."""
+    return 16 * ((int(total_bases) + 63) // 64)
+
+
 WEIGHT_READS, WEIGHT_BASES = 0, 1
 MAX_PARTS = 1024
 
@@ -448,6 +468,15 @@ def cg_status_str(s: int) -> str:
 
 
 # ------------------------------------------------------- convenience
+def contigs_2bit_host(g: Graph):
+    """Two-call size query, then contig offsets and the 2-bit stream into host arrays."""
+    n_contigs, total = cg_emit_contigs_2bit(g)
+    off = np.empty(n_contigs + 1, dtype=np.int64)
+    packed = np.empty(max(packed_bytes_2bit(total), 16), dtype=np.uint8)
+    cg_emit_contigs_2bit(g, off, packed)
+    return off, packed[: packed_bytes_2bit(total)], total
+
+
 def contigs_host(g: Graph):
     """Two-call size query, then every output into host numpy arrays."""
     n_contigs, total = cg_emit_contigs(g)

@@ -56,7 +56,7 @@ struct cg_graph {
   int64_t stage_bases_cap = 0;
   void* stage_reads = nullptr;
   unsigned long long* d_sum = nullptr;
-  StageExec execs[5];                  // mask, chains, offsets, emission, contig_off export
+  StageExec execs[6];                  // mask, chains, offsets, emission, contig_off export, 2-bit emission
   int batch_k = 0;                     // graphs of a batch (0: a single graph)
   int64_t* batch_R = nullptr;          // device: first read of each graph, batch_k + 1 entries
 };
@@ -841,6 +841,74 @@ cg_status cg_emit_contigs(cg_graph* g, int64_t* contig_off, int64_t contig_off_c
       CK(cudaMemcpyAsync(contig_off, g->s.contig_off, (size_t)(C + 1) * 8, cudaMemcpyDeviceToHost, c->stream),
          "copy contig_off");
     if (bases || contig_off) {
+      st = wait_and_read(g);
+      if (st != CG_OK) return st;
+    }
+  }
+  if (n_contigs) *n_contigs = (int64_t)c->h_ctr->n_contigs;
+  if (total_bases) *total_bases = c->h_ctr->total_bases;
+  return CG_OK;
+}
+
+cg_status cg_emit_contigs_2bit(cg_graph* g, int64_t* contig_off, int64_t contig_off_cap, uint8_t* packed_out,
+                               int64_t packed_cap, int mem, int64_t* n_contigs, int64_t* total_bases) {
+  if (!g) return CG_EINVAL;
+  cg_ctx* c = g->ctx;
+  cg_status st = check_ctx(c);
+  if (st != CG_OK) return st;
+  if (mem != CG_MEM_HOST && mem != CG_MEM_DEVICE) return fail(c, CG_EINVAL, "bad mem");
+  if ((packed_out && packed_cap < 0) || (contig_off && contig_off_cap < 1)) return fail(c, CG_EINVAL, "bad capacity");
+  st = run_offsets(g);
+  if (st != CG_OK) return st;
+  auto emit = [&](uint8_t* dst, int64_t cap) -> cg_status {
+    StageTimer tm(c, 3);
+    uint64_t key = mix_key(mix_key(mix_key((uint64_t)(uintptr_t)dst, (uint64_t)cap), (uint64_t)c->tune.tile_bytes),
+                           (uint64_t)c->tune.emit_blocks_per_sm);
+    return run_stage(g, 5, key, [&]() -> cg_status {
+      CK(cg::launch_emit2(g->g, g->s, c->tune, dst, cap, c->env), "2-bit emission kernel");
+      return CG_OK;
+    });
+  };
+  if (mem == CG_MEM_DEVICE) {
+    if (packed_out) {
+      if (!aligned(packed_out, 16)) return fail(c, CG_EINVAL, "device output buffer must be 16-byte aligned");
+      st = emit(packed_out, packed_cap);
+      if (st != CG_OK) return st;
+    }
+    if (contig_off) {
+      st = run_stage(g, 4, mix_key((uint64_t)(uintptr_t)contig_off, (uint64_t)contig_off_cap), [&]() -> cg_status {
+        CK(cg::launch_export_contig_off(g->s, contig_off, contig_off_cap, c->env), "export contig_off");
+        return CG_OK;
+      });
+      if (st != CG_OK) return st;
+    }
+    if (n_contigs || total_bases) {
+      st = wait_and_read(g);
+      if (st != CG_OK) return st;
+    }
+  } else {
+    st = wait_and_read(g);
+    if (st != CG_OK) return st;
+    const int64_t total = c->h_ctr->total_bases, C = c->h_ctr->n_contigs;
+    const int64_t need = 16 * ((total + 63) / 64);
+    if (packed_out && packed_cap < need)
+      return fail(c, CG_EINVAL, "packed capacity %lld < %lld", (long long)packed_cap, (long long)need);
+    if (contig_off && contig_off_cap < C + 1) return fail(c, CG_EINVAL, "contig_off capacity too small");
+    if (packed_out && need > 0) {
+      if (g->stage_bases_cap < need) {
+        if (g->stage_bases) dfree(c, g->stage_bases);
+        g->stage_bases = (uint8_t*)dalloc(c, (size_t)need, &st);
+        if (!g->stage_bases) { g->stage_bases_cap = 0; return st; }
+        g->stage_bases_cap = need;
+      }
+      st = emit(g->stage_bases, g->stage_bases_cap);
+      if (st != CG_OK) return st;
+      CK(cudaMemcpyAsync(packed_out, g->stage_bases, (size_t)need, cudaMemcpyDeviceToHost, c->stream), "copy packed");
+    }
+    if (contig_off)
+      CK(cudaMemcpyAsync(contig_off, g->s.contig_off, (size_t)(C + 1) * 8, cudaMemcpyDeviceToHost, c->stream),
+         "copy contig_off");
+    if (packed_out || contig_off) {
       st = wait_and_read(g);
       if (st != CG_OK) return st;
     }
