@@ -277,3 +277,47 @@ def csr_from_entries(n: int, entries):
     code = np.array([e[2] for e in ent], dtype=np.uint8)
     suf = np.array([e[3] for e in ent], dtype=np.int32)
     return rp, col, code, suf
+
+
+def xdrop_form(g, max_trim: int = 0, seed: int = 0, consistent: bool = True):
+    """(pre, post) per CSR entry: the x-drop coordinates of each overlap.
+
+    For entry (u -> v) the overlap covers the last ov = len[v] - suf bases of
+    u and the first ov bases of v, both in walk orientation (u walked in
+    orientation 1 - E_u, v in E_v); these are exact overlaps (the generator's
+    and the suffix form's). An aligner that stops early reports the overlap
+    starting t bases later: t_u on u, t_v on v, drawn per entry from `seed`
+    (equal when `consistent`) in [0, cap] with cap = min(max_trim, ov - 1,
+    slack of v), the slack of a read being the fewest bases it has before any
+    of its overlaps minus one, so that the reported overlaps of a read never
+    cross. pre = the stored index of u's last base before the reported overlap;
+    post = the stored index of v's first base in it. Returns int32 (pre, post)."""
+    rp = np.asarray(g.row_ptr, dtype=np.int64)
+    col = np.asarray(g.col, dtype=np.int64)
+    code = np.asarray(g.code, dtype=np.int64)
+    suf = np.asarray(g.suf, dtype=np.int64)
+    ln = np.asarray(g.len, dtype=np.int64)
+    m = col.shape[0]
+    u = np.repeat(np.arange(rp.shape[0] - 1, dtype=np.int64), np.diff(rp))
+    lu, lv = ln[u], ln[col]
+    ov = np.minimum(lv - suf, lu - 1)
+    o_u, o_v = 1 - (code & 1), (code >> 1) & 1
+    slack = np.full(ln.shape[0], np.iinfo(np.int64).max, dtype=np.int64)
+    np.minimum.at(slack, u, lu - ov - 1)
+    rng = np.random.default_rng(seed)
+    cap = np.maximum(np.minimum(np.minimum(max_trim, ov - 1), slack[col]), 0)
+    t_u = np.floor(rng.random(m) * (cap + 1)).astype(np.int64)
+    t_v = t_u if consistent else np.floor(rng.random(m) * (cap + 1)).astype(np.int64)
+    pre_w = lu - ov - 1 + t_u              # walk-orientation index in u
+    post_w = t_v                           # walk-orientation index in v
+    pre = np.where(o_u == 0, pre_w, lu - 1 - pre_w)
+    post = np.where(o_v == 0, post_w, lv - 1 - post_w)
+    return pre.astype(np.int32), post.astype(np.int32)
+
+
+def with_xdrop(g, max_trim: int = 0, seed: int = 0, consistent: bool = True):
+    """A view of graph `g` in the x-drop form: the same fields plus pre and post, suf left out."""
+    from types import SimpleNamespace
+    pre, post = xdrop_form(g, max_trim, seed, consistent)
+    fields = {k: getattr(g, k) for k in ("row_ptr", "col", "code", "len", "off", "packed")}
+    return SimpleNamespace(n=len(g.len), m=len(g.col), suf=None, pre=pre, post=post, **fields)

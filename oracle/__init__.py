@@ -41,6 +41,10 @@ def _bind(lib):
     lib.orc_validate.argtypes = [i64, i64] + [vp] * 6 + [i64, ctypes.c_char_p, ctypes.c_size_t]
     lib.orc_run.restype = vp
     lib.orc_run.argtypes = [i64, i64] + [vp] * 7 + [i64, i32, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    lib.orc_validate2.restype = ctypes.c_int
+    lib.orc_validate2.argtypes = [i64, i64] + [vp] * 8 + [i64, ctypes.c_char_p, ctypes.c_size_t]
+    lib.orc_run2.restype = vp
+    lib.orc_run2.argtypes = [i64, i64] + [vp] * 9 + [i64, i32, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     for f in ("orc_n_branch", "orc_n_contigs", "orc_n_cycles", "orc_total_bases", "orc_n_components",
               "orc_edge_entries_walked"):
         getattr(lib, f).restype = i64
@@ -83,18 +87,27 @@ def source() -> str:
 
 
 def _p(a):
-    return ctypes.c_void_p(a.ctypes.data)
+    return ctypes.c_void_p(a.ctypes.data) if a is not None else None
 
 
 def _inputs(g):
     rp = np.ascontiguousarray(g.row_ptr, dtype=np.int64)
     col = np.ascontiguousarray(g.col, dtype=np.int32)
     code = np.ascontiguousarray(g.code, dtype=np.uint8)
-    suf = np.ascontiguousarray(g.suf, dtype=np.int32)
+    suf = getattr(g, "suf", None)
+    suf = np.ascontiguousarray(suf, dtype=np.int32) if suf is not None else None
     ln = np.ascontiguousarray(g.len, dtype=np.int32)
     off = np.ascontiguousarray(g.off, dtype=np.int64)
     packed = np.ascontiguousarray(g.packed, dtype=np.uint8)
     return rp, col, code, suf, ln, off, packed
+
+
+def _prepost(g):
+    """The x-drop (pre, post) arrays of a graph, or (None, None) for the suffix form."""
+    pre, post = getattr(g, "pre", None), getattr(g, "post", None)
+    if pre is None or post is None:
+        return None, None
+    return np.ascontiguousarray(pre, dtype=np.int32), np.ascontiguousarray(post, dtype=np.int32)
 
 
 @dataclass
@@ -132,19 +145,22 @@ class OracleLib:
 
     def validate(self, g) -> tuple[bool, str]:
         rp, col, code, suf, ln, off, packed = _inputs(g)
+        pre, post = _prepost(g)
         msg = ctypes.create_string_buffer(200)
-        rc = self.lib.orc_validate(len(ln), len(col), _p(rp), _p(col), _p(code), _p(suf), _p(ln), _p(off),
-                                  packed.shape[0], msg, 200)
+        rc = self.lib.orc_validate2(len(ln), len(col), _p(rp), _p(col), _p(code), _p(suf), _p(pre), _p(post),
+                                   _p(ln), _p(off), packed.shape[0], msg, 200)
         return rc == OK, msg.value.decode()
 
     def run(self, g, min_chain_reads: int = 2, validate: bool = True) -> Result:
-        """Contig generation on graph `g` (any object with row_ptr, col, code, suf, len, off, packed)."""
+        """Contig generation on graph `g` (any object with row_ptr, col, code, suf, len, off, packed;
+        with `pre` and `post` arrays as well, the x-drop form of Sec. 4.4 is used and suf is not read)."""
         lib = self.lib
         rp, col, code, suf, ln, off, packed = _inputs(g)
+        pre, post = _prepost(g)
         n, m = len(ln), len(col)
         st = ctypes.c_int(0)
-        h = lib.orc_run(n, m, _p(rp), _p(col), _p(code), _p(suf), _p(ln), _p(off), _p(packed), packed.shape[0],
-                        int(min_chain_reads), 1 if validate else 0, ctypes.byref(st))
+        h = lib.orc_run2(n, m, _p(rp), _p(col), _p(code), _p(suf), _p(pre), _p(post), _p(ln), _p(off), _p(packed),
+                         packed.shape[0], int(min_chain_reads), 1 if validate else 0, ctypes.byref(st))
         if not h:
             raise OracleError(st.value)
         try:

@@ -68,9 +68,10 @@ static int stored_base(const uint8_t* packed, int64_t off, int64_t k) {
  * both directions (S is symmetric, Sec. 4.2) with the two end codes swapped,
  * no read overlaps itself, one entry per ordered pair, and a suffix is a
  * proper, non-empty part of the read it extends (no contained reads). */
-int orc_validate(int64_t n, int64_t m, const int64_t* rp, const int32_t* col, const uint8_t* code,
-                 const int32_t* suf, const int32_t* len, const int64_t* off, int64_t packed_bytes,
-                 char* msg, size_t msglen) {
+int orc_validate2(int64_t n, int64_t m, const int64_t* rp, const int32_t* col, const uint8_t* code,
+                  const int32_t* suf, const int32_t* pre, const int32_t* post, const int32_t* len,
+                  const int64_t* off, int64_t packed_bytes, char* msg, size_t msglen) {
+  const int xdrop = pre != NULL && post != NULL;
 #define BAD(...) do { if (msg && msglen) snprintf(msg, msglen, __VA_ARGS__); return ORC_EGRAPH; } while (0)
   if (n < 0 || m < 0) BAD("negative size");
   if (rp[0] != 0) BAD("row_ptr[0] != 0");
@@ -86,7 +87,12 @@ int orc_validate(int64_t n, int64_t m, const int64_t* rp, const int32_t* col, co
       if (v < 0 || v >= n) BAD("entry %lld: column out of range", (long long)x);
       if (v == u) BAD("entry %lld: self overlap", (long long)x);
       if (code[x] > 3) BAD("entry %lld: code > 3", (long long)x);
-      if (suf[x] < 1 || suf[x] > len[v] - 1) BAD("entry %lld: suffix outside [1, len-1]", (long long)x);
+      if (xdrop) {                 /* indices into the stored reads u and v (Sec. 4.4) */
+        if (pre[x] < 0 || pre[x] > len[u] - 1) BAD("entry %lld: pre outside [0, len-1]", (long long)x);
+        if (post[x] < 0 || post[x] > len[v] - 1) BAD("entry %lld: post outside [0, len-1]", (long long)x);
+      } else if (suf[x] < 1 || suf[x] > len[v] - 1) {
+        BAD("entry %lld: suffix outside [1, len-1]", (long long)x);
+      }
       for (int64_t y = rp[u]; y < x; ++y) if (col[y] == v) BAD("entry %lld: duplicate pair", (long long)x);
       int found = 0;
       for (int64_t y = rp[v]; y < rp[v + 1]; ++y) {
@@ -100,6 +106,12 @@ int orc_validate(int64_t n, int64_t m, const int64_t* rp, const int32_t* col, co
   }
   return ORC_OK;
 #undef BAD
+}
+
+int orc_validate(int64_t n, int64_t m, const int64_t* rp, const int32_t* col, const uint8_t* code,
+                 const int32_t* suf, const int32_t* len, const int64_t* off, int64_t packed_bytes,
+                 char* msg, size_t msglen) {
+  return orc_validate2(n, m, rp, col, code, suf, NULL, NULL, len, off, packed_bytes, msg, msglen);
 }
 
 /* --------------------------------------------------------- BranchRemoval */
@@ -196,7 +208,11 @@ static int deg_L(const int64_t* rp, const int32_t* col, const uint8_t* is_branch
   return d;
 }
 
-typedef struct { int32_t read; uint8_t o; int64_t contrib; } step_t;
+/* One read of a walk: its orientation, the entries through which the walk
+ * enters and leaves it (-1: none), and its piece: `contrib` bases of the
+ * stored read starting at index `first`, upward when o = 0, downward (and
+ * complemented) when o = 1. */
+typedef struct { int32_t read; uint8_t o; int64_t x_in, x_out, first, contrib; } step_t;
 
 /* Walk one component (Sec. 4.4): start at root r with orientation o_r, keep
  * leaving the current read through end 1-o and entering the next read w
@@ -208,7 +224,8 @@ static int64_t walk_component(const int64_t* rp, const int32_t* col, const uint8
                               step_t* out, int64_t* edges_touched) {
   int64_t k = 0, cur = r;
   int o = o_r;
-  out[k].read = (int32_t)r; out[k].o = (uint8_t)o; out[k].contrib = len[r]; ++k;
+  out[k].read = (int32_t)r; out[k].o = (uint8_t)o; out[k].contrib = len[r];
+  out[k].x_in = -1; out[k].x_out = -1; ++k;
   for (;;) {
     int64_t x = edge_at_end(rp, col, code, is_branch, cur, 1 - o);
     if (x < 0) break;
@@ -217,27 +234,60 @@ static int64_t walk_component(const int64_t* rp, const int32_t* col, const uint8
     if (k >= q) return -1;                      /* more reads than the component holds */
     *edges_touched += 2;                        /* the entry used and its mirror */
     o = (code[x] >> 1) & 1;
-    out[k].read = (int32_t)w; out[k].o = (uint8_t)o; out[k].contrib = suf[x]; ++k;
+    out[k - 1].x_out = x;
+    out[k].read = (int32_t)w; out[k].o = (uint8_t)o; out[k].contrib = suf ? suf[x] : 0;
+    out[k].x_in = x; out[k].x_out = -1; ++k;
     cur = w;
   }
   return k;
 }
 
-/* Bases of one step: the last `contrib` bases of read v in orientation o
- * (Sec. 4.4: l[i:j] for i<j is forward, l[j:i] its reverse complement). */
-static void spell(const uint8_t* packed, int64_t off, int32_t L, int o, int64_t contrib, uint8_t* out) {
-  for (int64_t k = L - contrib, t = 0; k < L; ++k, ++t) {
-    int b = (o == 0) ? stored_base(packed, off, k) : 3 - stored_base(packed, off, L - 1 - k);
+/* The piece of each read of a walk (Sec. 4.4), in stored coordinates.
+ * Suffix form: the first read is whole, each later read gives the last
+ * suf(e) bases of its oriented sequence (the bases beyond the overlap).
+ * x-drop form: the contig is l_r[alpha : pre(e_0)] + l_c1[post(e_0) : pre(e_1)]
+ * + ... + l_r'[post(e_last) : beta]: a read runs from post of the entry it is
+ * entered through (alpha, its first base in walk direction, for the first
+ * read) to pre of the entry it is left through (beta, its last base in walk
+ * direction, for the last read). A piece whose end comes before its start in
+ * walk direction is empty (the paper does not say). */
+static void pieces(step_t* w, int64_t k, const int32_t* pre, const int32_t* post, const int32_t* len) {
+  for (int64_t i = 0; i < k; ++i) {
+    step_t* s = &w[i];
+    const int64_t L = len[s->read];
+    const int o = s->o;
+    if (pre && post) {
+      const int64_t first = s->x_in < 0 ? (o == 0 ? 0 : L - 1) : post[s->x_in];
+      const int64_t last = s->x_out < 0 ? (o == 0 ? L - 1 : 0) : pre[s->x_out];
+      const int64_t c = o == 0 ? last - first + 1 : first - last + 1;
+      s->first = first;
+      s->contrib = c > 0 ? c : 0;
+    } else {
+      /* contrib is already len (first read) or suf(e_in); the last contrib
+       * oriented bases start at stored index L - contrib (o = 0) or contrib - 1 */
+      s->first = o == 0 ? L - s->contrib : s->contrib - 1;
+    }
+  }
+}
+
+/* Bases of one step (Sec. 4.4: l[i:j] for i<j is forward, l[j:i] its reverse
+ * complement): contrib bases from stored index `first`, upward for o = 0,
+ * downward and complemented for o = 1. */
+static void spell(const uint8_t* packed, int64_t off, int o, int64_t first, int64_t contrib, uint8_t* out) {
+  for (int64_t t = 0; t < contrib; ++t) {
+    int b = (o == 0) ? stored_base(packed, off, first + t) : 3 - stored_base(packed, off, first - t);
     out[t] = (uint8_t)ASCII[b];
   }
 }
 
-orc_result* orc_run(int64_t n, int64_t m, const int64_t* rp, const int32_t* col, const uint8_t* code,
-                    const int32_t* suf, const int32_t* len, const int64_t* off, const uint8_t* packed,
-                    int64_t packed_bytes, int32_t min_chain_reads, int validate, int* status) {
+orc_result* orc_run2(int64_t n, int64_t m, const int64_t* rp, const int32_t* col, const uint8_t* code,
+                     const int32_t* suf, const int32_t* pre, const int32_t* post, const int32_t* len,
+                     const int64_t* off, const uint8_t* packed, int64_t packed_bytes, int32_t min_chain_reads,
+                     int validate, int* status) {
   *status = ORC_OK;
+  if (!(pre && post)) pre = post = NULL;
   if (validate) {
-    int s = orc_validate(n, m, rp, col, code, suf, len, off, packed_bytes, NULL, 0);
+    int s = orc_validate2(n, m, rp, col, code, suf, pre, post, len, off, packed_bytes, NULL, 0);
     if (s != ORC_OK) { *status = s; return NULL; }
   }
   if (min_chain_reads < 1) min_chain_reads = 1;
@@ -302,6 +352,7 @@ orc_result* orc_run(int64_t n, int64_t m, const int64_t* rp, const int32_t* col,
     }
     r->n_cycles += cycle;
     if (q < min_chain_reads) continue;
+    pieces(walk + nw, k, pre, post, len);
     wstart[nc] = nw; cstart[nc] = total;
     for (int64_t i = 0; i < k; ++i) {
       step_t* s = &walk[nw + i];
@@ -319,13 +370,20 @@ orc_result* orc_run(int64_t n, int64_t m, const int64_t* rp, const int32_t* col,
     int64_t pos = 0;
     for (int64_t i = 0; i < nw; ++i) {
       step_t* s = &walk[i];
-      spell(packed, off[s->read], len[s->read], s->o, s->contrib, r->bases + pos);
+      spell(packed, off[s->read], s->o, s->first, s->contrib, r->bases + pos);
       pos += s->contrib;
     }
   }
   free(cnt); free(members); free(walk); free(wstart); free(cstart);
   if (*status != ORC_OK) { orc_free(r); return NULL; }
   return r;
+}
+
+orc_result* orc_run(int64_t n, int64_t m, const int64_t* rp, const int32_t* col, const uint8_t* code,
+                    const int32_t* suf, const int32_t* len, const int64_t* off, const uint8_t* packed,
+                    int64_t packed_bytes, int32_t min_chain_reads, int validate, int* status) {
+  return orc_run2(n, m, rp, col, code, suf, NULL, NULL, len, off, packed, packed_bytes, min_chain_reads, validate,
+                  status);
 }
 
 int64_t orc_n_branch(const orc_result* r) { return r->n_branch; }

@@ -29,6 +29,18 @@ orc_result* orc_run(int64_t n, int64_t m, const int64_t* row_ptr, const int32_t*
                     const int32_t* suf, const int32_t* len, const int64_t* off, const uint8_t* packed,
                     int64_t packed_bytes, int32_t min_chain_reads, int validate, int* status);
 
+/* The same with the x-drop form of the overlaps (Sec. 4.4) when pre and post
+ * are both non-NULL (then suf is not read and may be NULL): per entry (u->v),
+ * pre = index in stored u of u's last base before the overlap in walk
+ * direction, post = index in stored v of v's first base of the overlap. */
+int orc_validate2(int64_t n, int64_t m, const int64_t* row_ptr, const int32_t* col, const uint8_t* code,
+                  const int32_t* suf, const int32_t* pre, const int32_t* post, const int32_t* len,
+                  const int64_t* off, int64_t packed_bytes, char* msg, size_t msglen);
+orc_result* orc_run2(int64_t n, int64_t m, const int64_t* row_ptr, const int32_t* col, const uint8_t* code,
+                     const int32_t* suf, const int32_t* pre, const int32_t* post, const int32_t* len,
+                     const int64_t* off, const uint8_t* packed, int64_t packed_bytes, int32_t min_chain_reads,
+                     int validate, int* status);
+
 int64_t orc_n_branch(const orc_result* r);
 int64_t orc_n_contigs(const orc_result* r);
 int64_t orc_n_cycles(const orc_result* r);

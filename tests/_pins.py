@@ -525,6 +525,123 @@ def pin_validation(orc):
     assert not orc.validate(H)[0]
 
 
+# ------------------------------------------------------------ x-drop form
+def _xdrop_cases():
+    """The cases of xdrop_examples.txt: name -> (reads, [(pre, post) of l0->l1, of l1->l2], contig)."""
+    out, cur = {}, None
+    for row in golden("xdrop_examples.txt"):
+        if row[0] == "case":
+            cur = out.setdefault(row[1], {"reads": {}, "pp": [], "contig": None})
+        elif row[0] == "read":
+            cur["reads"][row[1]] = row[2]
+        elif row[0] == "prepost":
+            cur["pp"].append((int(row[3]), int(row[4])))
+        elif row[0] == "contig":
+            cur["contig"] = row[1]
+    return out
+
+
+def xdrop_chain(reads, pp, stored1_rc: bool):
+    """l0 - l1 - l2 in the x-drop form. pp holds the walk-direction (pre, post)
+    of the entries l0->l1 and l1->l2 in l1's walk coordinates; with stored1_rc
+    l1 is stored as its reverse complement, so its indices become 7 - i and
+    the codes change ends. The mirror entries get in-range values (the
+    canonical walk starts at l0 and never uses them)."""
+    l0, l1, l2 = reads["l0"], reads["l1"], reads["l2"]
+    L1 = len(l1)
+    t = (lambda i: L1 - 1 - i) if stored1_rc else (lambda i: i)
+    (pre01, post01), (pre12, post12) = pp
+    if not stored1_rc:
+        codes = {(0, 1): 1, (1, 0): 2, (1, 2): 1, (2, 1): 2}
+    else:
+        codes = {(0, 1): 3, (1, 0): 3, (1, 2): 0, (2, 1): 0}
+    vals = {(0, 1): (pre01, t(post01)), (1, 2): (t(pre12), post12),
+            (1, 0): (t(4), len(l0) - 1), (2, 1): (len(l2) - 2, t(L1 - 1))}
+    keys = sorted(vals)
+    ent = [(u, v, codes[(u, v)], 1) for u, v in keys]
+    G = graph_from([l0, rc(l1) if stored1_rc else l1, l2], ent)
+    G.suf = None
+    G.pre = np.array([vals[k][0] for k in keys], np.int32)
+    G.post = np.array([vals[k][1] for k in keys], np.int32)
+    return G
+
+
+def pin_xdrop_examples(orc):
+    """Sec. 4.4, x-drop form: the paper's (pre, post) example spells
+    AGAACTGAAGAA; an overlap reported one base later on one read skips that
+    base; crossing overlaps leave the middle read empty (hand-derived)."""
+    for name, c in _xdrop_cases().items():
+        for stored1_rc in (False, True):
+            G = xdrop_chain(c["reads"], c["pp"], stored1_rc)
+            ok, msg = orc.validate(G)
+            assert ok, (name, msg)
+            for mcr in (1, 3):
+                res = orc.run(G, min_chain_reads=mcr)
+                assert contigs_of(res) == [c["contig"]], (name, stored1_rc)
+                assert res.rank.tolist() == [0, 1, 2]
+                assert res.orient.tolist() == [0, 1 if stored1_rc else 0, 0]
+
+
+def circular_graph(seed: int, genome_len: int = 600, read_len: int = 90, step: int = 30):
+    """Reads tiling a circular genome at a fixed step, random strands: one
+    closed chain whose overlaps are exact (test input)."""
+    rnd = random.Random(seed)
+    genome = "".join(rnd.choice("ACGT") for _ in range(genome_len))
+    q = genome_len // step
+    reads, strand = [], []
+    for i in range(q):
+        s = (genome + genome)[i * step: i * step + read_len]
+        st = rnd.randint(0, 1)
+        reads.append(rc(s) if st else s)
+        strand.append(st)
+    ent = []
+    for i in range(q):
+        u, v = i, (i + 1) % q
+        code = (1 - strand[u]) | (strand[v] << 1)
+        ent.append((u, v, code, step))
+        ent.append((v, u, swap(code), step))
+    return graph_from(reads, ent)
+
+
+def pin_xdrop_matches_suffix_form(orc):
+    """Exact overlaps reported with equal early starts on both reads (any
+    trim) spell the same contigs in the x-drop form as in the suffix form:
+    the walk is the same and the pieces tile the same sequence. Generated
+    graphs (open chains, both strands) and a closed chain."""
+    graphs = [tiny_generated(), small_generated(3), circular_graph(4), circular_graph(9, 900, 120, 45)]
+    for G in graphs:
+        want = orc.run(G, min_chain_reads=1)
+        for trim, seed in ((0, 0), (40, 1), (5000, 2)):
+            X = gen.with_xdrop(G, max_trim=trim, seed=seed, consistent=True)
+            got = orc.run(X, min_chain_reads=1)
+            assert np.array_equal(got.contig_off, want.contig_off)
+            assert np.array_equal(got.bases, want.bases)
+            assert np.array_equal(got.chain_id, want.chain_id) and np.array_equal(got.rank, want.rank)
+    # unequal starts change the contigs (the skewed and crossed cases pin how)
+    X = gen.with_xdrop(graphs[2], max_trim=20, seed=3, consistent=False)
+    assert not np.array_equal(orc.run(X, min_chain_reads=1).bases, orc.run(graphs[2], min_chain_reads=1).bases)
+
+
+def pin_xdrop_validation(orc):
+    """x-drop coordinates index the stored reads: pre into u, post into v."""
+    c = _xdrop_cases()["paper"]
+    G = xdrop_chain(c["reads"], c["pp"], False)      # len l0 = 6, l1 = 8, l2 = 7
+    def with_(i, pre=None, post=None):
+        H = SimpleNamespace(**{k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in vars(G).items()})
+        if pre is not None:
+            H.pre[i] = pre
+        if post is not None:
+            H.post[i] = post
+        return H
+    # entries in CSR order: (0,1), (1,0), (1,2), (2,1)
+    assert orc.validate(with_(2, pre=7))[0]           # pre = len(l1) - 1 of u = l1 (> len(l2) - 1)
+    assert not orc.validate(with_(0, pre=6))[0]       # pre = len(l0) of u = l0 (< len(l1) - 1)
+    assert not orc.validate(with_(0, pre=-1))[0]
+    assert orc.validate(with_(0, post=7))[0]          # post into v = l1
+    assert not orc.validate(with_(2, post=7))[0]      # post = len(l2) of v = l2
+    assert not orc.validate(with_(1, post=-1))[0]
+
+
 ALL_PINS = [pin_paper_mask_example, pin_paper_concat_example, pin_paper_rc_example, pin_revcomp,
             pin_same_end_rule, pin_brute_force, pin_cycles, pin_generator_truth, pin_invariants, pin_lpt,
-            pin_validation]
+            pin_validation, pin_xdrop_examples, pin_xdrop_matches_suffix_form, pin_xdrop_validation]

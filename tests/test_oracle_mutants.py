@@ -8,12 +8,19 @@ from tests import _pins
 
 # (name, text in cg_oracle.c, replacement)
 MUTANTS = [
-    ("suffix_complement", "out[k].contrib = suf[x];", "out[k].contrib = len[w] - suf[x];"),
+    ("suffix_complement", "out[k].contrib = suf ? suf[x] : 0;", "out[k].contrib = suf ? len[w] - suf[x] : 0;"),
     ("entry_end_from_own_bit", "o = (code[x] >> 1) & 1;", "o = code[x] & 1;"),
     ("leave_through_entry_end", "edge_at_end(rp, col, code, is_branch, cur, 1 - o)", "edge_at_end(rp, col, code, is_branch, cur, o)"),
-    ("rc_without_complement", "3 - stored_base(packed, off, L - 1 - k)", "stored_base(packed, off, L - 1 - k)"),
-    ("rc_without_reversal", "3 - stored_base(packed, off, L - 1 - k)", "3 - stored_base(packed, off, k)"),
-    ("prefix_not_suffix", "for (int64_t k = L - contrib, t = 0; k < L; ++k, ++t)", "for (int64_t k = 0, t = 0; k < contrib; ++k, ++t)"),
+    ("rc_without_complement", "3 - stored_base(packed, off, first - t)", "stored_base(packed, off, first - t)"),
+    ("rc_without_reversal", "3 - stored_base(packed, off, first - t)", "3 - stored_base(packed, off, first + t)"),
+    ("prefix_not_suffix", "s->first = o == 0 ? L - s->contrib : s->contrib - 1;", "s->first = o == 0 ? 0 : L - 1;"),
+    ("xdrop_post_from_pre", ": post[s->x_in];", ": pre[s->x_in];"),
+    ("xdrop_exclusive_end", "o == 0 ? last - first + 1 : first - last + 1;", "o == 0 ? last - first : first - last;"),
+    ("xdrop_alpha_flipped", "s->x_in < 0 ? (o == 0 ? 0 : L - 1)", "s->x_in < 0 ? (o == 0 ? L - 1 : 0)"),
+    ("xdrop_beta_flipped", "s->x_out < 0 ? (o == 0 ? L - 1 : 0)", "s->x_out < 0 ? (o == 0 ? 0 : L - 1)"),
+    ("xdrop_cycle_keeps_closing_edge", "if (w == r) { *edges_touched += 2; break; }",
+     "if (w == r) { *edges_touched += 2; out[k - 1].x_out = x; break; }"),
+    ("xdrop_validate_pre_against_v", "if (pre[x] < 0 || pre[x] > len[u] - 1)", "if (pre[x] < 0 || pre[x] > len[v] - 1)"),
     ("degree_threshold_4", "b1[v] = (uint8_t)(d >= 3);", "b1[v] = (uint8_t)(d >= 4);"),
     ("degree_threshold_2", "b1[v] = (uint8_t)(d >= 3);", "b1[v] = (uint8_t)(d >= 2);"),
     ("no_same_end_rule", "if (cnt == 2 && ends[0] == ends[1]) br = 1;", "if (0) br = 1;"),
