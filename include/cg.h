@@ -89,6 +89,15 @@ typedef struct {
   int64_t packed_bytes;
   int32_t min_chain_reads; /* chains with fewer reads are not contigs; <= 0 means 2 (Sec. 4.4) */
   int32_t reserved;
+  /* The x-drop form of the overlaps (Sec. 4.4), optional. When both are
+   * non-NULL they replace suf (which may then be NULL) and each contig is
+   * l_r[alpha : pre(e_0)] + l_c1[post(e_0) : pre(e_1)] + ... + l_r'[post : beta].
+   * For entry (u->v): pre = index in stored u of u's last base before the
+   * overlap in walk direction, in [0, len[u]-1]; post = index in stored v of
+   * v's first base of the overlap, in [0, len[v]-1]. A read piece whose end
+   * comes before its start in walk direction adds no bases. */
+  const int32_t* pre;      /* m */
+  const int32_t* post;     /* m */
 } cg_graph_desc;
 
 /* Create a context on CUDA device `device`. hbm_budget_bytes caps the device

@@ -40,7 +40,8 @@ class GraphDesc(ctypes.Structure):
                 ("row_ptr_bytes", ctypes.c_int32), ("mem", ctypes.c_int32), ("col", ctypes.c_void_p),
                 ("code", ctypes.c_void_p), ("suf", ctypes.c_void_p), ("len", ctypes.c_void_p),
                 ("off", ctypes.c_void_p), ("packed", ctypes.c_void_p), ("packed_bytes", ctypes.c_int64),
-                ("min_chain_reads", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("min_chain_reads", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("pre", ctypes.c_void_p), ("post", ctypes.c_void_p)]
 
 
 class ServerOpts(ctypes.Structure):
@@ -205,33 +206,32 @@ def cg_destroy(ctx: Context):
 
 
 def cg_load_graph(ctx: Context, graph, flags: int = 0, min_chain_reads: int = 2) -> Graph:
-    """cg_load_graph from any object with row_ptr, col, code, suf, len, off, packed."""
-    arrs = [graph.row_ptr, graph.col, graph.code, graph.suf, graph.len, graph.off, graph.packed]
-    mem = _mem_of_all(arrs)
-    rp = graph.row_ptr
-    rp_bytes = rp.element_size() if _is_torch(rp) else rp.dtype.itemsize
-    d = GraphDesc()
-    d.n_reads = len(graph.len)
-    d.n_entries = len(graph.col)
-    d.row_ptr, d.row_ptr_bytes, d.mem = _ptr(rp), rp_bytes, mem
-    d.col, d.code, d.suf = _ptr(graph.col), _ptr(graph.code), _ptr(graph.suf)
-    d.len, d.off, d.packed = _ptr(graph.len), _ptr(graph.off), _ptr(graph.packed)
-    d.packed_bytes = _nbytes(graph.packed)
-    d.min_chain_reads = int(min_chain_reads)
+    """cg_load_graph from any object with row_ptr, col, code, suf, len, off, packed
+    (and pre, post for the x-drop form)."""
+    d = _desc(graph, min_chain_reads)
     out = ctypes.c_void_p()
     _check(ctx.ptr, lib().cg_load_graph(ctx.ptr, ctypes.byref(d), int(flags), ctypes.byref(out)))
-    return Graph(ctx, out, arrs if flags & BORROW_DEVICE else None, d.n_reads)
+    keep = [getattr(graph, k, None) for k in ("row_ptr", "col", "code", "suf", "len", "off", "packed", "pre", "post")]
+    return Graph(ctx, out, keep if flags & BORROW_DEVICE else None, d.n_reads)
 
 
 def _desc(graph, min_chain_reads):
-    arrs = [graph.row_ptr, graph.col, graph.code, graph.suf, graph.len, graph.off, graph.packed]
+    """The cg_graph_desc of `graph`: an object with row_ptr, col, code, suf, len,
+    off and packed (numpy arrays or torch tensors); with `pre` and `post` as
+    well it is in the x-drop form and suf may be None."""
+    pre, post = getattr(graph, "pre", None), getattr(graph, "post", None)
+    if pre is None or post is None:
+        pre = post = None
+    suf = getattr(graph, "suf", None)
+    arrs = [graph.row_ptr, graph.col, graph.code, suf, graph.len, graph.off, graph.packed, pre, post]
     mem = _mem_of_all(arrs)
     rp = graph.row_ptr
     d = GraphDesc()
     d.n_reads = len(graph.len)
     d.n_entries = len(graph.col)
     d.row_ptr, d.row_ptr_bytes, d.mem = _ptr(rp), (rp.element_size() if _is_torch(rp) else rp.dtype.itemsize), mem
-    d.col, d.code, d.suf = _ptr(graph.col), _ptr(graph.code), _ptr(graph.suf)
+    d.col, d.code, d.suf = _ptr(graph.col), _ptr(graph.code), _ptr(suf)
+    d.pre, d.post = _ptr(pre), _ptr(post)
     d.len, d.off, d.packed = _ptr(graph.len), _ptr(graph.off), _ptr(graph.packed)
     d.packed_bytes = _nbytes(graph.packed)
     d.min_chain_reads = int(min_chain_reads)

@@ -283,6 +283,10 @@ cg_status finish_load(cg_graph* g, uint32_t flags) {
   S.wp = galloc<unsigned>(g, NW, &st);
   S.succ = galloc<int2>(g, N, &st);
   S.sufin = galloc<int32_t>(g, N2, &st);
+  if (G.pre) {
+    S.preout = galloc<int32_t>(g, N2, &st);
+    S.pfirst = galloc<int32_t>(g, N, &st);
+  }
   S.rid = galloc<int32_t>(g, N2, &st);
   S.roff = galloc<int32_t>(g, N2, &st);
   S.rlist = galloc<int32_t>(g, N2, &st);
@@ -542,13 +546,15 @@ cg_status cg_load_graph(cg_ctx* c, const cg_graph_desc* d, uint32_t flags, cg_gr
   if (m < 0 || m >= (1ll << 31)) return fail(c, CG_EINVAL, "n_entries out of range");
   if (d->row_ptr_bytes != 4 && d->row_ptr_bytes != 8) return fail(c, CG_EINVAL, "row_ptr_bytes must be 4 or 8");
   if (d->mem != CG_MEM_HOST && d->mem != CG_MEM_DEVICE) return fail(c, CG_EINVAL, "bad mem");
-  if (!d->row_ptr || (m > 0 && (!d->col || !d->code || !d->suf)) || (n > 0 && (!d->len || !d->off)) ||
+  const bool xdrop = d->pre && d->post;
+  if (!d->row_ptr || (m > 0 && (!d->col || !d->code || (!xdrop && !d->suf))) || (n > 0 && (!d->len || !d->off)) ||
       d->packed_bytes < 0 || (d->packed_bytes > 0 && !d->packed))
     return fail(c, CG_EINVAL, "missing input array");
   const bool borrow = (flags & CG_BORROW_DEVICE) != 0;
   if (borrow && d->mem != CG_MEM_DEVICE) return fail(c, CG_EINVAL, "CG_BORROW_DEVICE needs device inputs");
   if (borrow && (!aligned(d->packed, 16) || !aligned(d->row_ptr, d->row_ptr_bytes) || !aligned(d->col, 4) ||
-                 !aligned(d->suf, 4) || !aligned(d->len, 4) || !aligned(d->off, 8)))
+                 (!xdrop && !aligned(d->suf, 4)) || (xdrop && (!aligned(d->pre, 4) || !aligned(d->post, 4))) ||
+                 !aligned(d->len, 4) || !aligned(d->off, 8)))
     return fail(c, CG_EINVAL, "borrowed device inputs are misaligned");
 
   cg_graph* g = new (std::nothrow) cg_graph();
@@ -571,7 +577,9 @@ cg_status cg_load_graph(cg_ctx* c, const cg_graph_desc* d, uint32_t flags, cg_gr
     G.row_ptr = d->row_ptr;
     G.col = d->col;
     G.code = d->code;
-    G.suf = d->suf;
+    G.suf = xdrop ? nullptr : d->suf;
+    G.pre = xdrop ? d->pre : nullptr;
+    G.post = xdrop ? d->post : nullptr;
     G.len = d->len;
     G.off = d->off;
     G.packed = d->packed;
@@ -590,7 +598,12 @@ cg_status cg_load_graph(cg_ctx* c, const cg_graph_desc* d, uint32_t flags, cg_gr
     G.row_ptr = copy_in(d->row_ptr, (size_t)(n + 1) * d->row_ptr_bytes, 0);
     if (st == CG_OK) G.col = (const int32_t*)copy_in(d->col, (size_t)m * 4, 0);
     if (st == CG_OK) G.code = (const uint8_t*)copy_in(d->code, (size_t)m, 0);
-    if (st == CG_OK) G.suf = (const int32_t*)copy_in(d->suf, (size_t)m * 4, 0);
+    if (xdrop) {
+      if (st == CG_OK) G.pre = (const int32_t*)copy_in(d->pre, (size_t)m * 4, 0);
+      if (st == CG_OK) G.post = (const int32_t*)copy_in(d->post, (size_t)m * 4, 0);
+    } else if (st == CG_OK) {
+      G.suf = (const int32_t*)copy_in(d->suf, (size_t)m * 4, 0);
+    }
     if (st == CG_OK) G.len = (const int32_t*)copy_in(d->len, (size_t)n * 4, 0);
     if (st == CG_OK) G.off = (const int64_t*)copy_in(d->off, (size_t)n * 8, 0);
     if (st == CG_OK) G.packed = (const uint8_t*)copy_in(d->packed, (size_t)d->packed_bytes, 16);
@@ -610,14 +623,15 @@ cg_status cg_load_batch(cg_ctx* c, const cg_graph_desc* d, int k, uint32_t flags
   *out = nullptr;
   if (flags & CG_BORROW_DEVICE) return fail(c, CG_EINVAL, "a batch is always copied into one union graph");
   const int mem = d[0].mem, rpb = d[0].row_ptr_bytes, mcr = d[0].min_chain_reads;
+  const bool xdrop = d[0].pre && d[0].post;
   std::vector<int64_t> R(k + 1, 0), E(k + 1, 0), PB(k + 1, 0), SR(k + 1, 0);
   for (int j = 0; j < k; ++j) {
     const cg_graph_desc& q = d[j];
-    if (q.mem != mem || q.row_ptr_bytes != rpb || q.min_chain_reads != mcr)
-      return fail(c, CG_EINVAL, "graph %d: mem, row_ptr_bytes and min_chain_reads must match the batch", j);
+    if (q.mem != mem || q.row_ptr_bytes != rpb || q.min_chain_reads != mcr || (q.pre && q.post) != xdrop)
+      return fail(c, CG_EINVAL, "graph %d: mem, row_ptr_bytes, min_chain_reads and the overlap form must match", j);
     if ((rpb != 4 && rpb != 8) || (mem != CG_MEM_HOST && mem != CG_MEM_DEVICE)) return fail(c, CG_EINVAL, "bad desc");
     if (q.n_reads < 0 || q.n_entries < 0 || q.packed_bytes < 0 || !q.row_ptr ||
-        (q.n_entries > 0 && (!q.col || !q.code || !q.suf)) || (q.n_reads > 0 && (!q.len || !q.off)) ||
+        (q.n_entries > 0 && (!q.col || !q.code || (!xdrop && !q.suf))) || (q.n_reads > 0 && (!q.len || !q.off)) ||
         (q.packed_bytes > 0 && !q.packed))
       return fail(c, CG_EINVAL, "graph %d: missing input array", j);
     R[j + 1] = R[j] + q.n_reads;
@@ -645,7 +659,9 @@ cg_status cg_load_batch(cg_ctx* c, const cg_graph_desc* d, int k, uint32_t flags
   int64_t* rp = galloc<int64_t>(g, (size_t)n + 1, &st);
   int32_t* col = galloc<int32_t>(g, (size_t)(m > 0 ? m : 1), &st);
   uint8_t* code = galloc<uint8_t>(g, (size_t)(m > 0 ? m : 1), &st);
-  int32_t* suf = galloc<int32_t>(g, (size_t)(m > 0 ? m : 1), &st);
+  int32_t* suf = xdrop ? nullptr : galloc<int32_t>(g, (size_t)(m > 0 ? m : 1), &st);
+  int32_t* pre = xdrop ? galloc<int32_t>(g, (size_t)(m > 0 ? m : 1), &st) : nullptr;
+  int32_t* post = xdrop ? galloc<int32_t>(g, (size_t)(m > 0 ? m : 1), &st) : nullptr;
   int32_t* len = galloc<int32_t>(g, (size_t)(n > 0 ? n : 1), &st);
   int64_t* off = galloc<int64_t>(g, (size_t)(n > 0 ? n : 1), &st);
   uint8_t* packed = galloc<uint8_t>(g, (size_t)PB[k] + 16, &st);
@@ -663,7 +679,9 @@ cg_status cg_load_batch(cg_ctx* c, const cg_graph_desc* d, int k, uint32_t flags
     cudaError_t e = cp((char*)stage_rp + (size_t)SR[j] * rpb, q.row_ptr, (size_t)(q.n_reads + 1) * rpb);
     if (e == cudaSuccess) e = cp(col + E[j], q.col, (size_t)q.n_entries * 4);
     if (e == cudaSuccess) e = cp(code + E[j], q.code, (size_t)q.n_entries);
-    if (e == cudaSuccess) e = cp(suf + E[j], q.suf, (size_t)q.n_entries * 4);
+    if (e == cudaSuccess && !xdrop) e = cp(suf + E[j], q.suf, (size_t)q.n_entries * 4);
+    if (e == cudaSuccess && xdrop) e = cp(pre + E[j], q.pre, (size_t)q.n_entries * 4);
+    if (e == cudaSuccess && xdrop) e = cp(post + E[j], q.post, (size_t)q.n_entries * 4);
     if (e == cudaSuccess) e = cp(len + R[j], q.len, (size_t)q.n_reads * 4);
     if (e == cudaSuccess) e = cp(off + R[j], q.off, (size_t)q.n_reads * 8);
     if (e == cudaSuccess) e = cp(packed + PB[j], q.packed, (size_t)q.packed_bytes);
@@ -683,6 +701,8 @@ cg_status cg_load_batch(cg_ctx* c, const cg_graph_desc* d, int k, uint32_t flags
   G.col = col;
   G.code = code;
   G.suf = suf;
+  G.pre = pre;
+  G.post = post;
   G.len = len;
   G.off = off;
   G.packed = packed;

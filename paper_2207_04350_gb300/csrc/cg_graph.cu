@@ -105,8 +105,13 @@ __global__ void k_validate_entries(DevGraph g, DevError* c) {
       int32_t v = g.col[x];
       uint8_t cd = g.code[x];
       if (v < 0 || v >= g.n || v == u || cd > 3) { set_error(c, DERR_GRAPH, K_VALIDATE2, x); continue; }
-      int32_t s = g.suf[x];
-      if (s < 1 || s > g.len[v] - 1) set_error(c, DERR_GRAPH, K_VALIDATE2, x);
+      if (g.pre) {                         // x-drop form: indices into the stored reads u and v
+        const int32_t p = g.pre[x], q = g.post[x];
+        if (p < 0 || p > g.len[u] - 1 || q < 0 || q > g.len[v] - 1) set_error(c, DERR_GRAPH, K_VALIDATE2, x);
+      } else {
+        const int32_t s = g.suf[x];
+        if (s < 1 || s > g.len[v] - 1) set_error(c, DERR_GRAPH, K_VALIDATE2, x);
+      }
       for (int64_t y = a; y < x; ++y)
         if (g.col[y] == v) set_error(c, DERR_GRAPH, K_VALIDATE2, x);
       int64_t va = max((int64_t)0, min(rowp(g, v), g.m)), vb = max(va, min(rowp(g, v + 1), g.m));
@@ -212,7 +217,12 @@ __global__ void __launch_bounds__(kBlock) k_succ(DevGraph g, Scratch s, int rule
         int ev = cd & 1, ew = cd >> 1;
         int to = 2 * w + ew;
         if (ev == 1) s0 = to; else s1 = to;
-        s.sufin[to] = g.suf[x];
+        if (g.pre) {                       // (v, 1-ev) leaves through end ev
+          s.sufin[to] = g.post[x];
+          s.preout[2 * v + 1 - ev] = g.pre[x];
+        } else {
+          s.sufin[to] = g.suf[x];
+        }
       }
       s.succ[v] = make_int2(s0, s1);
       if (s0 < 0 && s1 < 0) {            // every overlap leads to a branch read
@@ -371,6 +381,21 @@ __global__ void k_jump(Scratch s) {
   if (grid_tid() == 0) c->final_buf = (unsigned)cur;
 }
 
+// x-drop form (Sec. 4.4): read v, walked as oriented read y at rank rk of a
+// contig of q reads, contributes l_v[post(e_in) : pre(e_out)] with alpha (its
+// first base in walk direction) for the first read and beta (its last) for
+// the last one; a piece whose end comes before its start is empty.
+__device__ __forceinline__ void set_piece(const DevGraph& g, const Scratch& s, int32_t v, int32_t y, int32_t rk,
+                                          int32_t q) {
+  const int o = y & 1;
+  const int32_t L = g.len[v];
+  const int32_t first = rk == 0 ? (o == 0 ? 0 : L - 1) : s.sufin[y];
+  const int32_t last = rk == q - 1 ? (o == 0 ? L - 1 : 0) : s.preout[y];
+  const int32_t cnt = o == 0 ? last - first + 1 : first - last + 1;
+  s.contrib[v] = cnt > 0 ? cnt : 0;
+  s.pfirst[v] = first;
+}
+
 // Per chain read: combine its two oriented copies. head(list of (v,0)) is
 // the reverse of tail(list of (v,1)). The contig starts at the smaller-id
 // end read, so (v,0) is the walk orientation when that end heads the list
@@ -410,7 +435,8 @@ __global__ void k_final(DevGraph g, Scratch s) {
           s.cid[v] = m;
           s.rank[v] = rk;
           s.orient[v] = (uint8_t)o;
-          s.contrib[v] = rk == 0 ? g.len[v] : s.sufin[x0 + o];
+          if (g.pre) set_piece(g, s, v, x0 + o, rk, q);
+          else s.contrib[v] = rk == 0 ? g.len[v] : s.sufin[x0 + o];
           if (v == m) {
             mark_head(s, m, q);
             atomicAdd(&c->n_heads, 1u);
@@ -505,7 +531,8 @@ __global__ void k_cycles(DevGraph g, Scratch s) {
       s.cid[v] = m;
       s.rank[v] = rk;
       s.orient[v] = (uint8_t)(y & 1);
-      s.contrib[v] = rk == 0 ? g.len[v] : s.sufin[y];
+      if (g.pre) set_piece(g, s, v, y, rk, L);
+      else s.contrib[v] = rk == 0 ? g.len[v] : s.sufin[y];
       if (rk == 0) {
         mark_head(s, m, L);
         atomicAdd(&c->n_heads, 1u);

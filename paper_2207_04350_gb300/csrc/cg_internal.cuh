@@ -61,7 +61,9 @@ struct DevGraph {
   int min_chain;               // >= 1
   const int32_t* col;
   const uint8_t* code;
-  const int32_t* suf;
+  const int32_t* suf;          // suffix form, or
+  const int32_t* pre;          // x-drop form (Sec. 4.4): pre and post per entry, nullptr in the suffix form
+  const int32_t* post;
   const int32_t* len;
   const int64_t* off;
   const uint8_t* packed;
@@ -79,7 +81,9 @@ struct Scratch {
   unsigned* hb_mask;    // n/32+1: heads bitmap words of the mask stage
   unsigned* hb;         // n/32+1: bit m set when read m is the smallest read of a contig
   int2* succ;           // n: (successor of (v,fwd), successor of (v,rc)) as oriented ids 2w+o, or -1
-  int32_t* sufin;       // 2n: suffix of the overlap entering oriented read x
+  int32_t* sufin;       // 2n: suffix (x-drop form: post) of the overlap entering oriented read x
+  int32_t* preout;      // 2n, x-drop form only: pre of the overlap leaving oriented read x
+  int32_t* pfirst;      // n, x-drop form only: stored index of the piece's first base
   int32_t* rid;         // 2n: sublist of oriented read x (-1: not reached)
   int32_t* roff;        // 2n: position of x inside its sublist
   // sublists (capacity 2n)

@@ -224,8 +224,12 @@ __global__ void k_scatter(DevGraph g, Scratch s) {
     const int o = s.orient[v];
     const int32_t L = g.len[v], cb = s.contrib[v];
     const int64_t base = g.off[v];
-    const unsigned long long src = o == 0 ? (unsigned long long)(base + L - cb)
-                                          : ((unsigned long long)(base + cb - 1) | (1ull << 63));
+    // stored index of the piece's first base: suffix form, the last cb bases
+    // of the oriented read; x-drop form, set by the chain stage (a read spelled
+    // alone is whole and forward)
+    const int64_t first = !g.pre ? (o == 0 ? L - cb : cb - 1) : (k < L1 + L2 ? 0 : s.pfirst[v]);
+    const unsigned long long src = o == 0 ? (unsigned long long)(base + first)
+                                          : ((unsigned long long)(base + first) | (1ull << 63));
     s.wsrc[pos] = src;
     s.wlen[pos] = cb;
     if (rk == 0) s.cstart[cidx] = (int32_t)pos;

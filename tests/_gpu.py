@@ -12,8 +12,9 @@ def run_gpu(ctx, G, min_chain_reads=2, inputs="host", outputs="host", flags=0):
     import torch
     src = G
     if inputs == "device":
+        keys = ["row_ptr", "col", "code", "suf", "len", "off", "packed", "pre", "post"]
         src = SimpleNamespace(**{k: torch.from_numpy(np.ascontiguousarray(getattr(G, k))).cuda()
-                                 for k in ("row_ptr", "col", "code", "suf", "len", "off", "packed")})
+                                 if getattr(G, k, None) is not None else None for k in keys})
     g = cg.cg_load_graph(ctx, src, flags=flags, min_chain_reads=min_chain_reads)
     try:
         n = g.n
