@@ -525,7 +525,8 @@ def run_ours(args, rank, world, local_rank):
     g = cg.cg_load_graph(ctx, dg, flags=cg.BORROW_DEVICE, min_chain_reads=args.min_chain_reads)
     # sizes (untimed): walk positions, contigs, bases
     cid = np.empty(G.n, np.int32)
-    cg.cg_chains(g, cid, None, None)
+    rank_h = np.empty(G.n, np.int32)
+    cg.cg_chains(g, cid, rank_h, None)
     W = int((cid >= 0).sum())
     n_contigs, total = cg.cg_emit_contigs(g)
     bases = torch.empty(max(16, (total + 15) // 16 * 16), dtype=torch.uint8, device="cuda")
@@ -576,6 +577,11 @@ def run_ours(args, rank, world, local_rank):
         step()
         for name, kms in cg.cg_kernel_times(ctx):
             kern.setdefault(name, []).append(kms)
+    # assembly quality against the generator's truth (the paper's Table 4 analog)
+    from gen import quality as _quality
+    qual = _quality.contig_quality(G, cid, rank_h, contig_off.cpu().numpy())
+    qual["source"] = "this run's chains and contig offsets against the generator's read placements"
+
     # the same steps with the 2-bit output form (outside the timed steps above)
     packed2 = torch.empty(max(16, cg.packed_bytes_2bit(total)), dtype=torch.uint8, device="cuda")
 
@@ -722,6 +728,7 @@ def run_ours(args, rank, world, local_rank):
             "partition": partition,
             "emit_2bit": emit_2bit,
             "xdrop": xdrop,
+            "quality": qual,
             "B_min_bytes": B, "path_achieved_gbs": B / (ms * 1e-3) / 1e9,
             "path_roofline_frac": B / (ms * 1e-3) / 1e9 / pk["hbm_gbs"],
             "path_roofline_frac_8tbs": B / (ms * 1e-3) / 1e9 / 8000.0,
