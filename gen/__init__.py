@@ -51,7 +51,7 @@ class GenCfg(ctypes.Structure):
                 ("len_kind", ctypes.c_int32), ("len_min", ctypes.c_int32), ("len_a", ctypes.c_double),
                 ("len_b", ctypes.c_double), ("min_overlap", ctypes.c_int32), ("k_rep", ctypes.c_int32),
                 ("rep_div_accept", ctypes.c_double), ("threads", ctypes.c_int32), ("shuffle_ids", ctypes.c_int32),
-                ("off_align", ctypes.c_int32), ("_pad1", ctypes.c_int32)]
+                ("off_align", ctypes.c_int32), ("full_overlaps", ctypes.c_int32)]
 
 
 class GenInfo(ctypes.Structure):
@@ -143,6 +143,7 @@ def make_cfg(d: dict, threads: int | None = None, off_align: int = 32, shuffle_i
     c.threads = int(threads or min(32, os.cpu_count() or 1))
     c.shuffle_ids = 1 if shuffle_ids else 0
     c.off_align = int(off_align)
+    c.full_overlaps = int(d.get("full_overlaps", 0))
     return c
 
 

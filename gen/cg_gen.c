@@ -437,20 +437,34 @@ cg_gen* cg_gen_plan(const cg_gen_cfg* cfg) {
   }
 
   /* 7. edges among non-contained reads: consecutive overlaps >= min_overlap
-   * (the transitive reduction of an exact interval overlap graph), then
-   * repeat-induced ones; pair endpoints are kept-read indices here */
-  int64_t cap = K + (int64_t)K * (f->k_rep > 0 ? f->k_rep : 0) + 1;
+   * (the transitive reduction of an exact interval overlap graph), or with
+   * full_overlaps every overlapping pair (the graph before that reduction),
+   * then repeat-induced ones; pair endpoints are kept-read indices here.
+   * Kept reads are sorted by start and none contains another, so their ends
+   * increase too and the reads overlapping k by >= min_overlap are k+1 .. */
+  int64_t span_total = 0;
+  for (int64_t k = 0; k + 1 < K; ++k) {
+    int64_t j = k + 1;
+    if (f->full_overlaps)
+      while (j < K && g->ke[k] - g->ks[j] >= f->min_overlap) ++j;
+    else if (g->ke[k] - g->ks[j] >= f->min_overlap)
+      ++j;
+    span_total += j - (k + 1);
+  }
+  int64_t cap = span_total + (int64_t)K * (f->k_rep > 0 ? f->k_rep : 0) + 1;
   pair_t* pr = (pair_t*)malloc((size_t)cap * sizeof(pair_t));
   int64_t np = 0;
   for (int64_t k = 0; k + 1 < K; ++k) {
-    int64_t ov = g->ke[k] - g->ks[k + 1];
-    if (ov < f->min_overlap) continue;
-    pair_t* q = &pr[np++];
-    q->a = (int32_t)k; q->b = (int32_t)(k + 1); q->is_true = 1; q->pad = 0;
-    q->code_ab = (uint8_t)(e_right(g->kst[k]) | (e_left(g->kst[k + 1]) << 1));
-    q->code_ba = (uint8_t)(e_left(g->kst[k + 1]) | (e_right(g->kst[k]) << 1));
-    q->suf_ab = (int32_t)(g->ke[k + 1] - g->ke[k]);
-    q->suf_ba = (int32_t)(g->ks[k + 1] - g->ks[k]);
+    for (int64_t j = k + 1; j < K && (f->full_overlaps || j == k + 1); ++j) {
+      int64_t ov = g->ke[k] - g->ks[j];
+      if (ov < f->min_overlap) break;
+      pair_t* q = &pr[np++];
+      q->a = (int32_t)k; q->b = (int32_t)j; q->is_true = 1; q->pad = 0;
+      q->code_ab = (uint8_t)(e_right(g->kst[k]) | (e_left(g->kst[j]) << 1));
+      q->code_ba = (uint8_t)(e_left(g->kst[j]) | (e_right(g->kst[k]) << 1));
+      q->suf_ab = (int32_t)(g->ke[j] - g->ke[k]);
+      q->suf_ba = (int32_t)(g->ks[j] - g->ks[k]);
+    }
   }
   if (f->k_rep > 0 && g->n_copy > 0) {
     pair_t* rp = (pair_t*)malloc((size_t)K * f->k_rep * sizeof(pair_t));

@@ -30,7 +30,8 @@ typedef struct {
   double rep_div_accept; /* a repeat edge needs div(X) + div(Y) <= this */
   int32_t threads, shuffle_ids;
   int32_t off_align;   /* read start alignment in the packed stream, bases: 1, 4 or 32 */
-  int32_t _pad1;
+  int32_t full_overlaps; /* 1: every pair of reads overlapping >= min_overlap (the overlap
+                            graph before transitive reduction); 0: consecutive pairs only */
 } cg_gen_cfg;
 
 typedef struct {

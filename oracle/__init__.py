@@ -55,6 +55,8 @@ def _bind(lib):
     lib.orc_get_labels.argtypes = [vp, ctypes.c_int, vp]
     lib.orc_free.argtypes = [vp]
     lib.orc_revcomp.argtypes = [ctypes.c_char_p, i64, ctypes.c_char_p]
+    lib.orc_transitive_reduction.restype = i64
+    lib.orc_transitive_reduction.argtypes = [i64, i64] + [vp] * 4 + [i32] + [vp] * 4
     lib.orc_lpt.restype = ctypes.c_int
     lib.orc_lpt.argtypes = [vp, i64, i32, vp, vp]
     return lib
@@ -186,6 +188,19 @@ class OracleLib:
         self.lib.orc_revcomp(b, len(b), out)
         return out.raw[: len(b)].decode()
 
+    def transitive_reduction(self, g, fuzz: int = 0):
+        """The string graph S of overlap graph g (Alg. 1, Sec. 2): g's reads with the
+        non-transitive entries of g (row_ptr int64, col, code, suf)."""
+        from types import SimpleNamespace
+        rp, col, code, suf, ln, off, packed = _inputs(g)
+        n, m = len(ln), len(col)
+        orp = np.zeros(n + 1, np.int64)
+        ocol, ocode, osuf = np.empty(max(m, 1), np.int32), np.empty(max(m, 1), np.uint8), np.empty(max(m, 1), np.int32)
+        k = self.lib.orc_transitive_reduction(n, m, _p(rp), _p(col), _p(code), _p(suf), int(fuzz), _p(orp), _p(ocol),
+                                              _p(ocode), _p(osuf))
+        return SimpleNamespace(row_ptr=orp, col=ocol[:k].copy(), code=ocode[:k].copy(), suf=osuf[:k].copy(), len=ln,
+                               off=off, packed=packed, n=n, m=int(k))
+
     def lpt(self, sizes, P: int):
         sizes = np.ascontiguousarray(sizes, dtype=np.int64)
         assign = np.empty(len(sizes), np.int32)
@@ -221,6 +236,10 @@ def revcomp(s: str) -> str:
 
 def lpt(sizes, P: int):
     return default().lpt(sizes, P)
+
+
+def transitive_reduction(g, fuzz: int = 0):
+    return default().transitive_reduction(g, fuzz)
 
 
 _CODE2 = np.full(256, 255, dtype=np.uint8)

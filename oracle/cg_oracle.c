@@ -422,6 +422,55 @@ void orc_revcomp(const char* in, int64_t n, char* out) {
 
 /* Sec. 4.3: sort the sizes in decreasing order, then put each one in the
  * bin whose current sum is smallest. */
+/* ------------------------------------------------- TransitiveReduction */
+/* Alg. 1 (S <- TransitiveReduction(R)), Sec. 2: an overlap whose information
+ * a parallel path already carries is redundant. Entry x = (u->w) is
+ * transitive when some read v (not u, not w) gives a valid walk u -> v -> w
+ * that leaves u through the same end as x, passes through v (entered through
+ * one end, left through the other) and enters w through the same end as x,
+ * and whose suffixes add up to x's: |suf(u->v) + suf(v->w) - suf(u->w)| <=
+ * fuzz. A pair of reads keeps its two entries only when neither is
+ * transitive. Rows keep their order; returns the number of entries kept. */
+int64_t orc_transitive_reduction(int64_t n, int64_t m, const int64_t* rp, const int32_t* col, const uint8_t* code,
+                                 const int32_t* suf, int32_t fuzz, int64_t* out_rp, int32_t* out_col,
+                                 uint8_t* out_code, int32_t* out_suf) {
+  uint8_t* trans = (uint8_t*)calloc((size_t)(m > 0 ? m : 1), 1);
+  for (int64_t u = 0; u < n; ++u) {
+    for (int64_t x = rp[u]; x < rp[u + 1]; ++x) {
+      const int64_t w = col[x];
+      const int eu = code[x] & 1, ew = (code[x] >> 1) & 1;
+      for (int64_t y = rp[u]; y < rp[u + 1] && !trans[x]; ++y) {
+        const int64_t v = col[y];
+        if (v == w || (code[y] & 1) != eu) continue;          /* leave u through x's end */
+        const int ev_in = (code[y] >> 1) & 1;
+        for (int64_t z = rp[v]; z < rp[v + 1]; ++z) {
+          if (col[z] != w) continue;
+          if ((code[z] & 1) != 1 - ev_in) continue;            /* leave v through its other end */
+          if (((code[z] >> 1) & 1) != ew) continue;            /* enter w through x's end */
+          const int64_t d = (int64_t)suf[y] + suf[z] - suf[x];
+          if (d <= fuzz && d >= -fuzz) { trans[x] = 1; break; }
+        }
+      }
+    }
+  }
+  int64_t k = 0;
+  out_rp[0] = 0;
+  for (int64_t u = 0; u < n; ++u) {
+    for (int64_t x = rp[u]; x < rp[u + 1]; ++x) {
+      const int64_t w = col[x];
+      int mirror_trans = 0;
+      for (int64_t y = rp[w]; y < rp[w + 1]; ++y)
+        if (col[y] == u) mirror_trans = trans[y];
+      if (trans[x] || mirror_trans) continue;
+      out_col[k] = col[x]; out_code[k] = code[x]; out_suf[k] = suf[x];
+      ++k;
+    }
+    out_rp[u + 1] = k;
+  }
+  free(trans);
+  return k;
+}
+
 int orc_lpt(const int64_t* sizes, int64_t k, int32_t P, int32_t* assign, int64_t* loads) {
   if (P < 1 || k < 0) return ORC_EGRAPH;
   int64_t* order = (int64_t*)malloc((size_t)(k > 0 ? k : 1) * sizeof(int64_t));

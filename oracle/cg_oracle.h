@@ -41,6 +41,13 @@ orc_result* orc_run2(int64_t n, int64_t m, const int64_t* row_ptr, const int32_t
                      const int64_t* off, const uint8_t* packed, int64_t packed_bytes, int32_t min_chain_reads,
                      int validate, int* status);
 
+/* TransitiveReduction (Alg. 1, Sec. 2) of an overlap graph in the suffix
+ * form: the string graph's CSR into out_* (n+1 row pointers, up to m
+ * entries). Returns the number of entries kept. */
+int64_t orc_transitive_reduction(int64_t n, int64_t m, const int64_t* row_ptr, const int32_t* col, const uint8_t* code,
+                                 const int32_t* suf, int32_t fuzz, int64_t* out_rp, int32_t* out_col,
+                                 uint8_t* out_code, int32_t* out_suf);
+
 int64_t orc_n_branch(const orc_result* r);
 int64_t orc_n_contigs(const orc_result* r);
 int64_t orc_n_cycles(const orc_result* r);

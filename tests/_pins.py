@@ -642,6 +642,72 @@ def pin_xdrop_validation(orc):
     assert not orc.validate(with_(1, post=-1))[0]
 
 
+# ------------------------------------------------- transitive reduction
+def _tr_triangle(c01, c12, c02, s01, s12, s02, s10, s21, s20):
+    """Reads 0, 1, 2 (100 bases each) with overlaps 0-1, 1-2, 0-2 given by the
+    codes and suffixes of one direction and the mirror suffixes."""
+    rnd = random.Random(11)
+    reads = ["".join(rnd.choice("ACGT") for _ in range(100)) for _ in range(3)]
+    ent = [(0, 1, c01, s01), (1, 0, swap(c01), s10), (1, 2, c12, s12), (2, 1, swap(c12), s21),
+           (0, 2, c02, s02), (2, 0, swap(c02), s20)]
+    return graph_from(reads, ent)
+
+
+def _pairs(S):
+    rp = np.asarray(S.row_ptr)
+    return sorted((u, int(w)) for u in range(len(rp) - 1) for w in np.asarray(S.col)[rp[u]:rp[u + 1]])
+
+
+def pin_transitive_reduction_cases(orc):
+    """Alg. 1 / Sec. 2, by hand: the overlap 0-2 is redundant exactly when the
+    walk 0 -> 1 -> 2 is valid (leaves 0 and enters 2 through the same ends as
+    0 -> 2, passes through 1) and its suffixes add up to 0 -> 2's (within the
+    tolerance); a pair goes when either direction is redundant."""
+    line = [(0, 1), (1, 0), (1, 2), (2, 1)]
+    every = sorted(line + [(0, 2), (2, 0)])
+    cases = [  # (codes 01, 12, 02), suffixes 01, 12, 02, 10, 21, 20, fuzz, expected pairs
+        ((1, 1, 1), (10, 15, 25, 30, 20, 50), 0, line),     # forward line: redundant both ways
+        ((1, 1, 0), (10, 15, 25, 30, 20, 50), 0, every),    # 0 -> 2 leaves 0 through its 5' end
+        ((1, 0, 1), (10, 15, 25, 30, 20, 50), 0, every),    # 1 entered and left through one end
+        ((1, 1, 3), (10, 15, 25, 30, 20, 50), 0, every),    # 0 -> 2 enters 2 through its 3' end
+        ((1, 1, 1), (10, 15, 26, 30, 20, 51), 0, every),    # sums off by one both ways
+        ((1, 1, 1), (10, 15, 26, 30, 20, 51), 1, line),     # ... within a tolerance of 1
+        ((1, 1, 1), (10, 15, 30, 30, 20, 55), 1, every),    # 5 short both ways, beyond the tolerance
+        ((1, 1, 1), (10, 15, 26, 30, 20, 50), 0, line),     # only 2 -> 0 redundant: the pair goes
+        ((3, 2, 3), (10, 15, 25, 30, 20, 50), 0, line),     # 1 and 2 stored reversed: the same walk
+    ]
+    for (c01, c12, c02), (s01, s12, s02, s10, s21, s20), fuzz, want in cases:
+        G = _tr_triangle(c01, c12, c02, s01, s12, s02, s10, s21, s20)
+        assert orc.validate(G)[0]
+        S = orc.transitive_reduction(G, fuzz)
+        assert _pairs(S) == sorted(want), ((c01, c12, c02), (s01, s12, s02, s10, s21, s20), fuzz)
+
+
+def _csr_equal(S, R):
+    for k in ("row_ptr", "col", "code", "suf"):
+        a, b = np.asarray(getattr(S, k)), np.asarray(getattr(R, k))
+        if a.shape != b.shape or not np.array_equal(a.astype(np.int64), b.astype(np.int64)):
+            return False
+    return True
+
+
+def pin_transitive_reduction_interval_graphs(orc):
+    """Exact overlaps among reads of one genome (no repeat overlaps): the
+    reduction of the graph of all overlaps is the graph of consecutive
+    overlaps, entry for entry; the reduction is idempotent with repeats too."""
+    for d in (dict(gen.WORKLOADS["tiny-1Mb"](), k_rep=0),
+              dict(gen._cfg(77, 400_000, [(0.05, 2000, 6000, 2, 6, 0.0)], 15, 1, 7000, 3000, 2500), k_rep=0)):
+        full = gen.generate(dict(d, full_overlaps=1), threads=4, off_align=1)
+        red = gen.generate(d, threads=4, off_align=1)
+        assert full.m > 2 * red.m
+        assert _csr_equal(orc.transitive_reduction(full), red)
+    R = gen.generate(dict(gen.WORKLOADS["tiny-1Mb"](), full_overlaps=1), threads=4)
+    S = orc.transitive_reduction(R)
+    assert _csr_equal(orc.transitive_reduction(S), S)
+    assert orc.validate(S)[0]
+
+
 ALL_PINS = [pin_paper_mask_example, pin_paper_concat_example, pin_paper_rc_example, pin_revcomp,
             pin_same_end_rule, pin_brute_force, pin_cycles, pin_generator_truth, pin_invariants, pin_lpt,
-            pin_validation, pin_xdrop_examples, pin_xdrop_matches_suffix_form, pin_xdrop_validation]
+            pin_validation, pin_xdrop_examples, pin_xdrop_matches_suffix_form, pin_xdrop_validation,
+            pin_transitive_reduction_cases, pin_transitive_reduction_interval_graphs]

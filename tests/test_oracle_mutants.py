@@ -20,6 +20,11 @@ MUTANTS = [
     ("xdrop_beta_flipped", "s->x_out < 0 ? (o == 0 ? L - 1 : 0)", "s->x_out < 0 ? (o == 0 ? 0 : L - 1)"),
     ("xdrop_cycle_keeps_closing_edge", "if (w == r) { *edges_touched += 2; break; }",
      "if (w == r) { *edges_touched += 2; out[k - 1].x_out = x; break; }"),
+    ("tr_ignores_end_at_u", "if (v == w || (code[y] & 1) != eu) continue;", "if (v == w) continue;"),
+    ("tr_ignores_pass_through", "if ((code[z] & 1) != 1 - ev_in) continue;", "if (0) continue;"),
+    ("tr_ignores_end_at_w", "if (((code[z] >> 1) & 1) != ew) continue;", "if (0) continue;"),
+    ("tr_one_direction", "if (trans[x] || mirror_trans) continue;", "if (trans[x]) continue;"),
+    ("tr_tolerance_one_sided", "if (d <= fuzz && d >= -fuzz)", "if (d <= fuzz)"),
     ("xdrop_validate_pre_against_v", "if (pre[x] < 0 || pre[x] > len[u] - 1)", "if (pre[x] < 0 || pre[x] > len[v] - 1)"),
     ("degree_threshold_4", "b1[v] = (uint8_t)(d >= 3);", "b1[v] = (uint8_t)(d >= 4);"),
     ("degree_threshold_2", "b1[v] = (uint8_t)(d >= 3);", "b1[v] = (uint8_t)(d >= 2);"),
