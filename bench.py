@@ -87,6 +87,7 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU budget of the oracle baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-transitive", action="store_true", help="skip the transitive-reduction measurement")
     p.add_argument("--min-chain-reads", type=int, default=2)
     p.add_argument("--threads", type=int, default=0, help="generator threads (0 = all cores)")
     p.add_argument("--scale-genome", type=int, default=0,
@@ -650,6 +651,40 @@ def run_ours(args, rank, world, local_rank):
              "contig_bases": totx, "steps": len(x_ms),
              "note": "same graph in the x-drop (pre, post) form, early starts of up to 200 bases, unequal per side"}
 
+    # TransitiveReduction (Alg. 1) of the same recipe's overlap graph before
+    # reduction (every overlap >= 2 kb among the reads), device in and out
+    tr = None
+    if not args.no_transitive:
+        Rf = _gen.generate(dict(cfg, full_overlaps=1), threads=args.threads or None, keep_genome=False,
+                           with_packed=False)
+        rd = D()
+        for k in ("row_ptr", "col", "code", "suf", "len"):
+            setattr(rd, k, torch.from_numpy(getattr(Rf, k)).cuda())
+        rd.off = dev["off"]
+        rd.packed = torch.empty(0, dtype=torch.uint8, device="cuda")
+        cg.cg_set_timing(ctx, 2)
+        tr_ms, tr_wall, tr_kern = [], [], {}
+        for i in range(4):
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            S = cg.cg_transitive_reduction(ctx, rd, 0, device=True)
+            tr_wall.append((time.perf_counter() - a) * 1e3)
+            kt = cg.cg_kernel_times(ctx)
+            if i > 0:
+                tr_ms.append(sum(t for _, t in kt))
+                for name, t in kt:
+                    tr_kern.setdefault(name, []).append(t)
+        cg.cg_set_timing(ctx, 1)
+        red_m = int(G.m)
+        tr = {"entries_in": int(Rf.m), "entries_out": int(S.m), "reads": int(Rf.n),
+              "generated_string_graph_entries": red_m,
+              "kernel_ms": statistics.mean(tr_ms),
+              "kernel_ms_by_name": {k: statistics.mean(v) for k, v in tr_kern.items()},
+              "call_ms_two_calls": statistics.mean(tr_wall[1:]),
+              "note": "kernel_ms: one call's kernels (checks, mark, keep, row scan, scatter); the API's size query "
+                      "runs them once more"}
+        del S, rd, Rf
+
     # GreedyPartitioning of the contigs (Sec. 4.3) into parts, outside the timed steps
     part_d = torch.empty(max(n_contigs, 1), dtype=torch.int32, device="cuda")
     psum_d = torch.empty(cg.MAX_PARTS, dtype=torch.int64, device="cuda")
@@ -729,6 +764,7 @@ def run_ours(args, rank, world, local_rank):
             "emit_2bit": emit_2bit,
             "xdrop": xdrop,
             "quality": qual,
+            "transitive_reduction": tr,
             "B_min_bytes": B, "path_achieved_gbs": B / (ms * 1e-3) / 1e9,
             "path_roofline_frac": B / (ms * 1e-3) / 1e9 / pk["hbm_gbs"],
             "path_roofline_frac_8tbs": B / (ms * 1e-3) / 1e9 / 8000.0,

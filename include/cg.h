@@ -200,6 +200,25 @@ CG_API cg_status cg_emit_contigs(cg_graph* g, int64_t* contig_off, int64_t conti
 CG_API cg_status cg_emit_contigs_2bit(cg_graph* g, int64_t* contig_off, int64_t contig_off_cap, uint8_t* packed_out,
                                int64_t packed_cap, int mem, int64_t* n_contigs, int64_t* total_bases);
 
+/* TransitiveReduction (Alg. 1, S <- TransitiveReduction(R); Sec. 2): the
+ * string graph S of an overlap graph R given in the suffix form (rows sorted
+ * by column; d->len is read, d->off and d->packed are not). An entry (u->w) is
+ * transitive when some read v gives a valid walk u -> v -> w that leaves u and
+ * enters w through the same ends as (u->w), passes through v (one end in, the
+ * other out), and whose suffixes add up to suf(u->w) within +-fuzz; a pair of
+ * reads keeps both entries only when neither is transitive. Output: S's CSR
+ * with int64 row_ptr (n+1) and up to cap_entries entries of col, code, suf
+ * (rows keep their order), all in `mem`. With all outputs NULL only
+ * *n_entries is set (two-call size query); a cap below the count gives
+ * CG_EINVAL and writes nothing. Device inputs are read in place during the
+ * call, host inputs are copied; the call waits for the GPU. An invalid R
+ * (unsorted or repeated columns, bad offsets, codes, suffixes or mirrors)
+ * gives CG_EGRAPH. S keeps R's reads, so a descriptor with S's arrays and R's
+ * reads goes to cg_load_graph. */
+CG_API cg_status cg_transitive_reduction(cg_ctx* ctx, const cg_graph_desc* overlaps, int32_t fuzz, int64_t* row_ptr,
+                                  int32_t* col, uint8_t* code, int32_t* suf, int64_t cap_entries, int mem,
+                                  int64_t* n_entries);
+
 /* GreedyPartitioning (Alg. 2; Sec. 4.3): splits the contigs among n_parts
  * parts (processes, GPUs) with the longest-processing-time rule. Each contig
  * weighs its number of reads (weight CG_WEIGHT_READS, the size estimate of

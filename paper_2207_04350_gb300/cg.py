@@ -70,6 +70,9 @@ API = {
                         ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
     "cg_emit_contigs_2bit": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
                              ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
+    "cg_transitive_reduction": [ctypes.c_void_p, ctypes.POINTER(GraphDesc), ctypes.c_int32, ctypes.c_void_p,
+                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
+                                ctypes.POINTER(ctypes.c_int64)],
     "cg_partition_contigs": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64,
                              ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)],
     "cg_sync": [ctypes.c_void_p],
@@ -306,6 +309,34 @@ def cg_emit_contigs_2bit(g: Graph, contig_off=None, packed=None, want_counts: bo
 def packed_bytes_2bit(total_bases: int) -> int:
     """Output bytes of the 2-bit form: whole 16-byte chunks of 64 bases."""
     return 16 * ((int(total_bases) + 63) // 64)
+
+
+def cg_transitive_reduction(ctx: Context, graph, fuzz: int = 0, device: bool = False):
+    """TransitiveReduction (Alg. 1, Sec. 2) of the overlap graph `graph` (suffix
+    form, rows sorted). Returns the string graph: row_ptr (int64), col, code,
+    suf (numpy, or torch CUDA tensors with device=True) plus graph's len, off and
+    packed, ready for cg_load_graph. Two calls: the size, then the arrays."""
+    from types import SimpleNamespace
+    d = _desc(graph, 2)
+    cnt = ctypes.c_int64(-1)
+    _check(ctx.ptr, lib().cg_transitive_reduction(ctx.ptr, ctypes.byref(d), int(fuzz), None, None, None, None, 0,
+                                                  MEM_HOST, ctypes.byref(cnt)))
+    k, n = int(cnt.value), int(d.n_reads)
+    if device:
+        import torch
+        rp = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+        col = torch.empty(max(k, 1), dtype=torch.int32, device="cuda")
+        code = torch.empty(max(k, 1), dtype=torch.uint8, device="cuda")
+        suf = torch.empty(max(k, 1), dtype=torch.int32, device="cuda")
+        mem = MEM_DEVICE
+    else:
+        rp = np.empty(n + 1, np.int64)
+        col, code, suf = np.empty(max(k, 1), np.int32), np.empty(max(k, 1), np.uint8), np.empty(max(k, 1), np.int32)
+        mem = MEM_HOST
+    _check(ctx.ptr, lib().cg_transitive_reduction(ctx.ptr, ctypes.byref(d), int(fuzz), _ptr(rp), _ptr(col), _ptr(code),
+                                                  _ptr(suf), k, mem, ctypes.byref(cnt)))
+    return SimpleNamespace(row_ptr=rp, col=col[:k], code=code[:k], suf=suf[:k], len=graph.len, off=graph.off,
+                           packed=graph.packed, n=n, m=k)
 
 
 WEIGHT_READS, WEIGHT_BASES = 0, 1

@@ -938,6 +938,111 @@ cg_status cg_emit_contigs_2bit(cg_graph* g, int64_t* contig_off, int64_t contig_
   return CG_OK;
 }
 
+cg_status cg_transitive_reduction(cg_ctx* c, const cg_graph_desc* d, int32_t fuzz, int64_t* row_ptr, int32_t* col,
+                                  uint8_t* code, int32_t* suf, int64_t cap_entries, int mem, int64_t* n_entries) {
+  cg_status st = check_ctx(c);
+  if (st != CG_OK) return st;
+  if (!d) return fail(c, CG_EINVAL, "null argument");
+  const int64_t n = d->n_reads, m = d->n_entries;
+  if (n < 0 || n >= (1ll << 30) || m < 0 || m >= (1ll << 31)) return fail(c, CG_EINVAL, "sizes out of range");
+  if (fuzz < 0) return fail(c, CG_EINVAL, "negative tolerance");
+  if (mem != CG_MEM_HOST && mem != CG_MEM_DEVICE) return fail(c, CG_EINVAL, "bad mem");
+  if (d->mem != CG_MEM_HOST && d->mem != CG_MEM_DEVICE) return fail(c, CG_EINVAL, "bad input mem");
+  if (d->row_ptr_bytes != 4 && d->row_ptr_bytes != 8) return fail(c, CG_EINVAL, "row_ptr_bytes must be 4 or 8");
+  if (d->pre || d->post) return fail(c, CG_EINVAL, "the reduction takes the suffix form");
+  if (!d->row_ptr || (m > 0 && (!d->col || !d->code || !d->suf)) || (n > 0 && !d->len))
+    return fail(c, CG_EINVAL, "missing input array");
+  const bool want = row_ptr || col || code || suf;
+  if (want && (!row_ptr || (cap_entries > 0 && (!col || !code || !suf)) || cap_entries < 0))
+    return fail(c, CG_EINVAL, "outputs: row_ptr, col, code and suf together");
+  // device inputs are read in place for the duration of the call; host inputs are copied
+  std::vector<void*> tmp;
+  auto alloc = [&](size_t bytes) -> void* {
+    void* p = dalloc(c, bytes > 0 ? bytes : 1, &st);
+    if (p) tmp.push_back(p);
+    return p;
+  };
+  auto done = [&](cg_status s2) {
+    for (void* p : tmp) dfree(c, p);
+    return s2;
+  };
+  auto in = [&](const void* src, size_t bytes) -> const void* {
+    if (d->mem == CG_MEM_DEVICE) return src;
+    void* p = alloc(bytes);
+    if (p && bytes && cudaMemcpyAsync(p, src, bytes, cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
+      st = cuda_fail(c, cudaGetLastError(), "copy overlap graph");
+      return nullptr;
+    }
+    return p;
+  };
+  cg::DevGraph G{};
+  G.n = n;
+  G.m = m;
+  G.rp64 = d->row_ptr_bytes == 8;
+  G.min_chain = 2;
+  G.row_ptr = in(d->row_ptr, (size_t)(n + 1) * d->row_ptr_bytes);
+  G.col = (const int32_t*)in(d->col, (size_t)m * 4);
+  G.code = (const uint8_t*)in(d->code, (size_t)m);
+  G.suf = (const int32_t*)in(d->suf, (size_t)m * 4);
+  G.len = (const int32_t*)in(d->len, (size_t)n * 4);
+  cg::TrBuffers t{};
+  t.trans = (uint8_t*)alloc((size_t)m);
+  t.keep = (uint8_t*)alloc((size_t)m);
+  t.row_cnt = (int32_t*)alloc((size_t)n * 4);
+  t.out_rp = (int64_t*)alloc((size_t)(n + 1) * 8);
+  t.total = (unsigned long long*)alloc(8);
+  t.state_cap = (n + 2047) / 2048 + 1;
+  t.state = (unsigned long long*)alloc((size_t)(t.state_cap + 1) * 8);
+  t.derr = c->derr;
+  if (st != CG_OK) return done(st);
+  if (c->marks.on) {                   // per-kernel marks cover this call alone
+    c->marks.n = 0;
+    cudaEventRecord(c->marks.ev[0], c->stream);
+  }
+  // the rows (offsets, order), then the entries (columns, codes, suffixes,
+  // mirrors), each waited for: the reduction indexes rows by column values
+  cg_graph probe{};
+  probe.ctx = c;
+  cudaError_t e = cg::launch_transitive_check(G, c->derr, c->env);
+  if (e != cudaSuccess) return done(cuda_fail(c, e, "row checks"));
+  st = wait_and_read(&probe);
+  if (st != CG_OK) return done(st);
+  e = cg::launch_validate_entries(G, c->derr, c->env);
+  if (e != cudaSuccess) return done(cuda_fail(c, e, "entry checks"));
+  st = wait_and_read(&probe);
+  if (st != CG_OK) return done(st);
+  e = cg::launch_transitive(G, fuzz, t, c->env);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_u64, t.total, 8, cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return done(cuda_fail(c, e, "transitive reduction kernels"));
+  st = wait_and_read(&probe);
+  if (st != CG_OK) return done(st);
+  const int64_t total = (int64_t)*c->h_u64;
+  if (n_entries) *n_entries = total;
+  if (!want) return done(CG_OK);
+  if (cap_entries < total) return done(fail(c, CG_EINVAL, "capacity %lld < %lld entries", (long long)cap_entries,
+                                            (long long)total));
+  int32_t* oc = col;
+  uint8_t* ok = code;
+  int32_t* os = suf;
+  if (mem == CG_MEM_HOST) {
+    oc = (int32_t*)alloc((size_t)total * 4);
+    ok = (uint8_t*)alloc((size_t)total);
+    os = (int32_t*)alloc((size_t)total * 4);
+    if (st != CG_OK) return done(st);
+  }
+  e = cg::launch_transitive_scatter(G, t, oc, ok, os, c->env);
+  const cudaMemcpyKind k = mem == CG_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(row_ptr, t.out_rp, (size_t)(n + 1) * 8, k, c->stream);
+  if (mem == CG_MEM_HOST && total > 0) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(col, oc, (size_t)total * 4, k, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(code, ok, (size_t)total, k, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(suf, os, (size_t)total * 4, k, c->stream);
+  }
+  if (e != cudaSuccess) return done(cuda_fail(c, e, "write the reduced graph"));
+  st = wait_and_read(&probe);
+  return done(st);
+}
+
 static_assert(cg::kMaxParts == CG_MAX_PARTS, "part limit");
 
 cg_status cg_partition_contigs(cg_graph* g, int32_t n_parts, int32_t weight, int32_t* part, int64_t part_cap,

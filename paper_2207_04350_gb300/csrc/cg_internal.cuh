@@ -195,6 +195,27 @@ struct SortBuffers {
   unsigned long long* state;   // look-back descriptors of the digit scan, + 1 ticket
   long long tiles_cap, state_cap;
 };
+// Buffers of the transitive reduction (m entries, n rows).
+struct TrBuffers {
+  uint8_t* trans;              // m: entry is transitive
+  uint8_t* keep;               // m: entry kept (its pair is not transitive)
+  int32_t* row_cnt;            // n: kept entries per row
+  int64_t* out_rp;             // n + 1: the reduced graph's row offsets
+  unsigned long long* total;   // kept entries
+  unsigned long long* state;   // look-back descriptors of the row scan, + 1 ticket
+  long long state_cap;
+  DevError* derr;
+};
+// TransitiveReduction: row checks (launch_transitive_check, then the entry
+// checks), marks, keeps, scans (launch_transitive), then writes the kept
+// entries (launch_transitive_scatter). Each step needs the checks before it
+// to have passed: the later kernels index rows by column values.
+cudaError_t launch_transitive_check(const DevGraph& g, DevError* derr, const LaunchEnv& env);
+cudaError_t launch_transitive(const DevGraph& g, int fuzz, const TrBuffers& t, const LaunchEnv& env);
+cudaError_t launch_transitive_scatter(const DevGraph& g, const TrBuffers& t, int32_t* col, uint8_t* code, int32_t* suf,
+                                      const LaunchEnv& env);
+// Input checks of the entries (columns, codes, suffixes, mirrors).
+cudaError_t launch_validate_entries(const DevGraph& g, DevError* derr, const LaunchEnv& env);
 constexpr int kMaxParts = 1024;
 // GreedyPartitioning of the C contigs of the last offsets stage into P parts
 // (weight 0: reads per contig, 1: bases); max_weight bounds every part sum.
@@ -218,7 +239,7 @@ __device__ __forceinline__ long long block_round(long long n) { return (n + kBlo
 
 enum KernelId {
   K_VALIDATE1 = 1, K_VALIDATE2, K_MASK, K_SUCC, K_WALK, K_JUMP, K_FINAL, K_CYCLE, K_EXPORT,
-  K_SCAN_HEADS, K_SCATTER, K_SCAN_OFFSETS, K_CONTIG_OFF, K_EMIT, K_SORT
+  K_SCAN_HEADS, K_SCATTER, K_SCAN_OFFSETS, K_CONTIG_OFF, K_EMIT, K_SORT, K_TRANSITIVE
 };
 
 inline int grid_for(long long n, const LaunchEnv& env, int per_sm = 8) {

@@ -1,0 +1,171 @@
+// cg_reduce.cu - TransitiveReduction (Alg. 1: S <- TransitiveReduction(R);
+// Sec. 2) on sm_103a: the string graph of an overlap graph.
+//
+// An entry x = (u->w) is transitive when some read v gives a valid walk
+// u -> v -> w that leaves u through x's end of u, passes through v (entered
+// through one end, left through the other) and enters w through x's end of w,
+// and whose suffixes add up to x's within a tolerance. A pair of reads keeps
+// both entries only when neither is transitive.
+//
+// One warp per read u: each lane takes entries (u->v) of u's row, walks v's
+// row, and looks each w up in u's row (rows are sorted by column) by binary
+// search. Then a warp per row keeps the entries whose pair is not transitive
+// and counts them, a look-back scan gives the new row offsets, and a warp per
+// row writes the kept entries in order.
+#include <cuda_runtime.h>
+
+#include "cg_internal.cuh"
+#include "cg_lookback.cuh"
+
+namespace cg {
+
+namespace {
+
+// Position of column w in the sorted row [a, b), or -1.
+__device__ __forceinline__ int64_t find_col(const int32_t* col, int64_t a, int64_t b, int32_t w) {
+  int64_t lo = a, hi = b;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (__ldg(col + mid) < w) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo < b && __ldg(col + lo) == w ? lo : -1;
+}
+
+// Rows: offsets in [0, m] and increasing, columns strictly increasing (sorted,
+// no repeated pair), every read at least one base long.
+__global__ void k_tr_check(DevGraph g, DevError* e) {
+  for (long long u = grid_tid(); u < g.n; u += grid_threads()) {
+    const int64_t a = rowp(g, u), b = rowp(g, u + 1);
+    if (a < 0 || b < a || b > g.m || g.len[u] < 1) {
+      set_error(e, DERR_GRAPH, K_TRANSITIVE, u);
+      continue;
+    }
+    for (int64_t x = a + 1; x < b; ++x)
+      if (g.col[x] <= g.col[x - 1]) set_error(e, DERR_GRAPH, K_TRANSITIVE, x);
+  }
+  if (grid_tid() == 0 && (rowp(g, 0) != 0 || rowp(g, g.n) != g.m)) set_error(e, DERR_GRAPH, K_TRANSITIVE, -1);
+}
+
+__global__ void __launch_bounds__(kBlock) k_tr_mark(DevGraph g, int fuzz, uint8_t* trans) {
+  const int lane = threadIdx.x & 31;
+  const long long warps = grid_threads() >> 5;
+  for (long long u = grid_tid() >> 5; u < g.n; u += warps) {
+    const int64_t a = rowp(g, u), b = rowp(g, u + 1);
+    for (int64_t y = a + lane; y < b; y += 32) {
+      const int32_t v = g.col[y];
+      const int cy = g.code[y];
+      const int32_t sy = g.suf[y];
+      const int eu = cy & 1, ev_in = (cy >> 1) & 1;
+      const int64_t va = rowp(g, v), vb = rowp(g, v + 1);
+      for (int64_t z = va; z < vb; ++z) {
+        const int cz = g.code[z];
+        if ((cz & 1) != 1 - ev_in) continue;        // leave v through its other end
+        const int32_t w = g.col[z];
+        if (w == (int32_t)u) continue;
+        const int64_t x = find_col(g.col, a, b, w);
+        if (x < 0) continue;
+        const int cx = g.code[x];
+        if ((cx & 1) != eu || ((cx >> 1) & 1) != ((cz >> 1) & 1)) continue;   // the ends of x
+        const long long d = (long long)sy + g.suf[z] - g.suf[x];
+        if (d <= fuzz && d >= -fuzz) trans[x] = 1;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_tr_keep(DevGraph g, const uint8_t* trans, uint8_t* keep,
+                                                    int32_t* row_cnt) {
+  const int lane = threadIdx.x & 31;
+  const long long warps = grid_threads() >> 5;
+  for (long long u = grid_tid() >> 5; u < g.n; u += warps) {
+    const int64_t a = rowp(g, u), b = rowp(g, u + 1);
+    int cnt = 0;
+    for (int64_t x0 = a; x0 < b; x0 += 32) {          // warp-uniform
+      const int64_t x = x0 + lane;
+      bool k = false;
+      if (x < b) {
+        const int32_t w = g.col[x];
+        const int64_t y = find_col(g.col, rowp(g, w), rowp(g, w + 1), (int32_t)u);
+        k = !trans[x] && !(y >= 0 && trans[y]);
+        keep[x] = k;
+      }
+      cnt += __popc(__ballot_sync(0xffffffffu, k));
+    }
+    if (lane == 0) row_cnt[u] = cnt;
+  }
+}
+
+struct RowCntLoad {
+  const int32_t* cnt;
+  __device__ unsigned long long operator()(long long i) const { return (unsigned long long)cnt[i]; }
+};
+struct RowPtrStore {
+  int64_t* rp;
+  unsigned long long* total;
+  __device__ void item(long long i, unsigned long long e) const { rp[i] = (int64_t)e; }
+  __device__ void last(long long n, unsigned long long t) const {
+    rp[n] = (int64_t)t;
+    *total = t;
+  }
+};
+
+__global__ void __launch_bounds__(kBlock) k_tr_scatter(DevGraph g, const uint8_t* keep, const int64_t* out_rp,
+                                                       int32_t* col, uint8_t* code, int32_t* suf) {
+  const int lane = threadIdx.x & 31;
+  const long long warps = grid_threads() >> 5;
+  for (long long u = grid_tid() >> 5; u < g.n; u += warps) {
+    const int64_t a = rowp(g, u), b = rowp(g, u + 1);
+    int64_t pos = out_rp[u];
+    for (int64_t x0 = a; x0 < b; x0 += 32) {          // warp-uniform
+      const int64_t x = x0 + lane;
+      const bool k = x < b && keep[x];
+      const unsigned m = __ballot_sync(0xffffffffu, k);
+      if (k) {
+        const int64_t o = pos + __popc(m & ((1u << lane) - 1u));
+        col[o] = g.col[x];
+        code[o] = g.code[x];
+        suf[o] = g.suf[x];
+      }
+      pos += __popc(m);
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_transitive_check(const DevGraph& g, DevError* derr, const LaunchEnv& env) {
+  k_tr_check<<<grid_for(g.n, env), kBlock, 0, env.stream>>>(g, derr);
+  mark(env, "k_tr_check");
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transitive(const DevGraph& g, int fuzz, const TrBuffers& t, const LaunchEnv& env) {
+  const int warps_grid = grid_for(32 * g.n, env);
+  cudaMemsetAsync(t.trans, 0, (size_t)(g.m > 0 ? g.m : 1), env.stream);
+  k_tr_mark<<<warps_grid, kBlock, 0, env.stream>>>(g, fuzz, t.trans);
+  mark(env, "k_tr_mark");
+  k_tr_keep<<<warps_grid, kBlock, 0, env.stream>>>(g, t.trans, t.keep, t.row_cnt);
+  mark(env, "k_tr_keep");
+  cudaMemsetAsync(t.state, 0, (size_t)(t.state_cap + 1) * sizeof(unsigned long long), env.stream);
+  const long long tiles = (g.n + kTileItems - 1) / kTileItems;
+  if (tiles > t.state_cap) return cudaErrorInvalidValue;
+  if (g.n > 0) {
+    k_scan<<<(unsigned)tiles, kBlock, 0, env.stream>>>(RowCntLoad{t.row_cnt}, RowPtrStore{t.out_rp, t.total}, g.n,
+                                                       nullptr, t.state, t.state_cap, t.derr, K_TRANSITIVE);
+    mark(env, "k_scan_rows");
+  } else {
+    cudaMemsetAsync(t.out_rp, 0, sizeof(int64_t), env.stream);
+    cudaMemsetAsync(t.total, 0, sizeof(unsigned long long), env.stream);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transitive_scatter(const DevGraph& g, const TrBuffers& t, int32_t* col, uint8_t* code, int32_t* suf,
+                                      const LaunchEnv& env) {
+  k_tr_scatter<<<grid_for(32 * g.n, env), kBlock, 0, env.stream>>>(g, t.keep, t.out_rp, col, code, suf);
+  mark(env, "k_tr_scatter");
+  return cudaGetLastError();
+}
+
+}  // namespace cg
