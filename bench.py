@@ -72,7 +72,7 @@ def job_rate(units_per_rank: float, seconds_per_rank: float, world: int) -> floa
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=30)
+    p.add_argument("--steps", type=int, default=100)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--workload", default="genome-3.1Gb",
                    help="tiny-1Mb | genome-100Mb | genome-3.1Gb | batched-512 | served-2000")
@@ -125,7 +125,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -689,6 +689,7 @@ def run_ours(args, rank, world, local_rank):
     part_d = torch.empty(max(n_contigs, 1), dtype=torch.int32, device="cuda")
     psum_d = torch.empty(cg.MAX_PARTS, dtype=torch.int64, device="cuda")
     partition = {"weight": "reads per contig", "n_contigs": n_contigs, "by_parts": {}}
+    cg.cg_set_timing(ctx, 2)
     for P in args.partition_parts:
         kms, wall = [], []
         for _ in range(4):

@@ -1007,7 +1007,7 @@ cg_status cg_transitive_reduction(cg_ctx* c, const cg_graph_desc* d, int32_t fuz
   if (e != cudaSuccess) return done(cuda_fail(c, e, "row checks"));
   st = wait_and_read(&probe);
   if (st != CG_OK) return done(st);
-  e = cg::launch_validate_entries(G, c->derr, c->env);
+  e = cg::launch_transitive_entries(G, c->derr, c->env);
   if (e != cudaSuccess) return done(cuda_fail(c, e, "entry checks"));
   st = wait_and_read(&probe);
   if (st != CG_OK) return done(st);

@@ -597,12 +597,6 @@ int coop_blocks_for_grid_kernels(int num_sms) {
   return per * num_sms;
 }
 
-cudaError_t launch_validate_entries(const DevGraph& g, DevError* derr, const LaunchEnv& env) {
-  k_validate_entries<<<grid_for(g.n, env), kBlock, 0, env.stream>>>(g, derr);
-  mark(env, "k_validate_entries");
-  return cudaGetLastError();
-}
-
 cudaError_t launch_validate(const DevGraph& g, DevError* derr, const LaunchEnv& env) {
   k_validate_reads<<<grid_for(g.n, env), kBlock, 0, env.stream>>>(g, derr);
   mark(env, "k_validate_reads");

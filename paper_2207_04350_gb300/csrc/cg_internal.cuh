@@ -211,11 +211,10 @@ struct TrBuffers {
 // entries (launch_transitive_scatter). Each step needs the checks before it
 // to have passed: the later kernels index rows by column values.
 cudaError_t launch_transitive_check(const DevGraph& g, DevError* derr, const LaunchEnv& env);
+cudaError_t launch_transitive_entries(const DevGraph& g, DevError* derr, const LaunchEnv& env);
 cudaError_t launch_transitive(const DevGraph& g, int fuzz, const TrBuffers& t, const LaunchEnv& env);
 cudaError_t launch_transitive_scatter(const DevGraph& g, const TrBuffers& t, int32_t* col, uint8_t* code, int32_t* suf,
                                       const LaunchEnv& env);
-// Input checks of the entries (columns, codes, suffixes, mirrors).
-cudaError_t launch_validate_entries(const DevGraph& g, DevError* derr, const LaunchEnv& env);
 constexpr int kMaxParts = 1024;
 // GreedyPartitioning of the C contigs of the last offsets stage into P parts
 // (weight 0: reads per contig, 1: bases); max_weight bounds every part sum.

@@ -47,6 +47,27 @@ __global__ void k_tr_check(DevGraph g, DevError* e) {
   if (grid_tid() == 0 && (rowp(g, 0) != 0 || rowp(g, g.n) != g.m)) set_error(e, DERR_GRAPH, K_TRANSITIVE, -1);
 }
 
+// Entries, once the rows are known sorted: column in range and not the row
+// itself, code 0..3, suffix in [1, len-1], and exactly one mirror entry (found
+// by binary search) with the swapped code.
+__global__ void k_tr_entries(DevGraph g, DevError* e) {
+  for (long long u = grid_tid(); u < g.n; u += grid_threads()) {
+    const int64_t a = rowp(g, u), b = rowp(g, u + 1);
+    for (int64_t x = a; x < b; ++x) {
+      const int32_t w = g.col[x];
+      const int cd = g.code[x];
+      if (w < 0 || w >= g.n || w == (int32_t)u || cd > 3) {
+        set_error(e, DERR_GRAPH, K_TRANSITIVE, x);
+        continue;
+      }
+      const int32_t sf = g.suf[x];
+      if (sf < 1 || sf > g.len[w] - 1) set_error(e, DERR_GRAPH, K_TRANSITIVE, x);
+      const int64_t y = find_col(g.col, rowp(g, w), rowp(g, w + 1), (int32_t)u);
+      if (y < 0 || g.code[y] != (((cd & 1) << 1) | (cd >> 1))) set_error(e, DERR_GRAPH, K_TRANSITIVE, x);
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kBlock) k_tr_mark(DevGraph g, int fuzz, uint8_t* trans) {
   const int lane = threadIdx.x & 31;
   const long long warps = grid_threads() >> 5;
@@ -137,6 +158,12 @@ __global__ void __launch_bounds__(kBlock) k_tr_scatter(DevGraph g, const uint8_t
 cudaError_t launch_transitive_check(const DevGraph& g, DevError* derr, const LaunchEnv& env) {
   k_tr_check<<<grid_for(g.n, env), kBlock, 0, env.stream>>>(g, derr);
   mark(env, "k_tr_check");
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transitive_entries(const DevGraph& g, DevError* derr, const LaunchEnv& env) {
+  k_tr_entries<<<grid_for(g.n, env), kBlock, 0, env.stream>>>(g, derr);
+  mark(env, "k_tr_entries");
   return cudaGetLastError();
 }
 
