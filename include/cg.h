@@ -68,7 +68,11 @@ enum { CG_MEM_HOST = 0, CG_MEM_DEVICE = 1 };
 /* cg_load_graph flags */
 enum {
   CG_BORROW_DEVICE = 1u, /* desc pointers are device memory used in place (must outlive the graph) */
-  CG_NO_VALIDATE = 2u    /* skip the input checks (only for graphs known to be valid) */
+  CG_NO_VALIDATE = 2u,   /* skip the input checks (only for graphs known to be valid) */
+  CG_HOST_READS = 4u     /* host inputs whose packed reads are pinned host memory: the reads stay
+                            there (used in place, must outlive the graph) and the spelling reads
+                            only the bases it spells, over the host link; the other arrays are
+                            copied. CG_EINVAL when packed is not pinned host memory. */
 };
 
 typedef struct cg_ctx cg_ctx;
@@ -254,6 +258,12 @@ CG_API cg_status cg_get_tuning(cg_ctx* ctx, cg_tuning* out);
  * parameters, and replayed with one launch afterwards. Off: launched one by
  * one. Outputs are the same either way. */
 CG_API cg_status cg_set_graphs(cg_ctx* ctx, int enable);
+
+/* Host outputs in pinned host memory are written in place by the kernels
+ * over the host link (the default, enable = 1); with 0 they are written to
+ * device memory and copied. Other host memory is always staged and copied.
+ * Outputs are the same either way. */
+CG_API cg_status cg_set_host_direct(cg_ctx* ctx, int enable);
 
 /* Counters of a context, for measurement. */
 typedef struct {

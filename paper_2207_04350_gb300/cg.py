@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libcg.so")
 
 CG_OK, CG_EINVAL, CG_ENOMEM, CG_ECUDA, CG_EGRAPH, CG_ETIMEOUT, CG_EBUSY, CG_EKERNEL = range(8)
 MEM_HOST, MEM_DEVICE = 0, 1
-BORROW_DEVICE, NO_VALIDATE = 1, 2
+BORROW_DEVICE, NO_VALIDATE, HOST_READS = 1, 2, 4
 
 _lock = threading.Lock()
 _lib = None
@@ -78,6 +78,7 @@ API = {
     "cg_sync": [ctypes.c_void_p],
     "cg_set_timing": [ctypes.c_void_p, ctypes.c_int],
     "cg_set_graphs": [ctypes.c_void_p, ctypes.c_int],
+    "cg_set_host_direct": [ctypes.c_void_p, ctypes.c_int],
     "cg_set_tuning": [ctypes.c_void_p, ctypes.c_void_p],
     "cg_get_tuning": [ctypes.c_void_p, ctypes.c_void_p],
     "cg_kernel_time": [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_float)],
@@ -215,7 +216,7 @@ def cg_load_graph(ctx: Context, graph, flags: int = 0, min_chain_reads: int = 2)
     out = ctypes.c_void_p()
     _check(ctx.ptr, lib().cg_load_graph(ctx.ptr, ctypes.byref(d), int(flags), ctypes.byref(out)))
     keep = [getattr(graph, k, None) for k in ("row_ptr", "col", "code", "suf", "len", "off", "packed", "pre", "post")]
-    return Graph(ctx, out, keep if flags & BORROW_DEVICE else None, d.n_reads)
+    return Graph(ctx, out, keep if flags & (BORROW_DEVICE | HOST_READS) else None, d.n_reads)
 
 
 def _desc(graph, min_chain_reads):
@@ -388,6 +389,11 @@ def cg_get_tuning(ctx: Context) -> dict:
 
 class Stats(ctypes.Structure):
     _fields_ = [("kernels_launched", ctypes.c_uint64), ("stage_ms", ctypes.c_float * 4)]
+
+
+def cg_set_host_direct(ctx: Context, enable: bool):
+    """Kernels write pinned host outputs in place (True, the default) or via a device copy (False)."""
+    _check(ctx.ptr, lib().cg_set_host_direct(ctx.ptr, 1 if enable else 0))
 
 
 def cg_set_graphs(ctx: Context, enable: bool):

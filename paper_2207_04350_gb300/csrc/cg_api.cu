@@ -35,6 +35,7 @@ struct cg_ctx {
   bool recorded[4] = {false, false, false, false};
   cg::KernelMarks marks;               // per-kernel events of the last run (timing on)
   bool graphs = true;                  // replay each stage from a captured CUDA graph
+  bool host_direct = true;             // kernels write pinned host outputs in place
 };
 
 // A captured stage: the instantiated graph and what its capture recorded.
@@ -264,6 +265,20 @@ cg_status run_offsets(cg_graph* g) {
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
 
+// The device address of pinned (page-locked, mapped) host memory, or nullptr
+// for any other pointer: only such memory may be read or written by kernels.
+void* pinned_device_alias(const void* p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer || !a.hostPointer) return nullptr;
+  // the alias of p itself (p may lie inside a larger pinned allocation)
+  return (char*)a.devicePointer + ((const char*)p - (const char*)a.hostPointer);
+}
+
 // Scratch, input checks and output bounds of a graph whose inputs are in place.
 cg_status finish_load(cg_graph* g, uint32_t flags) {
   cg_ctx* c = g->ctx;
@@ -474,6 +489,13 @@ cg_status cg_set_graphs(cg_ctx* c, int enable) {
   return CG_OK;
 }
 
+cg_status cg_set_host_direct(cg_ctx* c, int enable) {
+  cg_status st = check_ctx(c);
+  if (st != CG_OK) return st;
+  c->host_direct = enable != 0;
+  return CG_OK;
+}
+
 cg_status cg_set_timing(cg_ctx* c, int enable) {
   cg_status st = check_ctx(c);
   if (st != CG_OK) return st;
@@ -552,6 +574,14 @@ cg_status cg_load_graph(cg_ctx* c, const cg_graph_desc* d, uint32_t flags, cg_gr
     return fail(c, CG_EINVAL, "missing input array");
   const bool borrow = (flags & CG_BORROW_DEVICE) != 0;
   if (borrow && d->mem != CG_MEM_DEVICE) return fail(c, CG_EINVAL, "CG_BORROW_DEVICE needs device inputs");
+  const bool host_reads = (flags & CG_HOST_READS) != 0;
+  const uint8_t* host_packed_dev = nullptr;      // device address of pinned host reads
+  if (host_reads) {
+    if (borrow || d->mem != CG_MEM_HOST) return fail(c, CG_EINVAL, "CG_HOST_READS needs host inputs");
+    host_packed_dev = (const uint8_t*)pinned_device_alias(d->packed);
+    if (d->packed_bytes > 0 && !host_packed_dev)
+      return fail(c, CG_EINVAL, "CG_HOST_READS needs the packed reads in pinned host memory");
+  }
   if (borrow && (!aligned(d->packed, 16) || !aligned(d->row_ptr, d->row_ptr_bytes) || !aligned(d->col, 4) ||
                  (!xdrop && !aligned(d->suf, 4)) || (xdrop && (!aligned(d->pre, 4) || !aligned(d->post, 4))) ||
                  !aligned(d->len, 4) || !aligned(d->off, 8)))
@@ -572,7 +602,7 @@ cg_status cg_load_graph(cg_ctx* c, const cg_graph_desc* d, uint32_t flags, cg_gr
   G.rp64 = d->row_ptr_bytes == 8;
   G.min_chain = d->min_chain_reads <= 0 ? 2 : d->min_chain_reads;
   G.packed_bytes = d->packed_bytes;
-  G.packed_readable = borrow ? d->packed_bytes : d->packed_bytes + 16;   // owned copies carry 16 zero bytes
+  G.packed_readable = borrow || host_reads ? d->packed_bytes : d->packed_bytes + 16;   // owned copies: 16 zero bytes
   if (borrow) {
     G.row_ptr = d->row_ptr;
     G.col = d->col;
@@ -606,7 +636,8 @@ cg_status cg_load_graph(cg_ctx* c, const cg_graph_desc* d, uint32_t flags, cg_gr
     }
     if (st == CG_OK) G.len = (const int32_t*)copy_in(d->len, (size_t)n * 4, 0);
     if (st == CG_OK) G.off = (const int64_t*)copy_in(d->off, (size_t)n * 8, 0);
-    if (st == CG_OK) G.packed = (const uint8_t*)copy_in(d->packed, (size_t)d->packed_bytes, 16);
+    if (host_reads) G.packed = host_packed_dev;
+    else if (st == CG_OK) G.packed = (const uint8_t*)copy_in(d->packed, (size_t)d->packed_bytes, 16);
     if (st != CG_OK) return bail(st);
   }
 
@@ -838,24 +869,33 @@ cg_status cg_emit_contigs(cg_graph* g, int64_t* contig_off, int64_t contig_off_c
     const int64_t total = c->h_ctr->total_bases, C = c->h_ctr->n_contigs;
     if (bases && bases_cap < total) return fail(c, CG_EINVAL, "bases capacity %lld < %lld", (long long)bases_cap, (long long)total);
     if (contig_off && contig_off_cap < C + 1) return fail(c, CG_EINVAL, "contig_off capacity too small");
+    // pinned host output: the kernel writes it over the host link; other host memory: staged and copied
+    uint8_t* direct = c->host_direct ? (uint8_t*)pinned_device_alias(bases) : nullptr;
+    if (direct && !aligned(direct, 16)) direct = nullptr;
     if (bases && total > 0) {
-      if (g->stage_bases_cap < total) {
-        if (g->stage_bases) dfree(c, g->stage_bases);
-        g->stage_bases = (uint8_t*)dalloc(c, (size_t)total, &st);
-        if (!g->stage_bases) { g->stage_bases_cap = 0; return st; }
-        g->stage_bases_cap = total;
+      uint8_t* dst = direct;
+      int64_t dcap = bases_cap;
+      if (!dst) {
+        if (g->stage_bases_cap < total) {
+          if (g->stage_bases) dfree(c, g->stage_bases);
+          g->stage_bases = (uint8_t*)dalloc(c, (size_t)total, &st);
+          if (!g->stage_bases) { g->stage_bases_cap = 0; return st; }
+          g->stage_bases_cap = total;
+        }
+        dst = g->stage_bases;
+        dcap = g->stage_bases_cap;
       }
       {
         StageTimer tm(c, 3);
-        uint64_t key = mix_key(mix_key(mix_key((uint64_t)(uintptr_t)g->stage_bases, (uint64_t)g->stage_bases_cap),
+        uint64_t key = mix_key(mix_key(mix_key((uint64_t)(uintptr_t)dst, (uint64_t)dcap),
                                        (uint64_t)c->tune.tile_bytes), (uint64_t)c->tune.emit_blocks_per_sm);
         st = run_stage(g, 3, key, [&]() -> cg_status {
-          CK(cg::launch_emit(g->g, g->s, c->tune, g->stage_bases, g->stage_bases_cap, c->env), "emission kernel");
+          CK(cg::launch_emit(g->g, g->s, c->tune, dst, dcap, c->env), "emission kernel");
           return CG_OK;
         });
         if (st != CG_OK) return st;
       }
-      CK(cudaMemcpyAsync(bases, g->stage_bases, (size_t)total, cudaMemcpyDeviceToHost, c->stream), "copy bases");
+      if (!direct) CK(cudaMemcpyAsync(bases, dst, (size_t)total, cudaMemcpyDeviceToHost, c->stream), "copy bases");
     }
     if (contig_off)
       CK(cudaMemcpyAsync(contig_off, g->s.contig_off, (size_t)(C + 1) * 8, cudaMemcpyDeviceToHost, c->stream),
@@ -914,16 +954,24 @@ cg_status cg_emit_contigs_2bit(cg_graph* g, int64_t* contig_off, int64_t contig_
     if (packed_out && packed_cap < need)
       return fail(c, CG_EINVAL, "packed capacity %lld < %lld", (long long)packed_cap, (long long)need);
     if (contig_off && contig_off_cap < C + 1) return fail(c, CG_EINVAL, "contig_off capacity too small");
+    uint8_t* direct = c->host_direct ? (uint8_t*)pinned_device_alias(packed_out) : nullptr;
+    if (direct && !aligned(direct, 16)) direct = nullptr;
     if (packed_out && need > 0) {
-      if (g->stage_bases_cap < need) {
-        if (g->stage_bases) dfree(c, g->stage_bases);
-        g->stage_bases = (uint8_t*)dalloc(c, (size_t)need, &st);
-        if (!g->stage_bases) { g->stage_bases_cap = 0; return st; }
-        g->stage_bases_cap = need;
+      if (direct) {
+        st = emit(direct, packed_cap);
+        if (st != CG_OK) return st;
+      } else {
+        if (g->stage_bases_cap < need) {
+          if (g->stage_bases) dfree(c, g->stage_bases);
+          g->stage_bases = (uint8_t*)dalloc(c, (size_t)need, &st);
+          if (!g->stage_bases) { g->stage_bases_cap = 0; return st; }
+          g->stage_bases_cap = need;
+        }
+        st = emit(g->stage_bases, g->stage_bases_cap);
+        if (st != CG_OK) return st;
+        CK(cudaMemcpyAsync(packed_out, g->stage_bases, (size_t)need, cudaMemcpyDeviceToHost, c->stream),
+           "copy packed");
       }
-      st = emit(g->stage_bases, g->stage_bases_cap);
-      if (st != CG_OK) return st;
-      CK(cudaMemcpyAsync(packed_out, g->stage_bases, (size_t)need, cudaMemcpyDeviceToHost, c->stream), "copy packed");
     }
     if (contig_off)
       CK(cudaMemcpyAsync(contig_off, g->s.contig_off, (size_t)(C + 1) * 8, cudaMemcpyDeviceToHost, c->stream),
