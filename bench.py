@@ -492,7 +492,7 @@ def cpu_baseline_graphs(args, graphs):
     t = statistics.mean(times)
     return {"value": bases / t / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"first {len(graphs)} graphs of the batch ({bases} contig bases), full oracle pipeline, "
-                      f"mean of {reps} runs, 1 thread", "ms_per_step": t * 1e3}
+                      f"mean of {reps} runs, 1 thread", "ms_per_step": t * 1e3, **host_cpu()}
 
 
 def run_ours(args, rank, world, local_rank):
@@ -780,6 +780,7 @@ def run_ours(args, rank, world, local_rank):
             "stage_names": ["mask", "chains", "offsets", "emit"],
             "kernel_ms_mean": {k: statistics.mean(v) for k, v in kern.items()},
             "kernel_ms_note": "3 extra untimed steps with a CUDA event after every kernel",
+            "step_ms_median": statistics.median(step_ms), "step_ms_min": min(step_ms), "step_ms_max": max(step_ms),
             "partition": partition,
             "emit_2bit": emit_2bit,
             "xdrop": xdrop,
@@ -805,6 +806,25 @@ def run_ours(args, rank, world, local_rank):
     g.close()
     ctx.close()
     return line
+
+
+def host_cpu() -> dict:
+    """The host's CPU model and logical cores (the oracle uses one of them)."""
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k = line.split(":")[0].strip().lower()
+                if k in ("model name", "cpu model", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+                if k == "cpu part" and not model:
+                    model = "cpu part " + line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return {"cpu": model or platform.processor() or platform.machine(), "machine": platform.machine(),
+            "host_cores_available": os.cpu_count(), "threads_used": 1}
 
 
 def cpu_baseline(args, cfg, steps=None, warmup=0):
@@ -833,7 +853,7 @@ def cpu_baseline(args, cfg, steps=None, warmup=0):
     return {"value": r.total_bases / t / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{args.workload} recipe on a {scale/1e6:.0f} Mb genome ({G.n} reads, {r.total_bases} contig "
                       f"bases), full oracle pipeline, mean of {len(times)} runs, {t:.2f} s each, 1 thread",
-            "ms_per_step": t * 1e3, "host_cores_available": os.cpu_count()}
+            "ms_per_step": t * 1e3, "median_ms": statistics.median(times) * 1e3, **host_cpu()}
 
 
 def run_reference(args, rank, world):
