@@ -96,6 +96,11 @@ def test_only_cycles_and_ruler_free_cycles(ctx):
 
 
 def test_degenerate_graphs(ctx):
+    # no reads at all
+    empty = structured(3, [], lone=0)
+    assert empty.n == 0
+    orc = check(ctx, empty, 2)
+    assert orc.n_contigs == 0 and orc.total_bases == 0
     # a single read, no overlaps at all, everything masked
     one = structured(1, [1])
     check(ctx, one, 1)
