@@ -88,6 +88,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-transitive", action="store_true", help="skip the transitive-reduction measurement")
+    p.add_argument("--pg-timeout", type=int, default=300, help="process-group timeout (s) for N > 1")
     p.add_argument("--min-chain-reads", type=int, default=2)
     p.add_argument("--threads", type=int, default=0, help="generator threads (0 = all cores)")
     p.add_argument("--scale-genome", type=int, default=0,
@@ -888,7 +889,9 @@ def main():
     import torch
     if world > 1:
         torch.cuda.set_device(local_rank)
-        torch.distributed.init_process_group("nccl")
+        import datetime
+        # a rank that dies ends the others' next collective with an error after this long
+        torch.distributed.init_process_group("nccl", timeout=datetime.timedelta(seconds=args.pg_timeout))
     import __graft_entry__
     if rank == 0 or world == 1:
         __graft_entry__.build()

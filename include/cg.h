@@ -265,6 +265,17 @@ CG_API cg_status cg_set_graphs(cg_ctx* ctx, int enable);
  * Outputs are the same either way. */
 CG_API cg_status cg_set_host_direct(cg_ctx* ctx, int enable);
 
+/* Host-side fault injection, for tests of the error paths that fault no GPU.
+ * spec: "site:n[:ms]" entries separated by commas; the n-th time (from 1) this
+ * context reaches `site` it fails as that step would: "alloc" (CG_ENOMEM),
+ * "h2d" (an input copy, CG_ECUDA), "timeout" (a bounded device wait,
+ * CG_ETIMEOUT), "kernel" (a kernel consistency check, CG_EKERNEL), "bad_graph"
+ * (input validation, CG_EGRAPH). NULL or "" clears the plan. The CG_FAULT
+ * environment variable gives the plan of every new context and server; a
+ * server also knows "admit" (cg_server_submit returns CG_EBUSY) and
+ * "queue_stall" (a worker sleeps ms milliseconds before its n-th batch). */
+CG_API cg_status cg_set_fault(cg_ctx* ctx, const char* spec);
+
 /* Counters of a context, for measurement. */
 typedef struct {
   uint64_t kernels_launched; /* CUDA kernels this context has launched so far */

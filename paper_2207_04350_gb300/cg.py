@@ -79,6 +79,7 @@ API = {
     "cg_set_timing": [ctypes.c_void_p, ctypes.c_int],
     "cg_set_graphs": [ctypes.c_void_p, ctypes.c_int],
     "cg_set_host_direct": [ctypes.c_void_p, ctypes.c_int],
+    "cg_set_fault": [ctypes.c_void_p, ctypes.c_char_p],
     "cg_set_tuning": [ctypes.c_void_p, ctypes.c_void_p],
     "cg_get_tuning": [ctypes.c_void_p, ctypes.c_void_p],
     "cg_kernel_time": [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_float)],
@@ -389,6 +390,11 @@ def cg_get_tuning(ctx: Context) -> dict:
 
 class Stats(ctypes.Structure):
     _fields_ = [("kernels_launched", ctypes.c_uint64), ("stage_ms", ctypes.c_float * 4)]
+
+
+def cg_set_fault(ctx: Context, spec: str | None):
+    """Host-side fault injection plan of a context ("site:n[:ms],..."; None clears)."""
+    _check(ctx.ptr, lib().cg_set_fault(ctx.ptr, spec.encode() if spec else None))
 
 
 def cg_set_host_direct(ctx: Context, enable: bool):

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "cg.h"
+#include "cg_fault.h"
 #include "cg_internal.cuh"
 
 struct cg_ctx {
@@ -36,6 +37,7 @@ struct cg_ctx {
   cg::KernelMarks marks;               // per-kernel events of the last run (timing on)
   bool graphs = true;                  // replay each stage from a captured CUDA graph
   bool host_direct = true;             // kernels write pinned host outputs in place
+  cg::FaultPlan fault;                 // host-side fault injection (tests)
 };
 
 // A captured stage: the instantiated graph and what its capture recorded.
@@ -98,6 +100,10 @@ void* dalloc(cg_ctx* c, size_t bytes, cg_status* st) {
                bytes, (unsigned long long)c->budget);
     return nullptr;
   }
+  if (c->fault.hit("alloc")) {
+    *st = fail(c, CG_ENOMEM, "injected: device allocation of %zu bytes", bytes);
+    return nullptr;
+  }
   void* p = nullptr;
   cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, c->mempool, c->stream);
   if (e != cudaSuccess) {
@@ -134,6 +140,8 @@ cg_status wait_and_read(cg_graph* g) {
     CK(cudaMemcpyAsync(c->h_ctr, g->s.ctr, sizeof(cg::Counters), cudaMemcpyDeviceToHost, c->stream), "read counters");
   CK(cudaStreamSynchronize(c->stream), "stream synchronize");
   cg::DevError e = *c->h_err;
+  if (c->fault.hit("timeout")) return fail(c, CG_ETIMEOUT, "injected: device wait timed out");
+  if (c->fault.hit("kernel")) return fail(c, CG_EKERNEL, "injected: kernel consistency check failed");
   if (e.err == cg::DERR_NONE) return CG_OK;
   if (e.err == cg::DERR_CAPACITY || e.err == cg::DERR_GRAPH) {
     CK(cudaMemsetAsync(c->derr, 0, sizeof(cg::DevError), c->stream), "clear error word");
@@ -350,6 +358,7 @@ cg_status finish_load(cg_graph* g, uint32_t flags) {
   CK(cudaMemcpyAsync(c->h_u64, g->d_sum, 8, cudaMemcpyDeviceToHost, c->stream), "read sum");
   st = wait_and_read(g);
   if (st != CG_OK) return st;
+  if (c->fault.hit("bad_graph")) return fail(c, CG_EGRAPH, "injected: invalid string graph");
   g->sum_len = (int64_t)*c->h_u64;
   // the longest possible output is every read spelled whole; tiles of at least 4 KiB
   S.tiles_cap = g->sum_len / 4096 + 2;
@@ -389,6 +398,7 @@ cg_status cg_create(cg_ctx** out, int device, uint64_t hbm_budget_bytes, void* c
   if (!c) return CG_ENOMEM;
   c->device = device;
   c->budget = hbm_budget_bytes;
+  c->fault.from_env();
   cudaError_t e = cudaSetDevice(device);
   if (e != cudaSuccess) { delete c; return CG_ECUDA; }
   if (cuda_stream) {
@@ -486,6 +496,12 @@ cg_status cg_set_graphs(cg_ctx* c, int enable) {
   cg_status st = check_ctx(c);
   if (st != CG_OK) return st;
   c->graphs = enable != 0;
+  return CG_OK;
+}
+
+cg_status cg_set_fault(cg_ctx* c, const char* spec) {
+  if (!c) return CG_EINVAL;
+  c->fault.set(spec);
   return CG_OK;
 }
 
@@ -618,6 +634,10 @@ cg_status cg_load_graph(cg_ctx* c, const cg_graph_desc* d, uint32_t flags, cg_gr
       void* p = dalloc(c, bytes + pad, &st);
       if (!p) return nullptr;
       g->owned.push_back(p);
+      if (c->fault.hit("h2d")) {
+        st = fail(c, CG_ECUDA, "injected: copy graph input failed");
+        return nullptr;
+      }
       if (bytes) {
         cudaError_t e = cudaMemcpyAsync(p, src, bytes, kind, c->stream);
         if (e != cudaSuccess) { st = cuda_fail(c, e, "copy graph input"); return nullptr; }

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "cg.h"
+#include "cg_fault.h"
 
 namespace {
 
@@ -55,6 +56,7 @@ struct cg_server {
   uint64_t in_flight_bytes = 0;          // estimates of admitted, unfinished requests
   bool stopping = false;
   std::vector<std::thread> workers;
+  cg::FaultPlan fault;                   // host-side fault injection (tests)
   std::vector<cg_ctx*> ctxs;
   std::vector<cudaStream_t> streams;
   uint64_t batches = 0, batched_requests = 0;
@@ -184,6 +186,9 @@ void worker_main(cg_server* s, int w) {
         s->admitted.pop_front();
       }
     }
+    int stall_ms = 0;
+    if (!batch.empty() && s->fault.hit("queue_stall", &stall_ms) && stall_ms > 0)
+      std::this_thread::sleep_for(std::chrono::milliseconds(stall_ms));
     if (!batch.empty()) run_batch(s, ctx, stream, wb, batch);
   }
 }
@@ -200,6 +205,7 @@ cg_status cg_server_start(int device, const cg_server_opts* opts, cg_server** ou
   if (!s) return CG_ENOMEM;
   s->device = device;
   s->opts = *opts;
+  s->fault.from_env();
   if (cudaSetDevice(device) != cudaSuccess) {
     cudaGetLastError();
     delete s;
@@ -233,6 +239,10 @@ cg_status cg_server_submit(cg_server* s, const cg_graph_desc* d, uint64_t* id) {
   if (!r) return CG_ENOMEM;
   r->desc = *d;
   r->est_bytes = estimate(*d);
+  if (s->fault.hit("admit")) {
+    delete r;
+    return CG_EBUSY;                     // injected: admission refused
+  }
   if (r->est_bytes > s->opts.hbm_budget_bytes) {
     delete r;
     return CG_EBUSY;                     // can never fit the budget

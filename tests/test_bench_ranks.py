@@ -55,3 +55,33 @@ def test_one_rank_is_identity():
     assert bench.max_over_ranks(2.5, 1) == 2.5
     assert bench.sum_over_ranks(7.0, 1) == 7.0
     assert bench.job_rate(10.0, 2.0, 1) == 5.0
+
+
+def _dead_rank_worker(rank, world, port, q):
+    import datetime
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=5))
+    import bench
+    bench.rank_barrier(world)                 # step 1: both ranks
+    if rank == 1:
+        os._exit(0)                           # rank 1 leaves between steps, without a word
+    try:
+        bench.rank_barrier(world)             # step 2: the other rank is gone
+        q.put((rank, "returned"))
+    except Exception as e:                    # the process group reports it instead of hanging
+        q.put((rank, type(e).__name__))
+    os._exit(0)
+
+
+def test_dead_rank_ends_in_an_error_not_a_hang():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_dead_rank_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    rank, outcome = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=60)
+    assert rank == 0 and outcome != "returned"
