@@ -89,6 +89,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-transitive", action="store_true", help="skip the transitive-reduction measurement")
     p.add_argument("--pg-timeout", type=int, default=300, help="process-group timeout (s) for N > 1")
+    p.add_argument("--autotune", action="store_true",
+                   help="tune the launch parameters for this size class first (cached as JSON)")
     p.add_argument("--min-chain-reads", type=int, default=2)
     p.add_argument("--threads", type=int, default=0, help="generator threads (0 = all cores)")
     p.add_argument("--scale-genome", type=int, default=0,
@@ -525,6 +527,10 @@ def run_ours(args, rank, world, local_rank):
     for k, v in dev.items():
         setattr(dg, k, v)
     g = cg.cg_load_graph(ctx, dg, flags=cg.BORROW_DEVICE, min_chain_reads=args.min_chain_reads)
+    tuned = None
+    if args.autotune:
+        from paper_2207_04350_gb300 import autotune
+        tuned = autotune.apply(ctx, g, (G.n, G.m, G.packed_bytes))
     # sizes (untimed): walk positions, contigs, bases
     cid = np.empty(G.n, np.int32)
     rank_h = np.empty(G.n, np.int32)
@@ -785,6 +791,7 @@ def run_ours(args, rank, world, local_rank):
             "partition": partition,
             "emit_2bit": emit_2bit,
             "xdrop": xdrop,
+            "autotune": tuned,
             "quality": qual,
             "transitive_reduction": tr,
             "e2e_copy_all_inputs": e2e_copy,
