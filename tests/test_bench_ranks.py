@@ -71,6 +71,8 @@ def _dead_rank_worker(rank, world, port, q):
         q.put((rank, "returned"))
     except Exception as e:                    # the process group reports it instead of hanging
         q.put((rank, type(e).__name__))
+    q.close()
+    q.join_thread()                           # the message is out before the process ends
     os._exit(0)
 
 
