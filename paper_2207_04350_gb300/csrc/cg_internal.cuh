@@ -127,7 +127,7 @@ struct Scratch {
 
 // Tuning knobs (chosen by the autotuner per size class).
 struct Tuning {
-  int ruler_log2 = 4;      // a read starts a sublist with probability 2^-ruler_log2
+  int ruler_log2 = 3;      // a read starts a sublist with probability 2^-ruler_log2
   int tile_bytes = 32768;  // emission tile: 4, 8, 16 or 32 KiB
   int emit_blocks_per_sm = 8;
   int grid_blocks_per_sm = 8;
