@@ -126,8 +126,12 @@ CG_API cg_status cg_free_graph(cg_graph* g);
 /* The batched form: k string graphs loaded as one disjoint union (reads,
  * entries and packed bases of graph j follow those of graphs 0..j-1), so
  * that each stage below runs as one launch over every graph. All descs must
- * share mem, row_ptr_bytes and min_chain_reads; inputs are always copied
- * (CG_BORROW_DEVICE is refused). Chains never cross graphs, so the union's
+ * share mem, row_ptr_bytes and min_chain_reads; inputs are copied
+ * (CG_BORROW_DEVICE is refused), except with CG_HOST_READS: host descs whose
+ * packed reads are pinned host memory, 4-byte aligned, keep them there, and
+ * each spelling call first gathers the words of the pieces it spells from the
+ * owning graph's stream over the host link (CG_EINVAL when a graph's reads
+ * are not pinned). Chains never cross graphs, so the union's
  * contigs are those of graph 0, then graph 1, ... in each graph's own order,
  * and read r of graph j is read R_j + r of the union (R_j = reads of graphs
  * before j). Waits for the GPU. */
@@ -169,6 +173,8 @@ CG_API cg_status cg_server_poll(cg_server* s, uint64_t id, int* done);
 CG_API cg_status cg_server_wait(cg_server* s, uint64_t id, int64_t timeout_ms, cg_server_result* out);
 CG_API cg_status cg_server_release(cg_server* s, uint64_t id);
 CG_API cg_status cg_server_stats(cg_server* s, uint64_t* batches, uint64_t* requests, uint64_t* in_flight_bytes);
+/* Kernels the server's contexts have launched so far (exact while no batch runs). */
+CG_API cg_status cg_server_kernels(cg_server* s, uint64_t* launched);
 /* Finishes every submitted request, then stops the workers. */
 CG_API cg_status cg_server_stop(cg_server* s);
 

@@ -91,6 +91,7 @@ API = {
     "cg_server_release": [ctypes.c_void_p, ctypes.c_uint64],
     "cg_server_stats": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                         ctypes.POINTER(ctypes.c_uint64)],
+    "cg_server_kernels": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)],
     "cg_server_stop": [ctypes.c_void_p],
     "cg_offsets_noalloc": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p],
     "cg_status_str": [ctypes.c_int],
@@ -249,7 +250,7 @@ def cg_load_batch(ctx: Context, graphs, flags: int = 0, min_chain_reads: int = 2
     descs = (GraphDesc * k)(*[_desc(gr, min_chain_reads) for gr in graphs])
     out = ctypes.c_void_p()
     _check(ctx.ptr, lib().cg_load_batch(ctx.ptr, descs, k, int(flags), ctypes.byref(out)))
-    g = Graph(ctx, out, None, int(sum(len(gr.len) for gr in graphs)))
+    g = Graph(ctx, out, list(graphs) if flags & HOST_READS else None, int(sum(len(gr.len) for gr in graphs)))
     g.batch_k = k
     return g
 
@@ -465,7 +466,9 @@ class Server:
     def stats(self) -> dict:
         b, q, f = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
         _check(None, lib().cg_server_stats(self.ptr, ctypes.byref(b), ctypes.byref(q), ctypes.byref(f)))
-        return {"batches": b.value, "requests": q.value, "in_flight_bytes": f.value}
+        n = ctypes.c_uint64()
+        _check(None, lib().cg_server_kernels(self.ptr, ctypes.byref(n)))
+        return {"batches": b.value, "requests": q.value, "in_flight_bytes": f.value, "kernels_launched": n.value}
 
     def stop(self):
         if self.ptr:

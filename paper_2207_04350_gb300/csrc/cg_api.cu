@@ -62,6 +62,18 @@ struct cg_graph {
   StageExec execs[6];                  // mask, chains, offsets, emission, contig_off export, 2-bit emission
   int batch_k = 0;                     // graphs of a batch (0: a single graph)
   int64_t* batch_R = nullptr;          // device: first read of each graph, batch_k + 1 entries
+  // a batch whose reads stay in pinned host memory: per graph its stream's
+  // device alias, length and virtual start; the gathered pieces' words
+  bool host_batch = false;
+  const uint8_t** hb_base = nullptr;
+  int64_t* hb_bytes = nullptr;
+  const int64_t* hb_PB = nullptr;
+  unsigned long long* hb_slot = nullptr;
+  unsigned long long* hb_state = nullptr;
+  long long hb_state_cap = 0;
+  uint32_t* hb_dst = nullptr;
+  int64_t hb_dst_words = 0;
+  cg::DevGraph g_emit{};               // the graph as the spelling sees it (gathered reads)
 };
 
 namespace {
@@ -272,6 +284,43 @@ cg_status run_offsets(cg_graph* g) {
 }
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
+
+// The graph the spelling kernels read: g itself, or for a batch with
+// host-resident reads the gathered pieces (prepare_emit).
+const cg::DevGraph& emit_graph(const cg_graph* g) { return g->host_batch ? g->g_emit : g->g; }
+
+// For a batch with host-resident reads, after the offsets stage: the words of
+// every piece, gathered from its graph's pinned host stream into one device
+// buffer (at most total/16 + 3 W words), and the pieces' sources moved there.
+cg_status prepare_emit(cg_graph* g) {
+  if (!g->host_batch) return CG_OK;
+  cg_ctx* c = g->ctx;
+  cg_status st = wait_and_read(g);                  // the walk positions and bases of this layout
+  if (st != CG_OK) return st;
+  const long long W = c->h_ctr->n_walk, total = c->h_ctr->total_bases;
+  if (!g->hb_slot) {
+    const long long n = g->g.n > 0 ? g->g.n : 1;
+    g->hb_state_cap = (n + 2047) / 2048 + 1;
+    g->hb_slot = galloc<unsigned long long>(g, (size_t)n + 1, &st);
+    g->hb_state = galloc<unsigned long long>(g, (size_t)g->hb_state_cap + 1, &st);
+    if (st != CG_OK) return st;
+  }
+  const long long need = total / 16 + 3 * W + 16;
+  if (g->hb_dst_words < need) {
+    if (g->hb_dst) dfree(c, g->hb_dst);
+    g->hb_dst = (uint32_t*)dalloc(c, (size_t)need * 4, &st);
+    g->hb_dst_words = g->hb_dst ? need : 0;
+    if (st != CG_OK) return st;
+  }
+  CK(cg::launch_gather_slots(g->s, W, g->hb_slot, g->hb_state, g->hb_state_cap, c->env), "gather slots");
+  CK(cg::launch_gather_pieces(g->s, g->batch_k, g->hb_PB, g->hb_base, g->hb_bytes, g->hb_slot, g->hb_dst,
+                              g->hb_dst_words, W, c->env), "gather pieces");
+  g->g_emit = g->g;
+  g->g_emit.packed = reinterpret_cast<const uint8_t*>(g->hb_dst);
+  g->g_emit.packed_bytes = 4 * g->hb_dst_words;
+  g->g_emit.packed_readable = 4 * g->hb_dst_words;
+  return CG_OK;
+}
 
 // The device address of pinned (page-locked, mapped) host memory, or nullptr
 // for any other pointer: only such memory may be read or written by kernels.
@@ -570,6 +619,7 @@ cg_status cg_free_graph(cg_graph* g) {
     if (e.exec) cudaGraphExecDestroy(e.exec);
   for (void* p : g->owned) dfree(c, p);
   dfree(c, g->stage_bases);
+  dfree(c, g->hb_dst);
   delete g;
   return CG_OK;
 }
@@ -673,6 +723,19 @@ cg_status cg_load_batch(cg_ctx* c, const cg_graph_desc* d, int k, uint32_t flags
   if (!d || !out || k < 1) return fail(c, CG_EINVAL, "null argument or empty batch");
   *out = nullptr;
   if (flags & CG_BORROW_DEVICE) return fail(c, CG_EINVAL, "a batch is always copied into one union graph");
+  const bool host_reads = (flags & CG_HOST_READS) != 0;
+  std::vector<const uint8_t*> alias(host_reads ? k : 0, nullptr);
+  std::vector<int64_t> gbytes(host_reads ? k : 0, 0);
+  if (host_reads) {
+    for (int j = 0; j < k; ++j) {
+      if (d[j].mem != CG_MEM_HOST) return fail(c, CG_EINVAL, "CG_HOST_READS needs host inputs");
+      gbytes[j] = d[j].packed_bytes;
+      if (d[j].packed_bytes == 0) continue;
+      alias[j] = (const uint8_t*)pinned_device_alias(d[j].packed);
+      if (!alias[j]) return fail(c, CG_EINVAL, "graph %d: CG_HOST_READS needs its reads in pinned host memory", j);
+      if (!aligned(alias[j], 4)) return fail(c, CG_EINVAL, "graph %d: pinned reads must start 4-byte aligned", j);
+    }
+  }
   const int mem = d[0].mem, rpb = d[0].row_ptr_bytes, mcr = d[0].min_chain_reads;
   const bool xdrop = d[0].pre && d[0].post;
   std::vector<int64_t> R(k + 1, 0), E(k + 1, 0), PB(k + 1, 0), SR(k + 1, 0);
@@ -715,13 +778,15 @@ cg_status cg_load_batch(cg_ctx* c, const cg_graph_desc* d, int k, uint32_t flags
   int32_t* post = xdrop ? galloc<int32_t>(g, (size_t)(m > 0 ? m : 1), &st) : nullptr;
   int32_t* len = galloc<int32_t>(g, (size_t)(n > 0 ? n : 1), &st);
   int64_t* off = galloc<int64_t>(g, (size_t)(n > 0 ? n : 1), &st);
-  uint8_t* packed = galloc<uint8_t>(g, (size_t)PB[k] + 16, &st);
+  uint8_t* packed = host_reads ? nullptr : galloc<uint8_t>(g, (size_t)PB[k] + 16, &st);
+  const uint8_t** hb_base = host_reads ? galloc<const uint8_t*>(g, (size_t)k, &st) : nullptr;
+  int64_t* hb_bytes = host_reads ? galloc<int64_t>(g, (size_t)k, &st) : nullptr;
   void* stage_rp = dalloc(c, (size_t)SR[k] * rpb, &st);
   int64_t* tab = galloc<int64_t>(g, 4 * (size_t)(k + 1), &st);
   if (st != CG_OK) { dfree(c, stage_rp); return bail(st); }
   g->batch_k = k;
   g->batch_R = tab;
-  CK(cudaMemsetAsync(packed, 0, (size_t)PB[k] + 16, c->stream), "clear packed");
+  if (!host_reads) CK(cudaMemsetAsync(packed, 0, (size_t)PB[k] + 16, c->stream), "clear packed");
   for (int j = 0; j < k; ++j) {
     const cg_graph_desc& q = d[j];
     auto cp = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
@@ -735,7 +800,7 @@ cg_status cg_load_batch(cg_ctx* c, const cg_graph_desc* d, int k, uint32_t flags
     if (e == cudaSuccess && xdrop) e = cp(post + E[j], q.post, (size_t)q.n_entries * 4);
     if (e == cudaSuccess) e = cp(len + R[j], q.len, (size_t)q.n_reads * 4);
     if (e == cudaSuccess) e = cp(off + R[j], q.off, (size_t)q.n_reads * 8);
-    if (e == cudaSuccess) e = cp(packed + PB[j], q.packed, (size_t)q.packed_bytes);
+    if (e == cudaSuccess && !host_reads) e = cp(packed + PB[j], q.packed, (size_t)q.packed_bytes);
     if (e != cudaSuccess) { dfree(c, stage_rp); return bail(cuda_fail(c, e, "copy batch input")); }
   }
   std::vector<int64_t> host_tab;
@@ -744,6 +809,12 @@ cg_status cg_load_batch(cg_ctx* c, const cg_graph_desc* d, int k, uint32_t flags
   host_tab.insert(host_tab.end(), PB.begin(), PB.end());
   host_tab.insert(host_tab.end(), SR.begin(), SR.end());
   CK(cudaMemcpyAsync(tab, host_tab.data(), host_tab.size() * 8, cudaMemcpyHostToDevice, c->stream), "copy tables");
+  if (host_reads) {
+    CK(cudaMemcpyAsync(hb_base, alias.data(), (size_t)k * sizeof(void*), cudaMemcpyHostToDevice, c->stream),
+       "copy read stream table");
+    CK(cudaMemcpyAsync(hb_bytes, gbytes.data(), (size_t)k * 8, cudaMemcpyHostToDevice, c->stream),
+       "copy read stream table");
+  }
   CK(cg::launch_batch_fixup(k, tab, tab + (k + 1), tab + 2 * (k + 1), tab + 3 * (k + 1), stage_rp, rpb, rp, col, off,
                             n, m, c->env), "batch fixup");
   CK(cudaStreamSynchronize(c->stream), "stream synchronize");   // host_tab is read by the copy above
@@ -757,6 +828,13 @@ cg_status cg_load_batch(cg_ctx* c, const cg_graph_desc* d, int k, uint32_t flags
   G.len = len;
   G.off = off;
   G.packed = packed;
+  if (host_reads) {
+    g->host_batch = true;
+    g->hb_base = hb_base;
+    g->hb_bytes = hb_bytes;
+    g->hb_PB = tab + 2 * (k + 1);
+    G.packed_readable = 0;          // no union stream on the device: the spelling reads gathered pieces
+  }
   st = finish_load(g, flags);
   if (st != CG_OK) return bail(st);
   *out = g;
@@ -860,14 +938,19 @@ cg_status cg_emit_contigs(cg_graph* g, int64_t* contig_off, int64_t contig_off_c
   if ((bases && bases_cap < 0) || (contig_off && contig_off_cap < 1)) return fail(c, CG_EINVAL, "bad capacity");
   st = run_offsets(g);
   if (st != CG_OK) return st;
+  if (bases) {
+    st = prepare_emit(g);
+    if (st != CG_OK) return st;
+  }
   if (mem == CG_MEM_DEVICE) {
     if (bases) {
       if (!aligned(bases, 16)) return fail(c, CG_EINVAL, "device bases buffer must be 16-byte aligned");
       StageTimer tm(c, 3);
-      uint64_t key = mix_key(mix_key(mix_key((uint64_t)(uintptr_t)bases, (uint64_t)bases_cap), (uint64_t)c->tune.tile_bytes),
+      uint64_t key = mix_key(mix_key(mix_key(mix_key((uint64_t)(uintptr_t)bases, (uint64_t)bases_cap),
+                                             (uint64_t)(uintptr_t)emit_graph(g).packed), (uint64_t)c->tune.tile_bytes),
                              (uint64_t)c->tune.emit_blocks_per_sm);
       st = run_stage(g, 3, key, [&]() -> cg_status {
-        CK(cg::launch_emit(g->g, g->s, c->tune, bases, bases_cap, c->env), "emission kernel");
+        CK(cg::launch_emit(emit_graph(g), g->s, c->tune, bases, bases_cap, c->env), "emission kernel");
         return CG_OK;
       });
       if (st != CG_OK) return st;
@@ -907,10 +990,11 @@ cg_status cg_emit_contigs(cg_graph* g, int64_t* contig_off, int64_t contig_off_c
       }
       {
         StageTimer tm(c, 3);
-        uint64_t key = mix_key(mix_key(mix_key((uint64_t)(uintptr_t)dst, (uint64_t)dcap),
+        uint64_t key = mix_key(mix_key(mix_key(mix_key((uint64_t)(uintptr_t)dst, (uint64_t)dcap),
+                                           (uint64_t)(uintptr_t)emit_graph(g).packed),
                                        (uint64_t)c->tune.tile_bytes), (uint64_t)c->tune.emit_blocks_per_sm);
         st = run_stage(g, 3, key, [&]() -> cg_status {
-          CK(cg::launch_emit(g->g, g->s, c->tune, dst, dcap, c->env), "emission kernel");
+          CK(cg::launch_emit(emit_graph(g), g->s, c->tune, dst, dcap, c->env), "emission kernel");
           return CG_OK;
         });
         if (st != CG_OK) return st;
@@ -940,12 +1024,17 @@ cg_status cg_emit_contigs_2bit(cg_graph* g, int64_t* contig_off, int64_t contig_
   if ((packed_out && packed_cap < 0) || (contig_off && contig_off_cap < 1)) return fail(c, CG_EINVAL, "bad capacity");
   st = run_offsets(g);
   if (st != CG_OK) return st;
+  if (packed_out) {
+    st = prepare_emit(g);
+    if (st != CG_OK) return st;
+  }
   auto emit = [&](uint8_t* dst, int64_t cap) -> cg_status {
     StageTimer tm(c, 3);
-    uint64_t key = mix_key(mix_key(mix_key((uint64_t)(uintptr_t)dst, (uint64_t)cap), (uint64_t)c->tune.tile_bytes),
+    uint64_t key = mix_key(mix_key(mix_key(mix_key((uint64_t)(uintptr_t)dst, (uint64_t)cap),
+                                           (uint64_t)(uintptr_t)emit_graph(g).packed), (uint64_t)c->tune.tile_bytes),
                            (uint64_t)c->tune.emit_blocks_per_sm);
     return run_stage(g, 5, key, [&]() -> cg_status {
-      CK(cg::launch_emit2(g->g, g->s, c->tune, dst, cap, c->env), "2-bit emission kernel");
+      CK(cg::launch_emit2(emit_graph(g), g->s, c->tune, dst, cap, c->env), "2-bit emission kernel");
       return CG_OK;
     });
   };

@@ -74,3 +74,111 @@ cudaError_t launch_batch_ranges(const Scratch& s, int k, const int64_t* R, long 
 }
 
 }  // namespace cg
+
+// ------------------------------------------------------------------------
+// Batches whose reads stay in pinned host memory (CG_HOST_READS): the union
+// keeps the virtual layout of the concatenated read streams (graph j's bytes
+// at [PB[j], PB[j+1]), 16-byte aligned) without holding it. After the
+// offsets stage every piece's words are gathered from its own graph's host
+// stream into one device buffer, slot after slot, and the piece's source is
+// rewritten into that buffer; the spelling kernels then run unchanged.
+#include "cg_lookback.cuh"
+
+namespace cg {
+
+namespace {
+
+// Words [lo >> 4, (hi >> 4) + 1] of a piece of stored bases [lo, hi]: the
+// spelling reads the word after the last one for its funnel shifts.
+__device__ __forceinline__ void piece_words(unsigned long long w, int32_t len, long long* w0, long long* nw) {
+  const long long first = (long long)(w & ~(1ull << 63));
+  const bool rc = (w >> 63) != 0;
+  const long long lo = rc ? first - len + 1 : first, hi = rc ? first : first + len - 1;
+  *w0 = lo >> 4;
+  *nw = len > 0 ? (hi >> 4) - (lo >> 4) + 2 : 0;
+}
+
+struct SlotLoad {
+  const unsigned long long* wsrc;
+  const int32_t* wlen;
+  __device__ unsigned long long operator()(long long j) const {
+    long long w0, nw;
+    piece_words(wsrc[j], wlen[j], &w0, &nw);
+    return (unsigned long long)nw;
+  }
+};
+struct SlotStore {
+  unsigned long long* slot;
+  __device__ void item(long long j, unsigned long long e) const { slot[j] = e; }
+  __device__ void last(long long n, unsigned long long t) const { slot[n] = t; }
+};
+
+// One warp per piece: the graph holding its first word, the words copied
+// with that graph's bounds (words past its stream read as 0), the source
+// moved into the slot.
+__global__ void __launch_bounds__(kBlock) k_gather_pieces(Scratch s, int k, const int64_t* PB,
+                                                          const uint8_t* const* base, const int64_t* bytes,
+                                                          const unsigned long long* slot, uint32_t* dst,
+                                                          long long cap_words) {
+  const long long W = *(const volatile unsigned*)&s.ctr->n_walk;
+  const int lane = threadIdx.x & 31;
+  for (long long j = grid_tid() >> 5; j < W; j += grid_threads() >> 5) {
+    const unsigned long long w = s.wsrc[j];
+    long long w0, nw;
+    piece_words(w, s.wlen[j], &w0, &nw);
+    const long long o = (long long)slot[j];
+    if (o + nw > cap_words) {
+      if (lane == 0) set_error(s.derr, DERR_KERNEL, K_BATCH_GATHER, j);
+      continue;
+    }
+    if (nw > 0) {
+      const int g = graph_of(PB, k, 4 * w0);                 // the graph of the piece's first byte
+      const long long gw0 = w0 - PB[g] / 4;                  // its first word in that graph's stream
+      const long long gbytes = bytes[g];
+      const uint8_t* src = base[g];
+      for (long long t = lane; t < nw; t += 32) {
+        const long long x = gw0 + t;
+        uint32_t v = 0;
+        if (4 * x + 4 <= gbytes) {
+          v = *reinterpret_cast<const uint32_t*>(src + 4 * x);
+        } else {
+          for (int b = 0; b < 4; ++b)
+            if (4 * x + b < gbytes) v |= (uint32_t)src[4 * x + b] << (8 * b);
+        }
+        dst[o + t] = v;
+      }
+    }
+    if (lane == 0) {
+      const long long first = (long long)(w & ~(1ull << 63)) + 16 * (o - w0);
+      s.wsrc[j] = (unsigned long long)first | (w & (1ull << 63));
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_gather_slots(const Scratch& s, long long W, unsigned long long* slot, unsigned long long* state,
+                                long long state_cap, const LaunchEnv& env) {
+  const long long tiles = (W + kTileItems - 1) / kTileItems;
+  if (tiles > state_cap) return cudaErrorInvalidValue;
+  cudaMemsetAsync(state, 0, (size_t)(state_cap + 1) * sizeof(unsigned long long), env.stream);
+  if (W > 0) {
+    k_scan<<<(unsigned)tiles, kBlock, 0, env.stream>>>(SlotLoad{s.wsrc, s.wlen}, SlotStore{slot}, W, nullptr, state,
+                                                       state_cap, s.derr, K_BATCH_GATHER);
+    mark(env, "k_scan_slots");
+  } else {
+    cudaMemsetAsync(slot, 0, sizeof(unsigned long long), env.stream);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_pieces(const Scratch& s, int k, const int64_t* PB, const uint8_t* const* base,
+                                 const int64_t* bytes, const unsigned long long* slot, uint32_t* dst,
+                                 long long cap_words, long long W, const LaunchEnv& env) {
+  k_gather_pieces<<<grid_for(32 * (W > 0 ? W : 1), env), kBlock, 0, env.stream>>>(s, k, PB, base, bytes, slot, dst,
+                                                                                 cap_words);
+  mark(env, "k_gather_pieces");
+  return cudaGetLastError();
+}
+
+}  // namespace cg

@@ -186,6 +186,14 @@ cudaError_t launch_batch_fixup(int k, const int64_t* R, const int64_t* E, const 
                                long long N, long long M, const LaunchEnv& env);
 cudaError_t launch_batch_ranges(const Scratch& s, int k, const int64_t* R, long long N, int64_t* first_contig,
                                 int64_t* first_base, const LaunchEnv& env);
+// Batches with host-resident reads: the slots of the pieces' words (exclusive
+// scan over walk positions, total at [W]), then the gather into one device
+// buffer, which rewrites every piece's source into it.
+cudaError_t launch_gather_slots(const Scratch& s, long long W, unsigned long long* slot, unsigned long long* state,
+                                long long state_cap, const LaunchEnv& env);
+cudaError_t launch_gather_pieces(const Scratch& s, int k, const int64_t* PB, const uint8_t* const* base,
+                                 const int64_t* bytes, const unsigned long long* slot, uint32_t* dst,
+                                 long long cap_words, long long W, const LaunchEnv& env);
 // Buffers of the contig-weight sort (capacity: the number of contigs).
 struct SortBuffers {
   unsigned long long* key[2];
@@ -238,7 +246,7 @@ __device__ __forceinline__ long long block_round(long long n) { return (n + kBlo
 
 enum KernelId {
   K_VALIDATE1 = 1, K_VALIDATE2, K_MASK, K_SUCC, K_WALK, K_JUMP, K_FINAL, K_CYCLE, K_EXPORT,
-  K_SCAN_HEADS, K_SCATTER, K_SCAN_OFFSETS, K_CONTIG_OFF, K_EMIT, K_SORT, K_TRANSITIVE
+  K_SCAN_HEADS, K_SCATTER, K_SCAN_OFFSETS, K_CONTIG_OFF, K_EMIT, K_SORT, K_TRANSITIVE, K_BATCH_GATHER
 };
 
 inline int grid_for(long long n, const LaunchEnv& env, int per_sm = 8) {

@@ -119,8 +119,12 @@ void run_batch(cg_server* s, cg_ctx* ctx, cudaStream_t stream, WorkerBuffers& wb
     batch[j]->t_start = t0;
     batch[j]->batch_size = k;
   }
+  // requests whose reads are pinned host memory leave them there: the batch
+  // gathers only the bases it spells over the host link; otherwise every
+  // request's reads are copied
   cg_graph* g = nullptr;
-  cg_status st = cg_load_batch(ctx, descs.data(), k, 0, &g);
+  cg_status st = cg_load_batch(ctx, descs.data(), k, CG_HOST_READS, &g);
+  if (st == CG_EINVAL) st = cg_load_batch(ctx, descs.data(), k, 0, &g);
   std::vector<int64_t> fc(k + 1), fb(k + 1);
   int64_t n_contigs = 0, total = 0;
   if (st == CG_OK) st = cg_mask_branches(g, nullptr, CG_MEM_DEVICE, nullptr);
@@ -308,6 +312,17 @@ cg_status cg_server_stats(cg_server* s, uint64_t* batches, uint64_t* requests, u
   if (batches) *batches = s->batches;
   if (requests) *requests = s->batched_requests;
   if (in_flight_bytes) *in_flight_bytes = s->in_flight_bytes;
+  return CG_OK;
+}
+
+cg_status cg_server_kernels(cg_server* s, uint64_t* launched) {
+  if (!s || !launched) return CG_EINVAL;
+  uint64_t n = 0;
+  for (cg_ctx* c : s->ctxs) {
+    cg_stats st{};
+    if (cg_get_stats(c, &st) == CG_OK) n += st.kernels_launched;
+  }
+  *launched = n;
   return CG_OK;
 }
 

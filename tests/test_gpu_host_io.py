@@ -110,3 +110,31 @@ def test_refusals(ctx):
     assert e.value.status == cg.CG_EINVAL
     g = cg.cg_load_graph(ctx, pinned_graph(G), flags=cg.HOST_READS)   # still usable
     g.close()
+
+
+def test_batch_with_host_reads(ctx):
+    """A batch whose reads stay in pinned host memory: the pieces are gathered
+    from each graph's own stream; every graph's contigs exact, in both forms."""
+    graphs = [gen.generate(gen.batched_graph(j), threads=8, off_align=(1, 4, 32)[j % 3]) for j in (0, 3, 7, 19, 40)]
+    S = structured(12, [3000, 5, 7] + [2] * 100, [False, True, True] + [False] * 100, min_len=9, max_len=70, align=1)
+    S.row_ptr = S.row_ptr.astype(graphs[0].row_ptr.dtype)    # a batch has one row_ptr width
+    graphs.append(S)
+    want = [oracle.run(G, min_chain_reads=2) for G in graphs]
+    P = [pinned_graph(G) for G in graphs]
+    for flags in (cg.HOST_READS, 0):
+        g = cg.cg_load_batch(ctx, P, flags=flags, min_chain_reads=2)
+        try:
+            off, bases = cg.contigs_host(g)
+            off2, packed, total = cg.contigs_2bit_host(g)
+            fc, fb = cg.cg_batch_ranges(g)
+            off_again, bases_again = cg.contigs_host(g)      # a second spelling gathers again
+        finally:
+            g.close()
+        assert np.array_equal(off_again, off) and np.array_equal(bases_again, bases)
+        for j, w in enumerate(want):
+            assert np.array_equal(off[fc[j]:fc[j + 1] + 1] - fb[j], w.contig_off), (flags, j)
+            assert np.array_equal(bases[fb[j]:fb[j + 1]], w.bases), (flags, j)
+        assert np.array_equal(packed[: (total + 3) // 4], oracle.pack2(bases))
+    with pytest.raises(cg.CgError) as e:                 # one graph's reads not pinned
+        cg.cg_load_batch(ctx, P[:2] + [graphs[2]], flags=cg.HOST_READS)
+    assert e.value.status == cg.CG_EINVAL
