@@ -138,3 +138,21 @@ def test_batch_with_host_reads(ctx):
     with pytest.raises(cg.CgError) as e:                 # one graph's reads not pinned
         cg.cg_load_batch(ctx, P[:2] + [graphs[2]], flags=cg.HOST_READS)
     assert e.value.status == cg.CG_EINVAL
+
+
+def test_server_with_pinned_requests(ctx):
+    """Requests whose reads are pinned: the server gathers their pieces over the
+    host link; every result exact, alone and batched, mixed with unpinned ones."""
+    graphs = [gen.generate(gen.served_graph(j), threads=8) for j in (1, 2, 6)]
+    want = [oracle.run(G, min_chain_reads=2) for G in graphs]
+    P = [pinned_graph(G) for G in graphs]
+    srv = cg.Server(0, hbm_budget_bytes=16 << 30, max_batch=8, workers=2)
+    try:
+        ids = [(srv.submit(P[i % 3] if i % 4 else graphs[i % 3]), i % 3) for i in range(12)]
+        for rid, j in ids:
+            r = srv.wait(rid)
+            assert r["status"] == cg.CG_OK
+            assert np.array_equal(r["contig_off"], want[j].contig_off) and np.array_equal(r["bases"], want[j].bases)
+            srv.release(rid)
+    finally:
+        srv.stop()
