@@ -359,19 +359,12 @@ cg_status finish_load(cg_graph* g, uint32_t flags) {
     S.preout = galloc<int32_t>(g, N2, &st);
     S.pfirst = galloc<int32_t>(g, N, &st);
   }
-  S.rid = galloc<int32_t>(g, N2, &st);
-  S.roff = galloc<int32_t>(g, N2, &st);
+  S.rr = galloc<int2>(g, N2, &st);
   S.rlist = galloc<int32_t>(g, N2, &st);
   S.hlist = galloc<int32_t>(g, N2, &st);
-  S.r_next_node = galloc<int32_t>(g, N2, &st);
-  S.r_len = galloc<int32_t>(g, N2, &st);
-  S.r_min = galloc<int32_t>(g, N2, &st);
-  S.r_last = galloc<int32_t>(g, N2, &st);
+  S.rec = galloc<int4>(g, N2, &st);
   for (int b = 0; b < 2; ++b) {
-    S.pj_next[b] = galloc<int32_t>(g, N2, &st);
-    S.pj_acc[b] = galloc<int32_t>(g, N2, &st);
-    S.pj_min[b] = galloc<int32_t>(g, N2, &st);
-    S.pj_tail[b] = galloc<int32_t>(g, N2, &st);
+    S.pj[b] = galloc<int4>(g, N2, &st);
     S.c_ptr[b] = galloc<int32_t>(g, N2, &st);
     S.c_val[b] = galloc<int32_t>(g, N2, &st);
   }

@@ -32,7 +32,7 @@ namespace {
 
 constexpr long long kSpinLimit = 1ll << 22;   // barrier polls before giving up (~1 s with backoff)
 constexpr int kListWalkMax = 64;              // sublists a list head follows before leaving it to jumping
-constexpr int kUnresolved = -2;               // pj_next value of a sublist no list walk has finished
+constexpr int kUnresolved = -2;               // pj next field of a sublist no list walk has finished
 
 __device__ __forceinline__ int sampled(int v, int ruler_log2) {
   unsigned h = (unsigned)v * 0x9E3779B1u;
@@ -237,8 +237,7 @@ __global__ void __launch_bounds__(kBlock) k_succ(DevGraph g, Scratch s, int rule
         }
       } else {
         chain = true;
-        s.rid[2 * v] = -1;               // not yet reached by a sublist walk
-        s.rid[2 * v + 1] = -1;
+        reinterpret_cast<int4*>(s.rr)[v] = make_int4(-1, 0, -1, 0);   // not yet reached by a sublist walk
         const bool smp = sampled(v, ruler_log2) != 0;
         r0 = s1 < 0 || smp;              // (v,0) has no predecessor when (v,1) has no successor
         r1 = s0 < 0 || smp;
@@ -273,8 +272,7 @@ __global__ void k_walk(Scratch s, int ruler_log2, int64_t limit) {
     int32_t y = x, z = (x & 1) ? sv.y : sv.x, mn = x >> 1, next_start = -1;
     int32_t cnt = 0;
     for (;;) {
-      s.rid[y] = (int32_t)r;
-      s.roff[y] = cnt;
+      s.rr[y] = make_int2((int32_t)r, cnt);
       ++cnt;
       mn = min(mn, y >> 1);
       if (z < 0) break;
@@ -284,11 +282,8 @@ __global__ void k_walk(Scratch s, int ruler_log2, int64_t limit) {
       z = (z & 1) ? sz.y : sz.x;
       if (cnt > limit) { set_error(s.derr, DERR_KERNEL, K_WALK, y); break; }
     }
-    s.r_next_node[r] = next_start;
-    s.r_len[r] = cnt;
-    s.r_min[r] = mn;
-    s.r_last[r] = y;
-    s.pj_next[0][r] = kUnresolved;
+    s.rec[r] = make_int4(next_start, cnt, mn, y);
+    s.pj[0][r].x = kUnresolved;
   }
 }
 
@@ -304,12 +299,12 @@ __global__ void k_listwalk(Scratch s) {
     long long total = 0;
     bool ok = true;
     for (;;) {
-      total += s.r_len[r];
-      mn = min(mn, s.r_min[r]);
-      const int32_t nn = s.r_next_node[r];
-      if (nn < 0) break;
+      const int4 rc = s.rec[r];
+      total += rc.y;
+      mn = min(mn, rc.z);
+      if (rc.x < 0) break;
       if (++steps >= kListWalkMax) { ok = false; break; }
-      r = s.rid[nn];
+      r = s.rr[rc.x].x;
     }
     if (!ok || total > 0x7fffffffll) {
       atomicOr(&c->need_jump, 1u);
@@ -319,14 +314,11 @@ __global__ void k_listwalk(Scratch s) {
     long long acc = total;
     r = r0;
     for (;;) {
-      s.pj_acc[0][r] = (int32_t)acc;
-      s.pj_min[0][r] = mn;
-      s.pj_tail[0][r] = tail;
-      s.pj_next[0][r] = -1;
-      acc -= s.r_len[r];
-      const int32_t nn = s.r_next_node[r];
-      if (nn < 0) break;
-      r = s.rid[nn];
+      s.pj[0][r] = make_int4(-1, (int32_t)acc, mn, tail);
+      const int4 rc = s.rec[r];
+      acc -= rc.y;
+      if (rc.x < 0) break;
+      r = s.rr[rc.x].x;
     }
   }
 }
@@ -341,11 +333,8 @@ __global__ void k_jump(Scratch s) {
   if (*(volatile unsigned*)&c->need_jump == 0) return;   // the same for every block: written by the kernel before
   unsigned R = *(volatile unsigned*)&c->n_rulers;
   for (long long i = grid_tid(); i < R; i += grid_threads()) {
-    int32_t nn = s.r_next_node[i];
-    s.pj_next[0][i] = nn >= 0 ? s.rid[nn] : -1;
-    s.pj_acc[0][i] = s.r_len[i];
-    s.pj_min[0][i] = s.r_min[i];
-    s.pj_tail[0][i] = (int32_t)i;
+    const int4 rc = s.rec[i];
+    s.pj[0][i] = make_int4(rc.x >= 0 ? s.rr[rc.x].x : -1, rc.y, rc.z, (int32_t)i);
   }
   int rounds = 1;
   while ((1u << rounds) < R + 1u && rounds < 31) ++rounds;
@@ -356,20 +345,15 @@ __global__ void k_jump(Scratch s) {
     int nxt = cur ^ 1;
     unsigned active = 0;
     for (long long i = grid_tid(); i < R; i += grid_threads()) {
-      int32_t j = s.pj_next[cur][i];
-      if (j >= 0) {
-        long long acc = (long long)s.pj_acc[cur][i] + s.pj_acc[cur][j];
-        s.pj_acc[nxt][i] = acc > 0x7fffffffll ? 0x7fffffff : (int32_t)acc;   // saturates on cycles
-        s.pj_min[nxt][i] = min(s.pj_min[cur][i], s.pj_min[cur][j]);
-        s.pj_tail[nxt][i] = s.pj_tail[cur][j];
-        int32_t jj = s.pj_next[cur][j];
-        s.pj_next[nxt][i] = jj;
-        active |= (jj >= 0);
+      const int4 a = s.pj[cur][i];
+      if (a.x >= 0) {
+        const int4 b = s.pj[cur][a.x];
+        const long long acc = (long long)a.y + b.y;
+        s.pj[nxt][i] = make_int4(b.x, acc > 0x7fffffffll ? 0x7fffffff : (int32_t)acc,   // saturates on cycles
+                                 min(a.z, b.z), b.w);
+        active |= (b.x >= 0);
       } else {
-        s.pj_acc[nxt][i] = s.pj_acc[cur][i];
-        s.pj_min[nxt][i] = s.pj_min[cur][i];
-        s.pj_tail[nxt][i] = s.pj_tail[cur][i];
-        s.pj_next[nxt][i] = -1;
+        s.pj[nxt][i] = make_int4(-1, a.y, a.z, a.w);
       }
     }
     active = __syncthreads_or(active);
@@ -406,27 +390,26 @@ __global__ void k_final(DevGraph g, Scratch s) {
   const int fb = (int)*(volatile unsigned*)&c->final_buf;
   const long long N = *(volatile unsigned*)&c->n_chain;
   const long long n = (N + 31) & ~31ll;
-  const int32_t* nx = s.pj_next[fb];
-  const int32_t* acc = s.pj_acc[fb];
-  const int32_t* mnv = s.pj_min[fb];
-  const int32_t* tl = s.pj_tail[fb];
+  const int4* pj = s.pj[fb];
   for (long long k = grid_tid(); k < n; k += grid_threads()) {   // warp-uniform trip count
     bool cyc = false;
     int32_t v = 0;
     if (k < N) {
       v = s.chain[k];
-      const int32_t x0 = 2 * v, x1 = x0 + 1;
-      const int32_t i0 = s.rid[x0], i1 = s.rid[x1];
-      if (i0 < 0 || i1 < 0 || nx[i0] != -1 || nx[i1] != -1) {
+      const int32_t x0 = 2 * v;
+      const int4 r01 = reinterpret_cast<const int4*>(s.rr)[v];   // (sublist, position) of (v,0) and (v,1)
+      const int32_t i0 = r01.x, i1 = r01.z;
+      const int4 p0 = i0 >= 0 ? pj[i0] : make_int4(0, 0, 0, 0), p1 = i1 >= 0 ? pj[i1] : make_int4(0, 0, 0, 0);
+      if (i0 < 0 || i1 < 0 || p0.x != -1 || p1.x != -1) {
         cyc = true;
       } else {
-        const int32_t d0 = acc[i0] - s.roff[x0] - 1;
-        const int32_t d1 = acc[i1] - s.roff[x1] - 1;
-        const int32_t t0 = s.r_last[tl[i0]];
-        const int32_t t1 = s.r_last[tl[i1]];
+        const int32_t d0 = p0.y - r01.y - 1;
+        const int32_t d1 = p1.y - r01.w - 1;
+        const int32_t t0 = s.rec[p0.w].w;
+        const int32_t t1 = s.rec[p1.w].w;
         const int32_t h0 = t1 >> 1, h1 = t0 >> 1;       // first read of the list of (v,0) / (v,1)
-        const int32_t hr = s.rid[t1 ^ 1];               // the head of (v,0)'s list starts a sublist
-        const int32_t m = hr >= 0 ? mnv[hr] : -1;
+        const int32_t hr = s.rr[t1 ^ 1].x;              // the head of (v,0)'s list starts a sublist
+        const int32_t m = hr >= 0 ? pj[hr].z : -1;
         const int32_t q = d0 + d1 + 1;
         const int o = h0 < h1 ? 0 : 1;
         const int32_t rk = o == 0 ? d1 : d0;

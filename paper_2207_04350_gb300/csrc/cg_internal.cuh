@@ -84,19 +84,16 @@ struct Scratch {
   int32_t* sufin;       // 2n: suffix (x-drop form: post) of the overlap entering oriented read x
   int32_t* preout;      // 2n, x-drop form only: pre of the overlap leaving oriented read x
   int32_t* pfirst;      // n, x-drop form only: stored index of the piece's first base
-  int32_t* rid;         // 2n: sublist of oriented read x (-1: not reached)
-  int32_t* roff;        // 2n: position of x inside its sublist
+  // Records read together sit together: one sector per random access.
+  int2* rr;             // 2n: oriented read x -> (sublist, -1 when not reached; position inside it);
+                        //     rr[2v] and rr[2v+1] form one 16-byte record
   // sublists (capacity 2n)
   int32_t* rlist;       // first oriented read of each sublist
   int32_t* hlist;       // sublists that start a list
-  int32_t* r_next_node; // first oriented read of the next sublist, -1 at the list end
-  int32_t* r_len;
-  int32_t* r_min;       // smallest read id inside the sublist
-  int32_t* r_last;      // last oriented read of the sublist
-  int32_t* pj_next[2];  // per sublist: -1 resolved, -2 unresolved; pointer jumping double buffers
-  int32_t* pj_acc[2];
-  int32_t* pj_min[2];
-  int32_t* pj_tail[2];
+  int4* rec;            // sublist -> (first oriented read of the next sublist, -1 at the list end;
+                        //             length; smallest read id inside; last oriented read)
+  int4* pj[2];          // sublist -> (next: -1 resolved, -2 unresolved; oriented reads to the list tail;
+                        //             smallest read id to the tail; tail sublist); jumping double buffers
   // per read
   int32_t* cid;         // smallest read id of the chain
   int32_t* rank;        // walk position
