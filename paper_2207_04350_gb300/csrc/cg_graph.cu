@@ -250,13 +250,17 @@ __global__ void __launch_bounds__(kBlock) k_succ(DevGraph g, Scratch s, int rule
     block_reserve4(ctrs, cnt, base);
     if (chain) s.chain[base[0]] = v;
     if (lone) s.lone2[base[1]] = v;
+    // a sublist start knows its sublist before any walk: the walk that
+    // reaches it from the previous sublist reads the id here
     if (r0) {
       s.rlist[base[2]] = 2 * v;
+      s.rr[2 * v] = make_int2((int32_t)base[2], 0);
       if (h0) s.hlist[base[3]++] = (int32_t)base[2];
       ++base[2];
     }
     if (r1) {
       s.rlist[base[2]] = 2 * v + 1;
+      s.rr[2 * v + 1] = make_int2((int32_t)base[2], 0);
       if (h1) s.hlist[base[3]] = (int32_t)base[2];
     }
   }
@@ -282,7 +286,8 @@ __global__ void k_walk(Scratch s, int ruler_log2, int64_t limit) {
       z = (z & 1) ? sz.y : sz.x;
       if (cnt > limit) { set_error(s.derr, DERR_KERNEL, K_WALK, y); break; }
     }
-    s.rec[r] = make_int4(next_start, cnt, mn, y);
+    // the next sublist's id, written by k_succ for every sublist start
+    s.rec[r] = make_int4(next_start >= 0 ? s.rr[next_start].x : -1, cnt, mn, y);
     s.pj[0][r].x = kUnresolved;
   }
 }
@@ -304,7 +309,7 @@ __global__ void k_listwalk(Scratch s) {
       mn = min(mn, rc.z);
       if (rc.x < 0) break;
       if (++steps >= kListWalkMax) { ok = false; break; }
-      r = s.rr[rc.x].x;
+      r = rc.x;
     }
     if (!ok || total > 0x7fffffffll) {
       atomicOr(&c->need_jump, 1u);
@@ -318,7 +323,7 @@ __global__ void k_listwalk(Scratch s) {
       const int4 rc = s.rec[r];
       acc -= rc.y;
       if (rc.x < 0) break;
-      r = s.rr[rc.x].x;
+      r = rc.x;
     }
   }
 }
@@ -334,7 +339,7 @@ __global__ void k_jump(Scratch s) {
   unsigned R = *(volatile unsigned*)&c->n_rulers;
   for (long long i = grid_tid(); i < R; i += grid_threads()) {
     const int4 rc = s.rec[i];
-    s.pj[0][i] = make_int4(rc.x >= 0 ? s.rr[rc.x].x : -1, rc.y, rc.z, (int32_t)i);
+    s.pj[0][i] = make_int4(rc.x, rc.y, rc.z, (int32_t)i);
   }
   int rounds = 1;
   while ((1u << rounds) < R + 1u && rounds < 31) ++rounds;

@@ -90,7 +90,7 @@ struct Scratch {
   // sublists (capacity 2n)
   int32_t* rlist;       // first oriented read of each sublist
   int32_t* hlist;       // sublists that start a list
-  int4* rec;            // sublist -> (first oriented read of the next sublist, -1 at the list end;
+  int4* rec;            // sublist -> (the next sublist, -1 at the list end;
                         //             length; smallest read id inside; last oriented read)
   int4* pj[2];          // sublist -> (next: -1 resolved, -2 unresolved; oriented reads to the list tail;
                         //             smallest read id to the tail; tail sublist); jumping double buffers
