@@ -300,14 +300,17 @@ __global__ void k_listwalk(Scratch s) {
   const long long H = *(volatile unsigned*)&c->n_hlist;
   for (long long h = grid_tid(); h < H; h += grid_threads()) {
     const int32_t r0 = s.hlist[h];
-    int32_t r = r0, mn = 0x7fffffff, steps = 0;
+    int32_t r = r0, mn = 0x7fffffff, steps = 0, tail = -1;
     long long total = 0;
     bool ok = true;
     for (;;) {
       const int4 rc = s.rec[r];
       total += rc.y;
       mn = min(mn, rc.z);
-      if (rc.x < 0) break;
+      if (rc.x < 0) {
+        tail = rc.w;                     // the list's last oriented read
+        break;
+      }
       if (++steps >= kListWalkMax) { ok = false; break; }
       r = rc.x;
     }
@@ -315,7 +318,6 @@ __global__ void k_listwalk(Scratch s) {
       atomicOr(&c->need_jump, 1u);
       continue;
     }
-    const int32_t tail = r;
     long long acc = total;
     r = r0;
     for (;;) {
@@ -331,15 +333,15 @@ __global__ void k_listwalk(Scratch s) {
 // Pointer jumping over all sublists (grid-synchronised rounds), only when a
 // list walk gave up (very long chains). After it, for a sublist on an open
 // list: acc = oriented reads from its start to the list tail, mn = smallest
-// read id over that span, tail = last sublist. Sublists on directed cycles
-// keep next >= 0.
+// read id over that span, tail = the list's last oriented read. Sublists on
+// directed cycles keep next >= 0.
 __global__ void k_jump(Scratch s) {
   Counters* c = s.ctr;
   if (*(volatile unsigned*)&c->need_jump == 0) return;   // the same for every block: written by the kernel before
   unsigned R = *(volatile unsigned*)&c->n_rulers;
   for (long long i = grid_tid(); i < R; i += grid_threads()) {
     const int4 rc = s.rec[i];
-    s.pj[0][i] = make_int4(rc.x, rc.y, rc.z, (int32_t)i);
+    s.pj[0][i] = make_int4(rc.x, rc.y, rc.z, rc.w);
   }
   int rounds = 1;
   while ((1u << rounds) < R + 1u && rounds < 31) ++rounds;
@@ -410,11 +412,11 @@ __global__ void k_final(DevGraph g, Scratch s) {
       } else {
         const int32_t d0 = p0.y - r01.y - 1;
         const int32_t d1 = p1.y - r01.w - 1;
-        const int32_t t0 = s.rec[p0.w].w;
-        const int32_t t1 = s.rec[p1.w].w;
+        const int32_t t0 = p0.w, t1 = p1.w;              // last oriented reads of both lists
         const int32_t h0 = t1 >> 1, h1 = t0 >> 1;       // first read of the list of (v,0) / (v,1)
-        const int32_t hr = s.rr[t1 ^ 1].x;              // the head of (v,0)'s list starts a sublist
-        const int32_t m = hr >= 0 ? pj[hr].z : -1;
+        // the smallest read of the chain: (v,0)'s list from v's sublist on and
+        // (v,1)'s list (the same reads, reversed) from v's sublist on cover it
+        const int32_t m = min(p0.z, p1.z);
         const int32_t q = d0 + d1 + 1;
         const int o = h0 < h1 ? 0 : 1;
         const int32_t rk = o == 0 ? d1 : d0;

@@ -93,7 +93,8 @@ struct Scratch {
   int4* rec;            // sublist -> (the next sublist, -1 at the list end;
                         //             length; smallest read id inside; last oriented read)
   int4* pj[2];          // sublist -> (next: -1 resolved, -2 unresolved; oriented reads to the list tail;
-                        //             smallest read id to the tail; tail sublist); jumping double buffers
+                        //             smallest read id to the tail; the list's last oriented read);
+                        //             jumping double buffers
   // per read
   int32_t* cid;         // smallest read id of the chain
   int32_t* rank;        // walk position
