@@ -369,10 +369,7 @@ cg_status finish_load(cg_graph* g, uint32_t flags) {
     S.c_val[b] = galloc<int32_t>(g, N2, &st);
   }
   S.c_head = galloc<int32_t>(g, N2, &st);
-  S.cid = galloc<int32_t>(g, N, &st);
-  S.rank = galloc<int32_t>(g, N, &st);
-  S.orient = galloc<uint8_t>(g, N, &st);
-  S.contrib = galloc<int32_t>(g, N, &st);
+  S.prd = galloc<int4>(g, N, &st);
   S.headq = galloc<int32_t>(g, N, &st);
   S.cyc = galloc<int32_t>(g, N, &st);
   S.qd = galloc<int32_t>(g, N, &st);

@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(kBlock) k_mask(DevGraph g, Scratch s) {
         if (!br && d == 0) {
           lone = g.min_chain <= 1;
           if (lone) {
-            s.cid[v] = (int32_t)v; s.rank[v] = 0; s.orient[v] = 0; s.contrib[v] = g.len[v]; s.headq[v] = 1;
+            s.prd[v] = make_int4((int32_t)v, 0, g.len[v], 0); s.headq[v] = 1;
             lonem |= 1u << k;
           }
         } else if (!br) {
@@ -227,10 +227,7 @@ __global__ void __launch_bounds__(kBlock) k_succ(DevGraph g, Scratch s, int rule
       s.succ[v] = make_int2(s0, s1);
       if (s0 < 0 && s1 < 0) {            // every overlap leads to a branch read
         lone = g.min_chain <= 1;
-        s.cid[v] = lone ? v : -1;
-        s.rank[v] = lone ? 0 : -1;
-        s.orient[v] = lone ? 0 : 255;
-        s.contrib[v] = g.len[v];
+        s.prd[v] = make_int4(lone ? v : -1, lone ? 0 : -1, g.len[v], lone ? 0 : 255);
         if (lone) {
           mark_head(s, v, 1);
           atomicAdd(&c->n_heads, 1u);
@@ -376,15 +373,25 @@ __global__ void k_jump(Scratch s) {
 // contig of q reads, contributes l_v[post(e_in) : pre(e_out)] with alpha (its
 // first base in walk direction) for the first read and beta (its last) for
 // the last one; a piece whose end comes before its start is empty.
-__device__ __forceinline__ void set_piece(const DevGraph& g, const Scratch& s, int32_t v, int32_t y, int32_t rk,
-                                          int32_t q) {
+// Returns the piece's length; its first stored base goes to pfirst.
+__device__ __forceinline__ int32_t set_piece(const DevGraph& g, const Scratch& s, int32_t v, int32_t y, int32_t rk,
+                                             int32_t q) {
   const int o = y & 1;
   const int32_t L = g.len[v];
   const int32_t first = rk == 0 ? (o == 0 ? 0 : L - 1) : s.sufin[y];
   const int32_t last = rk == q - 1 ? (o == 0 ? L - 1 : 0) : s.preout[y];
   const int32_t cnt = o == 0 ? last - first + 1 : first - last + 1;
-  s.contrib[v] = cnt > 0 ? cnt : 0;
   s.pfirst[v] = first;
+  return cnt > 0 ? cnt : 0;
+}
+
+// The bases a chain read adds: the first read whole, each later one the
+// suffix of the overlap it is entered through (or, in the x-drop form, its
+// piece).
+__device__ __forceinline__ int32_t piece_len(const DevGraph& g, const Scratch& s, int32_t v, int32_t y, int32_t rk,
+                                             int32_t q) {
+  if (g.pre) return set_piece(g, s, v, y, rk, q);
+  return rk == 0 ? g.len[v] : s.sufin[y];
 }
 
 // Per chain read: combine its two oriented copies. head(list of (v,0)) is
@@ -422,19 +429,13 @@ __global__ void k_final(DevGraph g, Scratch s) {
         const int32_t rk = o == 0 ? d1 : d0;
         if (m < 0 || h0 == h1) set_error(s.derr, DERR_KERNEL, K_FINAL, v);
         if (q >= g.min_chain) {
-          s.cid[v] = m;
-          s.rank[v] = rk;
-          s.orient[v] = (uint8_t)o;
-          if (g.pre) set_piece(g, s, v, x0 + o, rk, q);
-          else s.contrib[v] = rk == 0 ? g.len[v] : s.sufin[x0 + o];
+          s.prd[v] = make_int4(m, rk, piece_len(g, s, v, x0 + o, rk, q), o);
           if (v == m) {
             mark_head(s, m, q);
             atomicAdd(&c->n_heads, 1u);
           }
         } else {
-          s.cid[v] = -1;
-          s.rank[v] = -1;
-          s.orient[v] = 255;
+          s.prd[v] = make_int4(-1, -1, 0, 255);
         }
       }
     }
@@ -518,19 +519,13 @@ __global__ void k_cycles(DevGraph g, Scratch s) {
     int32_t rk = L - 1 - s.c_val[cur][y];
     int32_t m = head >> 1;
     if (L >= g.min_chain) {
-      s.cid[v] = m;
-      s.rank[v] = rk;
-      s.orient[v] = (uint8_t)(y & 1);
-      if (g.pre) set_piece(g, s, v, y, rk, L);
-      else s.contrib[v] = rk == 0 ? g.len[v] : s.sufin[y];
+      s.prd[v] = make_int4(m, rk, piece_len(g, s, v, y, rk, L), y & 1);
       if (rk == 0) {
         mark_head(s, m, L);
         atomicAdd(&c->n_heads, 1u);
       }
     } else {
-      s.cid[v] = -1;
-      s.rank[v] = -1;
-      s.orient[v] = 255;
+      s.prd[v] = make_int4(-1, -1, 0, 255);
     }
     if (rk == 0) atomicAdd(&c->n_cycles, 1u);
   }
@@ -544,7 +539,8 @@ __global__ void k_export_reads(DevGraph g, Scratch s, int32_t* cid, int32_t* ran
     if (d == 0) {
       if (g.min_chain <= 1) { a = (int32_t)v; b = 0; o = 0; }
     } else if (!s.branch[v]) {
-      a = s.cid[v]; b = s.rank[v]; o = s.orient[v];
+      const int4 p = s.prd[v];
+      a = p.x; b = p.y; o = (uint8_t)p.w;
     }
     if (cid) cid[v] = a;
     if (rank) rank[v] = b;

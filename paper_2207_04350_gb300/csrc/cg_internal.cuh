@@ -96,10 +96,8 @@ struct Scratch {
                         //             smallest read id to the tail; the list's last oriented read);
                         //             jumping double buffers
   // per read
-  int32_t* cid;         // smallest read id of the chain
-  int32_t* rank;        // walk position
-  uint8_t* orient;
-  int32_t* contrib;     // bases this read adds to its contig
+  int4* prd;            // n: (smallest read id of the chain, -1 in no contig; walk position;
+                        //     bases this read adds to its contig; orientation 0 / 1, 255 in no contig)
   int32_t* headq;       // at a contig's smallest read: its number of reads
   // closed chains
   int32_t* cyc;         // n: reads on closed chains

@@ -113,15 +113,16 @@ __global__ void k_scatter(DevGraph g, Scratch s) {
   const long long total = L1 + L2 + NC;
   for (long long k = grid_tid(); k < total; k += grid_threads()) {
     const int32_t v = k < L1 ? s.lone[k] : (k < L1 + L2 ? s.lone2[k - L1] : s.chain[k - L1 - L2]);
-    const int32_t m = s.cid[v];
+    const int4 p = s.prd[v];
+    const int32_t m = p.x;
     if (m < 0) continue;                 // a chain shorter than min_chain
     const unsigned word = s.hb[m >> 5];
     const long long cidx = (long long)s.wp[m >> 5] + __popc(word & ((1u << (m & 31)) - 1u));
-    const int32_t rk = s.rank[v];
+    const int32_t rk = p.y;
     const long long pos = (long long)s.cbase[cidx] + rk;
     if (!((word >> (m & 31)) & 1u) || pos >= W) { set_error(s.derr, DERR_KERNEL, K_SCATTER, v); continue; }
-    const int o = s.orient[v];
-    const int32_t L = g.len[v], cb = s.contrib[v];
+    const int o = p.w;
+    const int32_t L = g.len[v], cb = p.z;
     const int64_t base = g.off[v];
     // stored index of the piece's first base: suffix form, the last cb bases
     // of the oriented read; x-drop form, set by the chain stage (a read spelled
