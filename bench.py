@@ -345,7 +345,7 @@ def run_batched(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "ms_per_graph": ms / k,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
-        "data": "synthetic (seeded generator, workload recipe in DESIGN.md)",
+        "data": "synthetic (the seeded generator gen/: genome, repeats, reads and overlaps of the stated recipe)",
         "config": {
             "workload": f"batched-{k} (graphs log-U[0.5,12] Mb genome, 2% repeats, 30x, LN(10 kb, 5 kb))",
             "graphs": k, "n_reads": n_reads, "contig_bases": total, "n_contigs": n_contigs,
@@ -470,7 +470,7 @@ def run_served(args, rank, world, local_rank):
         "unit": UNIT, "n_gpus": world,
         "steps": R, "warmup": 0, "ms_per_step": 1e3 / served_max["graphs_per_s"],
         "ms_per_graph": 1e3 / served_max["graphs_per_s"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u8", "data": "synthetic (seeded generator, workload recipe in DESIGN.md)",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic (the seeded generator gen/: genome, repeats, reads and overlaps of the stated recipe)",
         "config": {
             "workload": f"served-{R} (Poisson requests over a pool of {P} graphs, genome log-U[1,200] Mb, 5% repeats, "
                         "30x, LN(12 kb, 6 kb))",
@@ -794,7 +794,7 @@ def run_ours(args, rank, world, local_rank):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "ms_per_graph": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u8", "data": "synthetic (seeded generator, workload recipe in DESIGN.md)",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic (the seeded generator gen/: genome, repeats, reads and overlaps of the stated recipe)",
         "config": {
             "workload": args.workload + (f" (recipe scaled to {args.scale_genome} bases)" if args.scale_genome else ""),
             "tuning": cg.cg_get_tuning(ctx), "n_reads": G.n, "n_entries": G.m, "walk_reads": W, "n_contigs": n_contigs,
