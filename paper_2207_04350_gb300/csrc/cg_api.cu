@@ -1133,6 +1133,7 @@ cg_status cg_transitive_reduction(cg_ctx* c, const cg_graph_desc* d, int32_t fuz
   G.suf = (const int32_t*)in(d->suf, (size_t)m * 4);
   G.len = (const int32_t*)in(d->len, (size_t)n * 4);
   cg::TrBuffers t{};
+  t.row_of = (int32_t*)alloc((size_t)m * 4);
   t.trans = (uint8_t*)alloc((size_t)m);
   t.keep = (uint8_t*)alloc((size_t)m);
   t.row_cnt = (int32_t*)alloc((size_t)n * 4);
@@ -1154,7 +1155,7 @@ cg_status cg_transitive_reduction(cg_ctx* c, const cg_graph_desc* d, int32_t fuz
   if (e != cudaSuccess) return done(cuda_fail(c, e, "row checks"));
   st = wait_and_read(&probe);
   if (st != CG_OK) return done(st);
-  e = cg::launch_transitive_entries(G, c->derr, c->env);
+  e = cg::launch_transitive_entries(G, t, c->env);
   if (e != cudaSuccess) return done(cuda_fail(c, e, "entry checks"));
   st = wait_and_read(&probe);
   if (st != CG_OK) return done(st);

@@ -201,6 +201,7 @@ struct SortBuffers {
 };
 // Buffers of the transitive reduction (m entries, n rows).
 struct TrBuffers {
+  int32_t* row_of;             // m: row of every entry
   uint8_t* trans;              // m: entry is transitive
   uint8_t* keep;               // m: entry kept (its pair is not transitive)
   int32_t* row_cnt;            // n: kept entries per row
@@ -215,7 +216,7 @@ struct TrBuffers {
 // entries (launch_transitive_scatter). Each step needs the checks before it
 // to have passed: the later kernels index rows by column values.
 cudaError_t launch_transitive_check(const DevGraph& g, DevError* derr, const LaunchEnv& env);
-cudaError_t launch_transitive_entries(const DevGraph& g, DevError* derr, const LaunchEnv& env);
+cudaError_t launch_transitive_entries(const DevGraph& g, const TrBuffers& t, const LaunchEnv& env);
 cudaError_t launch_transitive(const DevGraph& g, int fuzz, const TrBuffers& t, const LaunchEnv& env);
 cudaError_t launch_transitive_scatter(const DevGraph& g, const TrBuffers& t, int32_t* col, uint8_t* code, int32_t* suf,
                                       const LaunchEnv& env);

@@ -7,11 +7,12 @@
 // and whose suffixes add up to x's within a tolerance. A pair of reads keeps
 // both entries only when neither is transitive.
 //
-// One warp per read u: each lane takes entries (u->v) of u's row, walks v's
-// row, and looks each w up in u's row (rows are sorted by column) by binary
-// search. Then a warp per row keeps the entries whose pair is not transitive
-// and counts them, a look-back scan gives the new row offsets, and a warp per
-// row writes the kept entries in order.
+// Rows hold a few entries and most reads none, so after one pass that writes
+// every entry's row, the work takes one thread per entry: the entry (u->v)
+// walks v's row and looks each w up in u's row (rows are sorted by column) by
+// binary search; an entry is kept when neither it nor its mirror is
+// transitive; per-row counts and a look-back scan give the new row offsets;
+// every kept entry goes to its row's offset plus the kept entries before it.
 #include <cuda_runtime.h>
 
 #include "cg_internal.cuh"
@@ -47,73 +48,74 @@ __global__ void k_tr_check(DevGraph g, DevError* e) {
   if (grid_tid() == 0 && (rowp(g, 0) != 0 || rowp(g, g.n) != g.m)) set_error(e, DERR_GRAPH, K_TRANSITIVE, -1);
 }
 
+// Row of every entry (one thread per row), so that the kernels below can
+// take one thread per entry: rows hold few entries and most reads none.
+__global__ void k_tr_rowof(DevGraph g, int32_t* row_of) {
+  for (long long u = grid_tid(); u < g.n; u += grid_threads()) {
+    const int64_t a = rowp(g, u), b = rowp(g, u + 1);
+    for (int64_t x = a; x < b; ++x) row_of[x] = (int32_t)u;
+  }
+}
+
 // Entries, once the rows are known sorted: column in range and not the row
 // itself, code 0..3, suffix in [1, len-1], and exactly one mirror entry (found
 // by binary search) with the swapped code.
-__global__ void k_tr_entries(DevGraph g, DevError* e) {
+__global__ void k_tr_entries(DevGraph g, const int32_t* row_of, DevError* e) {
+  for (long long x = grid_tid(); x < g.m; x += grid_threads()) {
+    const int32_t u = row_of[x], w = g.col[x];
+    const int cd = g.code[x];
+    if (w < 0 || w >= g.n || w == u || cd > 3) {
+      set_error(e, DERR_GRAPH, K_TRANSITIVE, x);
+      continue;
+    }
+    const int32_t sf = g.suf[x];
+    if (sf < 1 || sf > g.len[w] - 1) set_error(e, DERR_GRAPH, K_TRANSITIVE, x);
+    const int64_t y = find_col(g.col, rowp(g, w), rowp(g, w + 1), u);
+    if (y < 0 || g.code[y] != (((cd & 1) << 1) | (cd >> 1))) set_error(e, DERR_GRAPH, K_TRANSITIVE, x);
+  }
+}
+
+// One thread per entry y = (u->v): every walk u -> v -> w through v's row,
+// each w looked up in u's sorted row; marks the transitive (u->w).
+__global__ void __launch_bounds__(kBlock) k_tr_mark(DevGraph g, const int32_t* row_of, int fuzz, uint8_t* trans) {
+  for (long long y = grid_tid(); y < g.m; y += grid_threads()) {
+    const int32_t u = row_of[y], v = g.col[y];
+    const int cy = g.code[y];
+    const int32_t sy = g.suf[y];
+    const int eu = cy & 1, ev_in = (cy >> 1) & 1;
+    const int64_t a = rowp(g, u), b = rowp(g, u + 1);
+    const int64_t va = rowp(g, v), vb = rowp(g, v + 1);
+    for (int64_t z = va; z < vb; ++z) {
+      const int cz = g.code[z];
+      if ((cz & 1) != 1 - ev_in) continue;        // leave v through its other end
+      const int32_t w = g.col[z];
+      if (w == u) continue;
+      const int64_t x = find_col(g.col, a, b, w);
+      if (x < 0) continue;
+      const int cx = g.code[x];
+      if ((cx & 1) != eu || ((cx >> 1) & 1) != ((cz >> 1) & 1)) continue;   // the ends of x
+      const long long d = (long long)sy + g.suf[z] - g.suf[x];
+      if (d <= fuzz && d >= -fuzz) trans[x] = 1;
+    }
+  }
+}
+
+// One thread per entry: kept when neither it nor its mirror is transitive.
+__global__ void k_tr_keep(DevGraph g, const int32_t* row_of, const uint8_t* trans, uint8_t* keep) {
+  for (long long x = grid_tid(); x < g.m; x += grid_threads()) {
+    const int32_t u = row_of[x], w = g.col[x];
+    const int64_t y = find_col(g.col, rowp(g, w), rowp(g, w + 1), u);
+    keep[x] = !trans[x] && !(y >= 0 && trans[y]);
+  }
+}
+
+// One thread per row: its kept entries.
+__global__ void k_tr_rowcnt(DevGraph g, const uint8_t* keep, int32_t* row_cnt) {
   for (long long u = grid_tid(); u < g.n; u += grid_threads()) {
     const int64_t a = rowp(g, u), b = rowp(g, u + 1);
-    for (int64_t x = a; x < b; ++x) {
-      const int32_t w = g.col[x];
-      const int cd = g.code[x];
-      if (w < 0 || w >= g.n || w == (int32_t)u || cd > 3) {
-        set_error(e, DERR_GRAPH, K_TRANSITIVE, x);
-        continue;
-      }
-      const int32_t sf = g.suf[x];
-      if (sf < 1 || sf > g.len[w] - 1) set_error(e, DERR_GRAPH, K_TRANSITIVE, x);
-      const int64_t y = find_col(g.col, rowp(g, w), rowp(g, w + 1), (int32_t)u);
-      if (y < 0 || g.code[y] != (((cd & 1) << 1) | (cd >> 1))) set_error(e, DERR_GRAPH, K_TRANSITIVE, x);
-    }
-  }
-}
-
-__global__ void __launch_bounds__(kBlock) k_tr_mark(DevGraph g, int fuzz, uint8_t* trans) {
-  const int lane = threadIdx.x & 31;
-  const long long warps = grid_threads() >> 5;
-  for (long long u = grid_tid() >> 5; u < g.n; u += warps) {
-    const int64_t a = rowp(g, u), b = rowp(g, u + 1);
-    for (int64_t y = a + lane; y < b; y += 32) {
-      const int32_t v = g.col[y];
-      const int cy = g.code[y];
-      const int32_t sy = g.suf[y];
-      const int eu = cy & 1, ev_in = (cy >> 1) & 1;
-      const int64_t va = rowp(g, v), vb = rowp(g, v + 1);
-      for (int64_t z = va; z < vb; ++z) {
-        const int cz = g.code[z];
-        if ((cz & 1) != 1 - ev_in) continue;        // leave v through its other end
-        const int32_t w = g.col[z];
-        if (w == (int32_t)u) continue;
-        const int64_t x = find_col(g.col, a, b, w);
-        if (x < 0) continue;
-        const int cx = g.code[x];
-        if ((cx & 1) != eu || ((cx >> 1) & 1) != ((cz >> 1) & 1)) continue;   // the ends of x
-        const long long d = (long long)sy + g.suf[z] - g.suf[x];
-        if (d <= fuzz && d >= -fuzz) trans[x] = 1;
-      }
-    }
-  }
-}
-
-__global__ void __launch_bounds__(kBlock) k_tr_keep(DevGraph g, const uint8_t* trans, uint8_t* keep,
-                                                    int32_t* row_cnt) {
-  const int lane = threadIdx.x & 31;
-  const long long warps = grid_threads() >> 5;
-  for (long long u = grid_tid() >> 5; u < g.n; u += warps) {
-    const int64_t a = rowp(g, u), b = rowp(g, u + 1);
     int cnt = 0;
-    for (int64_t x0 = a; x0 < b; x0 += 32) {          // warp-uniform
-      const int64_t x = x0 + lane;
-      bool k = false;
-      if (x < b) {
-        const int32_t w = g.col[x];
-        const int64_t y = find_col(g.col, rowp(g, w), rowp(g, w + 1), (int32_t)u);
-        k = !trans[x] && !(y >= 0 && trans[y]);
-        keep[x] = k;
-      }
-      cnt += __popc(__ballot_sync(0xffffffffu, k));
-    }
-    if (lane == 0) row_cnt[u] = cnt;
+    for (int64_t x = a; x < b; ++x) cnt += keep[x];
+    row_cnt[u] = cnt;
   }
 }
 
@@ -131,25 +133,18 @@ struct RowPtrStore {
   }
 };
 
-__global__ void __launch_bounds__(kBlock) k_tr_scatter(DevGraph g, const uint8_t* keep, const int64_t* out_rp,
-                                                       int32_t* col, uint8_t* code, int32_t* suf) {
-  const int lane = threadIdx.x & 31;
-  const long long warps = grid_threads() >> 5;
-  for (long long u = grid_tid() >> 5; u < g.n; u += warps) {
-    const int64_t a = rowp(g, u), b = rowp(g, u + 1);
-    int64_t pos = out_rp[u];
-    for (int64_t x0 = a; x0 < b; x0 += 32) {          // warp-uniform
-      const int64_t x = x0 + lane;
-      const bool k = x < b && keep[x];
-      const unsigned m = __ballot_sync(0xffffffffu, k);
-      if (k) {
-        const int64_t o = pos + __popc(m & ((1u << lane) - 1u));
-        col[o] = g.col[x];
-        code[o] = g.code[x];
-        suf[o] = g.suf[x];
-      }
-      pos += __popc(m);
-    }
+// One thread per kept entry: its row's new offset plus the kept entries
+// before it in the row (rows keep their order).
+__global__ void k_tr_scatter(DevGraph g, const int32_t* row_of, const uint8_t* keep, const int64_t* out_rp,
+                             int32_t* col, uint8_t* code, int32_t* suf) {
+  for (long long x = grid_tid(); x < g.m; x += grid_threads()) {
+    if (!keep[x]) continue;
+    const int32_t u = row_of[x];
+    int64_t o = out_rp[u];
+    for (int64_t y = rowp(g, u); y < x; ++y) o += keep[y];
+    col[o] = g.col[x];
+    code[o] = g.code[x];
+    suf[o] = g.suf[x];
   }
 }
 
@@ -161,19 +156,22 @@ cudaError_t launch_transitive_check(const DevGraph& g, DevError* derr, const Lau
   return cudaGetLastError();
 }
 
-cudaError_t launch_transitive_entries(const DevGraph& g, DevError* derr, const LaunchEnv& env) {
-  k_tr_entries<<<grid_for(g.n, env), kBlock, 0, env.stream>>>(g, derr);
+cudaError_t launch_transitive_entries(const DevGraph& g, const TrBuffers& t, const LaunchEnv& env) {
+  k_tr_rowof<<<grid_for(g.n, env), kBlock, 0, env.stream>>>(g, t.row_of);
+  mark(env, "k_tr_rowof");
+  k_tr_entries<<<grid_for(g.m, env), kBlock, 0, env.stream>>>(g, t.row_of, t.derr);
   mark(env, "k_tr_entries");
   return cudaGetLastError();
 }
 
 cudaError_t launch_transitive(const DevGraph& g, int fuzz, const TrBuffers& t, const LaunchEnv& env) {
-  const int warps_grid = grid_for(32 * g.n, env);
   cudaMemsetAsync(t.trans, 0, (size_t)(g.m > 0 ? g.m : 1), env.stream);
-  k_tr_mark<<<warps_grid, kBlock, 0, env.stream>>>(g, fuzz, t.trans);
+  k_tr_mark<<<grid_for(g.m, env), kBlock, 0, env.stream>>>(g, t.row_of, fuzz, t.trans);
   mark(env, "k_tr_mark");
-  k_tr_keep<<<warps_grid, kBlock, 0, env.stream>>>(g, t.trans, t.keep, t.row_cnt);
+  k_tr_keep<<<grid_for(g.m, env), kBlock, 0, env.stream>>>(g, t.row_of, t.trans, t.keep);
   mark(env, "k_tr_keep");
+  k_tr_rowcnt<<<grid_for(g.n, env), kBlock, 0, env.stream>>>(g, t.keep, t.row_cnt);
+  mark(env, "k_tr_rowcnt");
   cudaMemsetAsync(t.state, 0, (size_t)(t.state_cap + 1) * sizeof(unsigned long long), env.stream);
   const long long tiles = (g.n + kTileItems - 1) / kTileItems;
   if (tiles > t.state_cap) return cudaErrorInvalidValue;
@@ -190,7 +188,7 @@ cudaError_t launch_transitive(const DevGraph& g, int fuzz, const TrBuffers& t, c
 
 cudaError_t launch_transitive_scatter(const DevGraph& g, const TrBuffers& t, int32_t* col, uint8_t* code, int32_t* suf,
                                       const LaunchEnv& env) {
-  k_tr_scatter<<<grid_for(32 * g.n, env), kBlock, 0, env.stream>>>(g, t.keep, t.out_rp, col, code, suf);
+  k_tr_scatter<<<grid_for(g.m, env), kBlock, 0, env.stream>>>(g, t.row_of, t.keep, t.out_rp, col, code, suf);
   mark(env, "k_tr_scatter");
   return cudaGetLastError();
 }
