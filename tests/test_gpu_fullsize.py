@@ -1,12 +1,16 @@
-"""Parity at the benchmark's full sizes, in the launch configuration bench.py
-times (inputs borrowed from device memory, default tuning, stages replayed
-from CUDA graphs):
+"""Parity at the benchmark's full sizes, in the launch configurations bench.py
+times (device-resident inputs borrowed in place, default tuning, stages
+replayed from CUDA graphs; host-resident reads with in-place host outputs):
 
 - the 3.1 Gb genome-shaped graph (6.2M reads, 23 GB of packed reads, 3.3 Gb
   of contigs): every contig offset and base against the oracle, which runs
-  on the whole graph, plus the per-read chains and the 2-bit form;
-- the 512-graph batch as one union: every graph's contig count and base
-  count, and the full contigs of a sample of graphs.
+  on the whole graph, plus the per-read chains and the 2-bit form; the same
+  through CG_HOST_READS into pinned host buffers; the graph in the x-drop
+  form (early starts up to 200 bases, unequal); the transitive reduction of
+  the recipe's overlap graph before reduction (3.4M entries);
+- the 512-graph batch as one union: every graph's sizes, the full contigs of
+  a sample of graphs, with the reads copied and left in host memory;
+- the served pool through the server: a sample of requests in full.
 """
 import numpy as np
 import pytest
@@ -29,10 +33,30 @@ def ctx():
     c.close()
 
 
-def test_genome_3_1gb_full(ctx):
+@pytest.fixture(scope="module")
+def genome():
     import torch
-    G = gen.generate("genome-3.1Gb", keep_genome=False)
+    keep = []
+
+    def alloc(shape, dt):                       # pinned, as bench.py generates it
+        t = torch.empty(shape, dtype=getattr(torch, dt.__name__), pin_memory=True)
+        keep.append(t)
+        return t.numpy()
+    G = gen.generate("genome-3.1Gb", keep_genome=False, alloc=alloc)
+    G._pinned = keep
     orc = oracle.run(G, min_chain_reads=2, validate=False)
+    return G, orc
+
+
+def assert_bases(got, want):
+    if not np.array_equal(got, want):
+        bad = int(np.nonzero(got != want)[0][0]) if got.size == want.size else -1
+        raise AssertionError(f"bases differ (first at {bad}; sizes {got.size}, {want.size})")
+
+
+def test_genome_3_1gb_full(ctx, genome):
+    import torch
+    G, orc = genome
     D = type("D", (), {})()
     for k in ("row_ptr", "col", "code", "suf", "len", "off", "packed"):
         setattr(D, k, torch.from_numpy(getattr(G, k)).cuda())
@@ -45,11 +69,8 @@ def test_genome_3_1gb_full(ctx):
         cg.cg_emit_contigs(g, off, bases)
         cg.cg_sync(ctx)
         assert np.array_equal(off.cpu().numpy(), orc.contig_off)
-        got = bases[:total].cpu().numpy()
-        if not np.array_equal(got, orc.bases):
-            bad = int(np.nonzero(got != orc.bases)[0][0])
-            raise AssertionError(f"bases differ first at {bad} of {total}")
-        del got, bases
+        assert_bases(bases[:total].cpu().numpy(), orc.bases)
+        del bases
         cid, rank, orient = (np.empty(G.n, np.int32), np.empty(G.n, np.int32), np.empty(G.n, np.uint8))
         cg.cg_chains(g, cid, rank, orient)
         assert np.array_equal(cid, orc.chain_id) and np.array_equal(rank, orc.rank)
@@ -62,21 +83,88 @@ def test_genome_3_1gb_full(ctx):
         g.close()
 
 
-def test_batched_512_full(ctx):
-    graphs = [gen.generate(gen.batched_graph(j), keep_genome=False) for j in range(512)]
-    g = cg.cg_load_batch(ctx, graphs, min_chain_reads=2)
+def test_genome_3_1gb_host_reads(ctx, genome):
+    import torch
+    G, orc = genome
+    g = cg.cg_load_graph(ctx, G, flags=cg.HOST_READS, min_chain_reads=2)
     try:
-        off, bases = cg.contigs_host(g)
-        fc, fb = cg.cg_batch_ranges(g)
+        off = torch.empty(orc.n_contigs + 1, dtype=torch.int64, pin_memory=True).numpy()
+        bases = torch.empty(max(orc.total_bases, 16), dtype=torch.uint8, pin_memory=True).numpy()
+        cg.cg_emit_contigs(g, off, bases)
+        assert np.array_equal(off, orc.contig_off)
+        assert_bases(bases[: orc.total_bases], orc.bases)
     finally:
         g.close()
+
+
+def test_genome_3_1gb_xdrop(ctx, genome):
+    G, _ = genome
+    X = gen.with_xdrop(G, max_trim=200, seed=7, consistent=False)
+    orc = oracle.run(X, min_chain_reads=2, validate=False)
+    g = cg.cg_load_graph(ctx, X, min_chain_reads=2)
+    try:
+        off, bases = cg.contigs_host(g)
+    finally:
+        g.close()
+    assert np.array_equal(off, orc.contig_off)
+    assert_bases(bases, orc.bases)
+
+
+def test_transitive_reduction_3_1gb(ctx):
+    R = gen.generate(dict(gen.WORKLOADS["genome-3.1Gb"](), full_overlaps=1), keep_genome=False, with_packed=False)
+    S = cg.cg_transitive_reduction(ctx, R)
+    W = oracle.transitive_reduction(R)
+    for k in ("row_ptr", "col", "code", "suf"):
+        assert np.array_equal(np.asarray(getattr(S, k)).astype(np.int64), np.asarray(getattr(W, k)).astype(np.int64)), k
+
+
+def test_batched_512_full(ctx):
+    import torch
+    keep = []
+
+    def alloc(shape, dt):
+        t = torch.empty(shape, dtype=getattr(torch, dt.__name__), pin_memory=True)
+        keep.append(t)
+        return t.numpy()
+    graphs = [gen.generate(gen.batched_graph(j), keep_genome=False, alloc=alloc) for j in range(512)]
     rng = np.random.default_rng(5)
-    sample = set(rng.choice(512, size=24, replace=False).tolist()) | {0, 511}
-    for j in range(512):
-        if j not in sample:
-            continue
-        w = oracle.run(graphs[j], min_chain_reads=2, validate=False)
-        assert fc[j + 1] - fc[j] == w.n_contigs and fb[j + 1] - fb[j] == w.total_bases
-        assert np.array_equal(off[fc[j]:fc[j + 1] + 1] - fb[j], w.contig_off)
-        assert np.array_equal(bases[fb[j]:fb[j + 1]], w.bases)
-    assert fb[512] == len(bases)
+    sample = sorted(set(rng.choice(512, size=24, replace=False).tolist()) | {0, 511})
+    want = {j: oracle.run(graphs[j], min_chain_reads=2, validate=False) for j in sample}
+    for flags in (0, cg.HOST_READS):
+        g = cg.cg_load_batch(ctx, graphs, flags=flags, min_chain_reads=2)
+        try:
+            off, bases = cg.contigs_host(g)
+            fc, fb = cg.cg_batch_ranges(g)
+        finally:
+            g.close()
+        for j in sample:
+            w = want[j]
+            assert fc[j + 1] - fc[j] == w.n_contigs and fb[j + 1] - fb[j] == w.total_bases
+            assert np.array_equal(off[fc[j]:fc[j + 1] + 1] - fb[j], w.contig_off)
+            assert np.array_equal(bases[fb[j]:fb[j + 1]], w.bases)
+        assert fb[512] == len(bases)
+
+
+def test_served_pool(ctx):
+    import torch
+    keep = []
+
+    def alloc(shape, dt):
+        t = torch.empty(shape, dtype=getattr(torch, dt.__name__), pin_memory=True)
+        keep.append(t)
+        return t.numpy()
+    pool = [gen.generate(gen.served_graph(j), keep_genome=False, alloc=alloc) for j in range(32)]
+    sample = [0, 3, 9, 17, 31]
+    want = {j: oracle.run(pool[j], min_chain_reads=2, validate=False) for j in sample}
+    srv = cg.Server(0, hbm_budget_bytes=150 << 30, max_batch=64, workers=2)
+    try:
+        ids = [(srv.submit(pool[j]), j) for j in range(32) for _ in range(2)]
+        for rid, j in ids:
+            r = srv.wait(rid, copy=j in want)
+            assert r["status"] == cg.CG_OK
+            if j in want:
+                assert np.array_equal(r["contig_off"], want[j].contig_off)
+                assert np.array_equal(r["bases"], want[j].bases)
+            srv.release(rid)
+    finally:
+        srv.stop()
