@@ -134,63 +134,192 @@ __global__ void k_validate_entries(DevGraph g, DevError* c) {
 // no overlap are lone reads: a one-read contig when min_chain <= 1. Every
 // word of the mask-stage bitmap of contig heads is written here (the lone
 // reads' bits); the chain stage adds the other heads to a copy of it.
-constexpr int kMaskItems = 4;
+// A warp owns 128 consecutive reads per pass, four per lane: a lane loads
+// its four row starts with 16-byte loads (a read's degree is the next start
+// minus its own; the fourth read's end is the next lane's first start),
+// writes its four branch bytes as one word, and queues the reads of degree
+// 1 or 2, whose rule needs the neighbours' degrees. The whole warp then
+// resolves the queue together, so that a pass waits for three dependent
+// loads (row starts; col and code; the neighbours' rows) whatever the mix of
+// degrees in it. The candidate and lone-read lists gather in per-warp
+// shared-memory buffers and reach the global lists with one reservation per
+// block at the end (a warp flushes early only when a pass could overflow its
+// buffer): returning atomics on one counter, one per pass, would serialise.
+constexpr int kMaskSpan = 128;
+constexpr int kMaskWarps = kBlock / 32;
+constexpr int kMaskBuf = 256;
 
+template <typename RP>
+__device__ __forceinline__ void load4(const RP* p, int64_t r[4]);
+template <>
+__device__ __forceinline__ void load4<int64_t>(const int64_t* p, int64_t r[4]) {
+  const longlong2 x = __ldg(reinterpret_cast<const longlong2*>(p));
+  const longlong2 y = __ldg(reinterpret_cast<const longlong2*>(p) + 1);
+  r[0] = x.x; r[1] = x.y; r[2] = y.x; r[3] = y.y;
+}
+template <>
+__device__ __forceinline__ void load4<int32_t>(const int32_t* p, int64_t r[4]) {
+  const int4 x = __ldg(reinterpret_cast<const int4*>(p));
+  r[0] = x.x; r[1] = x.y; r[2] = x.z; r[3] = x.w;
+}
+
+// Appends n buffered entries of one warp to a global list with one atomic.
+__device__ __forceinline__ void warp_flush(unsigned* counter, int32_t* list, const int32_t* buf, unsigned n,
+                                           int lane) {
+  unsigned base = 0;
+  if (lane == 0) base = atomicAdd(counter, n);
+  base = __shfl_sync(0xffffffffu, base, 0);
+  for (unsigned i = lane; i < n; i += 32) list[base + i] = buf[i];
+}
+
+template <typename RP, bool kAligned>
 __global__ void __launch_bounds__(kBlock) k_mask(DevGraph g, Scratch s) {
+  __shared__ int64_t q_row[kMaskWarps][kMaskSpan];   // queued reads: row start
+  __shared__ uint16_t q_pos[kMaskWarps][kMaskSpan];  //   and position in the pass | (degree == 2) << 8
+  __shared__ int32_t b_cand[kMaskWarps][kMaskBuf];   // buffered list entries
+  __shared__ int32_t b_lone[kMaskWarps][kMaskBuf];
+  __shared__ unsigned blk_n[2], blk_base[2];
+  const RP* const rp = reinterpret_cast<const RP*>(g.row_ptr);
   Counters* c = s.ctr;
+  if (threadIdx.x < 2) blk_n[threadIdx.x] = 0;       // read after the first barrier below
   unsigned long long nb = 0;
-  const int lane = threadIdx.x & 31;
-  const long long step = (long long)gridDim.x * kBlock * kMaskItems;
-  for (long long base = (long long)blockIdx.x * kBlock * kMaskItems; base < g.n; base += step) {  // block-uniform
-    unsigned candm = 0, lonem = 0;
-    for (int k = 0; k < kMaskItems; ++k) {
-      const long long v = base + (long long)k * kBlock + threadIdx.x;
-      bool lone = false;
-      if (v < g.n) {
-        int64_t a = rowp(g, v), b = rowp(g, v + 1);
-        int64_t d = b - a;
-        uint8_t br = 0;
-        if (d >= 3) {
-          br = 1;
-        } else if (d > 0) {
-          int cnt = 0, e0 = -1, e1 = -1;
-          for (int64_t x = a; x < b; ++x) {
-            int32_t w = g.col[x];
-            int64_t dw = rowp(g, w + 1) - rowp(g, w);
-            if (dw >= 3) continue;
-            int e = g.code[x] & 1;
-            if (cnt == 0) e0 = e; else e1 = e;
-            ++cnt;
-          }
-          br = (cnt == 2 && e0 == e1) ? 1 : 0;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  int32_t* const bc = b_cand[wib];
+  int32_t* const bl = b_lone[wib];
+  unsigned nc = 0, nl = 0;                           // buffered entries (warp-uniform)
+  const long long stride = (long long)gridDim.x * kMaskWarps * kMaskSpan;
+  for (long long wbase = ((long long)blockIdx.x * kMaskWarps + wib) * kMaskSpan; wbase < g.n; wbase += stride) {
+    // warp-uniform trip count; row_ptr holds n + 1 entries
+    const int cnt = (int)min((long long)kMaskSpan, g.n - wbase);
+    const bool full = cnt == kMaskSpan;
+    const int p0 = 4 * lane;
+    int64_t r[4];
+    if (kAligned && full) {
+      load4<RP>(rp + wbase + p0, r);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) r[j] = p0 + j <= cnt ? (int64_t)rp[wbase + p0 + j] : 0;
+    }
+    int64_t e = __shfl_down_sync(0xffffffffu, r[0], 1);
+    if (lane == 31) e = full ? (int64_t)rp[wbase + kMaskSpan] : 0;
+    unsigned word = 0, pend = 0, lone = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t d = (j < 3 ? r[j + 1] : e) - r[j];
+      if (p0 + j < cnt) {
+        if (d >= 3) { word |= 1u << (8 * j); ++nb; }
+        else if (d > 0) pend |= 1u << j;
+        else lone |= 1u << j;
+      }
+    }
+    if (g.min_chain > 1) lone = 0;
+    if (full) {
+      *reinterpret_cast<uint32_t*>(s.branch + wbase + p0) = word;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (p0 + j < cnt) s.branch[wbase + p0 + j] = (uint8_t)(word >> (8 * j));
+    }
+    unsigned T = 0;                                    // queued reads of this pass
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const bool q = (pend >> j) & 1u;
+      const unsigned pm = __ballot_sync(0xffffffffu, q);
+      if (q) {
+        const unsigned slot = T + __popc(pm & lt);
+        q_row[wib][slot] = r[j];
+        q_pos[wib][slot] = (uint16_t)((p0 + j) | (((j < 3 ? r[j + 1] : e) - r[j] == 2) ? 256 : 0));
+      }
+      T += __popc(pm);
+    }
+    // the pass's four words of the heads bitmap: lane 8w + l holds bits 4l..4l+3 of word w
+    if (g.min_chain <= 1) {                            // uniform
+      unsigned x = lone << (4 * (lane & 7));
+      x |= __shfl_xor_sync(0xffffffffu, x, 1);
+      x |= __shfl_xor_sync(0xffffffffu, x, 2);
+      x |= __shfl_xor_sync(0xffffffffu, x, 4);
+      if ((lane & 7) == 0 && 4 * lane < cnt) s.hb_mask[(wbase >> 5) + (lane >> 3)] = x;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const bool l = (lone >> j) & 1u;
+        const unsigned lm = __ballot_sync(0xffffffffu, l);
+        if (l) {
+          const int32_t v = (int32_t)(wbase + p0 + j);
+          bl[nl + __popc(lm & lt)] = v;
+          s.prd[v] = make_int4(v, 0, g.len[v], 0);
+          s.headq[v] = 1;
         }
-        s.branch[v] = br;
-        nb += br;
-        if (!br && d == 0) {
-          lone = g.min_chain <= 1;
-          if (lone) {
-            s.prd[v] = make_int4((int32_t)v, 0, g.len[v], 0); s.headq[v] = 1;
-            lonem |= 1u << k;
-          }
-        } else if (!br) {
-          candm |= 1u << k;
+        nl += __popc(lm);
+      }
+    } else if (lane < 4 && 32 * lane < cnt) {
+      s.hb_mask[(wbase >> 5) + lane] = 0u;
+    }
+    __syncwarp();                                      // queue written; branch bytes ordered before the fix-ups
+    for (unsigned j0 = 0; j0 < T; j0 += 32) {          // warp-uniform
+      const unsigned jj = j0 + lane;
+      bool cand = false;
+      int32_t v = 0;
+      if (jj < T) {
+        const unsigned q = q_pos[wib][jj];
+        const int64_t x = q_row[wib][jj];
+        const bool two = (q >> 8) != 0;
+        v = (int32_t)(wbase + (q & 255u));
+        const int32_t w0 = g.col[x];
+        const int32_t w1 = two ? g.col[x + 1] : w0;
+        const int c0 = g.code[x] & 1, c1 = two ? (g.code[x + 1] & 1) : c0;
+        const bool k0 = (int64_t)rp[w0 + 1] - (int64_t)rp[w0] < 3;
+        const bool k1 = two && (int64_t)rp[w1 + 1] - (int64_t)rp[w1] < 3;
+        // two overlaps to reads of degree <= 2, both on one end: a branch
+        if (k0 && k1 && c0 == c1) {
+          s.branch[v] = 1;
+          ++nb;
+        } else {
+          cand = true;
         }
       }
-      // a warp holds 32 consecutive reads: one bitmap word
-      const unsigned word = __ballot_sync(0xffffffffu, lone);
-      const long long v0 = base + (long long)k * kBlock + (threadIdx.x & ~31);
-      if (lane == 0 && v0 < g.n) s.hb_mask[v0 >> 5] = word;
+      const unsigned cm = __ballot_sync(0xffffffffu, cand);
+      if (cand) bc[nc + __popc(cm & lt)] = v;
+      nc += __popc(cm);
     }
-    unsigned cs = block_reserve(&c->n_cand, __popc(candm));
-    unsigned ls = block_reserve(&c->n_lone, __popc(lonem));
-    for (int k = 0; k < kMaskItems; ++k) {
-      int32_t v = (int32_t)(base + (long long)k * kBlock + threadIdx.x);
-      if ((candm >> k) & 1u) s.cand[cs++] = v;
-      if ((lonem >> k) & 1u) s.lone[ls++] = v;
-    }
+    __syncwarp();                                      // queue and buffers reused next pass
+    // a pass adds at most kMaskSpan entries to a buffer
+    if (nc > kMaskBuf - kMaskSpan) { warp_flush(&c->n_cand, s.cand, bc, nc, lane); nc = 0; __syncwarp(); }
+    if (nl > kMaskBuf - kMaskSpan) { warp_flush(&c->n_lone, s.lone, bl, nl, lane); nl = 0; __syncwarp(); }
   }
+  // one reservation per block for the entries the warps still hold
+  __syncthreads();
+  unsigned oc = 0, ol = 0;
+  if (lane == 0) {
+    oc = nc ? atomicAdd(&blk_n[0], nc) : 0;
+    ol = nl ? atomicAdd(&blk_n[1], nl) : 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    blk_base[0] = blk_n[0] ? atomicAdd(&c->n_cand, blk_n[0]) : 0;
+    blk_base[1] = blk_n[1] ? atomicAdd(&c->n_lone, blk_n[1]) : 0;
+  }
+  __syncthreads();
+  oc = blk_base[0] + __shfl_sync(0xffffffffu, oc, 0);
+  ol = blk_base[1] + __shfl_sync(0xffffffffu, ol, 0);
+  for (unsigned i = lane; i < nc; i += 32) s.cand[oc + i] = bc[i];
+  for (unsigned i = lane; i < nl; i += 32) s.lone[ol + i] = bl[i];
   for (int o = 16; o > 0; o >>= 1) nb += __shfl_down_sync(0xffffffffu, nb, o);
-  if ((threadIdx.x & 31) == 0 && nb) atomicAdd(&c->n_branch, nb);
+  if (lane == 0 && nb) atomicAdd(&c->n_branch, nb);
+}
+
+template <typename RP, bool kAligned>
+void launch_mask_kernel(const DevGraph& g, const Scratch& s, const LaunchEnv& env) {
+  // a persistent grid: never more blocks than can be resident at once
+  static int resident = 0;
+  if (resident == 0) {
+    int r = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_mask<RP, kAligned>, kBlock, 0);
+    resident = r > 0 ? r : 1;
+  }
+  const long long need = (g.n + (long long)kMaskWarps * kMaskSpan - 1) / ((long long)kMaskWarps * kMaskSpan);
+  const int grid = (int)std::max(1LL, std::min(need, (long long)env.num_sms * resident));
+  k_mask<RP, kAligned><<<grid, kBlock, 0, env.stream>>>(g, s);
 }
 
 // Successor table of L for the unmasked reads that have overlaps:
@@ -599,7 +728,14 @@ cudaError_t launch_sum_len(const DevGraph& g, unsigned long long* out, const Lau
 
 cudaError_t launch_mask(const DevGraph& g, const Scratch& s, const LaunchEnv& env) {
   cudaMemsetAsync(&s.ctr->n_branch, 0, sizeof(Counters) - offsetof(Counters, n_branch), env.stream);
-  k_mask<<<grid_for((g.n + kMaskItems - 1) / kMaskItems, env), kBlock, 0, env.stream>>>(g, s);
+  const bool al = (reinterpret_cast<uintptr_t>(g.row_ptr) & 15) == 0;   // 16-byte row_ptr loads
+  if (g.rp64) {
+    if (al) launch_mask_kernel<int64_t, true>(g, s, env);
+    else launch_mask_kernel<int64_t, false>(g, s, env);
+  } else {
+    if (al) launch_mask_kernel<int32_t, true>(g, s, env);
+    else launch_mask_kernel<int32_t, false>(g, s, env);
+  }
   mark(env, "k_mask");
   return cudaGetLastError();
 }

@@ -70,6 +70,35 @@ def test_tiny_1mb(ctx, align, mcr):
     check(ctx, G, mcr)
 
 
+@pytest.mark.parametrize("rp_bytes", [4, 8])
+@pytest.mark.parametrize("mcr", [1, 2])
+def test_borrowed_row_ptr_not_16_byte_aligned(ctx, rp_bytes, mcr):
+    """A borrowed row_ptr that starts 4 or 8 bytes past a 16-byte boundary is
+    read without vector loads; the 1 Mb graph spans several 128-read passes
+    of the mask stage and a ragged tail."""
+    import torch
+    from types import SimpleNamespace
+    G = gen.generate("tiny-1Mb", threads=8, rp_bytes=rp_bytes)
+    orc = oracle.run(G, min_chain_reads=mcr)
+    rp = np.asarray(G.row_ptr)
+    padded = torch.zeros(rp.shape[0] + 1, dtype=torch.int64 if rp_bytes == 8 else torch.int32, device="cuda")
+    padded[1:] = torch.from_numpy(rp).cuda()
+    src = SimpleNamespace(row_ptr=padded[1:], **{k: torch.from_numpy(np.ascontiguousarray(getattr(G, k))).cuda()
+                                                 for k in ("col", "code", "suf", "len", "off", "packed")})
+    assert src.row_ptr.data_ptr() % 16 != 0
+    g = cg.cg_load_graph(ctx, src, flags=cg.BORROW_DEVICE, min_chain_reads=mcr)
+    try:
+        isb = np.empty(G.n, np.uint8)
+        assert cg.cg_mask_branches(g, isb) == orc.n_branch
+        assert np.array_equal(isb, orc.is_branch)
+        cid, rank, orient, nc, ncy = cg.chains_host(g)
+        assert np.array_equal(cid, orc.chain_id) and np.array_equal(rank, orc.rank)
+        off, bases = cg.contigs_host(g)
+        assert np.array_equal(off, orc.contig_off) and np.array_equal(bases, orc.bases)
+    finally:
+        g.close()
+
+
 def test_device_inputs_and_outputs(ctx):
     G = gen.generate("tiny-1Mb", threads=8)
     orc = oracle.run(G, min_chain_reads=2)
