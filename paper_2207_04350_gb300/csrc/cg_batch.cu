@@ -163,7 +163,7 @@ cudaError_t launch_gather_slots(const Scratch& s, long long W, unsigned long lon
   if (tiles > state_cap) return cudaErrorInvalidValue;
   cudaMemsetAsync(state, 0, (size_t)(state_cap + 1) * sizeof(unsigned long long), env.stream);
   if (W > 0) {
-    k_scan<<<(unsigned)tiles, kBlock, 0, env.stream>>>(SlotLoad{s.wsrc, s.wlen}, SlotStore{slot}, W, nullptr, state,
+    k_scan<<<scan_grid(tiles, env), kBlock, 0, env.stream>>>(SlotLoad{s.wsrc, s.wlen}, SlotStore{slot}, W, nullptr, state,
                                                        state_cap, s.derr, K_BATCH_GATHER);
     mark(env, "k_scan_slots");
   } else {

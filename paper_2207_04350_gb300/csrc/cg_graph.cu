@@ -327,31 +327,82 @@ void launch_mask_kernel(const DevGraph& g, const Scratch& s, const LaunchEnv& en
 // on end E_v is the way out of (v, 1-E_v) and enters (w, E_w), whose
 // incoming suffix is suf(v->w). Also lists the chain reads, the sublist
 // starts (list heads and sampled reads) and, among them, the list heads.
+// A candidate read has one or two overlaps: both entries' fields and their
+// reads' mask bits are loaded before any store. The lists gather in per-warp
+// shared-memory buffers and reach the global lists with one reservation per
+// block at the end (a warp flushes early only when its buffers run full); a
+// sublist start learns its sublist id, rr[x] = (id, 0), when it is written out.
+constexpr int kSuccWarps = kBlock / 32;
+constexpr int kSuccBuf = 128;       // chain reads, and reads cut off by branches, per warp
+constexpr int kSuccStarts = 256;    // sublist starts per warp: oriented read | list head << 31
+
+// Writes n buffered sublist starts of one warp to rlist[rbase..] with their
+// rr records, and the list heads among them to hlist[hbase..].
+__device__ __forceinline__ void put_starts(const Scratch& s, const uint32_t* buf, unsigned n, unsigned rbase,
+                                           unsigned hbase, int lane) {
+  const unsigned lt = (1u << lane) - 1u;
+  unsigned h = 0;
+  for (unsigned i0 = 0; i0 < n; i0 += 32) {          // warp-uniform
+    const unsigned i = i0 + lane;
+    bool head = false;
+    if (i < n) {
+      const uint32_t e = buf[i];
+      const int32_t x = (int32_t)(e & 0x7fffffffu);
+      head = (e >> 31) != 0;
+      s.rlist[rbase + i] = x;
+      s.rr[x] = make_int2((int32_t)(rbase + i), 0);
+    }
+    const unsigned hm = __ballot_sync(0xffffffffu, head);
+    if (head) s.hlist[hbase + h + __popc(hm & lt)] = (int32_t)(rbase + i);
+    h += __popc(hm);
+  }
+}
+
 __global__ void __launch_bounds__(kBlock) k_succ(DevGraph g, Scratch s, int ruler_log2) {
+  __shared__ int32_t b_chain[kSuccWarps][kSuccBuf];
+  __shared__ int32_t b_lone[kSuccWarps][kSuccBuf];
+  __shared__ uint32_t b_start[kSuccWarps][kSuccStarts];
+  __shared__ unsigned blk_n[4], blk_base[4];
   Counters* c = s.ctr;
   const long long N = *(volatile unsigned*)&c->n_cand;
-  const long long n = block_round(N);
-  unsigned* const ctrs[4] = {&c->n_chain, &c->n_lone2, &c->n_rulers, &c->n_hlist};
-  for (long long i = grid_tid(); i < n; i += grid_threads()) {   // block-uniform trip count
+  if (threadIdx.x < 4) blk_n[threadIdx.x] = 0;       // read after the first barrier below
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  int32_t* const bc = b_chain[wib];
+  int32_t* const bl = b_lone[wib];
+  uint32_t* const bs = b_start[wib];
+  unsigned nc = 0, nl = 0, ns = 0, nh = 0;           // buffered entries (warp-uniform); nh: heads among the starts
+  const long long Nw = (N + 31) / 32 * 32;           // whole warps iterate together
+  for (long long i = grid_tid(); i < Nw; i += grid_threads()) {
     int32_t v = 0;
     int s0 = -1, s1 = -1;
     bool chain = false, lone = false, r0 = false, r1 = false;
     if (i < N) {
       v = s.cand[i];
-      int64_t a = rowp(g, v), b = rowp(g, v + 1);
-      for (int64_t x = a; x < b; ++x) {
-        int32_t w = g.col[x];
-        if (s.branch[w]) continue;
-        int cd = g.code[x];
-        int ev = cd & 1, ew = cd >> 1;
-        int to = 2 * w + ew;
+      const int64_t a = rowp(g, v);
+      const bool two = rowp(g, v + 1) - a == 2;
+      const int32_t w0 = g.col[a], w1 = two ? g.col[a + 1] : 0;
+      const int cd0 = g.code[a], cd1 = two ? g.code[a + 1] : 0;
+      int32_t q0, q1 = 0, p0 = 0, p1 = 0;
+      if (g.pre) {
+        q0 = g.post[a]; p0 = g.pre[a];
+        if (two) { q1 = g.post[a + 1]; p1 = g.pre[a + 1]; }
+      } else {
+        q0 = g.suf[a];
+        if (two) q1 = g.suf[a + 1];
+      }
+      const bool k0 = !s.branch[w0], k1 = two && !s.branch[w1];
+      if (k0) {                          // (v, 1-ev) leaves through end ev
+        const int ev = cd0 & 1, to = 2 * w0 + (cd0 >> 1);
         if (ev == 1) s0 = to; else s1 = to;
-        if (g.pre) {                       // (v, 1-ev) leaves through end ev
-          s.sufin[to] = g.post[x];
-          s.preout[2 * v + 1 - ev] = g.pre[x];
-        } else {
-          s.sufin[to] = g.suf[x];
-        }
+        s.sufin[to] = q0;
+        if (g.pre) s.preout[2 * v + 1 - ev] = p0;
+      }
+      if (k1) {
+        const int ev = cd1 & 1, to = 2 * w1 + (cd1 >> 1);
+        if (ev == 1) s0 = to; else s1 = to;
+        s.sufin[to] = q1;
+        if (g.pre) s.preout[2 * v + 1 - ev] = p1;
       }
       s.succ[v] = make_int2(s0, s1);
       if (s0 < 0 && s1 < 0) {            // every overlap leads to a branch read
@@ -369,27 +420,49 @@ __global__ void __launch_bounds__(kBlock) k_succ(DevGraph g, Scratch s, int rule
         r1 = s0 < 0 || smp;
       }
     }
-    const bool h0 = chain && s1 < 0, h1 = chain && s0 < 0;
-    const unsigned long long cnt = (unsigned long long)chain | ((unsigned long long)lone << 16) |
-                                   ((unsigned long long)(r0 + r1) << 32) | ((unsigned long long)(h0 + h1) << 48);
-    unsigned base[4];
-    block_reserve4(ctrs, cnt, base);
-    if (chain) s.chain[base[0]] = v;
-    if (lone) s.lone2[base[1]] = v;
-    // a sublist start knows its sublist before any walk: the walk that
-    // reaches it from the previous sublist reads the id here
-    if (r0) {
-      s.rlist[base[2]] = 2 * v;
-      s.rr[2 * v] = make_int2((int32_t)base[2], 0);
-      if (h0) s.hlist[base[3]++] = (int32_t)base[2];
-      ++base[2];
+    const bool h0 = r0 && s1 < 0, h1 = r1 && s0 < 0;
+    const unsigned cm = __ballot_sync(0xffffffffu, chain);
+    if (chain) bc[nc + __popc(cm & lt)] = v;
+    nc += __popc(cm);
+    const unsigned lm = __ballot_sync(0xffffffffu, lone);
+    if (lone) bl[nl + __popc(lm & lt)] = v;
+    nl += __popc(lm);
+    const unsigned m0 = __ballot_sync(0xffffffffu, r0), m1 = __ballot_sync(0xffffffffu, r1);
+    const unsigned slot = ns + __popc(m0 & lt) + __popc(m1 & lt);
+    if (r0) bs[slot] = (uint32_t)(2 * v) | (h0 ? 0x80000000u : 0u);
+    if (r1) bs[slot + (r0 ? 1 : 0)] = (uint32_t)(2 * v + 1) | (h1 ? 0x80000000u : 0u);
+    ns += __popc(m0) + __popc(m1);
+    nh += __popc(__ballot_sync(0xffffffffu, h0)) + __popc(__ballot_sync(0xffffffffu, h1));
+    __syncwarp();
+    // an iteration adds at most 32 entries to a list buffer and 64 starts
+    if (nc > kSuccBuf - 32) { warp_flush(&c->n_chain, s.chain, bc, nc, lane); nc = 0; }
+    if (nl > kSuccBuf - 32) { warp_flush(&c->n_lone2, s.lone2, bl, nl, lane); nl = 0; }
+    if (ns > kSuccStarts - 64) {
+      unsigned rb = 0, hb = 0;
+      if (lane == 0) { rb = atomicAdd(&c->n_rulers, ns); hb = nh ? atomicAdd(&c->n_hlist, nh) : 0u; }
+      put_starts(s, bs, ns, __shfl_sync(0xffffffffu, rb, 0), __shfl_sync(0xffffffffu, hb, 0), lane);
+      ns = 0;
+      nh = 0;
     }
-    if (r1) {
-      s.rlist[base[2]] = 2 * v + 1;
-      s.rr[2 * v + 1] = make_int2((int32_t)base[2], 0);
-      if (h1) s.hlist[base[3]] = (int32_t)base[2];
-    }
+    __syncwarp();
   }
+  // one reservation per block for the entries the warps still hold
+  __syncthreads();
+  unsigned o[4] = {0, 0, 0, 0};
+  if (lane == 0) {
+    const unsigned cnt[4] = {nc, nl, ns, nh};
+    for (int f = 0; f < 4; ++f) o[f] = cnt[f] ? atomicAdd(&blk_n[f], cnt[f]) : 0u;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned* const ctrs[4] = {&c->n_chain, &c->n_lone2, &c->n_rulers, &c->n_hlist};
+    for (int f = 0; f < 4; ++f) blk_base[f] = blk_n[f] ? atomicAdd(ctrs[f], blk_n[f]) : 0u;
+  }
+  __syncthreads();
+  for (int f = 0; f < 4; ++f) o[f] = blk_base[f] + __shfl_sync(0xffffffffu, o[f], 0);
+  for (unsigned k = lane; k < nc; k += 32) s.chain[o[0] + k] = bc[k];
+  for (unsigned k = lane; k < nl; k += 32) s.lone2[o[1] + k] = bl[k];
+  put_starts(s, bs, ns, o[2], o[3], lane);
 }
 
 // One thread per sublist start: walk to the next start or the list end.
@@ -746,7 +819,16 @@ cudaError_t launch_chains(const DevGraph& g, const Scratch& s, const Tuning& t, 
   cudaMemsetAsync(&s.ctr->n_chain, 0, offsetof(Counters, n_contigs) - offsetof(Counters, n_chain), env.stream);
   cudaMemcpyAsync(s.hb, s.hb_mask, (size_t)((g.n + 31) / 32) * sizeof(unsigned), cudaMemcpyDeviceToDevice,
                   env.stream);
-  k_succ<<<grid_for(g.n, env), kBlock, 0, env.stream>>>(g, s, t.ruler_log2);
+  {
+    // a persistent grid: never more blocks than can be resident at once
+    static int resident = 0;
+    if (resident == 0) {
+      int r = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_succ, kBlock, 0);
+      resident = r > 0 ? r : 1;
+    }
+    k_succ<<<env.num_sms * resident, kBlock, 0, env.stream>>>(g, s, t.ruler_log2);
+  }
   mark(env, "k_succ");
   k_walk<<<grid_for(2 * g.n, env), kBlock, 0, env.stream>>>(s, t.ruler_log2, 2 * g.n + 1);
   mark(env, "k_walk");

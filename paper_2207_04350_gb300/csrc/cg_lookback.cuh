@@ -8,6 +8,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "cg_internal.cuh"
 
 namespace cg {
@@ -60,10 +62,22 @@ __device__ unsigned long long lookback(unsigned long long* state, long long tile
   return excl;
 }
 
+// A store may gather what it needs before it writes: with
+//   using Pre = ...; Pre pre(long long i) const;  void item(long long i, unsigned long long e, Pre p) const
+// the scan calls pre() for all of a thread's items first, so that their loads
+// overlap, then item().
+template <class S, class = void>
+struct has_pre : std::false_type {};
+template <class S>
+struct has_pre<S, std::void_t<typename S::Pre>> : std::true_type {};
+
 // Generic single-pass exclusive scan of `count` 64-bit values.
 //   Load:  unsigned long long operator()(long long i)
-//   Store: void item(long long i, unsigned long long exclusive)
+//   Store: void item(long long i, unsigned long long exclusive)   (or the pre/item pair above)
 //          void last(long long count, unsigned long long total)
+// Blocks loop over tiles by ticket; the blocks a count needs no tile of exit
+// at once without taking one, so a grid sized for the largest count costs
+// little when the count (read on the device) is small.
 template <class Load, class Store>
 __global__ void __launch_bounds__(kBlock) k_scan(Load ld, Store st, long long count_host, const unsigned* count_dev,
                                                  unsigned long long* state, long long ticket_index, DevError* derr,
@@ -72,50 +86,80 @@ __global__ void __launch_bounds__(kBlock) k_scan(Load ld, Store st, long long co
   __shared__ unsigned long long warp_tot[kBlock / 32];
   __shared__ long long s_tile;
   __shared__ unsigned long long s_excl;
-  long long count = count_dev ? (long long)*(const volatile unsigned*)count_dev : count_host;
-  int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) s_tile = (long long)atomicAdd(&state[ticket_index], 1ull);
-  __syncthreads();
-  long long tile = s_tile;
-  long long base = tile * kTileItems;
-  if (base >= count) return;
-  for (int k = 0; k < kItems; ++k) {
-    long long i = base + k * kBlock + tid;
-    sm[k * kBlock + tid] = i < count ? ld(i) : 0ull;
-  }
-  __syncthreads();
-  unsigned long long v[kItems], sum = 0;
-  for (int k = 0; k < kItems; ++k) { v[k] = sm[tid * kItems + k]; sum += v[k]; }
-  unsigned long long inc = sum;
-  for (int o = 1; o < 32; o <<= 1) {
-    unsigned long long t = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += t;
-  }
-  if (lane == 31) warp_tot[warp] = inc;
-  __syncthreads();
-  unsigned long long warp_excl = 0, agg = 0;
-  for (int w = 0; w < kBlock / 32; ++w) {
-    if (w < warp) warp_excl += warp_tot[w];
-    agg += warp_tot[w];
-  }
-  if (warp == 0) {
-    unsigned long long e = lookback(state, tile, agg, derr, where);
-    if (lane == 0) s_excl = e;
-  }
-  __syncthreads();
-  unsigned long long run = s_excl + warp_excl + inc - sum;
-  for (int k = 0; k < kItems; ++k) { sm[tid * kItems + k] = run; run += v[k]; }
-  __syncthreads();
-  for (int k = 0; k < kItems; ++k) {
-    long long i = base + k * kBlock + tid;
-    if (i < count) {
-      unsigned long long e = sm[k * kBlock + tid];
-      st.item(i, e);
-      if (i == count - 1) st.last(count, e + ld(i));
+  const long long count = count_dev ? (long long)*(const volatile unsigned*)count_dev : count_host;
+  const long long tiles = (count + kTileItems - 1) / kTileItems;
+  if ((long long)blockIdx.x >= tiles) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (;;) {
+    if (tid == 0) s_tile = (long long)atomicAdd(&state[ticket_index], 1ull);
+    __syncthreads();
+    const long long tile = s_tile;
+    if (tile >= tiles) return;                       // block-uniform
+    const long long base = tile * kTileItems;
+    for (int k = 0; k < kItems; ++k) {
+      long long i = base + k * kBlock + tid;
+      sm[k * kBlock + tid] = i < count ? ld(i) : 0ull;
     }
+    __syncthreads();
+    unsigned long long v[kItems], sum = 0;
+    for (int k = 0; k < kItems; ++k) { v[k] = sm[tid * kItems + k]; sum += v[k]; }
+    unsigned long long inc = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned long long t = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += t;
+    }
+    if (lane == 31) warp_tot[warp] = inc;
+    __syncthreads();
+    unsigned long long warp_excl = 0, agg = 0;
+    for (int w = 0; w < kBlock / 32; ++w) {
+      if (w < warp) warp_excl += warp_tot[w];
+      agg += warp_tot[w];
+    }
+    if (warp == 0) {
+      unsigned long long e = lookback(state, tile, agg, derr, where);
+      if (lane == 0) s_excl = e;
+    }
+    __syncthreads();
+    unsigned long long run = s_excl + warp_excl + inc - sum;
+    for (int k = 0; k < kItems; ++k) { sm[tid * kItems + k] = run; run += v[k]; }
+    __syncthreads();
+    if constexpr (has_pre<Store>::value) {
+      typename Store::Pre pr[kItems];
+#pragma unroll
+      for (int k = 0; k < kItems; ++k) {
+        long long i = base + k * kBlock + tid;
+        pr[k] = i < count ? st.pre(i) : typename Store::Pre{};
+      }
+#pragma unroll
+      for (int k = 0; k < kItems; ++k) {
+        long long i = base + k * kBlock + tid;
+        if (i < count) {
+          unsigned long long e = sm[k * kBlock + tid];
+          st.item(i, e, pr[k]);
+          if (i == count - 1) st.last(count, e + ld(i));
+        }
+      }
+    } else {
+      for (int k = 0; k < kItems; ++k) {
+        long long i = base + k * kBlock + tid;
+        if (i < count) {
+          unsigned long long e = sm[k * kBlock + tid];
+          st.item(i, e);
+          if (i == count - 1) st.last(count, e + ld(i));
+        }
+      }
+    }
+    __syncthreads();                                 // sm and s_tile are reused by the next tile
   }
 }
 
 }  // namespace
+
+// Grid of a scan over at most `tiles` tiles: blocks loop over tiles by
+// ticket, so the grid need not exceed what runs at once.
+inline unsigned scan_grid(long long tiles, const LaunchEnv& env) {
+  const long long cap = (long long)env.num_sms * 4;
+  return (unsigned)(tiles < 1 ? 1 : (tiles < cap ? tiles : cap));
+}
 
 }  // namespace cg

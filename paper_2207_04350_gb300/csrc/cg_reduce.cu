@@ -176,7 +176,7 @@ cudaError_t launch_transitive(const DevGraph& g, int fuzz, const TrBuffers& t, c
   const long long tiles = (g.n + kTileItems - 1) / kTileItems;
   if (tiles > t.state_cap) return cudaErrorInvalidValue;
   if (g.n > 0) {
-    k_scan<<<(unsigned)tiles, kBlock, 0, env.stream>>>(RowCntLoad{t.row_cnt}, RowPtrStore{t.out_rp, t.total}, g.n,
+    k_scan<<<scan_grid(tiles, env), kBlock, 0, env.stream>>>(RowCntLoad{t.row_cnt}, RowPtrStore{t.out_rp, t.total}, g.n,
                                                        nullptr, t.state, t.state_cap, t.derr, K_TRANSITIVE);
     mark(env, "k_scan_rows");
   } else {

@@ -40,14 +40,23 @@ struct HeadWordStore {
   const int32_t* headq;
   int32_t* qd;
   Counters* c;
-  __device__ void item(long long w, unsigned long long e) const {
+  // the word's bits and the read count of its first head, gathered before any store
+  using Pre = int2;
+  __device__ int2 pre(long long w) const {
+    const unsigned bits = hb[w];
+    return make_int2((int)bits, bits ? headq[32 * w + __ffs(bits) - 1] : 0);
+  }
+  __device__ void item(long long w, unsigned long long e, int2 p) const {
     wp[w] = (unsigned)e;
-    unsigned bits = hb[w];
+    unsigned bits = (unsigned)p.x;
+    if (!bits) return;
     unsigned k = (unsigned)e;
+    qd[k++] = p.y;                     // contigs in order of their smallest read
+    bits &= bits - 1;
     while (bits) {
       int b = __ffs(bits) - 1;
       bits &= bits - 1;
-      qd[k++] = headq[32 * w + b];     // contigs in order of their smallest read
+      qd[k++] = headq[32 * w + b];
     }
   }
   __device__ void last(long long, unsigned long long total) const { c->n_contigs = (unsigned)total; }
@@ -170,19 +179,19 @@ cudaError_t launch_offsets(const DevGraph& g, const Scratch& s, const Tuning& t,
   }
   HeadWordLoad hl{s.hb};
   HeadWordStore hs{s.hb, s.wp, s.headq, s.qd, s.ctr};
-  k_scan<<<(unsigned)tiles_w, kBlock, 0, env.stream>>>(hl, hs, words, nullptr, s.scan_state[0], s.scan_tiles_cap,
+  k_scan<<<scan_grid(tiles_w, env), kBlock, 0, env.stream>>>(hl, hs, words, nullptr, s.scan_state[0], s.scan_tiles_cap,
                                                        s.derr, K_SCAN_HEADS);
   mark(env, "k_scan_heads");
   ContigLoad cl{s.qd};
   ContigStore cs{s.cbase, s.ctr};
-  k_scan<<<(unsigned)tiles_n, kBlock, 0, env.stream>>>(cl, cs, 0, &s.ctr->n_contigs, s.scan_state[1],
+  k_scan<<<scan_grid(tiles_n, env), kBlock, 0, env.stream>>>(cl, cs, 0, &s.ctr->n_contigs, s.scan_state[1],
                                                        s.scan_tiles_cap, s.derr, K_SCAN_HEADS);
   mark(env, "k_scan_contigs");
   k_scatter<<<grid_for(g.n, env), kBlock, 0, env.stream>>>(g, s);
   mark(env, "k_scatter");
   PieceLoad pl{s.wlen};
   PieceStore ps{s.wlen, s.out_off, s.tile_seg, s.tiles_cap, t.tile_bytes, s.ctr, s.derr};
-  k_scan<<<(unsigned)tiles_n, kBlock, 0, env.stream>>>(pl, ps, 0, &s.ctr->n_walk, s.scan_state[2], s.scan_tiles_cap,
+  k_scan<<<scan_grid(tiles_n, env), kBlock, 0, env.stream>>>(pl, ps, 0, &s.ctr->n_walk, s.scan_state[2], s.scan_tiles_cap,
                                                        s.derr, K_SCAN_OFFSETS);
   mark(env, "k_scan_pieces");
   k_contig_off<<<grid_for(g.n + 1, env), kBlock, 0, env.stream>>>(s);
@@ -367,7 +376,7 @@ cudaError_t launch_partition(const Scratch& s, long long C, int weight, long lon
       k_sort_hist<<<grid, kBlock, 0, env.stream>>>(b.key[cur], C, pass, b.hist, tiles);
       mark(env, "k_sort_hist");
       cudaMemsetAsync(b.state, 0, (size_t)(b.state_cap + 1) * sizeof(unsigned long long), env.stream);
-      k_scan<<<(unsigned)scan_tiles, kBlock, 0, env.stream>>>(HistLoad{b.hist}, HistStore{b.base}, nh, nullptr,
+      k_scan<<<scan_grid(scan_tiles, env), kBlock, 0, env.stream>>>(HistLoad{b.hist}, HistStore{b.base}, nh, nullptr,
                                                               b.state, b.state_cap, s.derr, K_SORT);
       mark(env, "k_scan_digits");
       k_sort_scatter<<<grid, kBlock, 0, env.stream>>>(b.key[cur], b.val[cur], b.key[cur ^ 1], b.val[cur ^ 1], C,
