@@ -377,7 +377,7 @@ cg_status finish_load(cg_graph* g, uint32_t flags) {
   S.wsrc = galloc<unsigned long long>(g, N, &st);
   S.wlen = galloc<int32_t>(g, N, &st);
   S.out_off = galloc<int64_t>(g, N + 1, &st);
-  S.cstart = galloc<int32_t>(g, N, &st);
+  S.wfirst = galloc<int32_t>(g, N, &st);
   S.contig_off = galloc<int64_t>(g, N + 1, &st);
   S.scan_tiles_cap = (int64_t)(N + 2047) / 2048 + 1;
   S.scan_state[0] = galloc<unsigned long long>(g, 3 * ((size_t)S.scan_tiles_cap + 1), &st);

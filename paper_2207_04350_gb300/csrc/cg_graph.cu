@@ -310,13 +310,7 @@ __global__ void __launch_bounds__(kBlock) k_mask(DevGraph g, Scratch s) {
 
 template <typename RP, bool kAligned>
 void launch_mask_kernel(const DevGraph& g, const Scratch& s, const LaunchEnv& env) {
-  // a persistent grid: never more blocks than can be resident at once
-  static int resident = 0;
-  if (resident == 0) {
-    int r = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_mask<RP, kAligned>, kBlock, 0);
-    resident = r > 0 ? r : 1;
-  }
+  static const int resident = resident_blocks(k_mask<RP, kAligned>);   // a persistent grid
   const long long need = (g.n + (long long)kMaskWarps * kMaskSpan - 1) / ((long long)kMaskWarps * kMaskSpan);
   const int grid = (int)std::max(1LL, std::min(need, (long long)env.num_sms * resident));
   k_mask<RP, kAligned><<<grid, kBlock, 0, env.stream>>>(g, s);
@@ -600,49 +594,86 @@ __device__ __forceinline__ int32_t piece_len(const DevGraph& g, const Scratch& s
 // the reverse of tail(list of (v,1)). The contig starts at the smaller-id
 // end read, so (v,0) is the walk orientation when that end heads the list
 // of (v,0). Reads of closed chains (no list head reached them) are listed
-// for the cycle kernel.
+// for the cycle kernel. A thread takes two chain reads at a time and issues
+// each level of their dependent loads (chain list; rank records; list
+// records; length and entering overlap) together, before any store.
+constexpr int kFinalItems = 2;
+
 __global__ void k_final(DevGraph g, Scratch s) {
   Counters* c = s.ctr;
   const int fb = (int)*(volatile unsigned*)&c->final_buf;
   const long long N = *(volatile unsigned*)&c->n_chain;
   const long long n = (N + 31) & ~31ll;
   const int4* pj = s.pj[fb];
-  for (long long k = grid_tid(); k < n; k += grid_threads()) {   // warp-uniform trip count
-    bool cyc = false;
-    int32_t v = 0;
-    if (k < N) {
-      v = s.chain[k];
-      const int32_t x0 = 2 * v;
-      const int4 r01 = reinterpret_cast<const int4*>(s.rr)[v];   // (sublist, position) of (v,0) and (v,1)
-      const int32_t i0 = r01.x, i1 = r01.z;
-      const int4 p0 = i0 >= 0 ? pj[i0] : make_int4(0, 0, 0, 0), p1 = i1 >= 0 ? pj[i1] : make_int4(0, 0, 0, 0);
-      if (i0 < 0 || i1 < 0 || p0.x != -1 || p1.x != -1) {
-        cyc = true;
-      } else {
-        const int32_t d0 = p0.y - r01.y - 1;
-        const int32_t d1 = p1.y - r01.w - 1;
-        const int32_t t0 = p0.w, t1 = p1.w;              // last oriented reads of both lists
-        const int32_t h0 = t1 >> 1, h1 = t0 >> 1;       // first read of the list of (v,0) / (v,1)
-        // the smallest read of the chain: (v,0)'s list from v's sublist on and
-        // (v,1)'s list (the same reads, reversed) from v's sublist on cover it
-        const int32_t m = min(p0.z, p1.z);
-        const int32_t q = d0 + d1 + 1;
-        const int o = h0 < h1 ? 0 : 1;
-        const int32_t rk = o == 0 ? d1 : d0;
-        if (m < 0 || h0 == h1) set_error(s.derr, DERR_KERNEL, K_FINAL, v);
-        if (q >= g.min_chain) {
-          s.prd[v] = make_int4(m, rk, piece_len(g, s, v, x0 + o, rk, q), o);
-          if (v == m) {
-            mark_head(s, m, q);
-            atomicAdd(&c->n_heads, 1u);
-          }
-        } else {
-          s.prd[v] = make_int4(-1, -1, 0, 255);
-        }
-      }
+  const long long T = grid_threads();
+  for (long long k0 = grid_tid(); k0 < n; k0 += kFinalItems * T) {   // warp-uniform trip count
+    bool in[kFinalItems];
+    int32_t v[kFinalItems];
+    int4 r01[kFinalItems], p0[kFinalItems], p1[kFinalItems];
+#pragma unroll
+    for (int j = 0; j < kFinalItems; ++j) {
+      in[j] = k0 + j * T < N;
+      v[j] = in[j] ? s.chain[k0 + j * T] : 0;
     }
-    const unsigned slot = warp_append(&c->n_cycle_reads, cyc);
-    if (cyc) s.cyc[slot] = v;
+#pragma unroll
+    for (int j = 0; j < kFinalItems; ++j)   // (sublist, position) of (v,0) and (v,1)
+      r01[j] = in[j] ? reinterpret_cast<const int4*>(s.rr)[v[j]] : make_int4(-1, 0, -1, 0);
+#pragma unroll
+    for (int j = 0; j < kFinalItems; ++j) {
+      p0[j] = r01[j].x >= 0 ? pj[r01[j].x] : make_int4(0, 0, 0, 0);
+      p1[j] = r01[j].z >= 0 ? pj[r01[j].z] : make_int4(0, 0, 0, 0);
+    }
+    bool cyc[kFinalItems], ok[kFinalItems];
+    int32_t m[kFinalItems], q[kFinalItems], rk[kFinalItems], o[kFinalItems], L[kFinalItems], sin[kFinalItems],
+        pout[kFinalItems];
+#pragma unroll
+    for (int j = 0; j < kFinalItems; ++j) {
+      cyc[j] = in[j] && (r01[j].x < 0 || r01[j].z < 0 || p0[j].x != -1 || p1[j].x != -1);
+      ok[j] = in[j] && !cyc[j];
+      const int32_t d0 = p0[j].y - r01[j].y - 1;
+      const int32_t d1 = p1[j].y - r01[j].w - 1;
+      const int32_t h0 = p1[j].w >> 1, h1 = p0[j].w >> 1;   // first read of the list of (v,0) / (v,1)
+      // the smallest read of the chain: (v,0)'s list from v's sublist on and
+      // (v,1)'s list (the same reads, reversed) from v's sublist on cover it
+      m[j] = min(p0[j].z, p1[j].z);
+      q[j] = d0 + d1 + 1;
+      o[j] = h0 < h1 ? 0 : 1;
+      rk[j] = o[j] == 0 ? d1 : d0;
+      if (ok[j] && (m[j] < 0 || h0 == h1)) set_error(s.derr, DERR_KERNEL, K_FINAL, v[j]);
+      ok[j] = ok[j] && q[j] >= g.min_chain;
+    }
+    // the piece's inputs: the read's length and its walk copy's overlaps
+#pragma unroll
+    for (int j = 0; j < kFinalItems; ++j) {
+      const int32_t y = 2 * v[j] + o[j];
+      L[j] = ok[j] ? g.len[v[j]] : 0;
+      sin[j] = ok[j] && rk[j] > 0 ? s.sufin[y] : 0;
+      pout[j] = ok[j] && g.pre && rk[j] < q[j] - 1 ? s.preout[y] : 0;
+    }
+#pragma unroll
+    for (int j = 0; j < kFinalItems; ++j) {
+      if (ok[j]) {
+        int32_t len;
+        if (g.pre) {   // x-drop form: l_v[post(e_in) : pre(e_out)], alpha / beta at the contig's ends
+          const int32_t first = rk[j] == 0 ? (o[j] == 0 ? 0 : L[j] - 1) : sin[j];
+          const int32_t last = rk[j] == q[j] - 1 ? (o[j] == 0 ? L[j] - 1 : 0) : pout[j];
+          const int32_t cnt = o[j] == 0 ? last - first + 1 : first - last + 1;
+          s.pfirst[v[j]] = first;
+          len = cnt > 0 ? cnt : 0;
+        } else {       // the first read whole, each later one the suffix it is entered through
+          len = rk[j] == 0 ? L[j] : sin[j];
+        }
+        s.prd[v[j]] = make_int4(m[j], rk[j], len, o[j]);
+        if (v[j] == m[j]) {
+          mark_head(s, m[j], q[j]);
+          atomicAdd(&c->n_heads, 1u);
+        }
+      } else if (in[j] && !cyc[j]) {
+        s.prd[v[j]] = make_int4(-1, -1, 0, 255);
+      }
+      const unsigned slot = warp_append(&c->n_cycle_reads, cyc[j]);
+      if (cyc[j]) s.cyc[slot] = v[j];
+    }
   }
 }
 
@@ -819,16 +850,9 @@ cudaError_t launch_chains(const DevGraph& g, const Scratch& s, const Tuning& t, 
   cudaMemsetAsync(&s.ctr->n_chain, 0, offsetof(Counters, n_contigs) - offsetof(Counters, n_chain), env.stream);
   cudaMemcpyAsync(s.hb, s.hb_mask, (size_t)((g.n + 31) / 32) * sizeof(unsigned), cudaMemcpyDeviceToDevice,
                   env.stream);
-  {
-    // a persistent grid: never more blocks than can be resident at once
-    static int resident = 0;
-    if (resident == 0) {
-      int r = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_succ, kBlock, 0);
-      resident = r > 0 ? r : 1;
-    }
-    k_succ<<<env.num_sms * resident, kBlock, 0, env.stream>>>(g, s, t.ruler_log2);
-  }
+  static const int succ_resident = resident_blocks(k_succ);   // persistent grids
+  static const int final_resident = resident_blocks(k_final);
+  k_succ<<<env.num_sms * succ_resident, kBlock, 0, env.stream>>>(g, s, t.ruler_log2);
   mark(env, "k_succ");
   k_walk<<<grid_for(2 * g.n, env), kBlock, 0, env.stream>>>(s, t.ruler_log2, 2 * g.n + 1);
   mark(env, "k_walk");
@@ -840,7 +864,7 @@ cudaError_t launch_chains(const DevGraph& g, const Scratch& s, const Tuning& t, 
   if (e != cudaSuccess) return e;
   mark(env, "k_jump");
   DevGraph gg = g;
-  k_final<<<grid_for(g.n, env), kBlock, 0, env.stream>>>(gg, s);
+  k_final<<<env.num_sms * final_resident, kBlock, 0, env.stream>>>(gg, s);
   mark(env, "k_final");
   void* args2[] = {&gg, &sc};
   e = coop((const void*)k_cycles, env.coop_blocks, args2, env);

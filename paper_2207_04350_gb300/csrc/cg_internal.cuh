@@ -111,7 +111,7 @@ struct Scratch {
   unsigned long long* wsrc;  // n: first stored base of the piece | reverse flag << 63
   int32_t* wlen;        // n: piece length
   int64_t* out_off;     // n+1
-  int32_t* cstart;      // n: contig -> first walk position
+  int32_t* wfirst;      // n: per walk position, the contig whose first read it holds, or -1
   int64_t* contig_off;  // n+1
   int32_t* tile_seg;    // tiles_cap+1: walk position holding the first byte of each emission tile
   int64_t tiles_cap;
@@ -245,6 +245,14 @@ enum KernelId {
   K_VALIDATE1 = 1, K_VALIDATE2, K_MASK, K_SUCC, K_WALK, K_JUMP, K_FINAL, K_CYCLE, K_EXPORT,
   K_SCAN_HEADS, K_SCATTER, K_SCAN_OFFSETS, K_CONTIG_OFF, K_EMIT, K_SORT, K_TRANSITIVE, K_BATCH_GATHER
 };
+
+// Blocks of kBlock threads of `kernel` that fit on one SM at once.
+template <typename Kernel>
+inline int resident_blocks(Kernel kernel) {
+  int r = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, kernel, kBlock, 0);
+  return r > 0 ? r : 1;
+}
 
 inline int grid_for(long long n, const LaunchEnv& env, int per_sm = 8) {
   long long b = (n + kBlock - 1) / kBlock;

@@ -62,18 +62,22 @@ __device__ unsigned long long lookback(unsigned long long* state, long long tile
   return excl;
 }
 
-// A store may gather what it needs before it writes: with
-//   using Pre = ...; Pre pre(long long i) const;  void item(long long i, unsigned long long e, Pre p) const
-// the scan calls pre() for all of a thread's items first, so that their loads
-// overlap, then item().
-template <class S, class = void>
-struct has_pre : std::false_type {};
-template <class S>
-struct has_pre<S, std::void_t<typename S::Pre>> : std::true_type {};
+// A load may gather its inputs first: with
+//   using Item = ...; Item fetch(long long i) const; unsigned long long value(long long i, const Item&) const
+// the scan fetches all of a thread's items before computing any value, so
+// that their loads overlap, and hands each item to the store:
+//   void item(long long i, unsigned long long exclusive, const Item&) const
+struct NoItem {
+  using Item = char;
+};
+template <class L, class = void>
+struct has_item : std::false_type {};
+template <class L>
+struct has_item<L, std::void_t<typename L::Item>> : std::true_type {};
 
 // Generic single-pass exclusive scan of `count` 64-bit values.
 //   Load:  unsigned long long operator()(long long i)
-//   Store: void item(long long i, unsigned long long exclusive)   (or the pre/item pair above)
+//   Store: void item(long long i, unsigned long long exclusive)   (or with the load's Item, above)
 //          void last(long long count, unsigned long long total)
 // Blocks loop over tiles by ticket; the blocks a count needs no tile of exit
 // at once without taking one, so a grid sized for the largest count costs
@@ -96,9 +100,23 @@ __global__ void __launch_bounds__(kBlock) k_scan(Load ld, Store st, long long co
     const long long tile = s_tile;
     if (tile >= tiles) return;                       // block-uniform
     const long long base = tile * kTileItems;
-    for (int k = 0; k < kItems; ++k) {
-      long long i = base + k * kBlock + tid;
-      sm[k * kBlock + tid] = i < count ? ld(i) : 0ull;
+    typename std::conditional<has_item<Load>::value, Load, NoItem>::type::Item it[kItems];
+    if constexpr (has_item<Load>::value) {
+#pragma unroll
+      for (int k = 0; k < kItems; ++k) {
+        long long i = base + k * kBlock + tid;
+        it[k] = i < count ? ld.fetch(i) : typename Load::Item{};
+      }
+#pragma unroll
+      for (int k = 0; k < kItems; ++k) {
+        long long i = base + k * kBlock + tid;
+        sm[k * kBlock + tid] = i < count ? ld.value(i, it[k]) : 0ull;
+      }
+    } else {
+      for (int k = 0; k < kItems; ++k) {
+        long long i = base + k * kBlock + tid;
+        sm[k * kBlock + tid] = i < count ? ld(i) : 0ull;
+      }
     }
     __syncthreads();
     unsigned long long v[kItems], sum = 0;
@@ -123,20 +141,14 @@ __global__ void __launch_bounds__(kBlock) k_scan(Load ld, Store st, long long co
     unsigned long long run = s_excl + warp_excl + inc - sum;
     for (int k = 0; k < kItems; ++k) { sm[tid * kItems + k] = run; run += v[k]; }
     __syncthreads();
-    if constexpr (has_pre<Store>::value) {
-      typename Store::Pre pr[kItems];
-#pragma unroll
-      for (int k = 0; k < kItems; ++k) {
-        long long i = base + k * kBlock + tid;
-        pr[k] = i < count ? st.pre(i) : typename Store::Pre{};
-      }
+    if constexpr (has_item<Load>::value) {
 #pragma unroll
       for (int k = 0; k < kItems; ++k) {
         long long i = base + k * kBlock + tid;
         if (i < count) {
           unsigned long long e = sm[k * kBlock + tid];
-          st.item(i, e, pr[k]);
-          if (i == count - 1) st.last(count, e + ld(i));
+          st.item(i, e, it[k]);
+          if (i == count - 1) st.last(count, e + ld.value(i, it[k]));
         }
       }
     } else {

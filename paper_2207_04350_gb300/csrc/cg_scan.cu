@@ -3,13 +3,13 @@
 // the concatenation (Alg. 2, Sec. 4.2-4.4).
 //
 //   1. scan over the words of the heads bitmap (bit m set when read m is the
-//      smallest read of a contig) of their popcounts: the contig index of
-//      every head, listing contigs by smallest read id; each word's store
-//      step lays the heads' read counts out in contig order;
-//   2. scan of those read counts: every contig's first walk position;
-//   3. scatter every spelled read to walk position first(contig) + rank: the
+//      smallest read of a contig) of their heads and those heads' read
+//      counts: the contig index of every head, listing contigs by smallest
+//      read id, and every contig's first walk position; the store step lays
+//      the read counts out in contig order;
+//   2. scatter every spelled read to walk position first(contig) + rank: the
 //      on-device compaction that replaces the induced-subgraph exchange;
-//   4. scan over walk positions of the bases each read adds: the output
+//   3. scan over walk positions of the bases each read adds: the output
 //      offset of every piece, the contig offsets and the map from output
 //      tiles to the piece holding each tile's first byte.
 //
@@ -29,70 +29,89 @@ namespace cg {
 
 namespace {
 
-// ---- scan 1: contig index of every head (bitmap popcounts) ----
+// ---- scan 1: contig index and first walk position of every head ----
+// The value of bitmap word w packs the contigs headed in it (their count,
+// above bit kHeadShift) and their reads (below): both stay under 2^30, so
+// one scan gives every head its contig index and its contig's first walk
+// position at once.
+constexpr int kHeadShift = 31;
+constexpr unsigned long long kHeadLow = (1ull << kHeadShift) - 1;
+
 struct HeadWordLoad {
   const unsigned* hb;
-  __device__ unsigned long long operator()(long long w) const { return (unsigned long long)__popc(hb[w]); }
-};
-struct HeadWordStore {
-  const unsigned* hb;
-  unsigned* wp;
   const int32_t* headq;
-  int32_t* qd;
-  Counters* c;
-  // the word's bits and the read count of its first head, gathered before any store
-  using Pre = int2;
-  __device__ int2 pre(long long w) const {
+  // the word's bits and the read count of its first head
+  using Item = int2;
+  __device__ int2 fetch(long long w) const {
     const unsigned bits = hb[w];
     return make_int2((int)bits, bits ? headq[32 * w + __ffs(bits) - 1] : 0);
   }
-  __device__ void item(long long w, unsigned long long e, int2 p) const {
-    wp[w] = (unsigned)e;
-    unsigned bits = (unsigned)p.x;
-    if (!bits) return;
-    unsigned k = (unsigned)e;
-    qd[k++] = p.y;                     // contigs in order of their smallest read
-    bits &= bits - 1;
-    while (bits) {
-      int b = __ffs(bits) - 1;
+  __device__ unsigned long long value(long long w, const int2& it) const {
+    unsigned bits = (unsigned)it.x;
+    const unsigned long long heads = (unsigned long long)__popc(bits);
+    unsigned long long reads = (unsigned)it.y;
+    if (bits) bits &= bits - 1;
+    while (bits) {                     // a second head in one word: rare
+      reads += (unsigned)headq[32 * w + __ffs(bits) - 1];
       bits &= bits - 1;
-      qd[k++] = headq[32 * w + b];
+    }
+    return (heads << kHeadShift) | reads;
+  }
+};
+struct HeadWordStore {
+  unsigned* wp;
+  const int32_t* headq;
+  int32_t* qd;
+  unsigned long long* cbase;
+  int64_t* contig_off;
+  Counters* c;
+  __device__ void item(long long w, unsigned long long e, const int2& it) const {
+    unsigned k = (unsigned)(e >> kHeadShift);
+    wp[w] = k;
+    unsigned bits = (unsigned)it.x;
+    if (!bits) return;
+    unsigned long long r = e & kHeadLow;
+    int32_t q = it.y;
+    for (;;) {                         // contigs in order of their smallest read
+      qd[k] = q;
+      cbase[k] = r;
+      r += (unsigned)q;
+      ++k;
+      bits &= bits - 1;
+      if (!bits) break;
+      q = headq[32 * w + __ffs(bits) - 1];
     }
   }
-  __device__ void last(long long, unsigned long long total) const { c->n_contigs = (unsigned)total; }
-};
-
-// ---- scan 2: first walk position of every contig ----
-struct ContigLoad {
-  const int32_t* qd;
-  __device__ unsigned long long operator()(long long i) const { return (unsigned long long)(unsigned)qd[i]; }
-};
-struct ContigStore {
-  unsigned long long* cbase;
-  Counters* c;
-  __device__ void item(long long i, unsigned long long e) const { cbase[i] = e; }
-  __device__ void last(long long count, unsigned long long total) const {
-    cbase[count] = total;
-    c->n_walk = (unsigned)total;
+  __device__ void last(long long, unsigned long long total) const {
+    const unsigned C = (unsigned)(total >> kHeadShift);
+    c->n_contigs = C;
+    cbase[C] = total & kHeadLow;
+    c->n_walk = (unsigned)(total & kHeadLow);
+    if (C == 0) contig_off[0] = 0;     // no contigs: the piece scan has nothing to scan
   }
 };
 
-// ---- scan 4: piece offsets over walk positions ----
+// ---- scan 3: piece offsets over walk positions ----
 struct PieceLoad {
   const int32_t* wlen;
-  __device__ unsigned long long operator()(long long j) const { return (unsigned long long)(unsigned)wlen[j]; }
+  const int32_t* wfirst;
+  // the piece's length and the contig it starts, or -1
+  using Item = int2;
+  __device__ int2 fetch(long long j) const { return make_int2(wlen[j], wfirst[j]); }
+  __device__ unsigned long long value(long long, const int2& it) const { return (unsigned long long)(unsigned)it.x; }
 };
 struct PieceStore {
-  const int32_t* wlen;
   int64_t* out_off;
+  int64_t* contig_off;
   int32_t* tile_seg;
   long long tiles_cap;
   long long tile_bytes;
   Counters* c;
   DevError* derr;
-  __device__ void item(long long j, unsigned long long e) const {
-    long long o = (long long)e, L = wlen[j];
+  __device__ void item(long long j, unsigned long long e, const int2& it) const {
+    long long o = (long long)e, L = it.x;
     out_off[j] = o;
+    if (it.y >= 0) contig_off[it.y] = o;
     long long t0 = (o + tile_bytes - 1) / tile_bytes, t1 = (o + L + tile_bytes - 1) / tile_bytes;
     for (long long t = t0; t < t1; ++t) {
       if (t < tiles_cap) tile_seg[t] = (int32_t)j;
@@ -101,6 +120,7 @@ struct PieceStore {
   }
   __device__ void last(long long count, unsigned long long total) const {
     out_off[count] = (long long)total;
+    contig_off[c->n_contigs] = (long long)total;
     c->total_bases = (long long)total;
     long long nt = ((long long)total + tile_bytes - 1) / tile_bytes;
     c->n_tiles = (unsigned)nt;
@@ -115,41 +135,73 @@ struct PieceStore {
 // bases contrib-1 down to 0. The spelled reads are the lone reads of the
 // mask stage, those cut off by branch reads, and the chain reads of chains
 // long enough to be contigs.
+// A thread takes two reads at a time and issues each level of their
+// dependent loads together, before any store.
+constexpr int kScatterItems = 2;
+
 __global__ void k_scatter(DevGraph g, Scratch s) {
   Counters* c = s.ctr;
   const long long L1 = *(volatile unsigned*)&c->n_lone, L2 = *(volatile unsigned*)&c->n_lone2;
   const long long NC = *(volatile unsigned*)&c->n_chain, W = *(volatile unsigned*)&c->n_walk;
   const long long total = L1 + L2 + NC;
-  for (long long k = grid_tid(); k < total; k += grid_threads()) {
-    const int32_t v = k < L1 ? s.lone[k] : (k < L1 + L2 ? s.lone2[k - L1] : s.chain[k - L1 - L2]);
-    const int4 p = s.prd[v];
-    const int32_t m = p.x;
-    if (m < 0) continue;                 // a chain shorter than min_chain
-    const unsigned word = s.hb[m >> 5];
-    const long long cidx = (long long)s.wp[m >> 5] + __popc(word & ((1u << (m & 31)) - 1u));
-    const int32_t rk = p.y;
-    const long long pos = (long long)s.cbase[cidx] + rk;
-    if (!((word >> (m & 31)) & 1u) || pos >= W) { set_error(s.derr, DERR_KERNEL, K_SCATTER, v); continue; }
-    const int o = p.w;
-    const int32_t L = g.len[v], cb = p.z;
-    const int64_t base = g.off[v];
-    // stored index of the piece's first base: suffix form, the last cb bases
-    // of the oriented read; x-drop form, set by the chain stage (a read spelled
-    // alone is whole and forward)
-    const int64_t first = !g.pre ? (o == 0 ? L - cb : cb - 1) : (k < L1 + L2 ? 0 : s.pfirst[v]);
-    const unsigned long long src = o == 0 ? (unsigned long long)(base + first)
-                                          : ((unsigned long long)(base + first) | (1ull << 63));
-    s.wsrc[pos] = src;
-    s.wlen[pos] = cb;
-    if (rk == 0) s.cstart[cidx] = (int32_t)pos;
+  const long long T = grid_threads();
+  for (long long k0 = grid_tid(); k0 < total; k0 += kScatterItems * T) {
+    long long k[kScatterItems];
+    int32_t v[kScatterItems];
+    int4 p[kScatterItems];
+    bool ok[kScatterItems];
+#pragma unroll
+    for (int j = 0; j < kScatterItems; ++j) {
+      k[j] = k0 + j * T;
+      v[j] = k[j] >= total ? 0 : (k[j] < L1 ? s.lone[k[j]] : (k[j] < L1 + L2 ? s.lone2[k[j] - L1] : s.chain[k[j] - L1 - L2]));
+    }
+#pragma unroll
+    for (int j = 0; j < kScatterItems; ++j) {
+      p[j] = k[j] < total ? s.prd[v[j]] : make_int4(-1, 0, 0, 0);
+      ok[j] = p[j].x >= 0;                 // not a chain shorter than min_chain
+    }
+    unsigned word[kScatterItems], wpv[kScatterItems];
+    int32_t L[kScatterItems], pf[kScatterItems];
+    int64_t base[kScatterItems];
+#pragma unroll
+    for (int j = 0; j < kScatterItems; ++j) {
+      const int32_t m = ok[j] ? p[j].x : 0;
+      word[j] = ok[j] ? s.hb[m >> 5] : 0u;
+      wpv[j] = ok[j] ? s.wp[m >> 5] : 0u;
+      L[j] = ok[j] ? g.len[v[j]] : 0;
+      base[j] = ok[j] ? g.off[v[j]] : 0;
+      pf[j] = ok[j] && g.pre && k[j] >= L1 + L2 ? s.pfirst[v[j]] : 0;
+    }
+    long long cidx[kScatterItems], pos[kScatterItems];
+#pragma unroll
+    for (int j = 0; j < kScatterItems; ++j) {
+      const int32_t m = p[j].x;
+      cidx[j] = (long long)wpv[j] + __popc(word[j] & ((1u << (m & 31)) - 1u));
+      pos[j] = ok[j] ? (long long)s.cbase[cidx[j]] + p[j].y : 0;
+    }
+#pragma unroll
+    for (int j = 0; j < kScatterItems; ++j) {
+      if (!ok[j]) continue;
+      const int32_t m = p[j].x, rk = p[j].y;
+      if (!((word[j] >> (m & 31)) & 1u) || pos[j] >= W) { set_error(s.derr, DERR_KERNEL, K_SCATTER, v[j]); continue; }
+      const int o = p[j].w;
+      const int32_t cb = p[j].z;
+      // stored index of the piece's first base: suffix form, the last cb bases
+      // of the oriented read; x-drop form, set by the chain stage (a read spelled
+      // alone is whole and forward)
+      const int64_t first = !g.pre ? (o == 0 ? L[j] - cb : cb - 1) : pf[j];
+      const unsigned long long src = o == 0 ? (unsigned long long)(base[j] + first)
+                                            : ((unsigned long long)(base[j] + first) | (1ull << 63));
+      s.wsrc[pos[j]] = src;
+      s.wlen[pos[j]] = cb;
+      s.wfirst[pos[j]] = rk == 0 ? (int32_t)cidx[j] : -1;
+    }
   }
 }
 
+// An empty graph: no contigs, and the one offset 0.
 __global__ void k_contig_off(Scratch s) {
-  Counters* c = s.ctr;
-  long long C = *(volatile unsigned*)&c->n_contigs;
-  for (long long i = grid_tid(); i <= C; i += grid_threads())
-    s.contig_off[i] = i < C ? s.out_off[s.cstart[i]] : c->total_bases;
+  if (grid_tid() == 0) s.contig_off[0] = 0;
 }
 
 __global__ void k_export_contig_off(Scratch s, int64_t* out, long long cap) {
@@ -177,25 +229,19 @@ cudaError_t launch_offsets(const DevGraph& g, const Scratch& s, const Tuning& t,
     mark(env, "k_contig_off");
     return cudaGetLastError();
   }
-  HeadWordLoad hl{s.hb};
-  HeadWordStore hs{s.hb, s.wp, s.headq, s.qd, s.ctr};
+  HeadWordLoad hl{s.hb, s.headq};
+  HeadWordStore hs{s.wp, s.headq, s.qd, s.cbase, s.contig_off, s.ctr};
   k_scan<<<scan_grid(tiles_w, env), kBlock, 0, env.stream>>>(hl, hs, words, nullptr, s.scan_state[0], s.scan_tiles_cap,
                                                        s.derr, K_SCAN_HEADS);
   mark(env, "k_scan_heads");
-  ContigLoad cl{s.qd};
-  ContigStore cs{s.cbase, s.ctr};
-  k_scan<<<scan_grid(tiles_n, env), kBlock, 0, env.stream>>>(cl, cs, 0, &s.ctr->n_contigs, s.scan_state[1],
-                                                       s.scan_tiles_cap, s.derr, K_SCAN_HEADS);
-  mark(env, "k_scan_contigs");
-  k_scatter<<<grid_for(g.n, env), kBlock, 0, env.stream>>>(g, s);
+  static const int scatter_resident = resident_blocks(k_scatter);   // a persistent grid
+  k_scatter<<<env.num_sms * scatter_resident, kBlock, 0, env.stream>>>(g, s);
   mark(env, "k_scatter");
-  PieceLoad pl{s.wlen};
-  PieceStore ps{s.wlen, s.out_off, s.tile_seg, s.tiles_cap, t.tile_bytes, s.ctr, s.derr};
+  PieceLoad pl{s.wlen, s.wfirst};
+  PieceStore ps{s.out_off, s.contig_off, s.tile_seg, s.tiles_cap, t.tile_bytes, s.ctr, s.derr};
   k_scan<<<scan_grid(tiles_n, env), kBlock, 0, env.stream>>>(pl, ps, 0, &s.ctr->n_walk, s.scan_state[2], s.scan_tiles_cap,
                                                        s.derr, K_SCAN_OFFSETS);
   mark(env, "k_scan_pieces");
-  k_contig_off<<<grid_for(g.n + 1, env), kBlock, 0, env.stream>>>(s);
-  mark(env, "k_contig_off");
   return cudaGetLastError();
 }
 
