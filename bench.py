@@ -78,7 +78,7 @@ def parse():
                    help="tiny-1Mb | genome-100Mb | genome-3.1Gb | batched-512 | served-2000")
     p.add_argument("--batch-graphs", type=int, default=512, help="graphs of the batched workload")
     p.add_argument("--serve-requests", type=int, default=2000)
-    p.add_argument("--serve-pool", type=int, default=48, help="pre-generated graphs the requests draw from")
+    p.add_argument("--serve-pool", type=int, default=200, help="pre-generated graphs the requests draw from")
     p.add_argument("--serve-budget-gb", type=float, default=150.0)
     p.add_argument("--serve-max-batch", type=int, default=64)
     p.add_argument("--serve-load", type=float, default=0.8, help="offered load / plain one-at-a-time throughput")
