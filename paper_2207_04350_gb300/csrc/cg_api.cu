@@ -347,13 +347,12 @@ cg_status finish_load(cg_graph* g, uint32_t flags) {
   const size_t N = (size_t)(n > 0 ? n : 1), N2 = 2 * N, NW = N / 32 + 2;
   S.branch = galloc<uint8_t>(g, N, &st);
   S.cand = galloc<int32_t>(g, N, &st);
-  S.chain = galloc<int32_t>(g, N, &st);
+  S.cidx = galloc<int32_t>(g, N, &st);
   S.lone = galloc<int32_t>(g, N, &st);
-  S.lone2 = galloc<int32_t>(g, N, &st);
   S.hb_mask = galloc<unsigned>(g, NW, &st);
   S.hb = galloc<unsigned>(g, NW, &st);
   S.wp = galloc<unsigned>(g, NW, &st);
-  S.succ = galloc<int2>(g, N, &st);
+  S.succ = galloc<int4>(g, N, &st);
   S.sufin = galloc<int32_t>(g, N2, &st);
   if (G.pre) {
     S.preout = galloc<int32_t>(g, N2, &st);
@@ -366,7 +365,7 @@ cg_status finish_load(cg_graph* g, uint32_t flags) {
   for (int b = 0; b < 2; ++b) {
     S.pj[b] = galloc<int4>(g, N2, &st);
     S.c_ptr[b] = galloc<int32_t>(g, N2, &st);
-    S.c_val[b] = galloc<int32_t>(g, N2, &st);
+    S.c_val[b] = galloc<long long>(g, N2, &st);
   }
   S.c_head = galloc<int32_t>(g, N2, &st);
   S.prd = galloc<int4>(g, N, &st);

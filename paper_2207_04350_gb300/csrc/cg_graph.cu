@@ -172,6 +172,23 @@ __device__ __forceinline__ void warp_flush(unsigned* counter, int32_t* list, con
   for (unsigned i = lane; i < n; i += 32) list[base + i] = buf[i];
 }
 
+// Reserves n entries of a global list for one warp (one atomic); returns the first.
+__device__ __forceinline__ unsigned warp_reserve(unsigned* counter, unsigned n, int lane) {
+  unsigned base = 0;
+  if (lane == 0) base = atomicAdd(counter, n);
+  return __shfl_sync(0xffffffffu, base, 0);
+}
+
+// Candidates get their index when written out: cand[c] = v and cidx[v] = c.
+__device__ __forceinline__ void flush_cands(const Scratch& s, const int32_t* buf, unsigned n, unsigned base,
+                                            int lane) {
+  for (unsigned i = lane; i < n; i += 32) {
+    const int32_t v = buf[i];
+    s.cand[base + i] = v;
+    s.cidx[v] = (int32_t)(base + i);
+  }
+}
+
 template <typename RP, bool kAligned>
 __global__ void __launch_bounds__(kBlock) k_mask(DevGraph g, Scratch s) {
   __shared__ int64_t q_row[kMaskWarps][kMaskSpan];   // queued reads: row start
@@ -221,6 +238,9 @@ __global__ void __launch_bounds__(kBlock) k_mask(DevGraph g, Scratch s) {
       for (int j = 0; j < 4; ++j)
         if (p0 + j < cnt) s.branch[wbase + p0 + j] = (uint8_t)(word >> (8 * j));
     }
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if ((word >> (8 * j)) & 1u) s.cidx[wbase + p0 + j] = -1;
     unsigned T = 0;                                    // queued reads of this pass
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -247,7 +267,6 @@ __global__ void __launch_bounds__(kBlock) k_mask(DevGraph g, Scratch s) {
         if (l) {
           const int32_t v = (int32_t)(wbase + p0 + j);
           bl[nl + __popc(lm & lt)] = v;
-          s.prd[v] = make_int4(v, 0, g.len[v], 0);
           s.headq[v] = 1;
         }
         nl += __popc(lm);
@@ -273,6 +292,7 @@ __global__ void __launch_bounds__(kBlock) k_mask(DevGraph g, Scratch s) {
         // two overlaps to reads of degree <= 2, both on one end: a branch
         if (k0 && k1 && c0 == c1) {
           s.branch[v] = 1;
+          s.cidx[v] = -1;
           ++nb;
         } else {
           cand = true;
@@ -284,7 +304,7 @@ __global__ void __launch_bounds__(kBlock) k_mask(DevGraph g, Scratch s) {
     }
     __syncwarp();                                      // queue and buffers reused next pass
     // a pass adds at most kMaskSpan entries to a buffer
-    if (nc > kMaskBuf - kMaskSpan) { warp_flush(&c->n_cand, s.cand, bc, nc, lane); nc = 0; __syncwarp(); }
+    if (nc > kMaskBuf - kMaskSpan) { flush_cands(s, bc, nc, warp_reserve(&c->n_cand, nc, lane), lane); nc = 0; __syncwarp(); }
     if (nl > kMaskBuf - kMaskSpan) { warp_flush(&c->n_lone, s.lone, bl, nl, lane); nl = 0; __syncwarp(); }
   }
   // one reservation per block for the entries the warps still hold
@@ -302,7 +322,7 @@ __global__ void __launch_bounds__(kBlock) k_mask(DevGraph g, Scratch s) {
   __syncthreads();
   oc = blk_base[0] + __shfl_sync(0xffffffffu, oc, 0);
   ol = blk_base[1] + __shfl_sync(0xffffffffu, ol, 0);
-  for (unsigned i = lane; i < nc; i += 32) s.cand[oc + i] = bc[i];
+  flush_cands(s, bc, nc, oc, lane);
   for (unsigned i = lane; i < nl; i += 32) s.lone[ol + i] = bl[i];
   for (int o = 16; o > 0; o >>= 1) nb += __shfl_down_sync(0xffffffffu, nb, o);
   if (lane == 0 && nb) atomicAdd(&c->n_branch, nb);
@@ -316,19 +336,19 @@ void launch_mask_kernel(const DevGraph& g, const Scratch& s, const LaunchEnv& en
   k_mask<RP, kAligned><<<grid, kBlock, 0, env.stream>>>(g, s);
 }
 
-// Successor table of L for the unmasked reads that have overlaps:
-// succ[v] = (successor of (v,0), successor of (v,1)); the overlap (v->w)
-// on end E_v is the way out of (v, 1-E_v) and enters (w, E_w), whose
-// incoming suffix is suf(v->w). Also lists the chain reads, the sublist
-// starts (list heads and sampled reads) and, among them, the list heads.
-// A candidate read has one or two overlaps: both entries' fields and their
-// reads' mask bits are loaded before any store. The lists gather in per-warp
-// shared-memory buffers and reach the global lists with one reservation per
-// block at the end (a warp flushes early only when its buffers run full); a
-// sublist start learns its sublist id, rr[x] = (id, 0), when it is written out.
+// Successor table of L over the candidates (unmasked reads with overlaps),
+// in candidate order: succ[c] = (successor of (c,0), successor of (c,1), read
+// id); the overlap (v->w) on end E_v is the way out of (v, 1-E_v) and enters
+// (w, E_w), whose incoming suffix is suf(v->w). Also lists the sublist starts
+// (list heads and sampled reads) and, among them, the list heads. A
+// candidate has one or two overlaps: both entries' fields and their reads'
+// candidate indexes (-1: a branch read) are loaded before any store. The
+// start lists gather in per-warp shared-memory buffers and reach the global
+// lists with one reservation per block at the end (a warp flushes early only
+// when its buffer runs full); a start learns its sublist id, rr[u] = (id, 0),
+// when it is written out.
 constexpr int kSuccWarps = kBlock / 32;
-constexpr int kSuccBuf = 128;       // chain reads, and reads cut off by branches, per warp
-constexpr int kSuccStarts = 256;    // sublist starts per warp: oriented read | list head << 31
+constexpr int kSuccStarts = 256;    // sublist starts per warp: oriented candidate | list head << 31
 
 // Writes n buffered sublist starts of one warp to rlist[rbase..] with their
 // rr records, and the list heads among them to hlist[hbase..].
@@ -341,10 +361,10 @@ __device__ __forceinline__ void put_starts(const Scratch& s, const uint32_t* buf
     bool head = false;
     if (i < n) {
       const uint32_t e = buf[i];
-      const int32_t x = (int32_t)(e & 0x7fffffffu);
+      const int32_t u = (int32_t)(e & 0x7fffffffu);
       head = (e >> 31) != 0;
-      s.rlist[rbase + i] = x;
-      s.rr[x] = make_int2((int32_t)(rbase + i), 0);
+      s.rlist[rbase + i] = u;
+      s.rr[u] = make_int2((int32_t)(rbase + i), 0);
     }
     const unsigned hm = __ballot_sync(0xffffffffu, head);
     if (head) s.hlist[hbase + h + __popc(hm & lt)] = (int32_t)(rbase + i);
@@ -353,26 +373,21 @@ __device__ __forceinline__ void put_starts(const Scratch& s, const uint32_t* buf
 }
 
 __global__ void __launch_bounds__(kBlock) k_succ(DevGraph g, Scratch s, int ruler_log2) {
-  __shared__ int32_t b_chain[kSuccWarps][kSuccBuf];
-  __shared__ int32_t b_lone[kSuccWarps][kSuccBuf];
   __shared__ uint32_t b_start[kSuccWarps][kSuccStarts];
-  __shared__ unsigned blk_n[4], blk_base[4];
+  __shared__ unsigned blk_n[2], blk_base[2];
   Counters* c = s.ctr;
   const long long N = *(volatile unsigned*)&c->n_cand;
-  if (threadIdx.x < 4) blk_n[threadIdx.x] = 0;       // read after the first barrier below
+  if (threadIdx.x < 2) blk_n[threadIdx.x] = 0;       // read after the first barrier below
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
-  int32_t* const bc = b_chain[wib];
-  int32_t* const bl = b_lone[wib];
   uint32_t* const bs = b_start[wib];
-  unsigned nc = 0, nl = 0, ns = 0, nh = 0;           // buffered entries (warp-uniform); nh: heads among the starts
+  unsigned ns = 0, nh = 0;                           // buffered starts (warp-uniform), and the heads among them
   const long long Nw = (N + 31) / 32 * 32;           // whole warps iterate together
-  for (long long i = grid_tid(); i < Nw; i += grid_threads()) {
-    int32_t v = 0;
+  for (long long ci = grid_tid(); ci < Nw; ci += grid_threads()) {
     int s0 = -1, s1 = -1;
-    bool chain = false, lone = false, r0 = false, r1 = false;
-    if (i < N) {
-      v = s.cand[i];
+    bool r0 = false, r1 = false;
+    if (ci < N) {
+      const int32_t v = s.cand[ci];
       const int64_t a = rowp(g, v);
       const bool two = rowp(g, v + 1) - a == 2;
       const int32_t w0 = g.col[a], w1 = two ? g.col[a + 1] : 0;
@@ -385,53 +400,45 @@ __global__ void __launch_bounds__(kBlock) k_succ(DevGraph g, Scratch s, int rule
         q0 = g.suf[a];
         if (two) q1 = g.suf[a + 1];
       }
-      const bool k0 = !s.branch[w0], k1 = two && !s.branch[w1];
-      if (k0) {                          // (v, 1-ev) leaves through end ev
-        const int ev = cd0 & 1, to = 2 * w0 + (cd0 >> 1);
+      const int32_t c0 = s.cidx[w0], c1 = two ? s.cidx[w1] : -1;
+      const int32_t u0 = 2 * (int32_t)ci;
+      if (c0 >= 0) {                     // (v, 1-ev) leaves through end ev
+        const int ev = cd0 & 1, to = 2 * c0 + (cd0 >> 1);
         if (ev == 1) s0 = to; else s1 = to;
         s.sufin[to] = q0;
-        if (g.pre) s.preout[2 * v + 1 - ev] = p0;
+        if (g.pre) s.preout[u0 + 1 - ev] = p0;
       }
-      if (k1) {
-        const int ev = cd1 & 1, to = 2 * w1 + (cd1 >> 1);
+      if (c1 >= 0) {
+        const int ev = cd1 & 1, to = 2 * c1 + (cd1 >> 1);
         if (ev == 1) s0 = to; else s1 = to;
         s.sufin[to] = q1;
-        if (g.pre) s.preout[2 * v + 1 - ev] = p1;
+        if (g.pre) s.preout[u0 + 1 - ev] = p1;
       }
-      s.succ[v] = make_int2(s0, s1);
-      if (s0 < 0 && s1 < 0) {            // every overlap leads to a branch read
-        lone = g.min_chain <= 1;
-        s.prd[v] = make_int4(lone ? v : -1, lone ? 0 : -1, g.len[v], lone ? 0 : 255);
+      s.succ[ci] = make_int4(s0, s1, v, 0);
+      if (s0 < 0 && s1 < 0) {            // every overlap leads to a branch read: spelled alone, or in no contig
+        const bool lone = g.min_chain <= 1;
+        s.prd[ci] = make_int4(lone ? v : -1, lone ? 0 : -1, lone ? g.len[v] : 0, lone ? 0 : 255);
+        if (g.pre) s.pfirst[ci] = 0;
         if (lone) {
           mark_head(s, v, 1);
           atomicAdd(&c->n_heads, 1u);
         }
       } else {
-        chain = true;
-        reinterpret_cast<int4*>(s.rr)[v] = make_int4(-1, 0, -1, 0);   // not yet reached by a sublist walk
+        reinterpret_cast<int4*>(s.rr)[ci] = make_int4(-1, 0, -1, 0);   // not yet reached by a sublist walk
         const bool smp = sampled(v, ruler_log2) != 0;
-        r0 = s1 < 0 || smp;              // (v,0) has no predecessor when (v,1) has no successor
+        r0 = s1 < 0 || smp;              // (c,0) has no predecessor when (c,1) has no successor
         r1 = s0 < 0 || smp;
       }
     }
     const bool h0 = r0 && s1 < 0, h1 = r1 && s0 < 0;
-    const unsigned cm = __ballot_sync(0xffffffffu, chain);
-    if (chain) bc[nc + __popc(cm & lt)] = v;
-    nc += __popc(cm);
-    const unsigned lm = __ballot_sync(0xffffffffu, lone);
-    if (lone) bl[nl + __popc(lm & lt)] = v;
-    nl += __popc(lm);
     const unsigned m0 = __ballot_sync(0xffffffffu, r0), m1 = __ballot_sync(0xffffffffu, r1);
     const unsigned slot = ns + __popc(m0 & lt) + __popc(m1 & lt);
-    if (r0) bs[slot] = (uint32_t)(2 * v) | (h0 ? 0x80000000u : 0u);
-    if (r1) bs[slot + (r0 ? 1 : 0)] = (uint32_t)(2 * v + 1) | (h1 ? 0x80000000u : 0u);
+    if (r0) bs[slot] = (uint32_t)(2 * ci) | (h0 ? 0x80000000u : 0u);
+    if (r1) bs[slot + (r0 ? 1 : 0)] = (uint32_t)(2 * ci + 1) | (h1 ? 0x80000000u : 0u);
     ns += __popc(m0) + __popc(m1);
     nh += __popc(__ballot_sync(0xffffffffu, h0)) + __popc(__ballot_sync(0xffffffffu, h1));
     __syncwarp();
-    // an iteration adds at most 32 entries to a list buffer and 64 starts
-    if (nc > kSuccBuf - 32) { warp_flush(&c->n_chain, s.chain, bc, nc, lane); nc = 0; }
-    if (nl > kSuccBuf - 32) { warp_flush(&c->n_lone2, s.lone2, bl, nl, lane); nl = 0; }
-    if (ns > kSuccStarts - 64) {
+    if (ns > kSuccStarts - 64) {         // an iteration adds at most 64 starts
       unsigned rb = 0, hb = 0;
       if (lane == 0) { rb = atomicAdd(&c->n_rulers, ns); hb = nh ? atomicAdd(&c->n_hlist, nh) : 0u; }
       put_starts(s, bs, ns, __shfl_sync(0xffffffffu, rb, 0), __shfl_sync(0xffffffffu, hb, 0), lane);
@@ -440,47 +447,48 @@ __global__ void __launch_bounds__(kBlock) k_succ(DevGraph g, Scratch s, int rule
     }
     __syncwarp();
   }
-  // one reservation per block for the entries the warps still hold
+  // one reservation per block for the starts the warps still hold
   __syncthreads();
-  unsigned o[4] = {0, 0, 0, 0};
+  unsigned o[2] = {0, 0};
   if (lane == 0) {
-    const unsigned cnt[4] = {nc, nl, ns, nh};
-    for (int f = 0; f < 4; ++f) o[f] = cnt[f] ? atomicAdd(&blk_n[f], cnt[f]) : 0u;
+    o[0] = ns ? atomicAdd(&blk_n[0], ns) : 0u;
+    o[1] = nh ? atomicAdd(&blk_n[1], nh) : 0u;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    unsigned* const ctrs[4] = {&c->n_chain, &c->n_lone2, &c->n_rulers, &c->n_hlist};
-    for (int f = 0; f < 4; ++f) blk_base[f] = blk_n[f] ? atomicAdd(ctrs[f], blk_n[f]) : 0u;
+    blk_base[0] = blk_n[0] ? atomicAdd(&c->n_rulers, blk_n[0]) : 0u;
+    blk_base[1] = blk_n[1] ? atomicAdd(&c->n_hlist, blk_n[1]) : 0u;
   }
   __syncthreads();
-  for (int f = 0; f < 4; ++f) o[f] = blk_base[f] + __shfl_sync(0xffffffffu, o[f], 0);
-  for (unsigned k = lane; k < nc; k += 32) s.chain[o[0] + k] = bc[k];
-  for (unsigned k = lane; k < nl; k += 32) s.lone2[o[1] + k] = bl[k];
-  put_starts(s, bs, ns, o[2], o[3], lane);
+  for (int f = 0; f < 2; ++f) o[f] = blk_base[f] + __shfl_sync(0xffffffffu, o[f], 0);
+  put_starts(s, bs, ns, o[0], o[1], lane);
 }
 
-// One thread per sublist start: walk to the next start or the list end.
+// One thread per sublist start: walk to the next start or the list end. The
+// sublist's record keeps read ids: its smallest read and its last oriented
+// read as 2v + o.
 __global__ void k_walk(Scratch s, int ruler_log2, int64_t limit) {
   Counters* c = s.ctr;
   const long long R = *(volatile unsigned*)&c->n_rulers;
   for (long long r = grid_tid(); r < R; r += grid_threads()) {
     const int32_t x = s.rlist[r];
-    const int2 sv = s.succ[x >> 1];
-    int32_t y = x, z = (x & 1) ? sv.y : sv.x, mn = x >> 1, next_start = -1;
+    const int4 sv = s.succ[x >> 1];
+    int32_t y = x, z = (x & 1) ? sv.y : sv.x, vy = sv.z, mn = sv.z, next_start = -1;
     int32_t cnt = 0;
     for (;;) {
       s.rr[y] = make_int2((int32_t)r, cnt);
       ++cnt;
-      mn = min(mn, y >> 1);
+      mn = min(mn, vy);
       if (z < 0) break;
-      if (sampled(z >> 1, ruler_log2)) { next_start = z; break; }
-      const int2 sz = s.succ[z >> 1];
+      const int4 sz = s.succ[z >> 1];
+      if (sampled(sz.z, ruler_log2)) { next_start = z; break; }
       y = z;
+      vy = sz.z;
       z = (z & 1) ? sz.y : sz.x;
       if (cnt > limit) { set_error(s.derr, DERR_KERNEL, K_WALK, y); break; }
     }
     // the next sublist's id, written by k_succ for every sublist start
-    s.rec[r] = make_int4(next_start >= 0 ? s.rr[next_start].x : -1, cnt, mn, y);
+    s.rec[r] = make_int4(next_start >= 0 ? s.rr[next_start].x : -1, cnt, mn, 2 * vy + (y & 1));
     s.pj[0][r].x = kUnresolved;
   }
 }
@@ -565,44 +573,47 @@ __global__ void k_jump(Scratch s) {
   if (grid_tid() == 0) c->final_buf = (unsigned)cur;
 }
 
-// x-drop form (Sec. 4.4): read v, walked as oriented read y at rank rk of a
-// contig of q reads, contributes l_v[post(e_in) : pre(e_out)] with alpha (its
-// first base in walk direction) for the first read and beta (its last) for
-// the last one; a piece whose end comes before its start is empty.
-// Returns the piece's length; its first stored base goes to pfirst.
-__device__ __forceinline__ int32_t set_piece(const DevGraph& g, const Scratch& s, int32_t v, int32_t y, int32_t rk,
-                                             int32_t q) {
-  const int o = y & 1;
+// x-drop form (Sec. 4.4): read v (candidate ci), walked as oriented
+// candidate u at rank rk of a contig of q reads, contributes
+// l_v[post(e_in) : pre(e_out)] with alpha (its first base in walk direction)
+// for the first read and beta (its last) for the last one; a piece whose end
+// comes before its start is empty. Returns the piece's length; its first
+// stored base goes to pfirst.
+__device__ __forceinline__ int32_t set_piece(const DevGraph& g, const Scratch& s, int32_t v, int32_t ci, int32_t u,
+                                             int32_t rk, int32_t q) {
+  const int o = u & 1;
   const int32_t L = g.len[v];
-  const int32_t first = rk == 0 ? (o == 0 ? 0 : L - 1) : s.sufin[y];
-  const int32_t last = rk == q - 1 ? (o == 0 ? L - 1 : 0) : s.preout[y];
+  const int32_t first = rk == 0 ? (o == 0 ? 0 : L - 1) : s.sufin[u];
+  const int32_t last = rk == q - 1 ? (o == 0 ? L - 1 : 0) : s.preout[u];
   const int32_t cnt = o == 0 ? last - first + 1 : first - last + 1;
-  s.pfirst[v] = first;
+  s.pfirst[ci] = first;
   return cnt > 0 ? cnt : 0;
 }
 
 // The bases a chain read adds: the first read whole, each later one the
 // suffix of the overlap it is entered through (or, in the x-drop form, its
 // piece).
-__device__ __forceinline__ int32_t piece_len(const DevGraph& g, const Scratch& s, int32_t v, int32_t y, int32_t rk,
-                                             int32_t q) {
-  if (g.pre) return set_piece(g, s, v, y, rk, q);
-  return rk == 0 ? g.len[v] : s.sufin[y];
+__device__ __forceinline__ int32_t piece_len(const DevGraph& g, const Scratch& s, int32_t v, int32_t ci, int32_t u,
+                                             int32_t rk, int32_t q) {
+  if (g.pre) return set_piece(g, s, v, ci, u, rk, q);
+  return rk == 0 ? g.len[v] : s.sufin[u];
 }
 
-// Per chain read: combine its two oriented copies. head(list of (v,0)) is
-// the reverse of tail(list of (v,1)). The contig starts at the smaller-id
-// end read, so (v,0) is the walk orientation when that end heads the list
-// of (v,0). Reads of closed chains (no list head reached them) are listed
-// for the cycle kernel. A thread takes two chain reads at a time and issues
-// each level of their dependent loads (chain list; rank records; list
-// records; length and entering overlap) together, before any store.
+// Per chain candidate: combine its two oriented copies. head(list of (c,0))
+// is the reverse of tail(list of (c,1)). The contig starts at the
+// smaller-id end read, so (c,0) is the walk orientation when that end heads
+// the list of (c,0). Candidates of closed chains (no list head reached them)
+// are listed for the cycle kernel; candidates cut off by branch reads got
+// their record from the successor kernel. A thread takes two candidates at a
+// time and issues each level of their dependent loads (successor records;
+// rank records; list records; length and entering overlap) together, before
+// any store.
 constexpr int kFinalItems = 2;
 
 __global__ void k_final(DevGraph g, Scratch s) {
   Counters* c = s.ctr;
   const int fb = (int)*(volatile unsigned*)&c->final_buf;
-  const long long N = *(volatile unsigned*)&c->n_chain;
+  const long long N = *(volatile unsigned*)&c->n_cand;
   const long long n = (N + 31) & ~31ll;
   const int4* pj = s.pj[fb];
   const long long T = grid_threads();
@@ -612,12 +623,13 @@ __global__ void k_final(DevGraph g, Scratch s) {
     int4 r01[kFinalItems], p0[kFinalItems], p1[kFinalItems];
 #pragma unroll
     for (int j = 0; j < kFinalItems; ++j) {
-      in[j] = k0 + j * T < N;
-      v[j] = in[j] ? s.chain[k0 + j * T] : 0;
+      const int4 sv = k0 + j * T < N ? s.succ[k0 + j * T] : make_int4(-1, -1, 0, 0);
+      in[j] = sv.x >= 0 || sv.y >= 0;      // a chain candidate
+      v[j] = sv.z;
     }
 #pragma unroll
-    for (int j = 0; j < kFinalItems; ++j)   // (sublist, position) of (v,0) and (v,1)
-      r01[j] = in[j] ? reinterpret_cast<const int4*>(s.rr)[v[j]] : make_int4(-1, 0, -1, 0);
+    for (int j = 0; j < kFinalItems; ++j)   // (sublist, position) of (c,0) and (c,1)
+      r01[j] = in[j] ? reinterpret_cast<const int4*>(s.rr)[k0 + j * T] : make_int4(-1, 0, -1, 0);
 #pragma unroll
     for (int j = 0; j < kFinalItems; ++j) {
       p0[j] = r01[j].x >= 0 ? pj[r01[j].x] : make_int4(0, 0, 0, 0);
@@ -632,9 +644,9 @@ __global__ void k_final(DevGraph g, Scratch s) {
       ok[j] = in[j] && !cyc[j];
       const int32_t d0 = p0[j].y - r01[j].y - 1;
       const int32_t d1 = p1[j].y - r01[j].w - 1;
-      const int32_t h0 = p1[j].w >> 1, h1 = p0[j].w >> 1;   // first read of the list of (v,0) / (v,1)
-      // the smallest read of the chain: (v,0)'s list from v's sublist on and
-      // (v,1)'s list (the same reads, reversed) from v's sublist on cover it
+      const int32_t h0 = p1[j].w >> 1, h1 = p0[j].w >> 1;   // first read of the list of (c,0) / (c,1)
+      // the smallest read of the chain: (c,0)'s list from c's sublist on and
+      // (c,1)'s list (the same reads, reversed) from c's sublist on cover it
       m[j] = min(p0[j].z, p1[j].z);
       q[j] = d0 + d1 + 1;
       o[j] = h0 < h1 ? 0 : 1;
@@ -645,54 +657,56 @@ __global__ void k_final(DevGraph g, Scratch s) {
     // the piece's inputs: the read's length and its walk copy's overlaps
 #pragma unroll
     for (int j = 0; j < kFinalItems; ++j) {
-      const int32_t y = 2 * v[j] + o[j];
+      const long long u = 2 * (k0 + j * T) + o[j];
       L[j] = ok[j] ? g.len[v[j]] : 0;
-      sin[j] = ok[j] && rk[j] > 0 ? s.sufin[y] : 0;
-      pout[j] = ok[j] && g.pre && rk[j] < q[j] - 1 ? s.preout[y] : 0;
+      sin[j] = ok[j] && rk[j] > 0 ? s.sufin[u] : 0;
+      pout[j] = ok[j] && g.pre && rk[j] < q[j] - 1 ? s.preout[u] : 0;
     }
 #pragma unroll
     for (int j = 0; j < kFinalItems; ++j) {
+      const long long ci = k0 + j * T;
       if (ok[j]) {
         int32_t len;
         if (g.pre) {   // x-drop form: l_v[post(e_in) : pre(e_out)], alpha / beta at the contig's ends
           const int32_t first = rk[j] == 0 ? (o[j] == 0 ? 0 : L[j] - 1) : sin[j];
           const int32_t last = rk[j] == q[j] - 1 ? (o[j] == 0 ? L[j] - 1 : 0) : pout[j];
           const int32_t cnt = o[j] == 0 ? last - first + 1 : first - last + 1;
-          s.pfirst[v[j]] = first;
+          s.pfirst[ci] = first;
           len = cnt > 0 ? cnt : 0;
         } else {       // the first read whole, each later one the suffix it is entered through
           len = rk[j] == 0 ? L[j] : sin[j];
         }
-        s.prd[v[j]] = make_int4(m[j], rk[j], len, o[j]);
+        s.prd[ci] = make_int4(m[j], rk[j], len, o[j]);
         if (v[j] == m[j]) {
           mark_head(s, m[j], q[j]);
           atomicAdd(&c->n_heads, 1u);
         }
       } else if (in[j] && !cyc[j]) {
-        s.prd[v[j]] = make_int4(-1, -1, 0, 255);
+        s.prd[ci] = make_int4(-1, -1, 0, 255);
       }
       const unsigned slot = warp_append(&c->n_cycle_reads, cyc[j]);
-      if (cyc[j]) s.cyc[slot] = v[j];
+      if (cyc[j]) s.cyc[slot] = (int32_t)ci;
     }
   }
 }
 
-// Closed chains (rare). Over their oriented reads: pointer jumping for the
-// smallest oriented id of each directed cycle (the copy holding (m,0) is the
-// walk, m the smallest read), then cut the walk before (m,0) and rank by
-// pointer jumping again.
+// Closed chains (rare). Over their oriented candidates: pointer jumping for
+// the smallest oriented read 2v + o of each directed cycle, carried with the
+// oriented candidate that holds it (the copy holding (m,0) is the walk, m the
+// smallest read), then cut the walk before (m,0) and rank by pointer jumping
+// again.
 __global__ void k_cycles(DevGraph g, Scratch s) {
   Counters* c = s.ctr;
   unsigned C = *(volatile unsigned*)&c->n_cycle_reads;
   if (C == 0) return;
   long long N = 2ll * C;
   for (long long i = grid_tid(); i < N; i += grid_threads()) {
-    int32_t v = s.cyc[i >> 1], y = 2 * v + (int)(i & 1);
-    int2 sv = s.succ[v];
-    int32_t z = (y & 1) ? sv.y : sv.x;
-    if (z < 0) set_error(s.derr, DERR_KERNEL, K_CYCLE, y);
-    s.c_ptr[0][y] = z;
-    s.c_val[0][y] = y;
+    const int32_t ci = s.cyc[i >> 1], u = 2 * ci + (int)(i & 1);
+    const int4 sv = s.succ[ci];
+    const int32_t z = (u & 1) ? sv.y : sv.x;
+    if (z < 0) set_error(s.derr, DERR_KERNEL, K_CYCLE, u);
+    s.c_ptr[0][u] = z;
+    s.c_val[0][u] = ((long long)(2 * sv.z + (u & 1)) << 32) | (unsigned)u;
   }
   int rounds = 1;
   while ((1ll << rounds) < N + 1 && rounds < 31) ++rounds;
@@ -702,26 +716,26 @@ __global__ void k_cycles(DevGraph g, Scratch s) {
   for (int r = 0; r < rounds; ++r) {
     int nxt = cur ^ 1;
     for (long long i = grid_tid(); i < N; i += grid_threads()) {
-      int32_t y = 2 * s.cyc[i >> 1] + (int)(i & 1);
-      int32_t p = s.c_ptr[cur][y];
+      const int32_t u = 2 * s.cyc[i >> 1] + (int)(i & 1);
+      const int32_t p = s.c_ptr[cur][u];
       if (p < 0) continue;
-      s.c_val[nxt][y] = min(s.c_val[cur][y], s.c_val[cur][p]);
-      s.c_ptr[nxt][y] = s.c_ptr[cur][p];
+      s.c_val[nxt][u] = min(s.c_val[cur][u], s.c_val[cur][p]);
+      s.c_ptr[nxt][u] = s.c_ptr[cur][p];
     }
     cur = nxt;
     if (!grid_sync(c, s.derr)) return;
   }
-  // cut: on the walk copy, the oriented read before the start has no successor
+  // cut: on the walk copy, the oriented candidate before the start has no successor
   for (long long i = grid_tid(); i < N; i += grid_threads()) {
-    int32_t v = s.cyc[i >> 1], y = 2 * v + (int)(i & 1);
-    int32_t head = s.c_val[cur][y];
-    s.c_head[y] = head;
+    const int32_t ci = s.cyc[i >> 1], u = 2 * ci + (int)(i & 1);
+    const int32_t head = (int32_t)(s.c_val[cur][u] & 0xffffffffll);   // the oriented candidate holding the smallest read
+    s.c_head[u] = head;
     if ((head & 1) == 0) {
-      int2 sv = s.succ[v];
-      int32_t z = (y & 1) ? sv.y : sv.x;
-      int32_t p = (z == head) ? -1 : z;
-      s.c_ptr[0][y] = p;
-      s.c_val[0][y] = p < 0 ? 0 : 1;
+      const int4 sv = s.succ[ci];
+      const int32_t z = (u & 1) ? sv.y : sv.x;
+      const int32_t p = (z == head) ? -1 : z;
+      s.c_ptr[0][u] = p;
+      s.c_val[0][u] = p < 0 ? 0 : 1;
     }
   }
   cur = 0;
@@ -729,55 +743,61 @@ __global__ void k_cycles(DevGraph g, Scratch s) {
   for (int r = 0; r < rounds; ++r) {
     int nxt = cur ^ 1;
     for (long long i = grid_tid(); i < N; i += grid_threads()) {
-      int32_t y = 2 * s.cyc[i >> 1] + (int)(i & 1);
-      if (s.c_head[y] & 1) continue;
-      int32_t p = s.c_ptr[cur][y];
+      const int32_t u = 2 * s.cyc[i >> 1] + (int)(i & 1);
+      if (s.c_head[u] & 1) continue;
+      const int32_t p = s.c_ptr[cur][u];
       if (p >= 0) {
-        s.c_val[nxt][y] = s.c_val[cur][y] + s.c_val[cur][p];
-        s.c_ptr[nxt][y] = s.c_ptr[cur][p];
+        s.c_val[nxt][u] = s.c_val[cur][u] + s.c_val[cur][p];
+        s.c_ptr[nxt][u] = s.c_ptr[cur][p];
       } else {
-        s.c_val[nxt][y] = s.c_val[cur][y];
-        s.c_ptr[nxt][y] = -1;
+        s.c_val[nxt][u] = s.c_val[cur][u];
+        s.c_ptr[nxt][u] = -1;
       }
     }
     cur = nxt;
     if (!grid_sync(c, s.derr)) return;
   }
   for (long long i = grid_tid(); i < N; i += grid_threads()) {
-    int32_t v = s.cyc[i >> 1];
-    int32_t y = 2 * v + (int)(i & 1);
-    int32_t head = s.c_head[y];
+    const int32_t ci = s.cyc[i >> 1];
+    const int32_t u = 2 * ci + (int)(i & 1);
+    const int32_t head = s.c_head[u];
     if (head & 1) continue;
-    int32_t L = s.c_val[cur][head] + 1;       // distance from the start to the cut, plus one
-    int32_t rk = L - 1 - s.c_val[cur][y];
-    int32_t m = head >> 1;
+    const int32_t L = (int32_t)s.c_val[cur][head] + 1;      // distance from the start to the cut, plus one
+    const int32_t rk = L - 1 - (int32_t)s.c_val[cur][u];
+    const int32_t m = s.cand[head >> 1];
+    const int32_t v = s.cand[ci];
     if (L >= g.min_chain) {
-      s.prd[v] = make_int4(m, rk, piece_len(g, s, v, y, rk, L), y & 1);
+      s.prd[ci] = make_int4(m, rk, piece_len(g, s, v, ci, u, rk, L), u & 1);
       if (rk == 0) {
         mark_head(s, m, L);
         atomicAdd(&c->n_heads, 1u);
       }
     } else {
-      s.prd[v] = make_int4(-1, -1, 0, 255);
+      s.prd[ci] = make_int4(-1, -1, 0, 255);
     }
     if (rk == 0) atomicAdd(&c->n_cycles, 1u);
   }
 }
 
-__global__ void k_export_reads(DevGraph g, Scratch s, int32_t* cid, int32_t* rank, uint8_t* orient) {
+// Per-read chain outputs: first every read's default (a lone read, when
+// spelled, is its own one-read contig), then every candidate's record.
+__global__ void k_export_fill(DevGraph g, int32_t* cid, int32_t* rank, uint8_t* orient) {
   for (long long v = grid_tid(); v < g.n; v += grid_threads()) {
-    int64_t d = rowp(g, v + 1) - rowp(g, v);
-    int32_t a = -1, b = -1;
-    uint8_t o = 255;
-    if (d == 0) {
-      if (g.min_chain <= 1) { a = (int32_t)v; b = 0; o = 0; }
-    } else if (!s.branch[v]) {
-      const int4 p = s.prd[v];
-      a = p.x; b = p.y; o = (uint8_t)p.w;
-    }
-    if (cid) cid[v] = a;
-    if (rank) rank[v] = b;
-    if (orient) orient[v] = o;
+    const bool lone = rowp(g, v + 1) == rowp(g, v) && g.min_chain <= 1;
+    if (cid) cid[v] = lone ? (int32_t)v : -1;
+    if (rank) rank[v] = lone ? 0 : -1;
+    if (orient) orient[v] = lone ? 0 : 255;
+  }
+}
+
+__global__ void k_export_cands(Scratch s, int32_t* cid, int32_t* rank, uint8_t* orient) {
+  const long long N = *(volatile unsigned*)&s.ctr->n_cand;
+  for (long long ci = grid_tid(); ci < N; ci += grid_threads()) {
+    const int32_t v = s.cand[ci];
+    const int4 p = s.prd[ci];
+    if (cid) cid[v] = p.x;
+    if (rank) rank[v] = p.y;
+    if (orient) orient[v] = (uint8_t)p.w;
   }
 }
 
@@ -847,7 +867,7 @@ cudaError_t launch_mask(const DevGraph& g, const Scratch& s, const LaunchEnv& en
 cudaError_t launch_chains(const DevGraph& g, const Scratch& s, const Tuning& t, const LaunchEnv& env) {
   // restart the chain-stage counters; the head bitmap restarts from the mask
   // stage's words (lone reads) and gains the chain heads below
-  cudaMemsetAsync(&s.ctr->n_chain, 0, offsetof(Counters, n_contigs) - offsetof(Counters, n_chain), env.stream);
+  cudaMemsetAsync(&s.ctr->n_rulers, 0, offsetof(Counters, n_contigs) - offsetof(Counters, n_rulers), env.stream);
   cudaMemcpyAsync(s.hb, s.hb_mask, (size_t)((g.n + 31) / 32) * sizeof(unsigned), cudaMemcpyDeviceToDevice,
                   env.stream);
   static const int succ_resident = resident_blocks(k_succ);   // persistent grids
@@ -875,8 +895,10 @@ cudaError_t launch_chains(const DevGraph& g, const Scratch& s, const Tuning& t, 
 
 cudaError_t launch_export_reads(const DevGraph& g, const Scratch& s, int32_t* cid, int32_t* rank, uint8_t* orient,
                                 const LaunchEnv& env) {
-  k_export_reads<<<grid_for(g.n, env), kBlock, 0, env.stream>>>(g, s, cid, rank, orient);
-  mark(env, "k_export_reads");
+  k_export_fill<<<grid_for(g.n, env), kBlock, 0, env.stream>>>(g, cid, rank, orient);
+  mark(env, "k_export_fill");
+  k_export_cands<<<grid_for(g.n, env), kBlock, 0, env.stream>>>(s, cid, rank, orient);
+  mark(env, "k_export_cands");
   return cudaGetLastError();
 }
 

@@ -33,8 +33,6 @@ struct Counters {
   unsigned int n_cand;         // unmasked reads with at least one overlap
   unsigned int n_lone;         // reads without overlaps spelled as one-read contigs (min_chain <= 1)
   // chain stage
-  unsigned int n_chain;        // unmasked reads with at least one surviving overlap
-  unsigned int n_lone2;        // reads whose overlaps all lead to branch reads, spelled alone (min_chain <= 1)
   unsigned int n_rulers;       // sublist starts of the list ranking
   unsigned int n_hlist;        // sublists that start a list
   unsigned int n_cycle_reads;  // reads on closed chains
@@ -74,35 +72,37 @@ struct DevGraph {
 // Scratch owned by a loaded graph. Sizes in elements (n reads).
 struct Scratch {
   uint8_t* branch;      // n
-  int32_t* cand;        // n: reads to build successors for
-  int32_t* chain;       // n: reads to rank
+  int32_t* cand;        // n: candidate reads (unmasked, with overlaps), in candidate order
+  int32_t* cidx;        // n: per read with overlaps, its candidate index, -1 for a branch read
   int32_t* lone;        // n: reads without overlaps spelled alone
-  int32_t* lone2;       // n: reads cut off by branch reads spelled alone
   unsigned* hb_mask;    // n/32+1: heads bitmap words of the mask stage
   unsigned* hb;         // n/32+1: bit m set when read m is the smallest read of a contig
-  int2* succ;           // n: (successor of (v,fwd), successor of (v,rc)) as oriented ids 2w+o, or -1
-  int32_t* sufin;       // 2n: suffix (x-drop form: post) of the overlap entering oriented read x
-  int32_t* preout;      // 2n, x-drop form only: pre of the overlap leaving oriented read x
-  int32_t* pfirst;      // n, x-drop form only: stored index of the piece's first base
+  // The chain stage indexes candidates, c = cidx[v], and their oriented
+  // copies u = 2c + o: its records sit together in candidate order instead
+  // of spreading over arrays of n reads.
+  int4* succ;           // n: (successor of (c,fwd), successor of (c,rc) as oriented candidates, or -1; read id; 0)
+  int32_t* sufin;       // 2n: suffix (x-drop form: post) of the overlap entering oriented candidate u
+  int32_t* preout;      // 2n, x-drop form only: pre of the overlap leaving oriented candidate u
+  int32_t* pfirst;      // n, x-drop form only: per candidate, stored index of the piece's first base
   // Records read together sit together: one sector per random access.
-  int2* rr;             // 2n: oriented read x -> (sublist, -1 when not reached; position inside it);
-                        //     rr[2v] and rr[2v+1] form one 16-byte record
+  int2* rr;             // 2n: oriented candidate u -> (sublist, -1 when not reached; position inside it);
+                        //     rr[2c] and rr[2c+1] form one 16-byte record
   // sublists (capacity 2n)
-  int32_t* rlist;       // first oriented read of each sublist
+  int32_t* rlist;       // first oriented candidate of each sublist
   int32_t* hlist;       // sublists that start a list
   int4* rec;            // sublist -> (the next sublist, -1 at the list end;
-                        //             length; smallest read id inside; last oriented read)
+                        //             length; smallest read id inside; last oriented read, 2v + o)
   int4* pj[2];          // sublist -> (next: -1 resolved, -2 unresolved; oriented reads to the list tail;
                         //             smallest read id to the tail; the list's last oriented read);
                         //             jumping double buffers
-  // per read
+  // per candidate
   int4* prd;            // n: (smallest read id of the chain, -1 in no contig; walk position;
                         //     bases this read adds to its contig; orientation 0 / 1, 255 in no contig)
-  int32_t* headq;       // at a contig's smallest read: its number of reads
-  // closed chains
-  int32_t* cyc;         // n: reads on closed chains
+  int32_t* headq;       // per read, at a contig's smallest read: its number of reads
+  // closed chains (oriented candidates)
+  int32_t* cyc;         // n: candidates on closed chains
   int32_t* c_ptr[2];    // 2n
-  int32_t* c_val[2];    // 2n
+  long long* c_val[2];  // 2n: (2v + o) << 32 | u while finding each cycle's smallest read, then distances
   int32_t* c_head;      // 2n
   // contig order and walk order
   unsigned* wp;         // n/32+1: heads before each bitmap word

@@ -132,18 +132,18 @@ struct PieceStore {
 // Every spelled read goes to walk position first(contig) + rank, with the
 // stored-base address of its piece: forward reads add stored bases
 // [len-contrib, len), reverse-complement reads the complement of stored
-// bases contrib-1 down to 0. The spelled reads are the lone reads of the
-// mask stage, those cut off by branch reads, and the chain reads of chains
-// long enough to be contigs.
-// A thread takes two reads at a time and issues each level of their
-// dependent loads together, before any store.
+// bases contrib-1 down to 0. The spelled reads are the lone reads of the mask
+// stage (each its own contig, whole and forward) and the candidates with a
+// contig in their record (chains long enough, and reads cut off by branch
+// reads when those are spelled alone). A thread takes two reads at a time and
+// issues each level of their dependent loads together, before any store.
 constexpr int kScatterItems = 2;
 
 __global__ void k_scatter(DevGraph g, Scratch s) {
   Counters* c = s.ctr;
-  const long long L1 = *(volatile unsigned*)&c->n_lone, L2 = *(volatile unsigned*)&c->n_lone2;
-  const long long NC = *(volatile unsigned*)&c->n_chain, W = *(volatile unsigned*)&c->n_walk;
-  const long long total = L1 + L2 + NC;
+  const long long L1 = *(volatile unsigned*)&c->n_lone, NC = *(volatile unsigned*)&c->n_cand;
+  const long long W = *(volatile unsigned*)&c->n_walk;
+  const long long total = L1 + NC;
   const long long T = grid_threads();
   for (long long k0 = grid_tid(); k0 < total; k0 += kScatterItems * T) {
     long long k[kScatterItems];
@@ -153,11 +153,9 @@ __global__ void k_scatter(DevGraph g, Scratch s) {
 #pragma unroll
     for (int j = 0; j < kScatterItems; ++j) {
       k[j] = k0 + j * T;
-      v[j] = k[j] >= total ? 0 : (k[j] < L1 ? s.lone[k[j]] : (k[j] < L1 + L2 ? s.lone2[k[j] - L1] : s.chain[k[j] - L1 - L2]));
-    }
-#pragma unroll
-    for (int j = 0; j < kScatterItems; ++j) {
-      p[j] = k[j] < total ? s.prd[v[j]] : make_int4(-1, 0, 0, 0);
+      v[j] = k[j] >= total ? 0 : (k[j] < L1 ? s.lone[k[j]] : s.cand[k[j] - L1]);
+      // a lone read: its own contig, rank 0, whole and forward (its length is filled in below)
+      p[j] = k[j] >= total ? make_int4(-1, 0, 0, 0) : (k[j] < L1 ? make_int4(v[j], 0, -1, 0) : s.prd[k[j] - L1]);
       ok[j] = p[j].x >= 0;                 // not a chain shorter than min_chain
     }
     unsigned word[kScatterItems], wpv[kScatterItems];
@@ -170,7 +168,7 @@ __global__ void k_scatter(DevGraph g, Scratch s) {
       wpv[j] = ok[j] ? s.wp[m >> 5] : 0u;
       L[j] = ok[j] ? g.len[v[j]] : 0;
       base[j] = ok[j] ? g.off[v[j]] : 0;
-      pf[j] = ok[j] && g.pre && k[j] >= L1 + L2 ? s.pfirst[v[j]] : 0;
+      pf[j] = ok[j] && g.pre && k[j] >= L1 ? s.pfirst[k[j] - L1] : 0;
     }
     long long cidx[kScatterItems], pos[kScatterItems];
 #pragma unroll
@@ -185,7 +183,7 @@ __global__ void k_scatter(DevGraph g, Scratch s) {
       const int32_t m = p[j].x, rk = p[j].y;
       if (!((word[j] >> (m & 31)) & 1u) || pos[j] >= W) { set_error(s.derr, DERR_KERNEL, K_SCATTER, v[j]); continue; }
       const int o = p[j].w;
-      const int32_t cb = p[j].z;
+      const int32_t cb = p[j].z < 0 ? L[j] : p[j].z;
       // stored index of the piece's first base: suffix form, the last cb bases
       // of the oriented read; x-drop form, set by the chain stage (a read spelled
       // alone is whole and forward)
