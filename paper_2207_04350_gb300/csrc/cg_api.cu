@@ -59,7 +59,8 @@ struct cg_graph {
   int64_t stage_bases_cap = 0;
   void* stage_reads = nullptr;
   unsigned long long* d_sum = nullptr;
-  StageExec execs[6];                  // mask, chains, offsets, emission, contig_off export, 2-bit emission
+  StageExec execs[7];                  // mask, chains, offsets, emission, contig_off export, 2-bit emission,
+                                       // offsets + emission + export in one graph
   int batch_k = 0;                     // graphs of a batch (0: a single graph)
   int64_t* batch_R = nullptr;          // device: first read of each graph, batch_k + 1 entries
   // a batch whose reads stay in pinned host memory: per graph its stream's
@@ -188,6 +189,17 @@ struct StageTimer {
     }
   }
 };
+
+// A stage-boundary event inside a launch sequence that may be captured: a
+// captured record becomes an event-record node of the graph.
+void record_stage_event(cg_ctx* c, int i) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(c->stream, &cs);
+  if (cs == cudaStreamCaptureStatusActive)
+    cudaEventRecordWithFlags(c->ev[i], c->stream, cudaEventRecordExternal);
+  else
+    cudaEventRecord(c->ev[i], c->stream);
+}
 
 uint64_t mix_key(uint64_t h, uint64_t v) { return (h ^ (v + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2))); }
 
@@ -925,6 +937,41 @@ cg_status cg_emit_contigs(cg_graph* g, int64_t* contig_off, int64_t contig_off_c
   if (st != CG_OK) return st;
   if (mem != CG_MEM_HOST && mem != CG_MEM_DEVICE) return fail(c, CG_EINVAL, "bad mem");
   if ((bases && bases_cap < 0) || (contig_off && contig_off_cap < 1)) return fail(c, CG_EINVAL, "bad capacity");
+  if (mem == CG_MEM_DEVICE && bases && !g->host_batch) {
+    // the layout, the spelling and the offsets export replayed as one graph
+    if (!aligned(bases, 16)) return fail(c, CG_EINVAL, "device bases buffer must be 16-byte aligned");
+    if (g->stage < 2) {
+      st = run_chains(g);
+      if (st != CG_OK) return st;
+    }
+    const bool timing = c->timing != 0;
+    uint64_t key = mix_key(mix_key(mix_key(mix_key((uint64_t)(uintptr_t)bases, (uint64_t)bases_cap),
+                                           (uint64_t)(uintptr_t)g->g.packed), (uint64_t)c->tune.tile_bytes),
+                           (uint64_t)c->tune.emit_blocks_per_sm);
+    key = mix_key(mix_key(mix_key(key, (uint64_t)(uintptr_t)contig_off), (uint64_t)contig_off_cap), timing ? 3 : 4);
+    st = run_stage(g, 6, key, [&]() -> cg_status {
+      if (timing) record_stage_event(c, 4);
+      CK(cg::launch_offsets(g->g, g->s, c->tune, c->env), "offset kernels");
+      if (timing) {
+        record_stage_event(c, 5);
+        record_stage_event(c, 6);
+      }
+      CK(cg::launch_emit(g->g, g->s, c->tune, bases, bases_cap, c->env), "emission kernel");
+      if (timing) record_stage_event(c, 7);
+      if (contig_off) CK(cg::launch_export_contig_off(g->s, contig_off, contig_off_cap, c->env), "export contig_off");
+      return CG_OK;
+    });
+    if (st != CG_OK) return st;
+    if (timing) c->recorded[2] = c->recorded[3] = true;
+    g->stage = 3;
+    if (n_contigs || total_bases) {
+      st = wait_and_read(g);
+      if (st != CG_OK) return st;
+    }
+    if (n_contigs) *n_contigs = (int64_t)c->h_ctr->n_contigs;
+    if (total_bases) *total_bases = c->h_ctr->total_bases;
+    return CG_OK;
+  }
   st = run_offsets(g);
   if (st != CG_OK) return st;
   if (bases) {

@@ -382,6 +382,8 @@ __global__ void __launch_bounds__(kBlock) k_succ(DevGraph g, Scratch s, int rule
   const unsigned lt = (1u << lane) - 1u;
   uint32_t* const bs = b_start[wib];
   unsigned ns = 0, nh = 0;                           // buffered starts (warp-uniform), and the heads among them
+  // the chain stage's heads bitmap starts from the mask stage's words (lone reads)
+  for (long long w = grid_tid(); w < (g.n + 31) / 32; w += grid_threads()) s.hb[w] = s.hb_mask[w];
   const long long Nw = (N + 31) / 32 * 32;           // whole warps iterate together
   for (long long ci = grid_tid(); ci < Nw; ci += grid_threads()) {
     int s0 = -1, s1 = -1;
@@ -400,7 +402,13 @@ __global__ void __launch_bounds__(kBlock) k_succ(DevGraph g, Scratch s, int rule
         q0 = g.suf[a];
         if (two) q1 = g.suf[a + 1];
       }
-      const int32_t c0 = s.cidx[w0], c1 = two ? s.cidx[w1] : -1;
+      // a neighbour's candidate index, -1 for a branch read; an entry without its
+      // mirror (a graph loaded unvalidated) may reach a read whose index the mask
+      // stage never wrote: an out-of-range value counts as a branch read, so the
+      // successor and suffix stores below stay inside their arrays
+      int32_t c0 = s.cidx[w0], c1 = two ? s.cidx[w1] : -1;
+      if ((uint32_t)c0 >= (uint32_t)N) c0 = -1;
+      if ((uint32_t)c1 >= (uint32_t)N) c1 = -1;
       const int32_t u0 = 2 * (int32_t)ci;
       if (c0 >= 0) {                     // (v, 1-ev) leaves through end ev
         const int ev = cd0 & 1, to = 2 * c0 + (cd0 >> 1);
@@ -418,11 +426,7 @@ __global__ void __launch_bounds__(kBlock) k_succ(DevGraph g, Scratch s, int rule
       if (s0 < 0 && s1 < 0) {            // every overlap leads to a branch read: spelled alone, or in no contig
         const bool lone = g.min_chain <= 1;
         s.prd[ci] = make_int4(lone ? v : -1, lone ? 0 : -1, lone ? g.len[v] : 0, lone ? 0 : 255);
-        if (g.pre) s.pfirst[ci] = 0;
-        if (lone) {
-          mark_head(s, v, 1);
-          atomicAdd(&c->n_heads, 1u);
-        }
+        if (g.pre) s.pfirst[ci] = 0;   // its contig head is marked by k_final
       } else {
         reinterpret_cast<int4*>(s.rr)[ci] = make_int4(-1, 0, -1, 0);   // not yet reached by a sublist walk
         const bool smp = sampled(v, ruler_log2) != 0;
@@ -683,6 +687,9 @@ __global__ void k_final(DevGraph g, Scratch s) {
         }
       } else if (in[j] && !cyc[j]) {
         s.prd[ci] = make_int4(-1, -1, 0, 255);
+      } else if (!in[j] && ci < N && g.min_chain <= 1) {   // cut off by branch reads: its own contig
+        mark_head(s, v[j], 1);
+        atomicAdd(&c->n_heads, 1u);
       }
       const unsigned slot = warp_append(&c->n_cycle_reads, cyc[j]);
       if (cyc[j]) s.cyc[slot] = (int32_t)ci;
@@ -866,10 +873,8 @@ cudaError_t launch_mask(const DevGraph& g, const Scratch& s, const LaunchEnv& en
 
 cudaError_t launch_chains(const DevGraph& g, const Scratch& s, const Tuning& t, const LaunchEnv& env) {
   // restart the chain-stage counters; the head bitmap restarts from the mask
-  // stage's words (lone reads) and gains the chain heads below
+  // stage's words (lone reads; k_succ copies them) and gains the chain heads
   cudaMemsetAsync(&s.ctr->n_rulers, 0, offsetof(Counters, n_contigs) - offsetof(Counters, n_rulers), env.stream);
-  cudaMemcpyAsync(s.hb, s.hb_mask, (size_t)((g.n + 31) / 32) * sizeof(unsigned), cudaMemcpyDeviceToDevice,
-                  env.stream);
   static const int succ_resident = resident_blocks(k_succ);   // persistent grids
   static const int final_resident = resident_blocks(k_final);
   k_succ<<<env.num_sms * succ_resident, kBlock, 0, env.stream>>>(g, s, t.ruler_log2);
