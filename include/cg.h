@@ -290,8 +290,10 @@ typedef struct {
 } cg_stats;
 
 /* Timing: 0 off, 1 CUDA events around each stage, 2 also after every
- * kernel (for cg_kernel_time; the extra events cost some GPU time). Events
- * are recorded on the context stream; the work itself is unchanged. */
+ * kernel (for cg_kernel_time), 3 events around the spelling stage only
+ * (cg_stats.stage_ms[3]; the other stages read 0). Events are recorded on the
+ * context stream and the work itself is unchanged, but each event inside a
+ * replayed stage costs a few microseconds of GPU time. */
 CG_API cg_status cg_set_timing(cg_ctx* ctx, int enable);
 /* Fills *out; with timing on it waits for the last stages to finish. */
 CG_API cg_status cg_get_stats(cg_ctx* ctx, cg_stats* out);

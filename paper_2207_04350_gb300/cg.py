@@ -408,7 +408,7 @@ def cg_set_graphs(ctx: Context, enable: bool):
 
 
 def cg_set_timing(ctx: Context, level):
-    """0 off, 1 (or True) stage events, 2 stage and per-kernel events."""
+    """0 off, 1 (or True) stage events, 2 stage and per-kernel events, 3 events around the spelling stage only."""
     _check(ctx.ptr, lib().cg_set_timing(ctx.ptr, int(level)))
 
 

@@ -32,6 +32,7 @@ struct cg_ctx {
   std::map<void*, size_t> sizes;       // every live allocation of this context
   unsigned long long launches = 0;
   bool timing = false;
+  bool timing_emit_only = false;       // level 3: events around the spelling stage only
   cudaEvent_t ev[8] = {};              // start/end of mask, chains, offsets, emission
   bool recorded[4] = {false, false, false, false};
   cg::KernelMarks marks;               // per-kernel events of the last run (timing on)
@@ -179,11 +180,12 @@ cg_status check_ctx(cg_ctx* c) {
 struct StageTimer {
   cg_ctx* c;
   int k;
-  StageTimer(cg_ctx* c_, int k_) : c(c_), k(k_) {
-    if (c->timing) cudaEventRecord(c->ev[2 * k], c->stream);
+  bool on;
+  StageTimer(cg_ctx* c_, int k_) : c(c_), k(k_), on(c_->timing && (!c_->timing_emit_only || k_ == 3)) {
+    if (on) cudaEventRecord(c->ev[2 * k], c->stream);
   }
   ~StageTimer() {
-    if (c->timing) {
+    if (on) {
       cudaEventRecord(c->ev[2 * k + 1], c->stream);
       c->recorded[k] = true;
     }
@@ -570,7 +572,8 @@ cg_status cg_set_timing(cg_ctx* c, int enable) {
     for (cudaEvent_t& e : c->marks.ev) CK(cudaEventCreate(&e), "cudaEventCreate");
   }
   c->timing = enable != 0;
-  c->marks.on = enable >= 2;
+  c->timing_emit_only = enable == 3;
+  c->marks.on = enable == 2;
   c->marks.n = 0;
   for (bool& r : c->recorded) r = false;
   return CG_OK;
@@ -944,25 +947,25 @@ cg_status cg_emit_contigs(cg_graph* g, int64_t* contig_off, int64_t contig_off_c
       st = run_chains(g);
       if (st != CG_OK) return st;
     }
-    const bool timing = c->timing != 0;
+    const bool timing = c->timing != 0, stages = timing && !c->timing_emit_only;
     uint64_t key = mix_key(mix_key(mix_key(mix_key((uint64_t)(uintptr_t)bases, (uint64_t)bases_cap),
                                            (uint64_t)(uintptr_t)g->g.packed), (uint64_t)c->tune.tile_bytes),
                            (uint64_t)c->tune.emit_blocks_per_sm);
-    key = mix_key(mix_key(mix_key(key, (uint64_t)(uintptr_t)contig_off), (uint64_t)contig_off_cap), timing ? 3 : 4);
+    key = mix_key(mix_key(mix_key(key, (uint64_t)(uintptr_t)contig_off), (uint64_t)contig_off_cap),
+                  stages ? 3 : (timing ? 5 : 4));
     st = run_stage(g, 6, key, [&]() -> cg_status {
-      if (timing) record_stage_event(c, 4);
+      if (stages) record_stage_event(c, 4);
       CK(cg::launch_offsets(g->g, g->s, c->tune, c->env), "offset kernels");
-      if (timing) {
-        record_stage_event(c, 5);
-        record_stage_event(c, 6);
-      }
+      if (stages) record_stage_event(c, 5);
+      if (timing) record_stage_event(c, 6);
       CK(cg::launch_emit(g->g, g->s, c->tune, bases, bases_cap, c->env), "emission kernel");
       if (timing) record_stage_event(c, 7);
       if (contig_off) CK(cg::launch_export_contig_off(g->s, contig_off, contig_off_cap, c->env), "export contig_off");
       return CG_OK;
     });
     if (st != CG_OK) return st;
-    if (timing) c->recorded[2] = c->recorded[3] = true;
+    if (stages) c->recorded[2] = true;
+    if (timing) c->recorded[3] = true;
     g->stage = 3;
     if (n_contigs || total_bases) {
       st = wait_and_read(g);
