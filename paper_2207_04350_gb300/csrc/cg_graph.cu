@@ -134,33 +134,52 @@ __global__ void k_validate_entries(DevGraph g, DevError* c) {
 // no overlap are lone reads: a one-read contig when min_chain <= 1. Every
 // word of the mask-stage bitmap of contig heads is written here (the lone
 // reads' bits); the chain stage adds the other heads to a copy of it.
-// A warp owns 128 consecutive reads per pass, four per lane: a lane loads
-// its four row starts with 16-byte loads (a read's degree is the next start
-// minus its own; the fourth read's end is the next lane's first start),
-// writes its four branch bytes as one word, and queues the reads of degree
-// 1 or 2, whose rule needs the neighbours' degrees. The whole warp then
-// resolves the queue together, so that a pass waits for three dependent
+// A warp owns 256 consecutive reads per pass, eight per lane: a lane loads
+// its eight row starts with 16-byte loads (a read's degree is the next start
+// minus its own; the eighth read's end is the next lane's first start),
+// writes its eight branch bytes as one 8-byte store, and queues the reads of
+// degree 1 or 2, whose rule needs the neighbours' degrees. The whole warp
+// then resolves the queue together, so that a pass waits for three dependent
 // loads (row starts; col and code; the neighbours' rows) whatever the mix of
 // degrees in it. The candidate and lone-read lists gather in per-warp
 // shared-memory buffers and reach the global lists with one reservation per
-// block at the end (a warp flushes early only when a pass could overflow its
+// block at the end (a warp flushes early only when a pass would overflow its
 // buffer): returning atomics on one counter, one per pass, would serialise.
-constexpr int kMaskSpan = 128;
+constexpr int kMaskLane = 8;                  // reads per lane per pass
+constexpr int kMaskSpan = 32 * kMaskLane;     // reads per warp per pass
 constexpr int kMaskWarps = kBlock / 32;
-constexpr int kMaskBuf = 256;
+constexpr int kMaskBuf = 256;                 // buffered list entries per warp
 
 template <typename RP>
-__device__ __forceinline__ void load4(const RP* p, int64_t r[4]);
+__device__ __forceinline__ void load_rows(const RP* p, int64_t r[kMaskLane]);
 template <>
-__device__ __forceinline__ void load4<int64_t>(const int64_t* p, int64_t r[4]) {
-  const longlong2 x = __ldg(reinterpret_cast<const longlong2*>(p));
-  const longlong2 y = __ldg(reinterpret_cast<const longlong2*>(p) + 1);
-  r[0] = x.x; r[1] = x.y; r[2] = y.x; r[3] = y.y;
+__device__ __forceinline__ void load_rows<int64_t>(const int64_t* p, int64_t r[kMaskLane]) {
+#pragma unroll
+  for (int k = 0; k < kMaskLane / 2; ++k) {
+    const longlong2 x = __ldg(reinterpret_cast<const longlong2*>(p) + k);
+    r[2 * k] = x.x;
+    r[2 * k + 1] = x.y;
+  }
 }
 template <>
-__device__ __forceinline__ void load4<int32_t>(const int32_t* p, int64_t r[4]) {
-  const int4 x = __ldg(reinterpret_cast<const int4*>(p));
-  r[0] = x.x; r[1] = x.y; r[2] = x.z; r[3] = x.w;
+__device__ __forceinline__ void load_rows<int32_t>(const int32_t* p, int64_t r[kMaskLane]) {
+#pragma unroll
+  for (int k = 0; k < kMaskLane / 4; ++k) {
+    const int4 x = __ldg(reinterpret_cast<const int4*>(p) + k);
+    r[4 * k] = x.x; r[4 * k + 1] = x.y; r[4 * k + 2] = x.z; r[4 * k + 3] = x.w;
+  }
+}
+
+// Exclusive prefix of per-lane counts across the warp; the total in *tot.
+__device__ __forceinline__ unsigned warp_exclusive(unsigned x, unsigned* tot, int lane) {
+  unsigned inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  *tot = __shfl_sync(0xffffffffu, inc, 31);
+  return inc - x;
 }
 
 // Appends n buffered entries of one warp to a global list with one atomic.
@@ -201,7 +220,6 @@ __global__ void __launch_bounds__(kBlock) k_mask(DevGraph g, Scratch s) {
   if (threadIdx.x < 2) blk_n[threadIdx.x] = 0;       // read after the first barrier below
   unsigned long long nb = 0;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const unsigned lt = (1u << lane) - 1u;
   int32_t* const bc = b_cand[wib];
   int32_t* const bl = b_lone[wib];
   unsigned nc = 0, nl = 0;                           // buffered entries (warp-uniform)
@@ -210,69 +228,75 @@ __global__ void __launch_bounds__(kBlock) k_mask(DevGraph g, Scratch s) {
     // warp-uniform trip count; row_ptr holds n + 1 entries
     const int cnt = (int)min((long long)kMaskSpan, g.n - wbase);
     const bool full = cnt == kMaskSpan;
-    const int p0 = 4 * lane;
-    int64_t r[4];
+    const int p0 = kMaskLane * lane;
+    int64_t r[kMaskLane];
     if (kAligned && full) {
-      load4<RP>(rp + wbase + p0, r);
+      load_rows<RP>(rp + wbase + p0, r);
     } else {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) r[j] = p0 + j <= cnt ? (int64_t)rp[wbase + p0 + j] : 0;
+      for (int j = 0; j < kMaskLane; ++j) r[j] = p0 + j <= cnt ? (int64_t)rp[wbase + p0 + j] : 0;
     }
     int64_t e = __shfl_down_sync(0xffffffffu, r[0], 1);
     if (lane == 31) e = full ? (int64_t)rp[wbase + kMaskSpan] : 0;
-    unsigned word = 0, pend = 0, lone = 0;
+    uint32_t br[2] = {0u, 0u};
+    unsigned pend = 0, two = 0, lone = 0;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int64_t d = (j < 3 ? r[j + 1] : e) - r[j];
+    for (int j = 0; j < kMaskLane; ++j) {
+      const int64_t d = (j < kMaskLane - 1 ? r[j + 1] : e) - r[j];
       if (p0 + j < cnt) {
-        if (d >= 3) { word |= 1u << (8 * j); ++nb; }
-        else if (d > 0) pend |= 1u << j;
+        if (d >= 3) { br[j >> 2] |= 1u << (8 * (j & 3)); ++nb; }
+        else if (d > 0) { pend |= 1u << j; two |= (d == 2 ? 1u : 0u) << j; }
         else lone |= 1u << j;
       }
     }
     if (g.min_chain > 1) lone = 0;
     if (full) {
-      *reinterpret_cast<uint32_t*>(s.branch + wbase + p0) = word;
+      *reinterpret_cast<uint2*>(s.branch + wbase + p0) = make_uint2(br[0], br[1]);
     } else {
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if (p0 + j < cnt) s.branch[wbase + p0 + j] = (uint8_t)(word >> (8 * j));
+      for (int j = 0; j < kMaskLane; ++j)
+        if (p0 + j < cnt) s.branch[wbase + p0 + j] = (uint8_t)(br[j >> 2] >> (8 * (j & 3)));
     }
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-      if ((word >> (8 * j)) & 1u) s.cidx[wbase + p0 + j] = -1;
-    unsigned T = 0;                                    // queued reads of this pass
+    for (int j = 0; j < kMaskLane; ++j)
+      if ((br[j >> 2] >> (8 * (j & 3))) & 1u) s.cidx[wbase + p0 + j] = -1;
+    unsigned T;                                        // queued reads of this pass
+    unsigned k = warp_exclusive(__popc(pend), &T, lane);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const bool q = (pend >> j) & 1u;
-      const unsigned pm = __ballot_sync(0xffffffffu, q);
-      if (q) {
-        const unsigned slot = T + __popc(pm & lt);
-        q_row[wib][slot] = r[j];
-        q_pos[wib][slot] = (uint16_t)((p0 + j) | (((j < 3 ? r[j + 1] : e) - r[j] == 2) ? 256 : 0));
+    for (int j = 0; j < kMaskLane; ++j)
+      if ((pend >> j) & 1u) {
+        q_row[wib][k] = r[j];
+        q_pos[wib][k] = (uint16_t)((p0 + j) | (((two >> j) & 1u) << 8));
+        ++k;
       }
-      T += __popc(pm);
-    }
-    // the pass's four words of the heads bitmap: lane 8w + l holds bits 4l..4l+3 of word w
+    // the pass's eight words of the heads bitmap: lane 4w + l holds bits 8l..8l+7 of word w
     if (g.min_chain <= 1) {                            // uniform
-      unsigned x = lone << (4 * (lane & 7));
+      unsigned x = lone << (8 * (lane & 3));
       x |= __shfl_xor_sync(0xffffffffu, x, 1);
       x |= __shfl_xor_sync(0xffffffffu, x, 2);
-      x |= __shfl_xor_sync(0xffffffffu, x, 4);
-      if ((lane & 7) == 0 && 4 * lane < cnt) s.hb_mask[(wbase >> 5) + (lane >> 3)] = x;
+      if ((lane & 3) == 0 && kMaskLane * lane < cnt) s.hb_mask[(wbase >> 5) + (lane >> 2)] = x;
+      unsigned L;
+      unsigned kl = warp_exclusive(__popc(lone), &L, lane);
+      if (nl + L > kMaskBuf) {                         // uniform: this pass would overflow the buffer
+        warp_flush(&c->n_lone, s.lone, bl, nl, lane);
+        nl = 0;
+        __syncwarp();
+      }
+      kl += nl;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const bool l = (lone >> j) & 1u;
-        const unsigned lm = __ballot_sync(0xffffffffu, l);
-        if (l) {
+      for (int j = 0; j < kMaskLane; ++j)
+        if ((lone >> j) & 1u) {
           const int32_t v = (int32_t)(wbase + p0 + j);
-          bl[nl + __popc(lm & lt)] = v;
+          bl[kl++] = v;
           s.headq[v] = 1;
         }
-        nl += __popc(lm);
-      }
-    } else if (lane < 4 && 32 * lane < cnt) {
+      nl += L;
+    } else if (lane < kMaskSpan / 32 && 32 * lane < cnt) {
       s.hb_mask[(wbase >> 5) + lane] = 0u;
+    }
+    if (nc + T > kMaskBuf) {                           // uniform: the queue could overflow the buffer
+      flush_cands(s, bc, nc, warp_reserve(&c->n_cand, nc, lane), lane);
+      nc = 0;
     }
     __syncwarp();                                      // queue written; branch bytes ordered before the fix-ups
     for (unsigned j0 = 0; j0 < T; j0 += 32) {          // warp-uniform
@@ -282,13 +306,13 @@ __global__ void __launch_bounds__(kBlock) k_mask(DevGraph g, Scratch s) {
       if (jj < T) {
         const unsigned q = q_pos[wib][jj];
         const int64_t x = q_row[wib][jj];
-        const bool two = (q >> 8) != 0;
+        const bool two2 = (q >> 8) != 0;
         v = (int32_t)(wbase + (q & 255u));
         const int32_t w0 = g.col[x];
-        const int32_t w1 = two ? g.col[x + 1] : w0;
-        const int c0 = g.code[x] & 1, c1 = two ? (g.code[x + 1] & 1) : c0;
+        const int32_t w1 = two2 ? g.col[x + 1] : w0;
+        const int c0 = g.code[x] & 1, c1 = two2 ? (g.code[x + 1] & 1) : c0;
         const bool k0 = (int64_t)rp[w0 + 1] - (int64_t)rp[w0] < 3;
-        const bool k1 = two && (int64_t)rp[w1 + 1] - (int64_t)rp[w1] < 3;
+        const bool k1 = two2 && (int64_t)rp[w1 + 1] - (int64_t)rp[w1] < 3;
         // two overlaps to reads of degree <= 2, both on one end: a branch
         if (k0 && k1 && c0 == c1) {
           s.branch[v] = 1;
@@ -299,13 +323,10 @@ __global__ void __launch_bounds__(kBlock) k_mask(DevGraph g, Scratch s) {
         }
       }
       const unsigned cm = __ballot_sync(0xffffffffu, cand);
-      if (cand) bc[nc + __popc(cm & lt)] = v;
+      if (cand) bc[nc + __popc(cm & ((1u << lane) - 1u))] = v;
       nc += __popc(cm);
     }
     __syncwarp();                                      // queue and buffers reused next pass
-    // a pass adds at most kMaskSpan entries to a buffer
-    if (nc > kMaskBuf - kMaskSpan) { flush_cands(s, bc, nc, warp_reserve(&c->n_cand, nc, lane), lane); nc = 0; __syncwarp(); }
-    if (nl > kMaskBuf - kMaskSpan) { warp_flush(&c->n_lone, s.lone, bl, nl, lane); nl = 0; __syncwarp(); }
   }
   // one reservation per block for the entries the warps still hold
   __syncthreads();
