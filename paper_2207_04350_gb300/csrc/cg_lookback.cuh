@@ -81,7 +81,10 @@ struct has_item<L, std::void_t<typename L::Item>> : std::true_type {};
 //          void last(long long count, unsigned long long total)
 // Blocks loop over tiles by ticket; the blocks a count needs no tile of exit
 // at once without taking one, so a grid sized for the largest count costs
-// little when the count (read on the device) is small.
+// little when the count (read on the device) is small. When the grid has a
+// block for every tile, block b scans tile b with no ticket: the grid is then
+// at most the blocks resident at once, so every predecessor a tile waits for
+// is running.
 template <class Load, class Store>
 __global__ void __launch_bounds__(kBlock) k_scan(Load ld, Store st, long long count_host, const unsigned* count_dev,
                                                  unsigned long long* state, long long ticket_index, DevError* derr,
@@ -94,11 +97,15 @@ __global__ void __launch_bounds__(kBlock) k_scan(Load ld, Store st, long long co
   const long long tiles = (count + kTileItems - 1) / kTileItems;
   if ((long long)blockIdx.x >= tiles) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool direct = (long long)gridDim.x >= tiles;
   for (;;) {
-    if (tid == 0) s_tile = (long long)atomicAdd(&state[ticket_index], 1ull);
-    __syncthreads();
-    const long long tile = s_tile;
-    if (tile >= tiles) return;                       // block-uniform
+    long long tile = blockIdx.x;
+    if (!direct) {
+      if (tid == 0) s_tile = (long long)atomicAdd(&state[ticket_index], 1ull);
+      __syncthreads();
+      tile = s_tile;
+      if (tile >= tiles) return;                     // block-uniform
+    }
     const long long base = tile * kTileItems;
     typename std::conditional<has_item<Load>::value, Load, NoItem>::type::Item it[kItems];
     if constexpr (has_item<Load>::value) {
@@ -161,6 +168,7 @@ __global__ void __launch_bounds__(kBlock) k_scan(Load ld, Store st, long long co
         }
       }
     }
+    if (direct) return;
     __syncthreads();                                 // sm and s_tile are reused by the next tile
   }
 }
@@ -168,9 +176,11 @@ __global__ void __launch_bounds__(kBlock) k_scan(Load ld, Store st, long long co
 }  // namespace
 
 // Grid of a scan over at most `tiles` tiles: blocks loop over tiles by
-// ticket, so the grid need not exceed what runs at once.
+// ticket, so the grid need not exceed what runs at once (every scan here fits
+// three blocks per SM: at most 80 registers per thread and 16.5 KB of shared
+// memory per block).
 inline unsigned scan_grid(long long tiles, const LaunchEnv& env) {
-  const long long cap = (long long)env.num_sms * 4;
+  const long long cap = (long long)env.num_sms * 3;
   return (unsigned)(tiles < 1 ? 1 : (tiles < cap ? tiles : cap));
 }
 
