@@ -397,6 +397,9 @@ cg_status finish_load(cg_graph* g, uint32_t flags) {
   if (S.scan_state[0]) {
     S.scan_state[1] = S.scan_state[0] + (S.scan_tiles_cap + 1);
     S.scan_state[2] = S.scan_state[1] + (S.scan_tiles_cap + 1);
+    // zeroed once; afterwards each offsets-stage scan zeroes the other's descriptors
+    CK(cudaMemsetAsync(S.scan_state[0], 0, 3 * ((size_t)S.scan_tiles_cap + 1) * sizeof(unsigned long long),
+                       c->stream), "clear scan descriptors");
   }
   S.ctr = galloc<cg::Counters>(g, 1, &st);
   g->d_sum = galloc<unsigned long long>(g, 1, &st);

@@ -84,15 +84,19 @@ struct has_item<L, std::void_t<typename L::Item>> : std::true_type {};
 // little when the count (read on the device) is small. When the grid has a
 // block for every tile, block b scans tile b with no ticket: the grid is then
 // at most the blocks resident at once, so every predecessor a tile waits for
-// is running.
+// is running. A scan may also zero `clear` (clear_words words), another
+// scan's descriptors, so that no separate memset runs before that one.
 template <class Load, class Store>
 __global__ void __launch_bounds__(kBlock) k_scan(Load ld, Store st, long long count_host, const unsigned* count_dev,
                                                  unsigned long long* state, long long ticket_index, DevError* derr,
-                                                 int where) {
+                                                 int where, unsigned long long* clear = nullptr,
+                                                 long long clear_words = 0) {
   __shared__ unsigned long long sm[kTileItems];
   __shared__ unsigned long long warp_tot[kBlock / 32];
   __shared__ long long s_tile;
   __shared__ unsigned long long s_excl;
+  for (long long i = (long long)blockIdx.x * kBlock + threadIdx.x; i < clear_words; i += (long long)gridDim.x * kBlock)
+    clear[i] = 0ull;
   const long long count = count_dev ? (long long)*(const volatile unsigned*)count_dev : count_host;
   const long long tiles = (count + kTileItems - 1) / kTileItems;
   if ((long long)blockIdx.x >= tiles) return;

@@ -87,7 +87,11 @@ struct HeadWordStore {
     c->n_contigs = C;
     cbase[C] = total & kHeadLow;
     c->n_walk = (unsigned)(total & kHeadLow);
-    if (C == 0) contig_off[0] = 0;     // no contigs: the piece scan has nothing to scan
+    if (C == 0) {                      // no contigs: the piece scan has nothing to scan
+      contig_off[0] = 0;
+      c->total_bases = 0;
+      c->n_tiles = 0;
+    }
   }
 };
 
@@ -199,7 +203,13 @@ __global__ void k_scatter(DevGraph g, Scratch s) {
 
 // An empty graph: no contigs, and the one offset 0.
 __global__ void k_contig_off(Scratch s) {
-  if (grid_tid() == 0) s.contig_off[0] = 0;
+  if (grid_tid() == 0) {
+    s.contig_off[0] = 0;
+    s.ctr->n_contigs = 0;
+    s.ctr->n_walk = 0;
+    s.ctr->n_tiles = 0;
+    s.ctr->total_bases = 0;
+  }
 }
 
 __global__ void k_export_contig_off(Scratch s, int64_t* out, long long cap) {
@@ -215,13 +225,15 @@ __global__ void k_export_contig_off(Scratch s, int64_t* out, long long cap) {
 }  // namespace
 
 cudaError_t launch_offsets(const DevGraph& g, const Scratch& s, const Tuning& t, const LaunchEnv& env) {
-  cudaMemsetAsync(&s.ctr->n_contigs, 0, sizeof(Counters) - offsetof(Counters, n_contigs), env.stream);
+  // No memset: the scans' last steps assign every counter of this stage, and
+  // each scan zeroes the other one's descriptors (the heads scan the piece
+  // scan's, the piece scan the heads scan's, for the next run); the graph
+  // load zeroes both once.
   const long long words = (g.n + 31) / 32;
   const long long tiles_w = (words + kTileItems - 1) / kTileItems;
   const long long tiles_n = (g.n + kTileItems - 1) / kTileItems;
   if (tiles_n > s.scan_tiles_cap || tiles_w > s.scan_tiles_cap) return cudaErrorInvalidValue;
-  // the three scans' tile descriptors and tickets are contiguous: one memset
-  cudaMemsetAsync(s.scan_state[0], 0, (size_t)3 * (s.scan_tiles_cap + 1) * sizeof(unsigned long long), env.stream);
+  const long long state_words = s.scan_tiles_cap + 1;
   if (g.n == 0) {
     k_contig_off<<<1, kBlock, 0, env.stream>>>(s);
     mark(env, "k_contig_off");
@@ -230,7 +242,7 @@ cudaError_t launch_offsets(const DevGraph& g, const Scratch& s, const Tuning& t,
   HeadWordLoad hl{s.hb, s.headq};
   HeadWordStore hs{s.wp, s.headq, s.qd, s.cbase, s.contig_off, s.ctr};
   k_scan<<<scan_grid(tiles_w, env), kBlock, 0, env.stream>>>(hl, hs, words, nullptr, s.scan_state[0], s.scan_tiles_cap,
-                                                       s.derr, K_SCAN_HEADS);
+                                                       s.derr, K_SCAN_HEADS, s.scan_state[2], state_words);
   mark(env, "k_scan_heads");
   static const int scatter_resident = resident_blocks(k_scatter);   // a persistent grid
   k_scatter<<<env.num_sms * scatter_resident, kBlock, 0, env.stream>>>(g, s);
@@ -238,7 +250,7 @@ cudaError_t launch_offsets(const DevGraph& g, const Scratch& s, const Tuning& t,
   PieceLoad pl{s.wlen, s.wfirst};
   PieceStore ps{s.out_off, s.contig_off, s.tile_seg, s.tiles_cap, t.tile_bytes, s.ctr, s.derr};
   k_scan<<<scan_grid(tiles_n, env), kBlock, 0, env.stream>>>(pl, ps, 0, &s.ctr->n_walk, s.scan_state[2], s.scan_tiles_cap,
-                                                       s.derr, K_SCAN_OFFSETS);
+                                                       s.derr, K_SCAN_OFFSETS, s.scan_state[0], state_words);
   mark(env, "k_scan_pieces");
   return cudaGetLastError();
 }
