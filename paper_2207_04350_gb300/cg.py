@@ -7,6 +7,7 @@ tensors as host memory. If libcg.so has not been built the first call raises.
 """
 from __future__ import annotations
 
+import sys
 import ctypes
 import os
 import threading
@@ -169,6 +170,8 @@ class Context:
             self.ptr = None
 
     def __del__(self):
+        if sys.is_finalizing():       # the process is exiting: the driver releases everything
+            return
         try:
             self.close()
         except Exception:
@@ -188,6 +191,8 @@ class Graph:
             self._keep = None
 
     def __del__(self):
+        if sys.is_finalizing():       # the process is exiting: the driver releases everything
+            return
         try:
             self.close()
         except Exception:
