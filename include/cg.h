@@ -249,7 +249,7 @@ CG_API cg_status cg_partition_contigs(cg_graph* g, int32_t n_parts, int32_t weig
 /* Launch parameters of a context's kernels. None changes any output. */
 typedef struct {
   int32_t ruler_log2;         /* list ranking: a read starts a sublist with probability 2^-ruler_log2, 1..12 */
-  int32_t tile_bytes;         /* spelling: output tile per block iteration, 4096, 8192, 16384 or 32768 */
+  int32_t tile_bytes;         /* spelling: output tile per warp iteration, a power of two from 4096 to 131072 */
   int32_t emit_blocks_per_sm; /* spelling: resident blocks per SM, 1..8 */
   int32_t reserved;
 } cg_tuning;

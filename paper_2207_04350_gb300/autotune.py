@@ -21,7 +21,7 @@ import threading
 from . import cg
 
 GRID = [dict(ruler_log2=r, tile_bytes=t, emit_blocks_per_sm=b)
-        for r in (3, 4, 5) for t in (16384, 32768) for b in (4, 8)]
+        for r in (3, 4, 5) for t in (16384, 32768, 65536) for b in (4, 8)]
 
 
 def size_class(n_reads: int, n_entries: int, packed_bytes: int) -> str:

@@ -526,8 +526,8 @@ cg_status cg_set_tuning(cg_ctx* c, const cg_tuning* t) {
     n.ruler_log2 = t->ruler_log2;
   }
   if (t->tile_bytes > 0) {
-    if (t->tile_bytes != 4096 && t->tile_bytes != 8192 && t->tile_bytes != 16384 && t->tile_bytes != 32768)
-      return fail(c, CG_EINVAL, "tile_bytes must be 4096, 8192, 16384 or 32768");
+    if (t->tile_bytes < 4096 || t->tile_bytes > 131072 || (t->tile_bytes & (t->tile_bytes - 1)))
+      return fail(c, CG_EINVAL, "tile_bytes must be a power of two from 4096 to 131072");
     n.tile_bytes = t->tile_bytes;
   }
   if (t->emit_blocks_per_sm > 0) {

@@ -114,7 +114,7 @@ def test_generated_sweep(ctx):
         check(ctx, G, 1 + seed % 2)
 
 
-@pytest.mark.parametrize("tile", [4096, 8192, 16384, 32768])
+@pytest.mark.parametrize("tile", [4096, 8192, 16384, 32768, 65536, 131072])
 def test_tile_sizes(tile):
     c = cg.cg_create(0)
     try:

@@ -204,7 +204,7 @@ def test_small_capacity_rejected(ctx):
 
 
 @pytest.mark.parametrize("ruler_log2,tile_bytes,bps", [(1, 4096, 1), (2, 8192, 2), (4, 16384, 8), (7, 32768, 4),
-                                                       (12, 32768, 3)])
+                                                       (12, 32768, 3), (3, 65536, 8), (5, 131072, 6)])
 def test_tuning_does_not_change_output(ruler_log2, tile_bytes, bps):
     """Launch parameters chosen by the autotuner never change a byte."""
     c = cg.cg_create(0)
