@@ -22,6 +22,12 @@
 // own kernel. A read then knows, from its two oriented copies, the chain's
 // length, both end reads, its position from either end, and the chain's
 // smallest read id.
+//
+// The mask stage lists the candidates (unmasked reads with overlaps, in
+// candidate order c, with cidx[v] = c) and the chain stage indexes its records
+// by candidate, oriented copies u = 2c + o: they sit together instead of
+// spreading over arrays of n reads. Sublist records keep read ids, which the
+// canonical order compares.
 #include <cuda_runtime.h>
 
 #include "cg_internal.cuh"
