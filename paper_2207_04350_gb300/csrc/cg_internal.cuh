@@ -237,9 +237,6 @@ __device__ __forceinline__ void set_error(DevError* e, int code, int where, long
 
 __device__ __forceinline__ long long grid_tid() { return (long long)blockIdx.x * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ long long grid_threads() { return (long long)gridDim.x * blockDim.x; }
-// Rounded-up trip count so that whole blocks iterate together (block_reserve
-// synchronises the block).
-__device__ __forceinline__ long long block_round(long long n) { return (n + kBlock - 1) / kBlock * kBlock; }
 
 enum KernelId {
   K_VALIDATE1 = 1, K_VALIDATE2, K_MASK, K_SUCC, K_WALK, K_JUMP, K_FINAL, K_CYCLE, K_EXPORT,
@@ -277,68 +274,6 @@ __device__ __forceinline__ unsigned warp_append(unsigned* counter, bool want) {
   if (lane == leader) base = atomicAdd(counter, (unsigned)__popc(mask));
   base = __shfl_sync(mask, base, leader);
   return base + (unsigned)__popc(mask & ((1u << lane) - 1u));
-}
-
-// Block-wide reservation of `count` list slots per thread with one atomic per
-// block: every thread of the block must call it (block-uniform control flow).
-// Returns the first slot of this thread's items.
-__device__ __forceinline__ unsigned block_reserve(unsigned* counter, unsigned count) {
-  __shared__ unsigned s_w[kBlock / 32 + 1];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned inc = count;
-  for (int o = 1; o < 32; o <<= 1) {
-    unsigned t = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += t;
-  }
-  if (lane == 31) s_w[warp] = inc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned tot = 0;
-    for (int w = 0; w < kBlock / 32; ++w) {
-      unsigned c = s_w[w];
-      s_w[w] = tot;
-      tot += c;
-    }
-    s_w[kBlock / 32] = tot ? atomicAdd(counter, tot) : 0u;
-  }
-  __syncthreads();
-  unsigned base = s_w[kBlock / 32] + s_w[warp] + inc - count;
-  __syncthreads();
-  return base;
-}
-
-// Reserves slots in up to four lists with one block-wide scan: 16-bit field f
-// of `counts` is this thread's count for *counters[f] (at most 255 per
-// thread). base[f] receives the thread's first slot in list f. Every thread
-// of the block must call it (block-uniform control flow).
-__device__ __forceinline__ void block_reserve4(unsigned* const counters[4], unsigned long long counts,
-                                               unsigned base[4]) {
-  __shared__ unsigned long long s_w[kBlock / 32];
-  __shared__ unsigned s_g[4];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned long long inc = counts;
-  for (int o = 1; o < 32; o <<= 1) {
-    unsigned long long t = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += t;
-  }
-  if (lane == 31) s_w[warp] = inc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long tot = 0;
-    for (int w = 0; w < kBlock / 32; ++w) {
-      unsigned long long c = s_w[w];
-      s_w[w] = tot;
-      tot += c;
-    }
-    for (int f = 0; f < 4; ++f) {
-      unsigned tf = (unsigned)((tot >> (16 * f)) & 0xFFFFu);
-      s_g[f] = tf ? atomicAdd(counters[f], tf) : 0u;
-    }
-  }
-  __syncthreads();
-  const unsigned long long ex = s_w[warp] + inc - counts;
-  for (int f = 0; f < 4; ++f) base[f] = s_g[f] + (unsigned)((ex >> (16 * f)) & 0xFFFFu);
-  __syncthreads();
 }
 
 }  // namespace cg
