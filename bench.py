@@ -34,7 +34,7 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 # DRAM bytes (read + write) per contig base of k_emit from one ncu capture
 # (--set full, the 3.1 Gb recipe on a 450 Mb genome: 551.5 MB for 481,446,585
 # bases), valid only for the emission source it was taken on.
-EMIT_TRAFFIC = {"bytes_per_base": 551.5e6 / 481446585, "source_sha256_16": "c863d26b78abdb32"}
+EMIT_TRAFFIC = {"bytes_per_base": (129.624064e6 + 422.158336e6) / 481446585, "source_sha256_16": "08fafa686c29d54d"}
 
 
 def _reduce(x: float, world: int, op: str) -> float:

@@ -38,6 +38,8 @@ struct cg_ctx {
   cg::KernelMarks marks;               // per-kernel events of the last run (timing on)
   bool graphs = true;                  // replay each stage from a captured CUDA graph
   bool host_direct = true;             // kernels write pinned host outputs in place
+  cudaStream_t copy_stream = nullptr;  // device-to-host copies overlapping the spelling (created on first use)
+  cudaEvent_t copy_ev = nullptr;       //   a chunk spelled / the copies done
   cg::FaultPlan fault;                 // host-side fault injection (tests)
 };
 
@@ -512,6 +514,11 @@ cg_status cg_destroy(cg_ctx* c) {
     if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : c->marks.ev)
     if (e) cudaEventDestroy(e);
+  if (c->copy_stream) {
+    cudaStreamSynchronize(c->copy_stream);
+    cudaStreamDestroy(c->copy_stream);
+  }
+  if (c->copy_ev) cudaEventDestroy(c->copy_ev);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   cudaGetLastError();
   delete c;
@@ -1014,10 +1021,42 @@ cg_status cg_emit_contigs(cg_graph* g, int64_t* contig_off, int64_t contig_off_c
     const int64_t total = c->h_ctr->total_bases, C = c->h_ctr->n_contigs;
     if (bases && bases_cap < total) return fail(c, CG_EINVAL, "bases capacity %lld < %lld", (long long)bases_cap, (long long)total);
     if (contig_off && contig_off_cap < C + 1) return fail(c, CG_EINVAL, "contig_off capacity too small");
-    // pinned host output: the kernel writes it over the host link; other host memory: staged and copied
-    uint8_t* direct = c->host_direct ? (uint8_t*)pinned_device_alias(bases) : nullptr;
+    // Large outputs: spelled into HBM in chunks of tiles, each chunk copied to
+    // the host by the copy engines while the next one is spelled (the host
+    // link, not the spelling, bounds the step). Smaller ones, when pinned: the
+    // kernel writes them over the host link in place; otherwise staged and
+    // copied once.
+    const int64_t kPipelineMin = 64ll << 20, kChunk = 128ll << 20;
+    const bool pipelined = bases && total >= kPipelineMin;
+    uint8_t* direct = c->host_direct && !pipelined ? (uint8_t*)pinned_device_alias(bases) : nullptr;
     if (direct && !aligned(direct, 16)) direct = nullptr;
-    if (bases && total > 0) {
+    if (pipelined) {
+      if (g->stage_bases_cap < total) {
+        if (g->stage_bases) dfree(c, g->stage_bases);
+        g->stage_bases = (uint8_t*)dalloc(c, (size_t)total, &st);
+        if (!g->stage_bases) { g->stage_bases_cap = 0; return st; }
+        g->stage_bases_cap = total;
+      }
+      if (!c->copy_stream) {
+        CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking), "copy stream");
+        CK(cudaEventCreateWithFlags(&c->copy_ev, cudaEventDisableTiming), "copy event");
+      }
+      StageTimer tm(c, 3);
+      const int64_t tb = c->tune.tile_bytes;
+      const int64_t tiles = (total + tb - 1) / tb, per = std::max<int64_t>(1, kChunk / tb);
+      for (int64_t t0 = 0; t0 < tiles; t0 += per) {
+        const int64_t t1 = std::min(tiles, t0 + per);
+        const int64_t b0 = t0 * tb, b1 = std::min(total, t1 * tb);
+        CK(cg::launch_emit(emit_graph(g), g->s, c->tune, g->stage_bases, g->stage_bases_cap, c->env, t0, t1),
+           "emission kernel");
+        CK(cudaEventRecord(c->copy_ev, c->stream), "chunk event");
+        CK(cudaStreamWaitEvent(c->copy_stream, c->copy_ev, 0), "copy stream wait");
+        CK(cudaMemcpyAsync(bases + b0, g->stage_bases + b0, (size_t)(b1 - b0), cudaMemcpyDeviceToHost,
+                           c->copy_stream), "copy bases");
+      }
+      CK(cudaEventRecord(c->copy_ev, c->copy_stream), "copies done");
+      CK(cudaStreamWaitEvent(c->stream, c->copy_ev, 0), "stream waits for the copies");
+    } else if (bases && total > 0) {
       uint8_t* dst = direct;
       int64_t dcap = bases_cap;
       if (!dst) {

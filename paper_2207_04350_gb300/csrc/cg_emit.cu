@@ -65,7 +65,7 @@ __device__ __forceinline__ uint8_t base_at(const uint8_t* packed, unsigned long 
 template <int U>
 __global__ void __launch_bounds__(kBlock) k_emit(Scratch s, const uint8_t* packed, long long packed_bytes,
                                                  long long readable_words, uint8_t* out, long long cap,
-                                                 int tile_bytes) {
+                                                 int tile_bytes, long long t_begin, long long t_end) {
   __shared__ uint32_t lut[2][256];
   for (int i = threadIdx.x; i < 256; i += blockDim.x) {
     uint32_t f = 0, r = 0;
@@ -89,7 +89,8 @@ __global__ void __launch_bounds__(kBlock) k_emit(Scratch s, const uint8_t* packe
   const long long full_words = packed_bytes >> 2;
   const int64_t* oo = s.out_off;
   const unsigned long long* ws = s.wsrc;
-  for (long long t = grid_tid() >> 5; t < ntiles; t += grid_threads() >> 5) {
+  const long long t_stop = min(ntiles, t_end);          // the tiles [t_begin, t_end) of this launch
+  for (long long t = t_begin + (grid_tid() >> 5); t < t_stop; t += grid_threads() >> 5) {
     const int lo = s.tile_seg[t], hi = s.tile_seg[t + 1];
     const long long tbase = t * (long long)tile_bytes;
     const long long tend = min(tbase + (long long)tile_bytes, total);
@@ -165,7 +166,7 @@ __global__ void __launch_bounds__(kBlock) k_emit(Scratch s, const uint8_t* packe
 }  // namespace
 
 cudaError_t launch_emit(const DevGraph& g, const Scratch& s, const Tuning& t, uint8_t* out, int64_t cap,
-                        const LaunchEnv& env) {
+                        const LaunchEnv& env, long long t_begin, long long t_end) {
   // a persistent grid: never more blocks than can be resident at once
   static int resident = 0;
   if (resident == 0) {
@@ -176,7 +177,7 @@ cudaError_t launch_emit(const DevGraph& g, const Scratch& s, const Tuning& t, ui
   int per_sm = t.emit_blocks_per_sm < resident ? t.emit_blocks_per_sm : resident;
   int blocks = env.num_sms * per_sm;
   k_emit<4><<<blocks, kBlock, 0, env.stream>>>(s, g.packed, g.packed_bytes, g.packed_readable / 4, out, cap,
-                                               t.tile_bytes);
+                                               t.tile_bytes, t_begin, t_end);
   mark(env, "k_emit");
   return cudaGetLastError();
 }
