@@ -791,7 +791,8 @@ def run_ours(args, rank, world, local_rank):
                "h2d_note": "graph arrays copied + the 2-bit bases of the spelled pieces, read by the kernels over "
                            "the host link (the rest of the 23 GB of reads is never moved)",
                "path": "cg_load_graph(host, validated, CG_HOST_READS) -> cg_mask_branches -> cg_chains -> "
-                       "cg_emit_contigs(pinned host outputs, written in place) -> cg_free_graph"}
+                       "cg_emit_contigs(pinned host outputs: spelled in HBM in 128 MB chunks, each copied to "
+                       "the host while the next is spelled) -> cg_free_graph"}
         tc, nc2 = e2e_run(0)
         e2e_copy = {"value": job_rate(total, tc, world) / 1e9, "unit": UNIT,
                     "h2d_bytes_per_step": sum(getattr(G, k).nbytes for k in names), "d2h_bytes_per_step": d2h,
