@@ -1144,9 +1144,39 @@ cg_status cg_emit_contigs_2bit(cg_graph* g, int64_t* contig_off, int64_t contig_
     if (packed_out && packed_cap < need)
       return fail(c, CG_EINVAL, "packed capacity %lld < %lld", (long long)packed_cap, (long long)need);
     if (contig_off && contig_off_cap < C + 1) return fail(c, CG_EINVAL, "contig_off capacity too small");
-    uint8_t* direct = c->host_direct ? (uint8_t*)pinned_device_alias(packed_out) : nullptr;
+    // large outputs: spelled into HBM in chunks of tiles, each copied to the host
+    // while the next one is spelled (as for the ASCII form)
+    const int64_t kPipelineMin = 64ll << 20, kChunk = 128ll << 20;
+    const bool pipelined = packed_out && need >= kPipelineMin;
+    uint8_t* direct = c->host_direct && !pipelined ? (uint8_t*)pinned_device_alias(packed_out) : nullptr;
     if (direct && !aligned(direct, 16)) direct = nullptr;
-    if (packed_out && need > 0) {
+    if (pipelined) {
+      if (g->stage_bases_cap < need) {
+        if (g->stage_bases) dfree(c, g->stage_bases);
+        g->stage_bases = (uint8_t*)dalloc(c, (size_t)need, &st);
+        if (!g->stage_bases) { g->stage_bases_cap = 0; return st; }
+        g->stage_bases_cap = need;
+      }
+      if (!c->copy_stream) {
+        CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking), "copy stream");
+        CK(cudaEventCreateWithFlags(&c->copy_ev, cudaEventDisableTiming), "copy event");
+      }
+      StageTimer tm(c, 3);
+      const int64_t tb = c->tune.tile_bytes, tile_out = tb / 4;   // a tile holds tb bases, tb / 4 bytes
+      const int64_t tiles = (total + tb - 1) / tb, per = std::max<int64_t>(1, kChunk / tile_out);
+      for (int64_t t0 = 0; t0 < tiles; t0 += per) {
+        const int64_t t1 = std::min(tiles, t0 + per);
+        const int64_t b0 = t0 * tile_out, b1 = std::min(need, t1 * tile_out);
+        CK(cg::launch_emit2(emit_graph(g), g->s, c->tune, g->stage_bases, g->stage_bases_cap, c->env, t0, t1),
+           "2-bit emission kernel");
+        CK(cudaEventRecord(c->copy_ev, c->stream), "chunk event");
+        CK(cudaStreamWaitEvent(c->copy_stream, c->copy_ev, 0), "copy stream wait");
+        CK(cudaMemcpyAsync(packed_out + b0, g->stage_bases + b0, (size_t)(b1 - b0), cudaMemcpyDeviceToHost,
+                           c->copy_stream), "copy packed");
+      }
+      CK(cudaEventRecord(c->copy_ev, c->copy_stream), "copies done");
+      CK(cudaStreamWaitEvent(c->stream, c->copy_ev, 0), "stream waits for the copies");
+    } else if (packed_out && need > 0) {
       if (direct) {
         st = emit(direct, packed_cap);
         if (st != CG_OK) return st;

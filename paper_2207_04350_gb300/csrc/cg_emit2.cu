@@ -122,7 +122,8 @@ constexpr int kU = 2;              // chunks per lane in flight
 
 __global__ void __launch_bounds__(kBlock) k_emit2(Scratch s, const uint8_t* packed, long long packed_bytes,
                                                   long long readable_words, bool aligned16, uint4* out,
-                                                  long long cap_bytes, int tile_bases) {
+                                                  long long cap_bytes, int tile_bases, long long t_begin,
+                                                  long long t_end) {
   __shared__ long long s_oj[kWarps][32], s_w[kWarps][32], s_a[kWarps][32], s_b[kWarps][32];
   __shared__ int s_start[kWarps][32];
   const Counters* c = s.ctr;
@@ -138,7 +139,8 @@ __global__ void __launch_bounds__(kBlock) k_emit2(Scratch s, const uint8_t* pack
   const uint32_t* words = reinterpret_cast<const uint32_t*>(packed);
   uint32_t* out_words = reinterpret_cast<uint32_t*>(out);
   const long long full_words = packed_bytes >> 2;
-  for (long long t = grid_tid() >> 5; t < ntiles; t += grid_threads() >> 5) {
+  const long long t_stop = min(ntiles, t_end);          // the tiles [t_begin, t_end) of this launch
+  for (long long t = t_begin + (grid_tid() >> 5); t < t_stop; t += grid_threads() >> 5) {
     const int lo = s.tile_seg[t], hi = s.tile_seg[t + 1];
     const long long tbase = t * (long long)tile_bases;
     const long long tend = min(tbase + (long long)tile_bases, total);
@@ -226,7 +228,7 @@ __global__ void __launch_bounds__(kBlock) k_emit2(Scratch s, const uint8_t* pack
 }  // namespace
 
 cudaError_t launch_emit2(const DevGraph& g, const Scratch& s, const Tuning& t, uint8_t* out, int64_t cap,
-                         const LaunchEnv& env) {
+                         const LaunchEnv& env, long long t_begin, long long t_end) {
   static int resident = 0;
   if (resident == 0) {
     int r = 0;
@@ -237,7 +239,7 @@ cudaError_t launch_emit2(const DevGraph& g, const Scratch& s, const Tuning& t, u
   const bool aligned16 = (reinterpret_cast<uintptr_t>(g.packed) & 15) == 0;
   k_emit2<<<env.num_sms * per_sm, kBlock, 0, env.stream>>>(s, g.packed, g.packed_bytes, g.packed_readable / 4,
                                                            aligned16, reinterpret_cast<uint4*>(out), cap,
-                                                           t.tile_bytes);
+                                                           t.tile_bytes, t_begin, t_end);
   mark(env, "k_emit2");
   return cudaGetLastError();
 }

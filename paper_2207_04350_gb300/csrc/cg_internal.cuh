@@ -174,8 +174,9 @@ cudaError_t launch_emit(const DevGraph& g, const Scratch& s, const Tuning& t, ui
 cudaError_t launch_export_reads(const DevGraph& g, const Scratch& s, int32_t* cid, int32_t* rank, uint8_t* orient,
                                 const LaunchEnv& env);
 // 2-bit spelling: cap = bytes of `out`, which must hold 16 * ceil(total / 64).
+// The 2-bit form of the tiles [t_begin, t_end) (tiles of tile_bytes bases; all by default).
 cudaError_t launch_emit2(const DevGraph& g, const Scratch& s, const Tuning& t, uint8_t* out, int64_t cap,
-                         const LaunchEnv& env);
+                         const LaunchEnv& env, long long t_begin = 0, long long t_end = 1ll << 62);
 cudaError_t launch_export_contig_off(const Scratch& s, int64_t* out, int64_t cap, const LaunchEnv& env);
 cudaError_t launch_sum_len(const DevGraph& g, unsigned long long* out, const LaunchEnv& env);
 cudaError_t launch_batch_fixup(int k, const int64_t* R, const int64_t* E, const int64_t* PB, const int64_t* SR,
