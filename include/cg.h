@@ -265,10 +265,12 @@ CG_API cg_status cg_get_tuning(cg_ctx* ctx, cg_tuning* out);
  * one. Outputs are the same either way. */
 CG_API cg_status cg_set_graphs(cg_ctx* ctx, int enable);
 
-/* Host outputs in pinned host memory are written in place by the kernels
- * over the host link (the default, enable = 1); with 0 they are written to
- * device memory and copied. Other host memory is always staged and copied.
- * Outputs are the same either way. */
+/* Host outputs of 64 MB or more are spelled into device memory in chunks of
+ * 128 MB, each copied to the host while the next one is spelled. Smaller
+ * ones in pinned host memory are written in place by the kernels over the
+ * host link (the default, enable = 1); with 0 they are written to device
+ * memory and copied. Other host memory is always staged and copied. Outputs
+ * are the same either way. */
 CG_API cg_status cg_set_host_direct(cg_ctx* ctx, int enable);
 
 /* Host-side fault injection, for tests of the error paths that fault no GPU.
