@@ -475,6 +475,11 @@ def pin_lpt(orc):
     assert _opt_makespan(sizes, P) == int(g["optimum"][0])
     for b in range(P):
         assert loads[b] == sum(s for s, a in zip(sizes, assign) if a == b)
+    # the tie rules, on a hand-worked example: equal sizes in input order, ties to the lowest part
+    t = {k[0]: k[1:] for k in golden("lpt_ties.txt")}
+    assign, loads = orc.lpt([int(x) for x in t["sizes"]], int(t["P"][0]))
+    assert [int(a) for a in assign] == [int(x) for x in t["assign"]]
+    assert [int(x) for x in loads] == [int(x) for x in t["loads"]]
     rnd = random.Random(5)
     for _ in range(60):
         P = rnd.randint(1, 4)

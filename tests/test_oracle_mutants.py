@@ -41,6 +41,8 @@ MUTANTS = [
     ("validate_allows_full_suffix", "suf[x] > len[v] - 1", "suf[x] > len[v]"),
     ("lpt_most_loaded", "if (loads[b] < loads[best]) best = b;", "if (loads[b] > loads[best]) best = b;"),
     ("lpt_ascending", "while (j > 0 && sizes[order[j - 1]] < sizes[t])", "while (j > 0 && sizes[order[j - 1]] > sizes[t])"),
+    ("lpt_unstable_order", "while (j > 0 && sizes[order[j - 1]] < sizes[t])", "while (j > 0 && sizes[order[j - 1]] <= sizes[t])"),
+    ("lpt_tie_to_last_part", "if (loads[b] < loads[best]) best = b;", "if (loads[b] <= loads[best]) best = b;"),
     ("uf_ignores_mask", "int64_t v = col[x];\n      if (is_branch[v]) continue;\n      int64_t a = uf_find",
      "int64_t v = col[x];\n      int64_t a = uf_find"),
     ("contigs_in_root_order", "r->chain_id[s->read] = (int32_t)c;", "r->chain_id[s->read] = (int32_t)root;"),
