@@ -526,7 +526,18 @@ def pin_validation(orc):
     assert not orc.validate(dup)[0]
     nomirror = graph_from(G.reads, [(0, 1, 1, 4), (1, 0, 2, 2), (1, 2, 1, 2)])
     assert not orc.validate(nomirror)[0]
+    # a read overlapping itself and nothing else wrong: code 3 is its own mirror (its two
+    # end bits swapped), the suffix is in range, no pair repeats
+    selfloop = graph_from([l0], [(0, 0, 3, 2)])
+    assert not orc.validate(selfloop)[0]
     H = variant(row_ptr=lambda r: r.__setitem__(1, 5))             # row_ptr not monotone
+    assert not orc.validate(H)[0]
+    # the packed stream's end: a read whose last base is the stream's last base is
+    # in bounds, one base further is not
+    end = len(G.packed) * 4
+    H = variant(off=lambda o: o.__setitem__(2, end - int(G.len[2])))
+    assert orc.validate(H)[0]
+    H = variant(off=lambda o: o.__setitem__(2, end - int(G.len[2]) + 1))
     assert not orc.validate(H)[0]
 
 

@@ -175,6 +175,14 @@ def test_invalid_graphs_rejected(ctx):
         bad.append(H)
     bad.append(_pins.graph_from(G.reads, [(0, 1, 1, 4), (0, 1, 1, 3), (1, 0, 2, 2), (1, 2, 1, 2), (2, 1, 2, 5)]))
     bad.append(_pins.graph_from(G.reads, [(0, 1, 1, 4), (1, 0, 2, 2), (1, 2, 1, 2)]))
+    bad.append(_pins.graph_from(G.reads[:1], [(0, 0, 3, 2)]))   # a self overlap, nothing else wrong
+    # the last read one base past the packed stream's end
+    end = len(G.packed) * 4
+    H = _pins.graph_from(G.reads, [])
+    for k in ("row_ptr", "col", "code", "suf", "len", "off", "packed"):
+        setattr(H, k, getattr(G, k).copy())
+    H.off[2] = end - int(G.len[2]) + 1
+    bad.append(H)
     for H in bad:
         assert not oracle.validate(H)[0]
         with pytest.raises(cg.CgError) as e:
@@ -182,6 +190,10 @@ def test_invalid_graphs_rejected(ctx):
         assert e.value.status == cg.CG_EGRAPH
     # the context is still usable afterwards
     check(ctx, G, 2)
+    # a read that ends on the stream's last base is in bounds, on both sides
+    H.off[2] = end - int(G.len[2])
+    assert oracle.validate(H)[0]
+    check(ctx, H, 2)
 
 
 def test_small_capacity_rejected(ctx):

@@ -35,6 +35,12 @@ MUTANTS = [
     ("larger_root_first", "          o_root = 0;\n        }\n        break;", "          o_root = 0;\n        }\n        continue;"),
     ("cycle_starts_reverse", "if (root < 0) { root = c; o_root = 0; cycle = 1; }", "if (root < 0) { root = c; o_root = 1; cycle = 1; }"),
     ("no_min_chain_filter", "if (q < min_chain_reads) continue;", "if (0) continue;"),
+    ("min_chain_off_by_one", "if (q < min_chain_reads) continue;", "if (q <= min_chain_reads) continue;"),
+    ("lone_read_reverse", "        } else {\n          o_root = 0;\n        }", "        } else {\n          o_root = 1;\n        }"),
+    ("validate_allows_self_overlap", 'if (v == u) BAD("entry %lld: self overlap", (long long)x);', 'if (0) BAD("entry %lld: self overlap", (long long)x);'),
+    ("validate_stream_end_off_by_one", "off[v] + len[v] > packed_bytes * 4", "off[v] + len[v] > packed_bytes * 4 + 1"),
+    ("validate_xdrop_full_post", "post[x] > len[v] - 1", "post[x] > len[v]"),
+    ("validate_xdrop_negative_pre", "if (pre[x] < 0 ||", "if (pre[x] < -1 ||"),
     ("ascii_table_swapped", "{'A', 'C', 'G', 'T'}", "{'A', 'G', 'C', 'T'}"),
     ("packed_bit_order", "return (packed[q >> 2] >> (2 * (q & 3))) & 3;", "return (packed[q >> 2] >> (6 - 2 * (q & 3))) & 3;"),
     ("validate_skips_mirror_code", "if (code[y] != swapped) BAD", "if (0) BAD"),
