@@ -265,6 +265,15 @@ CG_API cg_status cg_get_tuning(cg_ctx* ctx, cg_tuning* out);
  * one. Outputs are the same either way. */
 CG_API cg_status cg_set_graphs(cg_ctx* ctx, int enable);
 
+/* Programmatic dependent launch (on by default): a kernel that directly follows
+ * another kernel of the same stage on the stream is launched with the
+ * programmatic stream-serialization attribute, so it is launched once the
+ * blocks of the kernel before it have exited; each of its blocks waits for
+ * that kernel to complete before it touches memory. Off: plain stream order. Kernels
+ * separated by a timing event, a copy or a memset are always launched in plain
+ * order. Outputs are the same either way. */
+CG_API cg_status cg_set_pdl(cg_ctx* ctx, int enable);
+
 /* Host outputs of 64 MB or more are spelled into device memory in chunks of
  * 128 MB, each copied to the host while the next one is spelled. Smaller
  * ones in pinned host memory are written in place by the kernels over the

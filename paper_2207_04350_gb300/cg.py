@@ -79,6 +79,7 @@ API = {
     "cg_sync": [ctypes.c_void_p],
     "cg_set_timing": [ctypes.c_void_p, ctypes.c_int],
     "cg_set_graphs": [ctypes.c_void_p, ctypes.c_int],
+    "cg_set_pdl": [ctypes.c_void_p, ctypes.c_int],
     "cg_set_host_direct": [ctypes.c_void_p, ctypes.c_int],
     "cg_set_fault": [ctypes.c_void_p, ctypes.c_char_p],
     "cg_set_tuning": [ctypes.c_void_p, ctypes.c_void_p],
@@ -410,6 +411,11 @@ def cg_set_host_direct(ctx: Context, enable: bool):
 
 def cg_set_graphs(ctx: Context, enable: bool):
     _check(ctx.ptr, lib().cg_set_graphs(ctx.ptr, 1 if enable else 0))
+
+
+def cg_set_pdl(ctx: Context, enable: bool):
+    """Programmatic dependent launch between consecutive kernels of a stage (on by default)."""
+    _check(ctx.ptr, lib().cg_set_pdl(ctx.ptr, 1 if enable else 0))
 
 
 def cg_set_timing(ctx: Context, level):

@@ -217,6 +217,7 @@ cg_status run_stage(cg_graph* g, int slot, uint64_t key, F&& launch) {
   if (!c->graphs) return launch();
   StageExec& e = g->execs[slot];
   key = mix_key(key, c->marks.on ? 1 : 2);
+  key = mix_key(key, c->env.pdl ? 3 : 4);
   if (e.exec && e.key == key) {
     c->launches += e.kernels;
     if (c->marks.on) c->marks.n = e.mark_end;
@@ -469,6 +470,8 @@ cg_status cg_create(cg_ctx** out, int device, uint64_t hbm_budget_bytes, void* c
   c->env.stream = c->stream;
   c->env.num_sms = sms > 0 ? sms : 1;
   c->env.coop_blocks = cg::coop_blocks_for_grid_kernels(c->env.num_sms);
+  c->env.pdl = true;
+  c->env.pdl_first = false;
   {
     cudaMemPoolProps props = {};
     props.allocType = cudaMemAllocationTypePinned;
@@ -558,6 +561,13 @@ cg_status cg_set_graphs(cg_ctx* c, int enable) {
   cg_status st = check_ctx(c);
   if (st != CG_OK) return st;
   c->graphs = enable != 0;
+  return CG_OK;
+}
+
+cg_status cg_set_pdl(cg_ctx* c, int enable) {
+  cg_status st = check_ctx(c);
+  if (st != CG_OK) return st;
+  c->env.pdl = enable != 0;
   return CG_OK;
 }
 
@@ -968,9 +978,11 @@ cg_status cg_emit_contigs(cg_graph* g, int64_t* contig_off, int64_t contig_off_c
       CK(cg::launch_offsets(g->g, g->s, c->tune, c->env), "offset kernels");
       if (stages) record_stage_event(c, 5);
       if (timing) record_stage_event(c, 6);
-      CK(cg::launch_emit(g->g, g->s, c->tune, bases, bases_cap, c->env), "emission kernel");
+      cg::LaunchEnv env = c->env;
+      env.pdl_first = !timing;           // no event node between these kernels and the ones before
+      CK(cg::launch_emit(g->g, g->s, c->tune, bases, bases_cap, env), "emission kernel");
       if (timing) record_stage_event(c, 7);
-      if (contig_off) CK(cg::launch_export_contig_off(g->s, contig_off, contig_off_cap, c->env), "export contig_off");
+      if (contig_off) CK(cg::launch_export_contig_off(g->s, contig_off, contig_off_cap, env), "export contig_off");
       return CG_OK;
     });
     if (st != CG_OK) return st;

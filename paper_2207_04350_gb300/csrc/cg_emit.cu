@@ -76,6 +76,7 @@ __global__ void __launch_bounds__(kBlock) k_emit(Scratch s, const uint8_t* packe
     lut[0][i] = f;
     lut[1][i] = r;
   }
+  pdl_enter();                 // the table needs nothing from the kernels before
   __syncthreads();
   const Counters* c = s.ctr;
   const long long total = *(const volatile long long*)&c->total_bases;
@@ -176,8 +177,9 @@ cudaError_t launch_emit(const DevGraph& g, const Scratch& s, const Tuning& t, ui
   }
   int per_sm = t.emit_blocks_per_sm < resident ? t.emit_blocks_per_sm : resident;
   int blocks = env.num_sms * per_sm;
-  k_emit<4><<<blocks, kBlock, 0, env.stream>>>(s, g.packed, g.packed_bytes, g.packed_readable / 4, out, cap,
-                                               t.tile_bytes, t_begin, t_end);
+  cudaError_t e = launch_k(k_emit<4>, blocks, env, env.pdl_first, s, g.packed, (long long)g.packed_bytes,
+                           (long long)(g.packed_readable / 4), out, (long long)cap, t.tile_bytes, t_begin, t_end);
+  if (e != cudaSuccess) return e;
   mark(env, "k_emit");
   return cudaGetLastError();
 }

@@ -124,6 +124,7 @@ __global__ void __launch_bounds__(kBlock) k_emit2(Scratch s, const uint8_t* pack
                                                   long long readable_words, bool aligned16, uint4* out,
                                                   long long cap_bytes, int tile_bases, long long t_begin,
                                                   long long t_end) {
+  pdl_enter();
   __shared__ long long s_oj[kWarps][32], s_w[kWarps][32], s_a[kWarps][32], s_b[kWarps][32];
   __shared__ int s_start[kWarps][32];
   const Counters* c = s.ctr;
@@ -237,9 +238,10 @@ cudaError_t launch_emit2(const DevGraph& g, const Scratch& s, const Tuning& t, u
   }
   const int per_sm = t.emit_blocks_per_sm < resident ? t.emit_blocks_per_sm : resident;
   const bool aligned16 = (reinterpret_cast<uintptr_t>(g.packed) & 15) == 0;
-  k_emit2<<<env.num_sms * per_sm, kBlock, 0, env.stream>>>(s, g.packed, g.packed_bytes, g.packed_readable / 4,
-                                                           aligned16, reinterpret_cast<uint4*>(out), cap,
-                                                           t.tile_bytes, t_begin, t_end);
+  cudaError_t e = launch_k(k_emit2, env.num_sms * per_sm, env, env.pdl_first, s, g.packed,
+                           (long long)g.packed_bytes, (long long)(g.packed_readable / 4), aligned16,
+                           reinterpret_cast<uint4*>(out), (long long)cap, t.tile_bytes, t_begin, t_end);
+  if (e != cudaSuccess) return e;
   mark(env, "k_emit2");
   return cudaGetLastError();
 }

@@ -216,6 +216,7 @@ __device__ __forceinline__ void flush_cands(const Scratch& s, const int32_t* buf
 
 template <typename RP, bool kAligned>
 __global__ void __launch_bounds__(kBlock) k_mask(DevGraph g, Scratch s) {
+  pdl_enter();
   __shared__ int64_t q_row[kMaskWarps][kMaskSpan];   // queued reads: row start
   __shared__ uint16_t q_pos[kMaskWarps][kMaskSpan];  //   and position in the pass | (degree == 2) << 8
   __shared__ int32_t b_cand[kMaskWarps][kMaskBuf];   // buffered list entries
@@ -400,6 +401,7 @@ __device__ __forceinline__ void put_starts(const Scratch& s, const uint32_t* buf
 }
 
 __global__ void __launch_bounds__(kBlock) k_succ(DevGraph g, Scratch s, int ruler_log2) {
+  pdl_enter();
   __shared__ uint32_t b_start[kSuccWarps][kSuccStarts];
   __shared__ unsigned blk_n[2], blk_base[2];
   Counters* c = s.ctr;
@@ -499,6 +501,7 @@ __global__ void __launch_bounds__(kBlock) k_succ(DevGraph g, Scratch s, int rule
 // sublist's record keeps read ids: its smallest read and its last oriented
 // read as 2v + o.
 __global__ void k_walk(Scratch s, int ruler_log2, int64_t limit) {
+  pdl_enter();
   Counters* c = s.ctr;
   const long long R = *(volatile unsigned*)&c->n_rulers;
   for (long long r = grid_tid(); r < R; r += grid_threads()) {
@@ -528,6 +531,7 @@ __global__ void k_walk(Scratch s, int ruler_log2, int64_t limit) {
 // the tail and the smallest read, then again to give each sublist its
 // distance to the tail. Longer lists are left to pointer jumping.
 __global__ void k_listwalk(Scratch s) {
+  pdl_enter();
   Counters* c = s.ctr;
   const long long H = *(volatile unsigned*)&c->n_hlist;
   for (long long h = grid_tid(); h < H; h += grid_threads()) {
@@ -568,6 +572,7 @@ __global__ void k_listwalk(Scratch s) {
 // read id over that span, tail = the list's last oriented read. Sublists on
 // directed cycles keep next >= 0.
 __global__ void k_jump(Scratch s) {
+  pdl_enter();
   Counters* c = s.ctr;
   if (*(volatile unsigned*)&c->need_jump == 0) return;   // the same for every block: written by the kernel before
   unsigned R = *(volatile unsigned*)&c->n_rulers;
@@ -642,6 +647,7 @@ __device__ __forceinline__ int32_t piece_len(const DevGraph& g, const Scratch& s
 constexpr int kFinalItems = 2;
 
 __global__ void k_final(DevGraph g, Scratch s) {
+  pdl_enter();
   Counters* c = s.ctr;
   const int fb = (int)*(volatile unsigned*)&c->final_buf;
   const long long N = *(volatile unsigned*)&c->n_cand;
@@ -730,6 +736,7 @@ __global__ void k_final(DevGraph g, Scratch s) {
 // smallest read), then cut the walk before (m,0) and rank by pointer jumping
 // again.
 __global__ void k_cycles(DevGraph g, Scratch s) {
+  pdl_enter();
   Counters* c = s.ctr;
   unsigned C = *(volatile unsigned*)&c->n_cycle_reads;
   if (C == 0) return;
@@ -816,6 +823,7 @@ __global__ void k_cycles(DevGraph g, Scratch s) {
 // Per-read chain outputs: first every read's default (a lone read, when
 // spelled, is its own one-read contig), then every candidate's record.
 __global__ void k_export_fill(DevGraph g, int32_t* cid, int32_t* rank, uint8_t* orient) {
+  pdl_enter();
   for (long long v = grid_tid(); v < g.n; v += grid_threads()) {
     const bool lone = rowp(g, v + 1) == rowp(g, v) && g.min_chain <= 1;
     if (cid) cid[v] = lone ? (int32_t)v : -1;
@@ -825,6 +833,7 @@ __global__ void k_export_fill(DevGraph g, int32_t* cid, int32_t* rank, uint8_t* 
 }
 
 __global__ void k_export_cands(Scratch s, int32_t* cid, int32_t* rank, uint8_t* orient) {
+  pdl_enter();
   const long long N = *(volatile unsigned*)&s.ctr->n_cand;
   for (long long ci = grid_tid(); ci < N; ci += grid_threads()) {
     const int32_t v = s.cand[ci];
@@ -906,17 +915,20 @@ cudaError_t launch_chains(const DevGraph& g, const Scratch& s, const Tuning& t, 
   static const int final_resident = resident_blocks(k_final);
   k_succ<<<env.num_sms * succ_resident, kBlock, 0, env.stream>>>(g, s, t.ruler_log2);
   mark(env, "k_succ");
-  k_walk<<<grid_for(2 * g.n, env), kBlock, 0, env.stream>>>(s, t.ruler_log2, 2 * g.n + 1);
+  cudaError_t e = launch_k(k_walk, grid_for(2 * g.n, env), env, true, s, t.ruler_log2, (int64_t)(2 * g.n + 1));
+  if (e != cudaSuccess) return e;
   mark(env, "k_walk");
-  k_listwalk<<<grid_for(2 * g.n, env), kBlock, 0, env.stream>>>(s);
+  e = launch_k(k_listwalk, grid_for(2 * g.n, env), env, true, s);
+  if (e != cudaSuccess) return e;
   mark(env, "k_listwalk");
   Scratch sc = s;
   void* args[] = {&sc};
-  cudaError_t e = coop((const void*)k_jump, env.coop_blocks, args, env);
+  e = coop((const void*)k_jump, env.coop_blocks, args, env);
   if (e != cudaSuccess) return e;
   mark(env, "k_jump");
   DevGraph gg = g;
-  k_final<<<env.num_sms * final_resident, kBlock, 0, env.stream>>>(gg, s);
+  e = launch_k(k_final, env.num_sms * final_resident, env, true, gg, s);
+  if (e != cudaSuccess) return e;
   mark(env, "k_final");
   void* args2[] = {&gg, &sc};
   e = coop((const void*)k_cycles, env.coop_blocks, args2, env);
@@ -929,7 +941,8 @@ cudaError_t launch_export_reads(const DevGraph& g, const Scratch& s, int32_t* ci
                                 const LaunchEnv& env) {
   k_export_fill<<<grid_for(g.n, env), kBlock, 0, env.stream>>>(g, cid, rank, orient);
   mark(env, "k_export_fill");
-  k_export_cands<<<grid_for(g.n, env), kBlock, 0, env.stream>>>(s, cid, rank, orient);
+  cudaError_t e = launch_k(k_export_cands, grid_for(g.n, env), env, true, s, cid, rank, orient);
+  if (e != cudaSuccess) return e;
   mark(env, "k_export_cands");
   return cudaGetLastError();
 }

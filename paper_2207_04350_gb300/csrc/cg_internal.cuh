@@ -144,6 +144,8 @@ struct LaunchEnv {
   int coop_blocks;         // co-resident blocks for the grid-synchronised kernels
   unsigned long long* launches;  // host counter of kernel launches
   KernelMarks* marks;
+  bool pdl;                // programmatic dependent launch between consecutive kernels
+  bool pdl_first;          // the first kernel of a launch_* call directly follows a kernel
 };
 
 // Counts the kernel just launched and, with timing on, records an event after it.
@@ -237,6 +239,18 @@ __device__ __forceinline__ void set_error(DevError* e, int code, int where, long
   }
 }
 
+// Programmatic dependent launch (sm_90 and later): wait until the grid before this
+// one on the stream has completed and its writes are visible. Every kernel of the
+// path calls it before it touches global memory, so each kernel also completes
+// after every kernel before it. No kernel signals its dependents early
+// (griddepcontrol.launch_dependents): the next grid is launched once every block
+// of this one has exited, ahead of the grid's completion. Signalling at kernel entry, which parks the next grid's blocks on the SMs
+// while this one runs, made the 3.1 Gb step 14 us slower. For a kernel launched
+// without the attribute the wait returns at once.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 __device__ __forceinline__ long long grid_tid() { return (long long)blockIdx.x * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ long long grid_threads() { return (long long)gridDim.x * blockDim.x; }
 
@@ -251,6 +265,28 @@ inline int resident_blocks(Kernel kernel) {
   int r = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, kernel, kBlock, 0);
   return r > 0 ? r : 1;
+}
+
+// Launches `kernel` with kBlock threads on env.stream. With `chained` (the stream's
+// previous operation is one of these kernels, with no event or copy between) and
+// programmatic dependent launch on, the launch carries the programmatic
+// stream-serialization attribute: it is launched once the previous grid's blocks
+// have exited rather than after the grid's completion, and each block waits in
+// pdl_enter() for that completion. Per-kernel timing events sit between every two
+// kernels, so they turn the attribute off.
+template <typename... P, typename... A>
+inline cudaError_t launch_k(void (*kernel)(P...), int grid, const LaunchEnv& env, bool chained, A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kBlock);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = env.stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = chained && env.pdl && !(env.marks && env.marks->on) ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<A&&>(args)...);
 }
 
 inline int grid_for(long long n, const LaunchEnv& env, int per_sm = 8) {

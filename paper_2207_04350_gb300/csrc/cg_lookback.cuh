@@ -91,6 +91,7 @@ __global__ void __launch_bounds__(kBlock) k_scan(Load ld, Store st, long long co
                                                  unsigned long long* state, long long ticket_index, DevError* derr,
                                                  int where, unsigned long long* clear = nullptr,
                                                  long long clear_words = 0) {
+  pdl_enter();
   __shared__ unsigned long long sm[kTileItems];
   __shared__ unsigned long long warp_tot[kBlock / 32];
   __shared__ long long s_tile;

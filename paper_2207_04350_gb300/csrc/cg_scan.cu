@@ -144,6 +144,7 @@ struct PieceStore {
 constexpr int kScatterItems = 2;
 
 __global__ void k_scatter(DevGraph g, Scratch s) {
+  pdl_enter();
   Counters* c = s.ctr;
   const long long L1 = *(volatile unsigned*)&c->n_lone, NC = *(volatile unsigned*)&c->n_cand;
   const long long W = *(volatile unsigned*)&c->n_walk;
@@ -203,6 +204,7 @@ __global__ void k_scatter(DevGraph g, Scratch s) {
 
 // An empty graph: no contigs, and the one offset 0.
 __global__ void k_contig_off(Scratch s) {
+  pdl_enter();
   if (grid_tid() == 0) {
     s.contig_off[0] = 0;
     s.ctr->n_contigs = 0;
@@ -213,6 +215,7 @@ __global__ void k_contig_off(Scratch s) {
 }
 
 __global__ void k_export_contig_off(Scratch s, int64_t* out, long long cap) {
+  pdl_enter();
   Counters* c = s.ctr;
   long long C = *(volatile unsigned*)&c->n_contigs;
   if (C + 1 > cap) {
@@ -241,22 +244,28 @@ cudaError_t launch_offsets(const DevGraph& g, const Scratch& s, const Tuning& t,
   }
   HeadWordLoad hl{s.hb, s.headq};
   HeadWordStore hs{s.wp, s.headq, s.qd, s.cbase, s.contig_off, s.ctr};
-  k_scan<<<scan_grid(tiles_w, env), kBlock, 0, env.stream>>>(hl, hs, words, nullptr, s.scan_state[0], s.scan_tiles_cap,
-                                                       s.derr, K_SCAN_HEADS, s.scan_state[2], state_words);
+  cudaError_t e = launch_k(k_scan<HeadWordLoad, HeadWordStore>, scan_grid(tiles_w, env), env, env.pdl_first, hl, hs,
+                           words, (const unsigned*)nullptr, s.scan_state[0], s.scan_tiles_cap, s.derr,
+                           (int)K_SCAN_HEADS, s.scan_state[2], state_words);
+  if (e != cudaSuccess) return e;
   mark(env, "k_scan_heads");
   static const int scatter_resident = resident_blocks(k_scatter);   // a persistent grid
-  k_scatter<<<env.num_sms * scatter_resident, kBlock, 0, env.stream>>>(g, s);
+  e = launch_k(k_scatter, env.num_sms * scatter_resident, env, true, g, s);
+  if (e != cudaSuccess) return e;
   mark(env, "k_scatter");
   PieceLoad pl{s.wlen, s.wfirst};
   PieceStore ps{s.out_off, s.contig_off, s.tile_seg, s.tiles_cap, t.tile_bytes, s.ctr, s.derr};
-  k_scan<<<scan_grid(tiles_n, env), kBlock, 0, env.stream>>>(pl, ps, 0, &s.ctr->n_walk, s.scan_state[2], s.scan_tiles_cap,
-                                                       s.derr, K_SCAN_OFFSETS, s.scan_state[0], state_words);
+  e = launch_k(k_scan<PieceLoad, PieceStore>, scan_grid(tiles_n, env), env, true, pl, ps, 0ll,
+               (const unsigned*)&s.ctr->n_walk, s.scan_state[2], s.scan_tiles_cap, s.derr, (int)K_SCAN_OFFSETS,
+               s.scan_state[0], state_words);
+  if (e != cudaSuccess) return e;
   mark(env, "k_scan_pieces");
   return cudaGetLastError();
 }
 
 cudaError_t launch_export_contig_off(const Scratch& s, int64_t* out, int64_t cap, const LaunchEnv& env) {
-  k_export_contig_off<<<env.num_sms, kBlock, 0, env.stream>>>(s, out, cap);
+  cudaError_t e = launch_k(k_export_contig_off, env.num_sms, env, env.pdl_first, s, out, (long long)cap);
+  if (e != cudaSuccess) return e;
   mark(env, "k_export_contig_off");
   return cudaGetLastError();
 }

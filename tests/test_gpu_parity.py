@@ -230,9 +230,11 @@ def test_tuning_does_not_change_output(ruler_log2, tile_bytes, bps):
         c.close()
 
 
-def test_graphs_off_and_replay_with_new_buffers():
+@pytest.mark.parametrize("pdl", [False, True])
+def test_graphs_off_and_replay_with_new_buffers(pdl):
     """Stages launched one by one give the same bytes as replayed CUDA graphs,
-    also when the output buffers change between replays."""
+    with or without programmatic dependent launch, also when the output
+    buffers change between replays."""
     import torch
     G = structured(31, [20_000, 5, 9] + [2] * 300 + [7] * 50, [False, True, True] + [False] * 350, lone=100)
     orc = oracle.run(G, min_chain_reads=1)
@@ -240,6 +242,7 @@ def test_graphs_off_and_replay_with_new_buffers():
         c = cg.cg_create(0)
         try:
             cg.cg_set_graphs(c, graphs)
+            cg.cg_set_pdl(c, pdl)
             assert_parity(run_gpu(c, G, 1), orc)
             g = cg.cg_load_graph(c, G, min_chain_reads=1)
             n_contigs, total = cg.cg_emit_contigs(g)
@@ -255,6 +258,41 @@ def test_graphs_off_and_replay_with_new_buffers():
             g.close()
         finally:
             c.close()
+
+
+@pytest.mark.parametrize("graphs,pdl,timing", [(False, True, 0), (True, False, 0), (True, True, 0), (True, True, 1),
+                                               (True, True, 2), (True, True, 3), (False, True, 2)])
+def test_launch_modes_repeat_identically(graphs, pdl, timing):
+    """Every launch mode (graphs, programmatic dependent launch, timing events
+    between kernels or around the spelling) gives the oracle's bytes, and
+    twenty back-to-back device-output runs of one graph stay identical."""
+    import torch
+    G = gen.generate("tiny-1Mb", threads=8)
+    orc = oracle.run(G)
+    c = cg.cg_create(0)
+    try:
+        cg.cg_set_graphs(c, graphs)
+        cg.cg_set_pdl(c, pdl)
+        cg.cg_set_timing(c, timing)
+        g = cg.cg_load_graph(c, G)
+        n_contigs, total = cg.cg_emit_contigs(g)
+        assert n_contigs == orc.n_contigs
+        off = torch.empty(n_contigs + 1, dtype=torch.int64, device="cuda")
+        bases = torch.empty((total + 15) // 16 * 16, dtype=torch.uint8, device="cuda")
+        outs = []
+        for rep in range(20):
+            cg.cg_mask_branches(g, want_count=False)
+            cg.cg_chains(g, want_counts=False)
+            cg.cg_emit_contigs(g, off, bases, want_counts=False)
+            if rep % 5 == 4:
+                outs.append((off.clone(), bases.clone()))
+        cg.cg_sync(c)
+        for o, b in outs:
+            assert np.array_equal(o.cpu().numpy(), orc.contig_off)
+            assert np.array_equal(b.cpu().numpy()[:total], orc.bases)
+        g.close()
+    finally:
+        c.close()
 
 
 def test_repeat_runs_are_identical(ctx):
