@@ -246,6 +246,23 @@ CG_API cg_status cg_transitive_reduction(cg_ctx* ctx, const cg_graph_desc* overl
 CG_API cg_status cg_partition_contigs(cg_graph* g, int32_t n_parts, int32_t weight, int32_t* part, int64_t part_cap,
                                int64_t* part_weight, int mem, int64_t* n_contigs);
 
+/* Spells the contigs of one part only, as each process does with the contigs
+ * assigned to it (Sec. 4.3-4.4): part[c] names the part of contig c (at least
+ * n_contigs entries, in `mem`, e.g. from cg_partition_contigs; any int32
+ * values), p the part to spell. The output holds the contigs c with
+ * part[c] == p back to back in contig order, each exactly as cg_emit_contigs
+ * spells it. contig_off (n_contigs + 1 entries) gives every contig's range in
+ * that output: [contig_off[c], contig_off[c+1]), empty for the contigs of other
+ * parts. *n_contigs is the graph's contig count, *total_bases the part's
+ * bases. Buffers, capacities, the two-call size query (NULL bases) and `mem`
+ * follow cg_emit_contigs; part may be NULL only when the graph has no contigs.
+ * Runs the earlier steps first. Not for a batch loaded with CG_HOST_READS
+ * (CG_EINVAL). A later cg_emit_contigs or cg_partition_contigs lays out the
+ * whole graph again. */
+CG_API cg_status cg_emit_part(cg_graph* g, const int32_t* part, int64_t part_cap, int32_t p, int64_t* contig_off,
+                              int64_t contig_off_cap, uint8_t* bases, int64_t bases_cap, int mem, int64_t* n_contigs,
+                              int64_t* total_bases);
+
 /* Launch parameters of a context's kernels. None changes any output. */
 typedef struct {
   int32_t ruler_log2;         /* list ranking: a read starts a sublist with probability 2^-ruler_log2, 1..12 */

@@ -69,6 +69,9 @@ API = {
                   ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
     "cg_emit_contigs": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
                         ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
+    "cg_emit_part": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
+                     ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                     ctypes.POINTER(ctypes.c_int64)],
     "cg_emit_contigs_2bit": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
                              ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
     "cg_transitive_reduction": [ctypes.c_void_p, ctypes.POINTER(GraphDesc), ctypes.c_int32, ctypes.c_void_p,
@@ -373,6 +376,37 @@ def cg_partition_contigs(g: Graph, n_parts: int, weight: int = WEIGHT_READS, par
                                                  len(part) if part is not None else 0, _ptr(part_weight), mem,
                                                  ctypes.byref(out)))
     return out.value
+
+
+def cg_emit_part(g: Graph, part, p: int, contig_off=None, bases=None, want_counts: bool = True):
+    """The contigs c with part[c] == p back to back, each spelled as cg_emit_contigs
+    spells it (Sec. 4.3-4.4); contig_off (n_contigs + 1) gets every contig's range
+    in that output, empty for the contigs of other parts. part is int32 (at least
+    n_contigs entries); part, contig_off and bases are all host or all device.
+    NULL bases: sizes only. Returns (the graph's n_contigs, the part's bases)."""
+    if part is not None:
+        dt = str(part.dtype)
+        if dt not in ("int32", "torch.int32"):
+            raise ValueError("part must be int32")
+    nc, tot = ctypes.c_int64(-1), ctypes.c_int64(-1)
+    mem = _mem_of_all([part, contig_off, bases])
+    pcap = len(part) if part is not None else 0
+    ocap = len(contig_off) if contig_off is not None else 0
+    bcap = _nbytes(bases) if bases is not None else 0
+    _check(g.ctx.ptr, lib().cg_emit_part(g.ptr, _ptr(part), pcap, int(p), _ptr(contig_off), ocap, _ptr(bases), bcap,
+                                         mem, ctypes.byref(nc) if want_counts else None,
+                                         ctypes.byref(tot) if want_counts else None))
+    return (nc.value, tot.value) if want_counts else None
+
+
+def contigs_part_host(g: Graph, part, p: int):
+    """Host copies (contig_off, bases) of part p's spelling (see cg_emit_part)."""
+    part = np.ascontiguousarray(part, dtype=np.int32)
+    nc, tot = cg_emit_part(g, part, p)
+    off = np.empty(nc + 1, dtype=np.int64)
+    bases = np.empty(max(tot, 1), dtype=np.uint8)
+    cg_emit_part(g, part, p, off, bases)
+    return off, bases[:tot]
 
 
 def cg_sync(ctx: Context):

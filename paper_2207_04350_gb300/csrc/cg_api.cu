@@ -61,6 +61,8 @@ struct cg_graph {
   uint8_t* stage_bases = nullptr; // device staging for host outputs
   int64_t stage_bases_cap = 0;
   void* stage_reads = nullptr;
+  int32_t* part_buf = nullptr;         // device copy of a host part assignment (cg_emit_part)
+  int64_t part_buf_cap = 0;
   unsigned long long* d_sum = nullptr;
   StageExec execs[7];                  // mask, chains, offsets, emission, contig_off export, 2-bit emission,
                                        // offsets + emission + export in one graph
@@ -218,6 +220,7 @@ cg_status run_stage(cg_graph* g, int slot, uint64_t key, F&& launch) {
   StageExec& e = g->execs[slot];
   key = mix_key(key, c->marks.on ? 1 : 2);
   key = mix_key(key, c->env.pdl ? 3 : 4);
+  key = mix_key(mix_key(key, (uint64_t)(uintptr_t)g->s.part), (uint64_t)(uint32_t)g->s.part_p);
   if (e.exec && e.key == key) {
     c->launches += e.kernels;
     if (c->marks.on) c->marks.n = e.mark_end;
@@ -644,6 +647,7 @@ cg_status cg_free_graph(cg_graph* g) {
   for (void* p : g->owned) dfree(c, p);
   dfree(c, g->stage_bases);
   dfree(c, g->hb_dst);
+  dfree(c, g->part_buf);
   delete g;
   return CG_OK;
 }
@@ -1105,6 +1109,45 @@ cg_status cg_emit_contigs(cg_graph* g, int64_t* contig_off, int64_t contig_off_c
   if (n_contigs) *n_contigs = (int64_t)c->h_ctr->n_contigs;
   if (total_bases) *total_bases = c->h_ctr->total_bases;
   return CG_OK;
+}
+
+cg_status cg_emit_part(cg_graph* g, const int32_t* part, int64_t part_cap, int32_t p, int64_t* contig_off,
+                       int64_t contig_off_cap, uint8_t* bases, int64_t bases_cap, int mem, int64_t* n_contigs,
+                       int64_t* total_bases) {
+  if (!g) return CG_EINVAL;
+  cg_ctx* c = g->ctx;
+  cg_status st = check_ctx(c);
+  if (st != CG_OK) return st;
+  if (mem != CG_MEM_HOST && mem != CG_MEM_DEVICE) return fail(c, CG_EINVAL, "bad mem");
+  if (g->host_batch) return fail(c, CG_EINVAL, "cg_emit_part: not for a batch with host-resident reads");
+  if (g->stage < 2) {                  // the contig count: lone reads and chain heads
+    st = run_chains(g);
+    if (st != CG_OK) return st;
+  }
+  st = wait_and_read(g);
+  if (st != CG_OK) return st;
+  const int64_t C = (int64_t)c->h_ctr->n_lone + (int64_t)c->h_ctr->n_heads;
+  if (C > 0 && (!part || part_cap < C)) return fail(c, CG_EINVAL, "part capacity %lld < %lld", (long long)part_cap,
+                                                    (long long)C);
+  const int32_t* d_part = part;
+  if (C > 0 && mem == CG_MEM_HOST) {
+    if (g->part_buf_cap < C) {
+      if (g->part_buf) dfree(c, g->part_buf);
+      g->part_buf = (int32_t*)dalloc(c, (size_t)C * 4, &st);
+      g->part_buf_cap = g->part_buf ? C : 0;
+      if (!g->part_buf) return st;
+    }
+    CK(cudaMemcpyAsync(g->part_buf, part, (size_t)C * 4, cudaMemcpyHostToDevice, c->stream), "copy part");
+    d_part = g->part_buf;
+  }
+  g->s.part = C > 0 ? d_part : nullptr;
+  g->s.part_p = C > 0 ? p : 0;
+  g->stage = 2;                        // the offsets stage runs again, on the part's layout
+  st = cg_emit_contigs(g, contig_off, contig_off_cap, bases, bases_cap, mem, n_contigs, total_bases);
+  g->s.part = nullptr;
+  g->s.part_p = 0;
+  g->stage = 2;                        // the layout on the device is the part's: a later call redoes it
+  return st;
 }
 
 cg_status cg_emit_contigs_2bit(cg_graph* g, int64_t* contig_off, int64_t contig_off_cap, uint8_t* packed_out,

@@ -115,6 +115,10 @@ struct Scratch {
   int64_t* contig_off;  // n+1
   int32_t* tile_seg;    // tiles_cap+1: walk position holding the first byte of each emission tile
   int64_t tiles_cap;
+  // one part's layout (Sec. 4.3): when part is set, the reads of a contig c with
+  // part[c] != part_p add no bases, so the layout holds that part's contigs only
+  const int32_t* part;  // n_contigs, or nullptr for the whole layout
+  int32_t part_p;
   unsigned long long* scan_state[3];  // look-back tile descriptors (+1 ticket word) of the three scans
   int64_t scan_tiles_cap;
   Counters* ctr;

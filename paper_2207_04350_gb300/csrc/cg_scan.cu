@@ -134,7 +134,8 @@ struct PieceStore {
 };
 
 // Every spelled read goes to walk position first(contig) + rank, with the
-// stored-base address of its piece: forward reads add stored bases
+// stored-base address of its piece (for one part's layout, an empty piece
+// when its contig belongs to another part): forward reads add stored bases
 // [len-contrib, len), reverse-complement reads the complement of stored
 // bases contrib-1 down to 0. The spelled reads are the lone reads of the mask
 // stage (each its own contig, whole and forward) and the candidates with a
@@ -196,7 +197,7 @@ __global__ void k_scatter(DevGraph g, Scratch s) {
       const unsigned long long src = o == 0 ? (unsigned long long)(base[j] + first)
                                             : ((unsigned long long)(base[j] + first) | (1ull << 63));
       s.wsrc[pos[j]] = src;
-      s.wlen[pos[j]] = cb;
+      s.wlen[pos[j]] = s.part && s.part[cidx[j]] != s.part_p ? 0 : cb;   // another part's contig: empty
       s.wfirst[pos[j]] = rk == 0 ? (int32_t)cidx[j] : -1;
     }
   }
