@@ -34,7 +34,7 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 # DRAM bytes (read + write) per contig base of k_emit from one ncu capture
 # (--set full, the 3.1 Gb recipe on a 450 Mb genome: 551.5 MB for 481,446,585
 # bases), valid only for the emission source it was taken on.
-EMIT_TRAFFIC = {"bytes_per_base": (129.624064e6 + 422.158336e6) / 481446585, "source_sha256_16": "08fafa686c29d54d"}
+EMIT_TRAFFIC = {"bytes_per_base": (129.657344e6 + 422.573824e6) / 481446585, "source_sha256_16": "f900c359479bfcf8"}
 
 
 def _reduce(x: float, world: int, op: str) -> float:
@@ -746,6 +746,29 @@ def run_ours(args, rank, world, local_rank):
             "kernel_ms": statistics.mean(kms[1:]), "call_ms": statistics.mean(wall[1:]),
             "max_over_mean_part": float(psum.max() / max(psum.mean(), 1e-9))}
     cg.cg_set_timing(ctx, 1)
+    # one part's spelling (Sec. 4.3-4.4), the per-GPU work of a sharded run after
+    # the chain stage it shares: an 8-way LPT split by bases, each part laid out
+    # and spelled alone into the device buffers; GPU time of the offsets and
+    # spelling stages from the stage events inside the replayed graph
+    n_split = 8
+    part_h, part_w = cg.cg_partition_contigs(g, n_split, cg.WEIGHT_BASES)
+    d_part = torch.from_numpy(np.ascontiguousarray(part_h)).cuda()
+    part_ms = []
+    for p in range(n_split):
+        ts = []
+        for r in range(5):
+            with torch.cuda.stream(stream):
+                flush.fill_(9)
+            cg.cg_emit_part(g, d_part, p, contig_off, bases, want_counts=False)
+            sm = cg.cg_get_stats(ctx)["stage_ms"]
+            if r >= 2:
+                ts.append(sm[2] + sm[3])
+        part_ms.append(statistics.median(ts))
+    parts = {"n_parts": n_split, "weight": "bases (cg_partition_contigs)", "part_bases": [int(x) for x in part_w],
+             "offsets_plus_emit_ms": part_ms, "max_part_ms": max(part_ms),
+             "whole_offsets_plus_emit_ms": statistics.mean(s[2] + s[3] for s in stage),
+             "note": "cg_emit_part per part after the shared chain stage, device outputs, L2 flushed before each "
+                     "call; median of 3 after 2 warm-up calls per part; one GPU, not a multi-GPU run"}
     if world > 1:
         torch.distributed.barrier()
     time.sleep(0.2)
@@ -851,6 +874,7 @@ def run_ours(args, rank, world, local_rank):
             "kernel_ms_note": "3 extra untimed steps with a CUDA event after every kernel",
             "step_ms_median": statistics.median(step_ms), "step_ms_min": min(step_ms), "step_ms_max": max(step_ms),
             "partition": partition,
+            "parts": parts,
             "emit_2bit": emit_2bit,
             "xdrop": xdrop,
             "autotune": tuned,

@@ -63,7 +63,7 @@ __device__ __forceinline__ uint8_t base_at(const uint8_t* packed, unsigned long 
 // one funnel shift and four lookups in a shared table that maps a byte (four
 // bases) to four ASCII characters, forward or reverse-complemented.
 template <int U>
-__global__ void __launch_bounds__(kBlock) k_emit(Scratch s, const uint8_t* packed, long long packed_bytes,
+__global__ void __launch_bounds__(kBlock, 4) k_emit(Scratch s, const uint8_t* packed, long long packed_bytes,
                                                  long long readable_words, uint8_t* out, long long cap,
                                                  int tile_bytes, long long t_begin, long long t_end) {
   __shared__ uint32_t lut[2][256];
@@ -96,8 +96,32 @@ __global__ void __launch_bounds__(kBlock) k_emit(Scratch s, const uint8_t* packe
     const long long tbase = t * (long long)tile_bytes;
     const long long tend = min(tbase + (long long)tile_bytes, total);
     for (int jb = lo; jb <= hi; jb += 32) {
-      const int jl = jb + lane;
-      const long long my_o = jl <= hi ? oo[jl] : 0, my_e = jl <= hi ? oo[jl + 1] : 0;
+      int jl = jb + lane;
+      long long my_o = jl <= hi ? oo[jl] : 0, my_e = jl <= hi ? oo[jl + 1] : 0;
+      if (jb + 31 <= hi && __all_sync(0xffffffffu, my_e == my_o)) {
+        // 32 empty pieces in a row (another part's contigs, in one part's
+        // layout): they all end at one offset X, and the next piece with bytes
+        // is the first j >= jb + 32 with out_off[j+1] > X (offsets never
+        // decrease), found by a 32-way search instead of stepping over the run
+        const long long X = my_o;
+        int L = jb + 32, R = hi + 1;                // the answer is in [L, R]; R = hi + 1: none
+        while (R - L > 32) {
+          const int step = (R - L + 31) / 32;
+          const int pj = min(L + lane * step, R - 1);
+          const unsigned hit = __ballot_sync(0xffffffffu, oo[pj + 1] > X);
+          if (!hit) {
+            L = __shfl_sync(0xffffffffu, pj, 31) + 1;
+          } else {
+            const int f = __ffs(hit) - 1;
+            const int prev = __shfl_sync(0xffffffffu, pj, f > 0 ? f - 1 : 0);
+            R = __shfl_sync(0xffffffffu, pj, f);
+            if (f > 0) L = prev + 1;
+          }
+        }
+        const unsigned hit = __ballot_sync(0xffffffffu, L + lane < R && oo[L + lane + 1] > X);
+        jb = (hit ? L + __ffs(hit) - 1 : R) - 32;     // the loop step adds the 32 back
+        continue;
+      }
       const long long my_w = jl <= hi ? (long long)ws[jl] : 0;
       const int cnt = min(32, hi - jb + 1);
       for (int q = 0; q < cnt; ++q) {

@@ -94,6 +94,32 @@ def test_arbitrary_part_values(ctx):
         g.close()
 
 
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_runs_of_other_parts(ctx, seed):
+    """Another part's contigs between two of this part's are a run of empty
+    pieces that the spelling skips by a search over the offsets: runs of 31,
+    32, 33, 64 and thousands of pieces, inside one output tile and across
+    tiles, with alternating and random assignments."""
+    sizes = [31, 32, 33, 64, 1, 2, 31, 32, 33, 65, 3000, 5, 32, 7000, 31, 1, 33] * 3
+    G = structured(100 + seed, sizes, [False] * len(sizes), min_len=20, max_len=60, lone=17)
+    orc = oracle.run(G, min_chain_reads=1)
+    g = cg.cg_load_graph(ctx, G, min_chain_reads=1)
+    try:
+        C = orc.n_contigs
+        alt = (np.arange(C) % 2).astype(np.int32)
+        for p in (0, 1):
+            check_part(g, orc, alt, p)
+        rnd = np.random.default_rng(seed).integers(0, 3, size=C).astype(np.int32)
+        for p in (0, 1, 2):
+            check_part(g, orc, rnd, p)
+        one = np.zeros(C, np.int32)
+        one[C // 2] = 1                     # a single contig in the middle
+        check_part(g, orc, one, 1)
+        check_part(g, orc, one, 0)
+    finally:
+        g.close()
+
+
 def test_device_buffers_and_replay(ctx):
     """Device part array and outputs (the replayed CUDA graph of the spelling),
     parts taken in turn and repeated, then the whole output again."""
