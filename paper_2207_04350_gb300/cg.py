@@ -174,7 +174,7 @@ class Context:
             self.ptr = None
 
     def __del__(self):
-        if sys.is_finalizing():       # the process is exiting: the driver releases everything
+        if sys.is_finalizing():       # the process is exiting: the CUDA driver releases everything
             return
         try:
             self.close()
@@ -195,7 +195,7 @@ class Graph:
             self._keep = None
 
     def __del__(self):
-        if sys.is_finalizing():       # the process is exiting: the driver releases everything
+        if sys.is_finalizing():       # the process is exiting: the CUDA driver releases everything
             return
         try:
             self.close()
