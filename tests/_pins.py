@@ -515,6 +515,7 @@ def pin_validation(orc):
         variant(suf=lambda s: s.__setitem__(0, 8)),                # suffix = whole read
         variant(code=lambda c: c.__setitem__(0, 4)),               # code out of range
         variant(off=lambda o: o.__setitem__(2, 10**6)),            # read outside the stream
+        variant(off=lambda o: o.__setitem__(0, -1)),               # read starting before the stream
         variant(len=lambda ln: ln.__setitem__(0, 0)),               # empty read
     ]
     for H in bad:
@@ -531,6 +532,10 @@ def pin_validation(orc):
     selfloop = graph_from([l0], [(0, 0, 3, 2)])
     assert not orc.validate(selfloop)[0]
     H = variant(row_ptr=lambda r: r.__setitem__(1, 5))             # row_ptr not monotone
+    assert not orc.validate(H)[0]
+    # one entry more than row_ptr[n] counts (a well-formed entry after the last row)
+    H = variant()
+    H.col, H.code, H.suf = (np.append(a, a[0]).astype(a.dtype) for a in (G.col, G.code, G.suf))
     assert not orc.validate(H)[0]
     # the packed stream's end: a read whose last base is the stream's last base is
     # in bounds, one base further is not
@@ -585,7 +590,8 @@ def xdrop_chain(reads, pp, stored1_rc: bool):
 def pin_xdrop_examples(orc):
     """Sec. 4.4, x-drop form: the paper's (pre, post) example spells
     AGAACTGAAGAA; an overlap reported one base later on one read skips that
-    base; crossing overlaps leave the middle read empty (hand-derived)."""
+    base; crossing overlaps leave the middle read empty; overlaps meeting at
+    one base of the middle read let it add exactly that base (hand-derived)."""
     for name, c in _xdrop_cases().items():
         for stored1_rc in (False, True):
             G = xdrop_chain(c["reads"], c["pp"], stored1_rc)

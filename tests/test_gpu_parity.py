@@ -167,7 +167,7 @@ def test_invalid_graphs_rejected(ctx):
     G, _ = _pins._concat_graph(False)
     bad = []
     for field, idx, val in [("code", 1, 0), ("col", 0, 7), ("col", 0, 0), ("suf", 0, 0), ("suf", 0, 8),
-                            ("code", 0, 4), ("off", 2, 10**6), ("len", 0, 0), ("row_ptr", 1, 5)]:
+                            ("code", 0, 4), ("off", 2, 10**6), ("off", 0, -1), ("len", 0, 0), ("row_ptr", 1, 5)]:
         H = _pins.graph_from(G.reads, [])
         for k in ("row_ptr", "col", "code", "suf", "len", "off", "packed"):
             setattr(H, k, getattr(G, k).copy())
@@ -176,6 +176,12 @@ def test_invalid_graphs_rejected(ctx):
     bad.append(_pins.graph_from(G.reads, [(0, 1, 1, 4), (0, 1, 1, 3), (1, 0, 2, 2), (1, 2, 1, 2), (2, 1, 2, 5)]))
     bad.append(_pins.graph_from(G.reads, [(0, 1, 1, 4), (1, 0, 2, 2), (1, 2, 1, 2)]))
     bad.append(_pins.graph_from(G.reads[:1], [(0, 0, 3, 2)]))   # a self overlap, nothing else wrong
+    # one well-formed entry more than row_ptr[n] counts
+    H = _pins.graph_from(G.reads, [])
+    for k in ("row_ptr", "len", "off", "packed"):
+        setattr(H, k, getattr(G, k).copy())
+    H.col, H.code, H.suf = (np.append(a, a[0]).astype(a.dtype) for a in (G.col, G.code, G.suf))
+    bad.append(H)
     # the last read one base past the packed stream's end
     end = len(G.packed) * 4
     H = _pins.graph_from(G.reads, [])

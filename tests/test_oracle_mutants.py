@@ -41,6 +41,17 @@ MUTANTS = [
     ("validate_stream_end_off_by_one", "off[v] + len[v] > packed_bytes * 4", "off[v] + len[v] > packed_bytes * 4 + 1"),
     ("validate_xdrop_full_post", "post[x] > len[v] - 1", "post[x] > len[v]"),
     ("validate_xdrop_negative_pre", "if (pre[x] < 0 ||", "if (pre[x] < -1 ||"),
+    ("uf_root_larger", "if (a < b) parent[b] = a; else parent[a] = b;", "if (a > b) parent[b] = a; else parent[a] = b;"),
+    ("cycle_starts_at_largest", "if (root < 0) { root = c; o_root = 0; cycle = 1; }",
+     "if (root < 0) { root = members[cnt[c + 1] - 1]; o_root = 0; cycle = 1; }"),
+    ("same_end_uses_far_end", "if (cnt < 2) ends[cnt] = code[x] & 1;", "if (cnt < 2) ends[cnt] = (code[x] >> 1) & 1;"),
+    ("xdrop_single_base_piece_dropped", "s->contrib = c > 0 ? c : 0;", "s->contrib = c > 1 ? c : 0;"),
+    ("validate_skips_row_ptr_end", 'if (rp[n] != m) BAD("row_ptr[n] != n_entries");', "if (0) {}"),
+    ("validate_allows_negative_off", "if (off[v] < 0 || off[v] + len[v] > packed_bytes * 4)",
+     "if (off[v] + len[v] > packed_bytes * 4)"),
+    ("walk_into_branch_reads", "if (!is_branch[col[x]] && (code[x] & 1) == e) return x;", "if ((code[x] & 1) == e) return x;"),
+    ("deg_L_counts_masked", "for (int64_t x = rp[v]; x < rp[v + 1]; ++x) d += !is_branch[col[x]];",
+     "for (int64_t x = rp[v]; x < rp[v + 1]; ++x) d += 1;"),
     ("ascii_table_swapped", "{'A', 'C', 'G', 'T'}", "{'A', 'G', 'C', 'T'}"),
     ("packed_bit_order", "return (packed[q >> 2] >> (2 * (q & 3))) & 3;", "return (packed[q >> 2] >> (6 - 2 * (q & 3))) & 3;"),
     ("validate_skips_mirror_code", "if (code[y] != swapped) BAD", "if (0) BAD"),
