@@ -52,6 +52,11 @@ MUTANTS = [
     ("walk_into_branch_reads", "if (!is_branch[col[x]] && (code[x] & 1) == e) return x;", "if ((code[x] & 1) == e) return x;"),
     ("deg_L_counts_masked", "for (int64_t x = rp[v]; x < rp[v + 1]; ++x) d += !is_branch[col[x]];",
      "for (int64_t x = rp[v]; x < rp[v + 1]; ++x) d += 1;"),
+    ("tr_suffix_terms_swapped", "const int64_t d = (int64_t)suf[y] + suf[z] - suf[x];",
+     "const int64_t d = (int64_t)suf[y] + suf[x] - suf[z];"),
+    ("tr_output_mirror_code", "out_col[k] = col[x]; out_code[k] = code[x];",
+     "out_col[k] = col[x]; out_code[k] = (uint8_t)(((code[x] & 1) << 1) | (code[x] >> 1));"),
+    ("tr_tolerance_off_by_one", "if (d <= fuzz && d >= -fuzz)", "if (d <= fuzz + 1 && d >= -fuzz - 1)"),
     ("ascii_table_swapped", "{'A', 'C', 'G', 'T'}", "{'A', 'G', 'C', 'T'}"),
     ("packed_bit_order", "return (packed[q >> 2] >> (2 * (q & 3))) & 3;", "return (packed[q >> 2] >> (6 - 2 * (q & 3))) & 3;"),
     ("validate_skips_mirror_code", "if (code[y] != swapped) BAD", "if (0) BAD"),
