@@ -147,6 +147,42 @@ def test_device_buffers_and_replay(ctx):
         g.close()
 
 
+def test_xdrop_and_host_reads(ctx):
+    """The x-drop (pre, post) form, whose pieces the layout takes from the chain
+    stage, and a graph whose packed reads stay in pinned host memory
+    (CG_HOST_READS, spelled over the host link): each part equals the oracle's."""
+    import torch
+    G = gen.generate("tiny-1Mb", threads=8)
+    X = gen.with_xdrop(G, max_trim=60, seed=3, consistent=False)
+    orc = oracle.run(X, min_chain_reads=1)
+    g = cg.cg_load_graph(ctx, X, min_chain_reads=1)
+    try:
+        part, _ = cg.cg_partition_contigs(g, 3, cg.WEIGHT_BASES)
+        for p in range(3):
+            check_part(g, orc, part, p)
+    finally:
+        g.close()
+
+    keep = []
+
+    def pinned(a):
+        t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        keep.append(t)                       # the pinned buffers outlive the graph
+        return t.numpy()
+
+    P = type("P", (), {})()
+    for k in ("row_ptr", "col", "code", "suf", "len", "off", "packed"):
+        setattr(P, k, pinned(getattr(G, k)))
+    orc = oracle.run(G)
+    g = cg.cg_load_graph(ctx, P, flags=cg.HOST_READS)
+    try:
+        part, _ = cg.cg_partition_contigs(g, 4, cg.WEIGHT_READS)
+        for p in range(4):
+            check_part(g, orc, part, p)
+    finally:
+        g.close()
+
+
 def test_part_errors(ctx):
     G = gen.generate("tiny-1Mb", threads=8)
     g = cg.cg_load_graph(ctx, G)
