@@ -80,3 +80,20 @@ def test_no_gpu_here_reports_cuda_error(libpath):
     with pytest.raises(cg.CgError) as e:
         cg.cg_create(0)
     assert e.value.status == cg.CG_ECUDA
+
+
+def test_binding_checks_before_the_library():
+    """An argument check of the binding that runs before any library call: a
+    part assignment must be int32 (numpy or torch)."""
+    import numpy as np
+    with pytest.raises(ValueError):
+        cg.cg_emit_part(None, np.zeros(4, np.int64), 0)
+    with pytest.raises(ValueError):
+        cg.cg_emit_part(None, np.zeros(4, np.float32), 0)
+    try:
+        import torch
+    except ImportError:
+        return
+    t = torch.zeros(4, dtype=torch.int64)          # a host tensor of the wrong type
+    with pytest.raises(ValueError):
+        cg.cg_emit_part(None, t, 0)
