@@ -28,7 +28,9 @@
  *     smaller-id end read (oriented to leave through its one overlap), the
  *     first read whole, every later read by the suffix of the overlap used
  *     (Sec. 4.4); a closed chain starts at its smallest read, forward;
- *   - contig i occupies bases[contig_off[i], contig_off[i+1]) as ASCII A/C/G/T.
+ *   - contig i occupies bases[contig_off[i], contig_off[i+1]) as ASCII A/C/G/T;
+ *   - for a partition of the contigs (cg_partition_contigs, Sec. 4.3), one
+ *     part alone: its contigs back to back in the same order (cg_emit_part).
  *
  * Ownership and ordering: the caller owns every buffer it passes. Calls on
  * one context are ordered on the context's CUDA stream; a context is not

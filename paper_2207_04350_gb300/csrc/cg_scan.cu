@@ -13,6 +13,10 @@
 //      offset of every piece, the contig offsets and the map from output
 //      tiles to the piece holding each tile's first byte.
 //
+// For one part of a contig partition (cg_emit_part, Sec. 4.3) step 2 gives
+// the reads of other parts' contigs empty pieces, so step 3 lays out that
+// part's contigs alone, back to back.
+//
 // The scans are single-pass decoupled look-back scans: tiles take tickets in
 // order, publish their aggregate, then look back over predecessors with one
 // warp (32 descriptors at a time) until an inclusive prefix is found. The
