@@ -57,6 +57,10 @@ MUTANTS = [
     ("tr_output_mirror_code", "out_col[k] = col[x]; out_code[k] = code[x];",
      "out_col[k] = col[x]; out_code[k] = (uint8_t)(((code[x] & 1) << 1) | (code[x] >> 1));"),
     ("tr_tolerance_off_by_one", "if (d <= fuzz && d >= -fuzz)", "if (d <= fuzz + 1 && d >= -fuzz - 1)"),
+    ("lpt_assign_by_position", "assign[order[i]] = best;", "assign[i] = best;"),
+    ("lpt_load_of_wrong_job", "loads[best] += sizes[order[i]];", "loads[best] += sizes[i];"),
+    ("revcomp_without_reversal", "char c = in[n - 1 - i], d = 'N';", "char c = in[i], d = 'N';"),
+    ("revcomp_c_not_complemented", "case 'C': d = 'G'; break;", "case 'C': d = 'C'; break;"),
     ("ascii_table_swapped", "{'A', 'C', 'G', 'T'}", "{'A', 'G', 'C', 'T'}"),
     ("packed_bit_order", "return (packed[q >> 2] >> (2 * (q & 3))) & 3;", "return (packed[q >> 2] >> (6 - 2 * (q & 3))) & 3;"),
     ("validate_skips_mirror_code", "if (code[y] != swapped) BAD", "if (0) BAD"),
