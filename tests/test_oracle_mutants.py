@@ -61,6 +61,8 @@ MUTANTS = [
     ("lpt_load_of_wrong_job", "loads[best] += sizes[order[i]];", "loads[best] += sizes[i];"),
     ("revcomp_without_reversal", "char c = in[n - 1 - i], d = 'N';", "char c = in[i], d = 'N';"),
     ("revcomp_c_not_complemented", "case 'C': d = 'G'; break;", "case 'C': d = 'C'; break;"),
+    ("bfs_crosses_branch_reads", "if (is_branch[v] || label[v] != -2) continue;", "if (label[v] != -2) continue;"),
+    ("bfs_label_of_last_reached", "label[v] = (int32_t)s; queue[tail++] = v;", "label[v] = (int32_t)v; queue[tail++] = v;"),
     ("ascii_table_swapped", "{'A', 'C', 'G', 'T'}", "{'A', 'G', 'C', 'T'}"),
     ("packed_bit_order", "return (packed[q >> 2] >> (2 * (q & 3))) & 3;", "return (packed[q >> 2] >> (6 - 2 * (q & 3))) & 3;"),
     ("validate_skips_mirror_code", "if (code[y] != swapped) BAD", "if (0) BAD"),
