@@ -11,7 +11,12 @@
  *   ConnectedComponent -> components_uf()     Sec. 4.2 (union-find stands in for
  *                         components_bfs()    LACC; BFS is the cross-check)
  *   LocalAssembly      -> walk_component()    Sec. 4.4 (walk from a root vertex)
+ *                         pieces()            Sec. 4.4 (each read's part: the suffix
+ *                                             form, or l[post : pre] in the x-drop form)
  *                         spell()             Sec. 4.4 (concatenate read parts)
+ *
+ * and the step before it in Alg. 1: TransitiveReduction -> orc_transitive_reduction()
+ * (Sec. 2), plus the input checks of a string graph -> orc_validate2().
  *
  * The partitioning and induced-subgraph steps of Alg. 2 only move data
  * between processes; on one address space they change no result, so the
