@@ -400,8 +400,10 @@ def cg_emit_part(g: Graph, part, p: int, contig_off=None, bases=None, want_count
 
 
 def contigs_part_host(g: Graph, part, p: int):
-    """Host copies (contig_off, bases) of part p's spelling (see cg_emit_part)."""
-    part = np.ascontiguousarray(part, dtype=np.int32)
+    """Host copies (contig_off, bases) of part p's spelling (see cg_emit_part);
+    part may be None for a graph without contigs."""
+    if part is not None:
+        part = np.ascontiguousarray(part, dtype=np.int32)
     nc, tot = cg_emit_part(g, part, p)
     off = np.empty(nc + 1, dtype=np.int64)
     bases = np.empty(max(tot, 1), dtype=np.uint8)
