@@ -152,8 +152,10 @@ CG_API cg_status cg_batch_ranges(cg_graph* g, int64_t* first_contig, int64_t* fi
  * within hbm_budget_bytes; a request that alone exceeds it is refused with
  * CG_EBUSY. `workers` threads, each with its own context and stream, take
  * every admitted request waiting at that moment (at most max_batch) as one
- * batch (continuous batching), so batches overlap on the device. Results
- * stay in server-owned host memory until cg_server_release. */
+ * batch (continuous batching), so batches overlap on the device. Each
+ * worker's device output buffers come from a stream-ordered memory pool, so
+ * a growing batch never synchronises the device. Results stay in
+ * server-owned host memory until cg_server_release. */
 typedef struct cg_server cg_server;
 typedef struct {
   int32_t max_batch;          /* requests per batch, >= 1 */
@@ -177,6 +179,14 @@ CG_API cg_status cg_server_release(cg_server* s, uint64_t id);
 CG_API cg_status cg_server_stats(cg_server* s, uint64_t* batches, uint64_t* requests, uint64_t* in_flight_bytes);
 /* Kernels the server's contexts have launched so far (exact while no batch runs). */
 CG_API cg_status cg_server_kernels(cg_server* s, uint64_t* launched);
+/* Contexts the workers have replaced so far: a worker whose context returns
+ * CG_ECUDA, CG_ETIMEOUT or CG_EKERNEL (after which a context refuses all
+ * work) destroys it and creates a fresh one on the same stream before its
+ * next batch. The requests of the failed batch report that status; later
+ * batches run normally. A batch that fails with CG_EGRAPH or CG_EINVAL (one
+ * malformed request makes the whole union fail) is run again one request at
+ * a time, so that only the malformed requests report the error. */
+CG_API cg_status cg_server_contexts_replaced(cg_server* s, uint64_t* replaced);
 /* Finishes every submitted request, then stops the workers. */
 CG_API cg_status cg_server_stop(cg_server* s);
 
@@ -309,7 +319,9 @@ CG_API cg_status cg_set_host_direct(cg_ctx* ctx, int enable);
  * (input validation, CG_EGRAPH). NULL or "" clears the plan. The CG_FAULT
  * environment variable gives the plan of every new context and server; a
  * server also knows "admit" (cg_server_submit returns CG_EBUSY) and
- * "queue_stall" (a worker sleeps ms milliseconds before its n-th batch). */
+ * "queue_stall" (a worker sleeps ms milliseconds before its n-th batch) and
+ * "batch_timeout" (the n-th batch's first device wait reports CG_ETIMEOUT, so
+ * its worker replaces its context). */
 CG_API cg_status cg_set_fault(cg_ctx* ctx, const char* spec);
 
 /* Counters of a context, for measurement. */
@@ -333,28 +345,48 @@ CG_API cg_status cg_get_stats(cg_ctx* ctx, cg_stats* out);
  * queued between kernels. Waits for the GPU. CG_EINVAL past the last one. */
 CG_API cg_status cg_kernel_time(cg_ctx* ctx, int k, const char** name, float* ms);
 
-/* Exclusive prefix offsets without any device allocation, for callers that
- * cannot call cudaMalloc: code running while another allocator owns the
- * device memory (a caching allocator, or a hard HBM budget the caller must
- * not exceed), or a latency-critical loop where an allocation would stall or
- * synchronise the device. The paper has no counterpart: this is the offset
- * scan that places contigs and read pieces in the output (the one behind
- * contig_off of cg_emit_contigs), with its scratch in a fixed device array.
- *   lengths: device memory, count values >= 0; offsets: device memory,
- *   count + 1 entries; offsets[i] = lengths[0] + ... + lengths[i-1] and
- *   offsets[count] = the total. count <= CG_NOALLOC_MAX_COUNT, else CG_EINVAL.
+/* Exclusive prefix offsets without any device allocation. The paper has no
+ * counterpart. This is the library's offset scan -- the one that places
+ * contigs and read pieces in the output (contig_off of cg_emit_contigs) --
+ * for callers that cannot call cudaMalloc: code that runs while another
+ * allocator owns the device memory (a caching allocator that must see every
+ * allocation, or a hard HBM budget the caller may not exceed), where a
+ * cudaMalloc of the library's own would take memory that allocator counts
+ * on, or would synchronise the device under it. Its look-back scratch is one
+ * file-scope device array instead of allocated buffers.
+ *   lengths: device memory, 4-byte aligned, count values >= 0; offsets:
+ *   device memory, 8-byte aligned, count + 1 entries; offsets[i] =
+ *   lengths[0] + ... + lengths[i-1] and offsets[count] = the total.
+ *   count <= CG_NOALLOC_MAX_COUNT; a larger count, a NULL, misaligned or
+ *   non-device pointer gives CG_EINVAL and nothing is queued.
  * Work is queued on cuda_stream (NULL = the legacy default stream) of the
- * current device; the call then waits for that stream so that it can return
+ * current device, and every call then waits for that stream (it copies the
+ * status word to the host and synchronises), so that it can return
  * CG_ETIMEOUT if the kernel's bounded wait gave up (else CG_OK / CG_ECUDA).
+ * After CG_ETIMEOUT the contents of offsets are undefined.
  * The scratch is one file-scope device array of 8 * (CG_NOALLOC_MAX_COUNT /
- * 2048 + 2) bytes (64 KiB + 16) that every GPU which loads the library holds
+ * 2048 + 3) bytes (64 KiB + 24) that every GPU which loads the library holds
  * until the process exits. The first call on a device, with that device
- * current, looks up the array's device address (cudaGetSymbolAddress); make
- * that first call before any stream capture. Every call shares the array and
- * clears the part it uses first, so calls that overlap on the GPU (other
- * streams, other threads) race and must be serialised by the caller. */
+ * current, looks up the array's device address (cudaGetSymbolAddress) and the
+ * SM count; make that first call before any stream capture. Every call
+ * shares the array and clears the part it uses first, so calls that overlap
+ * on the GPU (other streams, other threads) race and must be serialised by
+ * the caller. */
 #define CG_NOALLOC_MAX_COUNT 16777216
 CG_API cg_status cg_offsets_noalloc(const int32_t* lengths, int64_t count, int64_t* offsets, void* cuda_stream);
+
+/* Self-test of the bounded device waits (the paper has none: its steps are
+ * separated by MPI collectives). Runs the library's look-back scan -- the
+ * one that lays out contigs and read pieces (Sec. 4.4 offsets) -- over
+ * `tiles` tiles (2..4096) of zeros on the context's stream, with the ticket
+ * of tile 0 never handed out, so the tiles after it wait on a descriptor that
+ * no block publishes. Their wait is bounded (2^22 polls with a 200 ns back-off,
+ * about one to two seconds); it then gives up, the kernel records the timeout
+ * in the context's error word and returns. Nothing faults or hangs. Returns
+ * CG_ETIMEOUT, after which the context refuses all work until cg_destroy as
+ * after any device timeout; CG_EKERNEL if the wait did not run out. Waits
+ * for the GPU. */
+CG_API cg_status cg_selftest_wait_timeout(cg_ctx* ctx, int32_t tiles);
 
 /* Waits for all work of the context; returns the first error its kernels found. */
 CG_API cg_status cg_sync(cg_ctx* ctx);

@@ -31,7 +31,7 @@
  *   A read with orientation o (0 forward, 1 reverse complement) is left through
  *   end 1-o and entered through end o (a valid walk, Sec. 2).
  *
- * Readings where the paper is silent (each also listed in the design notes):
+ * Readings where the paper is silent:
  *   - branch = degree >= 3 (Sec. 4.2) OR exactly two surviving edges on the
  *     same end of the read (no valid walk passes through such a read);
  *     one masking pass, no iteration;

@@ -80,6 +80,7 @@ API = {
     "cg_partition_contigs": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64,
                              ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)],
     "cg_sync": [ctypes.c_void_p],
+    "cg_selftest_wait_timeout": [ctypes.c_void_p, ctypes.c_int32],
     "cg_set_timing": [ctypes.c_void_p, ctypes.c_int],
     "cg_set_graphs": [ctypes.c_void_p, ctypes.c_int],
     "cg_set_pdl": [ctypes.c_void_p, ctypes.c_int],
@@ -97,6 +98,7 @@ API = {
     "cg_server_stats": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                         ctypes.POINTER(ctypes.c_uint64)],
     "cg_server_kernels": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)],
+    "cg_server_contexts_replaced": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)],
     "cg_server_stop": [ctypes.c_void_p],
     "cg_offsets_noalloc": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p],
     "cg_status_str": [ctypes.c_int],
@@ -415,6 +417,13 @@ def cg_sync(ctx: Context):
     _check(ctx.ptr, lib().cg_sync(ctx.ptr))
 
 
+def cg_selftest_wait_timeout(ctx: Context, tiles: int = 2) -> int:
+    """Runs the look-back scan with its first tile withheld so that the bounded
+    device wait runs out; returns the status (CG_ETIMEOUT expected; the context
+    then refuses work until it is destroyed)."""
+    return int(lib().cg_selftest_wait_timeout(ctx.ptr, int(tiles)))
+
+
 class Tuning(ctypes.Structure):
     _fields_ = [("ruler_log2", ctypes.c_int32), ("tile_bytes", ctypes.c_int32), ("emit_blocks_per_sm", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]
@@ -513,9 +522,11 @@ class Server:
     def stats(self) -> dict:
         b, q, f = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
         _check(None, lib().cg_server_stats(self.ptr, ctypes.byref(b), ctypes.byref(q), ctypes.byref(f)))
-        n = ctypes.c_uint64()
+        n, rep = ctypes.c_uint64(), ctypes.c_uint64()
         _check(None, lib().cg_server_kernels(self.ptr, ctypes.byref(n)))
-        return {"batches": b.value, "requests": q.value, "in_flight_bytes": f.value, "kernels_launched": n.value}
+        _check(None, lib().cg_server_contexts_replaced(self.ptr, ctypes.byref(rep)))
+        return {"batches": b.value, "requests": q.value, "in_flight_bytes": f.value, "kernels_launched": n.value,
+                "contexts_replaced": rep.value}
 
     def stop(self):
         if self.ptr:
@@ -534,7 +545,11 @@ NOALLOC_MAX_COUNT = 16777216
 
 
 def cg_offsets_noalloc(lengths, offsets, stream=None):
-    """cg_offsets_noalloc on device tensors: offsets[i] = sum(lengths[:i]), offsets[-1] = total."""
+    """cg_offsets_noalloc on device tensors: offsets[i] = sum(lengths[:i]), offsets[-1] = total.
+    lengths: a CUDA int32 tensor; offsets: a CUDA int64 tensor of len(lengths) + 1 entries."""
+    for name, t, dt in (("lengths", lengths, "torch.int32"), ("offsets", offsets, "torch.int64")):
+        if not _is_torch(t) or not t.is_cuda or str(t.dtype) != dt:
+            raise ValueError(f"{name} must be a CUDA tensor of {dt}")
     handle = None
     if stream is not None:
         handle = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))

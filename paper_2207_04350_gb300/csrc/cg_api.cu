@@ -629,12 +629,39 @@ cg_status cg_kernel_time(cg_ctx* c, int k, const char** name, float* ms) {
   return CG_OK;
 }
 
-cg_status cg_sync(cg_ctx* c) {
-  if (!c) return CG_EINVAL;
-  if (c->sticky != CG_OK) return c->sticky;
+static cg_status wait_and_read_ctx(cg_ctx* c) {
   cg_graph tmp;
   tmp.ctx = c;
   return wait_and_read(&tmp);
+}
+
+cg_status cg_sync(cg_ctx* c) {
+  if (!c) return CG_EINVAL;
+  if (c->sticky != CG_OK) return c->sticky;
+  return wait_and_read_ctx(c);
+}
+
+cg_status cg_selftest_wait_timeout(cg_ctx* c, int32_t tiles) {
+  cg_status st = check_ctx(c);
+  if (st != CG_OK) return st;
+  if (tiles < 2 || tiles > 4096) return fail(c, CG_EINVAL, "selftest: tiles must be in 2..4096");
+  CK(cudaStreamSynchronize(c->stream), "stream synchronize");   // earlier work reports its own errors first
+  st = wait_and_read_ctx(c);
+  if (st != CG_OK) return st;
+  unsigned long long* state = static_cast<unsigned long long*>(dalloc(c, (size_t)(tiles + 1) * 8, &st));
+  if (!state) return st;
+  CK(cudaMemsetAsync(state, 0, (size_t)(tiles + 1) * 8, c->stream), "clear descriptors");
+  *c->h_u64 = 1;   // the first ticket handed out is 1: no block ever takes tile 0
+  CK(cudaMemcpyAsync(state + tiles, c->h_u64, 8, cudaMemcpyHostToDevice, c->stream), "seed ticket");
+  CK(cg::launch_selftest_wait(state, tiles, c->derr, c->env), "launch selftest scan");
+  CK(cudaMemcpyAsync(c->h_err, c->derr, sizeof(cg::DevError), cudaMemcpyDeviceToHost, c->stream), "read error word");
+  CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+  dfree(c, state);
+  const cg::DevError e = *c->h_err;
+  if (e.err == cg::DERR_TIMEOUT && e.where == cg::K_SELFTEST_WAIT)
+    return fail(c, CG_ETIMEOUT, "device wait timed out in kernel %d at tile %lld (self-test)", e.where, e.index);
+  return fail(c, CG_EKERNEL, "self-test: the withheld tile's wait did not run out (error %d, kernel %d)", e.err,
+              e.where);
 }
 
 cg_status cg_free_graph(cg_graph* g) {

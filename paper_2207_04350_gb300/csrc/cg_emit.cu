@@ -192,13 +192,9 @@ __global__ void __launch_bounds__(kBlock, 4) k_emit(Scratch s, const uint8_t* pa
 
 cudaError_t launch_emit(const DevGraph& g, const Scratch& s, const Tuning& t, uint8_t* out, int64_t cap,
                         const LaunchEnv& env, long long t_begin, long long t_end) {
-  // a persistent grid: never more blocks than can be resident at once
-  static int resident = 0;
-  if (resident == 0) {
-    int r = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_emit<4>, kBlock, 0);
-    resident = r > 0 ? r : 1;
-  }
+  // a persistent grid: never more blocks than can be resident at once (a
+  // function-local static is initialised once, safely across threads)
+  static const int resident = resident_blocks(k_emit<4>);
   int per_sm = t.emit_blocks_per_sm < resident ? t.emit_blocks_per_sm : resident;
   int blocks = env.num_sms * per_sm;
   cudaError_t e = launch_k(k_emit<4>, blocks, env, env.pdl_first, s, g.packed, (long long)g.packed_bytes,

@@ -230,12 +230,7 @@ __global__ void __launch_bounds__(kBlock) k_emit2(Scratch s, const uint8_t* pack
 
 cudaError_t launch_emit2(const DevGraph& g, const Scratch& s, const Tuning& t, uint8_t* out, int64_t cap,
                          const LaunchEnv& env, long long t_begin, long long t_end) {
-  static int resident = 0;
-  if (resident == 0) {
-    int r = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_emit2, kBlock, 0);
-    resident = r > 0 ? r : 1;
-  }
+  static const int resident = resident_blocks(k_emit2);   // once, safely across threads
   const int per_sm = t.emit_blocks_per_sm < resident ? t.emit_blocks_per_sm : resident;
   const bool aligned16 = (reinterpret_cast<uintptr_t>(g.packed) & 15) == 0;
   cudaError_t e = launch_k(k_emit2, env.num_sms * per_sm, env, env.pdl_first, s, g.packed,

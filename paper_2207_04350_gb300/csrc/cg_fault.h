@@ -6,8 +6,9 @@
 // failed: an allocation ("alloc", CG_ENOMEM), an input copy ("h2d",
 // CG_ECUDA), a bounded device wait ("timeout", CG_ETIMEOUT), a kernel's
 // consistency check ("kernel", CG_EKERNEL), input validation ("bad_graph",
-// CG_EGRAPH), server admission ("admit", CG_EBUSY), or a server worker that
-// stalls for ms milliseconds before its batch ("queue_stall"). Plans come from
+// CG_EGRAPH), server admission ("admit", CG_EBUSY), a server worker that
+// stalls for ms milliseconds before its batch ("queue_stall"), or a server
+// batch whose first device wait reports a timeout ("batch_timeout"). Plans come from
 // the CG_FAULT environment variable when a context or server starts, or from
 // cg_set_fault.
 #pragma once

@@ -234,6 +234,11 @@ constexpr int kMaxParts = 1024;
 cudaError_t launch_partition(const Scratch& s, long long C, int weight, long long max_weight, int P,
                              const SortBuffers& b, int32_t* part, int64_t* psum, const LaunchEnv& env);
 int coop_blocks_for_grid_kernels(int num_sms);
+// Self-test of the look-back scan's bounded wait: scans `tiles` tiles of
+// zeros with `state` (tiles descriptors + the ticket word) prepared by the
+// caller; a ticket that starts at 1 withholds tile 0, so the later tiles'
+// waits run out and the kernel records DERR_TIMEOUT.
+cudaError_t launch_selftest_wait(unsigned long long* state, long long tiles, DevError* derr, const LaunchEnv& env);
 
 // ---- device helpers ----
 __device__ __forceinline__ void set_error(DevError* e, int code, int where, long long index) {
@@ -260,7 +265,8 @@ __device__ __forceinline__ long long grid_threads() { return (long long)gridDim.
 
 enum KernelId {
   K_VALIDATE1 = 1, K_VALIDATE2, K_MASK, K_SUCC, K_WALK, K_JUMP, K_FINAL, K_CYCLE, K_EXPORT,
-  K_SCAN_HEADS, K_SCATTER, K_SCAN_OFFSETS, K_CONTIG_OFF, K_EMIT, K_SORT, K_TRANSITIVE, K_BATCH_GATHER
+  K_SCAN_HEADS, K_SCATTER, K_SCAN_OFFSETS, K_CONTIG_OFF, K_EMIT, K_SORT, K_TRANSITIVE, K_BATCH_GATHER,
+  K_SELFTEST_WAIT
 };
 
 // Blocks of kBlock threads of `kernel` that fit on one SM at once.

@@ -79,13 +79,14 @@ struct has_item<L, std::void_t<typename L::Item>> : std::true_type {};
 //   Load:  unsigned long long operator()(long long i)
 //   Store: void item(long long i, unsigned long long exclusive)   (or with the load's Item, above)
 //          void last(long long count, unsigned long long total)
-// Blocks loop over tiles by ticket; the blocks a count needs no tile of exit
-// at once without taking one, so a grid sized for the largest count costs
-// little when the count (read on the device) is small. When the grid has a
-// block for every tile, block b scans tile b with no ticket: the grid is then
-// at most the blocks resident at once, so every predecessor a tile waits for
-// is running. A scan may also zero `clear` (clear_words words), another
-// scan's descriptors, so that no separate memset runs before that one.
+// Blocks loop over tiles by ticket (state[ticket_index], zero before the
+// scan), so every tile a block waits for was taken earlier by a block that is
+// already running, whatever the grid and however many blocks the GPU runs at
+// once (a GPU shared with other work included). The blocks a count needs no
+// tile of exit at once without taking one, so a grid sized for the largest
+// count costs little when the count (read on the device) is small. A scan may
+// also zero `clear` (clear_words words), another scan's descriptors, so that
+// no separate memset runs before that one.
 template <class Load, class Store>
 __global__ void __launch_bounds__(kBlock) k_scan(Load ld, Store st, long long count_host, const unsigned* count_dev,
                                                  unsigned long long* state, long long ticket_index, DevError* derr,
@@ -102,15 +103,11 @@ __global__ void __launch_bounds__(kBlock) k_scan(Load ld, Store st, long long co
   const long long tiles = (count + kTileItems - 1) / kTileItems;
   if ((long long)blockIdx.x >= tiles) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const bool direct = (long long)gridDim.x >= tiles;
   for (;;) {
-    long long tile = blockIdx.x;
-    if (!direct) {
-      if (tid == 0) s_tile = (long long)atomicAdd(&state[ticket_index], 1ull);
-      __syncthreads();
-      tile = s_tile;
-      if (tile >= tiles) return;                     // block-uniform
-    }
+    if (tid == 0) s_tile = (long long)atomicAdd(&state[ticket_index], 1ull);
+    __syncthreads();
+    const long long tile = s_tile;
+    if (tile >= tiles) return;                       // block-uniform
     const long long base = tile * kTileItems;
     typename std::conditional<has_item<Load>::value, Load, NoItem>::type::Item it[kItems];
     if constexpr (has_item<Load>::value) {
@@ -173,7 +170,6 @@ __global__ void __launch_bounds__(kBlock) k_scan(Load ld, Store st, long long co
         }
       }
     }
-    if (direct) return;
     __syncthreads();                                 // sm and s_tile are reused by the next tile
   }
 }

@@ -268,6 +268,23 @@ cudaError_t launch_offsets(const DevGraph& g, const Scratch& s, const Tuning& t,
   return cudaGetLastError();
 }
 
+namespace {
+struct ZeroLoad {
+  __device__ unsigned long long operator()(long long) const { return 0ull; }
+};
+struct NoStore {
+  __device__ void item(long long, unsigned long long) const {}
+  __device__ void last(long long, unsigned long long) const {}
+};
+}  // namespace
+
+cudaError_t launch_selftest_wait(unsigned long long* state, long long tiles, DevError* derr, const LaunchEnv& env) {
+  k_scan<<<scan_grid(tiles, env), kBlock, 0, env.stream>>>(ZeroLoad{}, NoStore{}, tiles * kTileItems, nullptr, state,
+                                                           tiles, derr, (int)K_SELFTEST_WAIT);
+  mark(env, "k_scan_selftest");
+  return cudaGetLastError();
+}
+
 cudaError_t launch_export_contig_off(const Scratch& s, int64_t* out, int64_t cap, const LaunchEnv& env) {
   cudaError_t e = launch_k(k_export_contig_off, env.num_sms, env, env.pdl_first, s, out, (long long)cap);
   if (e != cudaSuccess) return e;

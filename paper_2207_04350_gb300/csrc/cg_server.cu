@@ -57,9 +57,11 @@ struct cg_server {
   bool stopping = false;
   std::vector<std::thread> workers;
   cg::FaultPlan fault;                   // host-side fault injection (tests)
-  std::vector<cg_ctx*> ctxs;
+  std::vector<cg_ctx*> ctxs;             // one per worker (under mu: a worker may replace its own)
   std::vector<cudaStream_t> streams;
-  uint64_t batches = 0, batched_requests = 0;
+  cudaMemPool_t pool = nullptr;          // the workers' device output buffers (stream-ordered)
+  uint64_t batches = 0, batched_requests = 0, contexts_replaced = 0;
+  uint64_t retired_kernels = 0;          // kernels launched by replaced contexts
 };
 
 namespace {
@@ -81,43 +83,94 @@ void admit_locked(cg_server* s) {
   }
 }
 
-// A worker's device output buffers, grown when a batch needs more.
+// A worker's device output buffers, grown when a batch needs more. They come
+// from the server's stream-ordered memory pool on the worker's stream, so
+// growing them never calls cudaMalloc or cudaFree, which would synchronise
+// the whole device and stall the other worker's batch.
 struct WorkerBuffers {
   uint8_t* bases = nullptr;
   int64_t bases_cap = 0;
   int64_t* off = nullptr;
   int64_t off_cap = 0;
-  void release() {
-    if (bases) cudaFree(bases);
-    if (off) cudaFree(off);
-    bases = nullptr;
-    off = nullptr;
-    bases_cap = off_cap = 0;
-  }
 };
 
-cg_status grow(WorkerBuffers& wb, int64_t total, int64_t contigs) {
+struct Worker {
+  int index = 0;
+  cg_ctx* ctx = nullptr;               // replaced after an error that leaves it refusing work
+  cudaStream_t stream = nullptr;
+  WorkerBuffers wb;
+  unsigned long long kernels_seen = 0;   // kernels of the current context before its last batch
+};
+
+bool leaves_context_refusing(cg_status st) { return st == CG_ECUDA || st == CG_ETIMEOUT || st == CG_EKERNEL; }
+
+cg_status grow(cg_server* s, Worker& w, int64_t total, int64_t contigs) {
+  WorkerBuffers& wb = w.wb;
   if (total > wb.bases_cap) {
-    if (wb.bases) cudaFree(wb.bases);
-    wb.bases_cap = total + total / 4 + 4096;
-    if (cudaMalloc(&wb.bases, (size_t)wb.bases_cap) != cudaSuccess) { cudaGetLastError(); wb.bases = nullptr; wb.bases_cap = 0; return CG_ENOMEM; }
+    if (wb.bases) cudaFreeAsync(wb.bases, w.stream);
+    wb.bases = nullptr;
+    const int64_t cap = total + total / 4 + 4096;
+    if (cudaMallocFromPoolAsync((void**)&wb.bases, (size_t)cap, s->pool, w.stream) != cudaSuccess) {
+      cudaGetLastError();
+      wb.bases = nullptr;
+      wb.bases_cap = 0;
+      return CG_ENOMEM;
+    }
+    wb.bases_cap = cap;
   }
   if (contigs + 1 > wb.off_cap) {
-    if (wb.off) cudaFree(wb.off);
-    wb.off_cap = contigs + contigs / 4 + 1024;
-    if (cudaMalloc(&wb.off, (size_t)wb.off_cap * 8) != cudaSuccess) { cudaGetLastError(); wb.off = nullptr; wb.off_cap = 0; return CG_ENOMEM; }
+    if (wb.off) cudaFreeAsync(wb.off, w.stream);
+    wb.off = nullptr;
+    const int64_t cap = contigs + contigs / 4 + 1024;
+    if (cudaMallocFromPoolAsync((void**)&wb.off, (size_t)cap * 8, s->pool, w.stream) != cudaSuccess) {
+      cudaGetLastError();
+      wb.off = nullptr;
+      wb.off_cap = 0;
+      return CG_ENOMEM;
+    }
+    wb.off_cap = cap;
   }
   return CG_OK;
 }
 
-void run_batch(cg_server* s, cg_ctx* ctx, cudaStream_t stream, WorkerBuffers& wb, std::vector<Request*>& batch) {
+void release_buffers(Worker& w) {
+  if (w.wb.bases) cudaFreeAsync(w.wb.bases, w.stream);
+  if (w.wb.off) cudaFreeAsync(w.wb.off, w.stream);
+  cudaStreamSynchronize(w.stream);
+  w.wb = WorkerBuffers{};
+}
+
+// A context that returned CG_ECUDA, CG_ETIMEOUT or CG_EKERNEL refuses all
+// further work; the worker destroys it and creates a fresh one on its stream
+// (its device output buffers belong to the server's pool and stay).
+void replace_context(cg_server* s, Worker& w) {
+  cg_ctx* fresh = nullptr;
+  if (cg_create(&fresh, s->device, s->opts.hbm_budget_bytes, w.stream) == CG_OK) cg_set_graphs(fresh, 0);
+  else fresh = nullptr;
+  cg_ctx* old = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    old = w.ctx;
+    w.ctx = fresh;
+    s->ctxs[(size_t)w.index] = fresh;
+    s->contexts_replaced += 1;
+    s->retired_kernels += w.kernels_seen;   // a refusing context no longer reports its count
+    w.kernels_seen = 0;
+  }
+  if (old) cg_destroy(old);
+}
+
+// One union graph over `batch` on the worker's context: fills each request's
+// contigs and counts (not its status). Returns the batch's status.
+cg_status run_union(cg_server* s, Worker& w, std::vector<Request*>& batch) {
+  if (!w.ctx) return CG_ECUDA;
+  cg_ctx* ctx = w.ctx;
   const int k = (int)batch.size();
   std::vector<cg_graph_desc> descs(k);
-  const int64_t t0 = now_ns();
-  for (int j = 0; j < k; ++j) {
-    descs[j] = batch[j]->desc;
-    batch[j]->t_start = t0;
-    batch[j]->batch_size = k;
+  for (int j = 0; j < k; ++j) descs[j] = batch[j]->desc;
+  {
+    cg_stats stt{};
+    if (cg_get_stats(ctx, &stt) == CG_OK) w.kernels_seen = stt.kernels_launched;
   }
   // requests whose reads are pinned host memory leave them there: the batch
   // gathers only the bases it spells over the host link; otherwise every
@@ -130,7 +183,8 @@ void run_batch(cg_server* s, cg_ctx* ctx, cudaStream_t stream, WorkerBuffers& wb
   if (st == CG_OK) st = cg_mask_branches(g, nullptr, CG_MEM_DEVICE, nullptr);
   if (st == CG_OK) st = cg_chains(g, nullptr, nullptr, nullptr, CG_MEM_DEVICE, nullptr, nullptr);
   if (st == CG_OK) st = cg_emit_contigs(g, nullptr, 0, nullptr, 0, CG_MEM_DEVICE, &n_contigs, &total);
-  if (st == CG_OK) st = grow(wb, total, n_contigs);
+  if (st == CG_OK) st = grow(s, w, total, n_contigs);
+  WorkerBuffers& wb = w.wb;
   if (st == CG_OK)
     st = cg_emit_contigs(g, wb.off, wb.off_cap, wb.bases, wb.bases_cap, CG_MEM_DEVICE, nullptr, nullptr);
   if (st == CG_OK) st = cg_batch_ranges(g, fc.data(), fb.data(), CG_MEM_HOST);   // waits for the stream
@@ -144,22 +198,52 @@ void run_batch(cg_server* s, cg_ctx* ctx, cudaStream_t stream, WorkerBuffers& wb
       r->contig_off.resize((size_t)(c1 - c0) + 1);
       r->bases.resize((size_t)(b1 - b0));
       if (cudaMemcpyAsync(r->contig_off.data(), wb.off + c0, (size_t)(c1 - c0 + 1) * 8, cudaMemcpyDeviceToHost,
-                          stream) != cudaSuccess ||
+                          w.stream) != cudaSuccess ||
           (b1 > b0 && cudaMemcpyAsync(r->bases.data(), wb.bases + b0, (size_t)(b1 - b0), cudaMemcpyDeviceToHost,
-                                      stream) != cudaSuccess))
+                                      w.stream) != cudaSuccess))
         st = CG_ECUDA;
     }
-    if (cudaStreamSynchronize(stream) != cudaSuccess) st = CG_ECUDA;
+    if (cudaStreamSynchronize(w.stream) != cudaSuccess) st = CG_ECUDA;
     for (int j = 0; j < k; ++j)
       for (int64_t& o : batch[j]->contig_off) o -= fb[j];
   }
   if (g) cg_free_graph(g);
   cudaGetLastError();
+  if (st != CG_OK)
+    for (Request* r : batch) {
+      r->n_contigs = r->total_bases = 0;
+      r->contig_off.clear();
+      r->bases.clear();
+    }
+  return st;
+}
+
+void run_batch(cg_server* s, Worker& w, std::vector<Request*>& batch) {
+  const int k = (int)batch.size();
+  const int64_t t0 = now_ns();
+  for (Request* r : batch) {
+    r->t_start = t0;
+    r->batch_size = k;
+  }
+  if (w.ctx && s->fault.hit("batch_timeout")) cg_set_fault(w.ctx, "timeout:1");   // injected: a device wait runs out
+  std::vector<cg_status> sts((size_t)k, run_union(s, w, batch));
+  const cg_status st = sts[0];
+  if (leaves_context_refusing(st)) replace_context(s, w);
+  if ((st == CG_EGRAPH || st == CG_EINVAL) && k > 1) {
+    // One malformed request fails the whole union (its input checks, or its
+    // sizes): run every member alone, so that only the bad ones report it.
+    for (int j = 0; j < k; ++j) {
+      std::vector<Request*> one{batch[(size_t)j]};
+      batch[(size_t)j]->batch_size = 1;
+      sts[(size_t)j] = run_union(s, w, one);
+      if (leaves_context_refusing(sts[(size_t)j])) replace_context(s, w);
+    }
+  }
   const int64_t t1 = now_ns();
   std::lock_guard<std::mutex> lk(s->mu);
   for (int j = 0; j < k; ++j) {
-    Request* r = batch[j];
-    r->status = st;
+    Request* r = batch[(size_t)j];
+    r->status = sts[(size_t)j];
     r->t_done = t1;
     r->done = 1;
     s->in_flight_bytes -= r->est_bytes;
@@ -171,20 +255,21 @@ void run_batch(cg_server* s, cg_ctx* ctx, cudaStream_t stream, WorkerBuffers& wb
   s->cv_work.notify_all();
 }
 
-void worker_main(cg_server* s, int w) {
-  cg_ctx* ctx = s->ctxs[(size_t)w];
-  cudaStream_t stream = s->streams[(size_t)w];
+void worker_main(cg_server* s, int index) {
+  Worker w;
+  w.index = index;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    w.ctx = s->ctxs[(size_t)index];
+  }
+  w.stream = s->streams[(size_t)index];
   cudaSetDevice(s->device);
-  WorkerBuffers wb;
   for (;;) {
     std::vector<Request*> batch;
     {
       std::unique_lock<std::mutex> lk(s->mu);
       s->cv_work.wait(lk, [&] { return s->stopping || !s->admitted.empty(); });
-      if (s->admitted.empty() && s->stopping) {
-        wb.release();
-        return;
-      }
+      if (s->admitted.empty() && s->stopping) break;
       while (!s->admitted.empty() && (int)batch.size() < s->opts.max_batch) {
         batch.push_back(s->admitted.front());
         s->admitted.pop_front();
@@ -193,8 +278,9 @@ void worker_main(cg_server* s, int w) {
     int stall_ms = 0;
     if (!batch.empty() && s->fault.hit("queue_stall", &stall_ms) && stall_ms > 0)
       std::this_thread::sleep_for(std::chrono::milliseconds(stall_ms));
-    if (!batch.empty()) run_batch(s, ctx, stream, wb, batch);
+    if (!batch.empty()) run_batch(s, w, batch);
   }
+  release_buffers(w);
 }
 
 }  // namespace
@@ -215,6 +301,19 @@ cg_status cg_server_start(int device, const cg_server_opts* opts, cg_server** ou
     delete s;
     return CG_ECUDA;
   }
+  {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    if (cudaMemPoolCreate(&s->pool, &props) != cudaSuccess) {
+      cudaGetLastError();
+      delete s;
+      return CG_ECUDA;
+    }
+    uint64_t keep = ~0ull;   // freed buffers stay in the pool for the next batch
+    cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
   for (int w = 0; w < opts->workers; ++w) {
     cg_ctx* c = nullptr;
     cudaStream_t st_w = nullptr;
@@ -224,6 +323,7 @@ cg_status cg_server_start(int device, const cg_server_opts* opts, cg_server** ou
       if (st_w) cudaStreamDestroy(st_w);
       for (cg_ctx* x : s->ctxs) cg_destroy(x);
       for (cudaStream_t y : s->streams) cudaStreamDestroy(y);
+      cudaMemPoolDestroy(s->pool);
       delete s;
       return st;
     }
@@ -317,12 +417,20 @@ cg_status cg_server_stats(cg_server* s, uint64_t* batches, uint64_t* requests, u
 
 cg_status cg_server_kernels(cg_server* s, uint64_t* launched) {
   if (!s || !launched) return CG_EINVAL;
-  uint64_t n = 0;
+  std::lock_guard<std::mutex> lk(s->mu);
+  uint64_t n = s->retired_kernels;
   for (cg_ctx* c : s->ctxs) {
     cg_stats st{};
-    if (cg_get_stats(c, &st) == CG_OK) n += st.kernels_launched;
+    if (c && cg_get_stats(c, &st) == CG_OK) n += st.kernels_launched;
   }
   *launched = n;
+  return CG_OK;
+}
+
+cg_status cg_server_contexts_replaced(cg_server* s, uint64_t* replaced) {
+  if (!s || !replaced) return CG_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  *replaced = s->contexts_replaced;
   return CG_OK;
 }
 
@@ -334,8 +442,10 @@ cg_status cg_server_stop(cg_server* s) {
   }
   s->cv_work.notify_all();
   for (std::thread& t : s->workers) t.join();
-  for (cg_ctx* c : s->ctxs) cg_destroy(c);
+  for (cg_ctx* c : s->ctxs)
+    if (c) cg_destroy(c);
   for (cudaStream_t y : s->streams) cudaStreamDestroy(y);
+  if (s->pool) cudaMemPoolDestroy(s->pool);
   for (auto& kv : s->all) delete kv.second;   // every request is in `all` until released; workers drained them
   delete s;
   return CG_OK;

@@ -4,7 +4,8 @@ CG_ETIMEOUT and CG_EKERNEL make the context refuse further work until it is
 destroyed, CG_ENOMEM and CG_EGRAPH do not; a fresh context (or the same one,
 for the recoverable ones) then gives bit-exact results. Server: admission
 refusals and a stalled worker (a bounded wait gives up, the request still
-completes)."""
+completes). One device wait really runs out: the look-back scan with its
+first tile withheld returns by itself with CG_ETIMEOUT."""
 import os
 
 import numpy as np
@@ -38,6 +39,35 @@ def contigs(ctx, G):
 def exact(ctx, G, orc):
     off, bases = contigs(ctx, G)
     assert np.array_equal(off, orc.contig_off) and np.array_equal(bases, orc.bases)
+
+
+def test_device_wait_runs_out(tiny):
+    """A real device-side wait that runs out, not an injected status: the
+    look-back scan with tile 0 withheld, so the later tiles wait on a
+    descriptor that nothing publishes until their bounded wait gives up. The
+    kernel returns by itself with CG_ETIMEOUT recorded; the context then
+    refuses work, and a fresh context on the same GPU is bit-exact."""
+    import time
+    G, orc = tiny
+    ctx = cg.cg_create(0)
+    try:
+        exact(ctx, G, orc)
+        t0 = time.perf_counter()
+        st = cg.cg_selftest_wait_timeout(ctx, 4)
+        waited = time.perf_counter() - t0
+        assert st == cg.CG_ETIMEOUT, cg.cg_status_str(st)
+        assert waited < 30.0
+        for call in (lambda: cg.cg_sync(ctx), lambda: contigs(ctx, G)):
+            with pytest.raises(cg.CgError) as e:
+                call()
+            assert e.value.status == cg.CG_ETIMEOUT
+    finally:
+        ctx.close()
+    ctx = cg.cg_create(0)
+    try:
+        exact(ctx, G, orc)
+    finally:
+        ctx.close()
 
 
 @pytest.mark.parametrize("site,at,status,sticky", [
@@ -127,5 +157,54 @@ def test_server_worker_stall(tiny):
         assert e.value.status == cg.CG_ETIMEOUT
         check_result(srv.wait(rid), orc)         # and the request still completes
         srv.release(rid)
+    finally:
+        srv.stop()
+
+
+def test_server_replaces_a_refusing_context(tiny):
+    """A batch whose device wait reports a timeout leaves its context refusing
+    work; the worker replaces that context, so the failed batch's request
+    reports CG_ETIMEOUT and every later request is bit-exact."""
+    G, orc = tiny
+    srv = server_with("batch_timeout:1", hbm_budget_bytes=8 << 30, max_batch=4, workers=1)
+    try:
+        rid = srv.submit(G)
+        res = srv.wait(rid)
+        assert res["status"] == cg.CG_ETIMEOUT
+        srv.release(rid)
+        for _ in range(3):
+            rid = srv.submit(G)
+            check_result(srv.wait(rid), orc)
+            srv.release(rid)
+        assert srv.stats()["contexts_replaced"] == 1
+    finally:
+        srv.stop()
+
+
+def test_server_malformed_request_fails_alone(tiny):
+    """One malformed graph batched with valid ones: the union fails its input
+    checks, the batch is run again one request at a time, and only the
+    malformed request reports CG_EGRAPH; the others are bit-exact."""
+    G, orc = tiny
+    B = type("B", (), {})()
+    for k in ("row_ptr", "col", "code", "suf", "len", "off", "packed"):
+        setattr(B, k, np.array(getattr(G, k), copy=True))
+    B.code[0] ^= 1                                # the entry no longer matches its mirror
+    assert not oracle.validate(B)[0]
+    # the first batch stalls, so the requests submitted meanwhile form one batch
+    srv = server_with("queue_stall:1:500", hbm_budget_bytes=8 << 30, max_batch=16, workers=1)
+    try:
+        first = srv.submit(G)
+        ids = [(srv.submit(B if i == 2 else G), i == 2) for i in range(5)]
+        check_result(srv.wait(first), orc)
+        srv.release(first)
+        for rid, bad in ids:
+            res = srv.wait(rid)
+            if bad:
+                assert res["status"] == cg.CG_EGRAPH
+            else:
+                check_result(res, orc)
+            srv.release(rid)
+        assert srv.stats()["batches"] == 2       # the five shared one batch
     finally:
         srv.stop()

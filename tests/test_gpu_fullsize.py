@@ -8,9 +8,7 @@ replayed from CUDA graphs; host-resident reads with in-place host outputs):
   through CG_HOST_READS into pinned host buffers; the graph in the x-drop
   form (early starts up to 200 bases, unequal); the transitive reduction of
   the recipe's overlap graph before reduction (3.4M entries);
-- the 512-graph batch as one union: every graph's sizes, the full contigs of
-  a sample of graphs, with the reads copied and left in host memory;
-- the served pool through the server: a sample of requests in full.
+The batched and served workloads are in test_gpu_fullsize_forms.py.
 """
 import numpy as np
 import pytest
@@ -116,55 +114,3 @@ def test_transitive_reduction_3_1gb(ctx):
     W = oracle.transitive_reduction(R)
     for k in ("row_ptr", "col", "code", "suf"):
         assert np.array_equal(np.asarray(getattr(S, k)).astype(np.int64), np.asarray(getattr(W, k)).astype(np.int64)), k
-
-
-def test_batched_512_full(ctx):
-    import torch
-    keep = []
-
-    def alloc(shape, dt):
-        t = torch.empty(shape, dtype=getattr(torch, dt.__name__), pin_memory=True)
-        keep.append(t)
-        return t.numpy()
-    graphs = [gen.generate(gen.batched_graph(j), keep_genome=False, alloc=alloc) for j in range(512)]
-    rng = np.random.default_rng(5)
-    sample = sorted(set(rng.choice(512, size=24, replace=False).tolist()) | {0, 511})
-    want = {j: oracle.run(graphs[j], min_chain_reads=2, validate=False) for j in sample}
-    for flags in (0, cg.HOST_READS):
-        g = cg.cg_load_batch(ctx, graphs, flags=flags, min_chain_reads=2)
-        try:
-            off, bases = cg.contigs_host(g)
-            fc, fb = cg.cg_batch_ranges(g)
-        finally:
-            g.close()
-        for j in sample:
-            w = want[j]
-            assert fc[j + 1] - fc[j] == w.n_contigs and fb[j + 1] - fb[j] == w.total_bases
-            assert np.array_equal(off[fc[j]:fc[j + 1] + 1] - fb[j], w.contig_off)
-            assert np.array_equal(bases[fb[j]:fb[j + 1]], w.bases)
-        assert fb[512] == len(bases)
-
-
-def test_served_pool(ctx):
-    import torch
-    keep = []
-
-    def alloc(shape, dt):
-        t = torch.empty(shape, dtype=getattr(torch, dt.__name__), pin_memory=True)
-        keep.append(t)
-        return t.numpy()
-    pool = [gen.generate(gen.served_graph(j), keep_genome=False, alloc=alloc) for j in range(32)]
-    sample = [0, 3, 9, 17, 31]
-    want = {j: oracle.run(pool[j], min_chain_reads=2, validate=False) for j in sample}
-    srv = cg.Server(0, hbm_budget_bytes=150 << 30, max_batch=64, workers=2)
-    try:
-        ids = [(srv.submit(pool[j]), j) for j in range(32) for _ in range(2)]
-        for rid, j in ids:
-            r = srv.wait(rid, copy=j in want)
-            assert r["status"] == cg.CG_OK
-            if j in want:
-                assert np.array_equal(r["contig_off"], want[j].contig_off)
-                assert np.array_equal(r["bases"], want[j].bases)
-            srv.release(rid)
-    finally:
-        srv.stop()
