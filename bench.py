@@ -87,6 +87,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=5.0, help="CPU budget of the scaled oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--shard", default="", choices=["", "tiles", "lpt"],
+                   help="split one graph over the ranks (strong scaling) instead of one replica per rank")
     p.add_argument("--no-forms", action="store_true",
                    help="main workload only: skip the compact records of the other four workloads")
     p.add_argument("--no-transitive", action="store_true", help="skip the transitive-reduction measurement")
@@ -784,29 +786,11 @@ def run_ours(args, rank, world, local_rank):
             "kernel_ms": statistics.mean(kms[1:]), "call_ms": statistics.mean(wall[1:]),
             "max_over_mean_part": float(psum.max() / max(psum.mean(), 1e-9))}
     cg.cg_set_timing(ctx, 1)
-    # one part's spelling (Sec. 4.3-4.4), the per-GPU work of a sharded run after
-    # the chain stage it shares: an 8-way LPT split by bases, each part laid out
-    # and spelled alone into the device buffers; GPU time of the offsets and
-    # spelling stages from the stage events inside the replayed graph
-    n_split = 8
-    part_h, part_w = cg.cg_partition_contigs(g, n_split, cg.WEIGHT_BASES)
-    d_part = torch.from_numpy(np.ascontiguousarray(part_h)).cuda()
-    part_ms = []
-    for p in range(n_split):
-        ts = []
-        for r in range(5):
-            with torch.cuda.stream(stream):
-                flush.fill_(9)
-            cg.cg_emit_part(g, d_part, p, contig_off, bases, want_counts=False)
-            sm = cg.cg_get_stats(ctx)["stage_ms"]
-            if r >= 2:
-                ts.append(sm[2] + sm[3])
-        part_ms.append(statistics.median(ts))
-    parts = {"n_parts": n_split, "weight": "bases (cg_partition_contigs)", "part_bases": [int(x) for x in part_w],
-             "offsets_plus_emit_ms": part_ms, "max_part_ms": max(part_ms),
-             "whole_offsets_plus_emit_ms": statistics.mean(s[2] + s[3] for s in stage),
-             "note": "cg_emit_part per part after the shared chain stage, device outputs, L2 flushed before each "
-                     "call; median of 3 after 2 warm-up calls per part; one GPU, not a multi-GPU run"}
+    # the per-rank step of an 8-way split of this graph over 8 GPUs (each rank
+    # with the whole graph: mask, chains, then its share of the spelling), every
+    # rank's step timed alone on this one GPU, one rank after another
+    sharded = sharded_on_one_gpu(args, ctx, stream, dg, flush, total, statistics.mean(step_ms)) \
+        if world == 1 and not args.no_forms else None
     if world > 1:
         torch.distributed.barrier()
     time.sleep(0.2)
@@ -919,7 +903,7 @@ def run_ours(args, rank, world, local_rank):
             "kernel_ms_note": "3 extra untimed steps with a CUDA event after every kernel",
             "step_ms_median": statistics.median(step_ms), "step_ms_min": min(step_ms), "step_ms_max": max(step_ms),
             "partition": partition,
-            "parts": parts,
+            "sharded_on_one_gpu": sharded,
             "emit_2bit": emit_2bit,
             "xdrop": xdrop,
             "autotune": tuned,
@@ -943,6 +927,140 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": launches,
     }
     g.close()
+    ctx.close()
+    return line
+
+
+def sharded_on_one_gpu(args, ctx, stream, dg, flush, total, whole_ms, n_ranks=8, steps=5):
+    """Every rank's step of an n_ranks-way split of one graph (paper_2207_04350_gb300.shard:
+    each rank loads the whole graph, runs the mask and chain stages, and spells
+    its share), timed one rank after another on this one GPU with CUDA events
+    on the context stream, L2 flushed before each step: the slowest rank's step
+    is what one step of the split would take on n_ranks GPUs, collectives
+    aside (the split has none on its data path). Not a multi-GPU run."""
+    import torch
+
+    from paper_2207_04350_gb300 import cg, shard
+    out = {"n_ranks": n_ranks, "steps_per_rank": steps, "whole_graph_step_ms": whole_ms,
+           "note": "per-rank device time of the rank's whole step (mask, chains, [LPT], its spelling), ranks timed one "
+                   "after another on one GPU; max over ranks = the split's step on n_ranks GPUs without collectives"}
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    cg.cg_set_timing(ctx, 0)
+    for mode in shard.MODES:
+        per_rank, sizes = [], []
+        for r in range(n_ranks):
+            run = shard.ShardedRun(ctx, dg, r, n_ranks, mode=mode, flags=cg.BORROW_DEVICE,
+                                   min_chain_reads=args.min_chain_reads)
+            ts = []
+            for i in range(steps + 2):
+                with torch.cuda.stream(stream):
+                    flush.fill_(11)
+                ev0.record(stream)
+                run.step()
+                ev1.record(stream)
+                ev1.synchronize()
+                if i >= 2:
+                    ts.append(ev0.elapsed_time(ev1))
+            cg.cg_sync(ctx)
+            sizes.append(int(run.n_bases))
+            per_rank.append(statistics.median(ts))
+            run.close()
+        mx = max(per_rank)
+        out[mode] = {"rank_step_ms": per_rank, "max_rank_step_ms": mx, "rank_bases": sizes,
+                     "bases_max_over_mean": max(sizes) / max(1e-9, sum(sizes) / len(sizes)),
+                     "speedup_over_one_gpu": whole_ms / mx,
+                     "gbases_per_s_n_ranks": total / (mx * 1e-3) / 1e9}
+    out["lpt"]["weight"] = "bases (cg_partition_contigs, recomputed by every rank every step)"
+    out["tiles"]["split"] = "equal runs of 32 KiB output tiles (cg_emit_share)"
+    return out
+
+
+def run_sharded(args, rank, world, local_rank):
+    """One graph split over the ranks (paper_2207_04350_gb300.shard): every rank
+    holds the whole graph and reads in its HBM, runs the mask and chain stages
+    and spells its own share ("tiles": equal runs of output tiles; "lpt": the
+    paper's GreedyPartitioning of whole contigs). No collective on the data
+    path; the step time is the slowest rank's. Strong scaling: the work per
+    step is one graph whatever the number of ranks."""
+    import torch
+
+    from paper_2207_04350_gb300 import cg, shard
+
+    torch.cuda.set_device(local_rank)
+    pk, pk_kind = peaks()
+    cfg = workload_cfg(args.workload)
+    t_gen = time.time()
+    G = generate_pinned(cfg, args.threads)
+    t_gen = time.time() - t_gen
+    stream = torch.cuda.Stream()
+    ctx = cg.cg_create(local_rank, stream=stream)
+    names = ("row_ptr", "col", "code", "suf", "len", "off", "packed")
+    with torch.cuda.stream(stream):
+        dev = {k: torch.from_numpy(getattr(G, k)).to("cuda", non_blocking=True) for k in names}
+    stream.synchronize()
+    dg = type("D", (), {})()
+    for k, v in dev.items():
+        setattr(dg, k, v)
+    run = shard.ShardedRun(ctx, dg, rank, world, mode=args.shard, flags=cg.BORROW_DEVICE,
+                           min_chain_reads=args.min_chain_reads)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    cg.cg_set_timing(ctx, 3)
+    for _ in range(args.warmup):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+        run.step()
+    cg.cg_sync(ctx)
+    rank_barrier(world)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = cg.cg_get_stats(ctx)["kernels_launched"]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step_ms, emit_ms = [], []
+    rank_barrier(world)
+    t0 = time.time()
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(2)
+        ev0.record(stream)
+        run.step()
+        ev1.record(stream)
+        ev1.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+        emit_ms.append(cg.cg_get_stats(ctx)["stage_ms"][3])
+    cg.cg_sync(ctx)
+    torch.cuda.synchronize()
+    rank_barrier(world)
+    t1 = time.time()
+    launches = cg.cg_get_stats(ctx)["kernels_launched"] - launches0
+    time.sleep(0.2)
+    clocks.stop()
+    ms_rank = statistics.mean(step_ms)
+    value = job_rate(run.n_bases, ms_rank * 1e-3, world) / 1e9
+    ms = max_over_ranks(ms_rank, world)
+    total = run.total
+    ms_emit = statistics.mean(emit_ms)
+    emit_bytes = run.n_bases + (run.n_bases + 3) // 4
+    ach = emit_bytes / (ms_emit * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "ms_per_graph": ms, "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic (the seeded generator gen/: genome, repeats, reads and overlaps of the stated recipe)",
+        "config": {"workload": cfg_name(args) + f", split over {world} rank(s) ({args.shard})",
+                   "shard_mode": args.shard, "n_contigs": run.n_contigs, "contig_bases": total,
+                   "rank0_bases": run.n_bases, "inputs": "whole graph and reads resident in every rank's HBM",
+                   "l2": "flushed between steps (512 MiB write, outside the timed events)",
+                   "generate_s": round(t_gen, 1), "wall_s_timed": t1 - t0},
+        "roofline": {"kernel": "k_emit (this rank's share)", "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"],
+                     "unit": "GB/s", "frac": ach / pk["hbm_gbs"], "traffic": None,
+                     "algorithmic_bytes_per_launch": emit_bytes, "bytes_per_unit": 1.25,
+                     "units_per_launch": run.n_bases, "ms_per_launch": ms_emit,
+                     "peak_kind": pk_kind + " (hbm_gbs, copy)"},
+        "cpu_baseline": None, "e2e": None, "clocks": clocks.summary(t0, t1), "gpu_launches": launches,
+    }
+    run.close()
     ctx.close()
     return line
 
@@ -1189,7 +1307,9 @@ def main():
     if world > 1:
         torch.distributed.barrier()
         __graft_entry__.build()
-    if args.workload.startswith("batched"):
+    if args.shard:
+        line = run_sharded(args, rank, world, local_rank)
+    elif args.workload.startswith("batched"):
         line = run_batched(args, rank, world, local_rank)
     elif args.workload.startswith("served"):
         line = run_served(args, rank, world, local_rank)

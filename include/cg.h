@@ -275,6 +275,26 @@ CG_API cg_status cg_emit_part(cg_graph* g, const int32_t* part, int64_t part_cap
                               int64_t contig_off_cap, uint8_t* bases, int64_t bases_cap, int mem, int64_t* n_contigs,
                               int64_t* total_bases);
 
+/* One share of the whole spelling, for a run over several GPUs or processes
+ * that each hold the whole graph and its reads and split the LocalAssembly
+ * work among themselves (Sec. 4.3-4.4). Where the paper gives each process
+ * whole contigs (cg_partition_contigs + cg_emit_part), this call cuts the
+ * output stream of cg_emit_contigs itself into n_shares runs of whole output
+ * tiles (tiles of the context's tuning.tile_bytes; runs as equal as the tiles
+ * allow) and spells share `share` only, so every share is the same work
+ * whatever the contig sizes, and a contig may span two shares. Output:
+ * bases[0 .. n_bases) = stream bytes [first_base, first_base + n_bases);
+ * concatenating the shares 0..n_shares-1 gives the stream of
+ * cg_emit_contigs. contig_off (optional, n_contigs + 1 entries) gets the
+ * whole stream's contig offsets. Every share of one split must use the same
+ * tile_bytes. bases: NULL (sizes only) or bases_cap >= the share's size,
+ * 16-byte aligned in device memory; first_base and n_bases are optional
+ * (asking for them waits for the GPU). 0 <= share < n_shares, else
+ * CG_EINVAL. Runs the earlier steps first. */
+CG_API cg_status cg_emit_share(cg_graph* g, int32_t share, int32_t n_shares, int64_t* contig_off,
+                               int64_t contig_off_cap, uint8_t* bases, int64_t bases_cap, int mem,
+                               int64_t* first_base, int64_t* n_bases);
+
 /* Launch parameters of a context's kernels. None changes any output. */
 typedef struct {
   int32_t ruler_log2;         /* list ranking: a read starts a sublist with probability 2^-ruler_log2, 1..12 */

@@ -72,6 +72,9 @@ API = {
     "cg_emit_part": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
                      ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
                      ctypes.POINTER(ctypes.c_int64)],
+    "cg_emit_share": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64,
+                      ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                      ctypes.POINTER(ctypes.c_int64)],
     "cg_emit_contigs_2bit": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
                              ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
     "cg_transitive_reduction": [ctypes.c_void_p, ctypes.POINTER(GraphDesc), ctypes.c_int32, ctypes.c_void_p,
@@ -399,6 +402,21 @@ def cg_emit_part(g: Graph, part, p: int, contig_off=None, bases=None, want_count
                                          mem, ctypes.byref(nc) if want_counts else None,
                                          ctypes.byref(tot) if want_counts else None))
     return (nc.value, tot.value) if want_counts else None
+
+
+def cg_emit_share(g: Graph, share: int, n_shares: int, contig_off=None, bases=None, want_range: bool = True):
+    """Share `share` of n_shares equal runs of output tiles of the whole contig
+    stream (Sec. 4.3-4.4 with the work split by output bytes): bases[:n] = stream
+    bytes [first_base, first_base + n). contig_off (n_contigs + 1) gets the whole
+    stream's offsets. Buffers all host or all device. Returns (first_base, n)."""
+    fb, nb = ctypes.c_int64(-1), ctypes.c_int64(-1)
+    mem = _mem_of_all([contig_off, bases])
+    ocap = len(contig_off) if contig_off is not None else 0
+    bcap = _nbytes(bases) if bases is not None else 0
+    _check(g.ctx.ptr, lib().cg_emit_share(g.ptr, int(share), int(n_shares), _ptr(contig_off), ocap, _ptr(bases), bcap,
+                                          mem, ctypes.byref(fb) if want_range else None,
+                                          ctypes.byref(nb) if want_range else None))
+    return (fb.value, nb.value) if want_range else None
 
 
 def contigs_part_host(g: Graph, part, p: int):

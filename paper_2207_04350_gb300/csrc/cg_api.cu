@@ -1177,6 +1177,92 @@ cg_status cg_emit_part(cg_graph* g, const int32_t* part, int64_t part_cap, int32
   return st;
 }
 
+cg_status cg_emit_share(cg_graph* g, int32_t share, int32_t n_shares, int64_t* contig_off, int64_t contig_off_cap,
+                        uint8_t* bases, int64_t bases_cap, int mem, int64_t* first_base, int64_t* n_bases) {
+  if (!g) return CG_EINVAL;
+  cg_ctx* c = g->ctx;
+  cg_status st = check_ctx(c);
+  if (st != CG_OK) return st;
+  if (mem != CG_MEM_HOST && mem != CG_MEM_DEVICE) return fail(c, CG_EINVAL, "bad mem");
+  if (n_shares < 1 || share < 0 || share >= n_shares)
+    return fail(c, CG_EINVAL, "share %d of %d shares", (int)share, (int)n_shares);
+  if ((bases && bases_cap < 0) || (contig_off && contig_off_cap < 1)) return fail(c, CG_EINVAL, "bad capacity");
+  st = run_offsets(g);
+  if (st != CG_OK) return st;
+  if (bases) {
+    st = prepare_emit(g);
+    if (st != CG_OK) return st;
+  }
+  // the share's stream range, from the stream's size (known on the host after a wait)
+  const int64_t tb = c->tune.tile_bytes;
+  auto range = [&](int64_t total, int64_t* fb, int64_t* nb) {
+    const int64_t T = (total + tb - 1) / tb;
+    const int64_t t0 = (int64_t)share * T / n_shares, t1 = (int64_t)(share + 1) * T / n_shares;
+    *fb = t0 * tb;
+    *nb = std::max<int64_t>(0, std::min(total, t1 * tb) - t0 * tb);
+  };
+  auto spell = [&](uint8_t* dst, int64_t cap) -> cg_status {
+    StageTimer tm(c, 3);
+    uint64_t key = mix_key(mix_key(mix_key(mix_key((uint64_t)(uintptr_t)dst, (uint64_t)cap),
+                                           (uint64_t)(uintptr_t)emit_graph(g).packed), (uint64_t)tb),
+                           (uint64_t)c->tune.emit_blocks_per_sm);
+    key = mix_key(mix_key(key, (uint64_t)share), (uint64_t)n_shares);
+    return run_stage(g, 3, key, [&]() -> cg_status {
+      CK(cg::launch_emit(emit_graph(g), g->s, c->tune, dst, cap, c->env, 0, 1ll << 62, share, n_shares),
+         "emission kernel (one share)");
+      return CG_OK;
+    });
+  };
+  int64_t fb = 0, nb = 0;
+  if (mem == CG_MEM_DEVICE) {
+    if (bases) {
+      if (!aligned(bases, 16)) return fail(c, CG_EINVAL, "device bases buffer must be 16-byte aligned");
+      st = spell(bases, bases_cap);
+      if (st != CG_OK) return st;
+    }
+    if (contig_off) {
+      st = run_stage(g, 4, mix_key((uint64_t)(uintptr_t)contig_off, (uint64_t)contig_off_cap), [&]() -> cg_status {
+        CK(cg::launch_export_contig_off(g->s, contig_off, contig_off_cap, c->env), "export contig_off");
+        return CG_OK;
+      });
+      if (st != CG_OK) return st;
+    }
+    if (first_base || n_bases) {
+      st = wait_and_read(g);
+      if (st != CG_OK) return st;
+      range(c->h_ctr->total_bases, &fb, &nb);
+    }
+  } else {
+    st = wait_and_read(g);
+    if (st != CG_OK) return st;
+    const int64_t C = c->h_ctr->n_contigs;
+    range(c->h_ctr->total_bases, &fb, &nb);
+    if (bases && bases_cap < nb) return fail(c, CG_EINVAL, "bases capacity %lld < %lld", (long long)bases_cap, (long long)nb);
+    if (contig_off && contig_off_cap < C + 1) return fail(c, CG_EINVAL, "contig_off capacity too small");
+    if (bases && nb > 0) {
+      if (g->stage_bases_cap < nb) {
+        if (g->stage_bases) dfree(c, g->stage_bases);
+        g->stage_bases = (uint8_t*)dalloc(c, (size_t)nb, &st);
+        if (!g->stage_bases) { g->stage_bases_cap = 0; return st; }
+        g->stage_bases_cap = nb;
+      }
+      st = spell(g->stage_bases, g->stage_bases_cap);
+      if (st != CG_OK) return st;
+      CK(cudaMemcpyAsync(bases, g->stage_bases, (size_t)nb, cudaMemcpyDeviceToHost, c->stream), "copy bases");
+    }
+    if (contig_off)
+      CK(cudaMemcpyAsync(contig_off, g->s.contig_off, (size_t)(C + 1) * 8, cudaMemcpyDeviceToHost, c->stream),
+         "copy contig_off");
+    if (bases || contig_off) {
+      st = wait_and_read(g);
+      if (st != CG_OK) return st;
+    }
+  }
+  if (first_base) *first_base = fb;
+  if (n_bases) *n_bases = nb;
+  return CG_OK;
+}
+
 cg_status cg_emit_contigs_2bit(cg_graph* g, int64_t* contig_off, int64_t contig_off_cap, uint8_t* packed_out,
                                int64_t packed_cap, int mem, int64_t* n_contigs, int64_t* total_bases) {
   if (!g) return CG_EINVAL;

@@ -62,10 +62,15 @@ __device__ __forceinline__ uint8_t base_at(const uint8_t* packed, unsigned long 
 // address arithmetic is done once per piece. Each chunk is two word loads,
 // one funnel shift and four lookups in a shared table that maps a byte (four
 // bases) to four ASCII characters, forward or reverse-complemented.
+// With n_shares > 1 the launch spells share `share` of the stream cut into
+// n_shares runs of whole tiles (tiles [share * T / n_shares, (share + 1) * T /
+// n_shares) of the T tiles), written from out[0] on: out and cap then hold
+// that share only.
 template <int U>
 __global__ void __launch_bounds__(kBlock, 4) k_emit(Scratch s, const uint8_t* packed, long long packed_bytes,
                                                  long long readable_words, uint8_t* out, long long cap,
-                                                 int tile_bytes, long long t_begin, long long t_end) {
+                                                 int tile_bytes, long long t_begin, long long t_end, int share,
+                                                 int n_shares) {
   __shared__ uint32_t lut[2][256];
   for (int i = threadIdx.x; i < 256; i += blockDim.x) {
     uint32_t f = 0, r = 0;
@@ -80,12 +85,22 @@ __global__ void __launch_bounds__(kBlock, 4) k_emit(Scratch s, const uint8_t* pa
   __syncthreads();
   const Counters* c = s.ctr;
   const long long total = *(const volatile long long*)&c->total_bases;
-  if (total > cap) {
+  const long long ntiles = (total + tile_bytes - 1) / tile_bytes;
+  if (n_shares > 1) {
+    t_begin = (long long)share * ntiles / n_shares;
+    t_end = (long long)(share + 1) * ntiles / n_shares;
+    const long long first = t_begin * tile_bytes;
+    const long long bytes = max(0ll, min(total, t_end * (long long)tile_bytes) - first);
+    if (bytes > cap) {
+      if (grid_tid() == 0) set_error(s.derr, DERR_CAPACITY, K_EMIT, bytes);
+      return;
+    }
+    out -= first;                                        // stream position X goes to out[X - first]
+  } else if (total > cap) {
     if (grid_tid() == 0) set_error(s.derr, DERR_CAPACITY, K_EMIT, total);
     return;
   }
   const int lane = threadIdx.x & 31;
-  const long long ntiles = (total + tile_bytes - 1) / tile_bytes;
   const uint32_t* words = reinterpret_cast<const uint32_t*>(packed);
   const long long full_words = packed_bytes >> 2;
   const int64_t* oo = s.out_off;
@@ -191,14 +206,15 @@ __global__ void __launch_bounds__(kBlock, 4) k_emit(Scratch s, const uint8_t* pa
 }  // namespace
 
 cudaError_t launch_emit(const DevGraph& g, const Scratch& s, const Tuning& t, uint8_t* out, int64_t cap,
-                        const LaunchEnv& env, long long t_begin, long long t_end) {
+                        const LaunchEnv& env, long long t_begin, long long t_end, int share, int n_shares) {
   // a persistent grid: never more blocks than can be resident at once (a
   // function-local static is initialised once, safely across threads)
   static const int resident = resident_blocks(k_emit<4>);
   int per_sm = t.emit_blocks_per_sm < resident ? t.emit_blocks_per_sm : resident;
   int blocks = env.num_sms * per_sm;
   cudaError_t e = launch_k(k_emit<4>, blocks, env, env.pdl_first, s, g.packed, (long long)g.packed_bytes,
-                           (long long)(g.packed_readable / 4), out, (long long)cap, t.tile_bytes, t_begin, t_end);
+                           (long long)(g.packed_readable / 4), out, (long long)cap, t.tile_bytes, t_begin, t_end,
+                           share, n_shares);
   if (e != cudaSuccess) return e;
   mark(env, "k_emit");
   return cudaGetLastError();

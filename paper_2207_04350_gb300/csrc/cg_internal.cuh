@@ -174,9 +174,12 @@ cudaError_t launch_validate(const DevGraph& g, DevError* derr, const LaunchEnv& 
 cudaError_t launch_mask(const DevGraph& g, const Scratch& s, const LaunchEnv& env);
 cudaError_t launch_chains(const DevGraph& g, const Scratch& s, const Tuning& t, const LaunchEnv& env);
 cudaError_t launch_offsets(const DevGraph& g, const Scratch& s, const Tuning& t, const LaunchEnv& env);
-// Spells the output tiles [t_begin, t_end) (all of them by default).
+// Spells the output tiles [t_begin, t_end) (all of them by default); with
+// n_shares > 1, share `share` of the tiles cut into n_shares equal runs,
+// written from out[0] on (out and cap hold that share only).
 cudaError_t launch_emit(const DevGraph& g, const Scratch& s, const Tuning& t, uint8_t* out, int64_t cap,
-                        const LaunchEnv& env, long long t_begin = 0, long long t_end = 1ll << 62);
+                        const LaunchEnv& env, long long t_begin = 0, long long t_end = 1ll << 62, int share = 0,
+                        int n_shares = 1);
 cudaError_t launch_export_reads(const DevGraph& g, const Scratch& s, int32_t* cid, int32_t* rank, uint8_t* orient,
                                 const LaunchEnv& env);
 // 2-bit spelling: cap = bytes of `out`, which must hold 16 * ceil(total / 64).
