@@ -761,7 +761,10 @@ cg_status cg_load_graph(cg_ctx* c, const cg_graph_desc* d, uint32_t flags, cg_gr
     }
     if (st == CG_OK) G.len = (const int32_t*)copy_in(d->len, (size_t)n * 4, 0);
     if (st == CG_OK) G.off = (const int64_t*)copy_in(d->off, (size_t)n * 8, 0);
-    if (host_reads) G.packed = host_packed_dev;
+    if (host_reads) {
+      G.packed = host_packed_dev;
+      G.packed_host = true;
+    }
     else if (st == CG_OK) G.packed = (const uint8_t*)copy_in(d->packed, (size_t)d->packed_bytes, 16);
     if (st != CG_OK) return bail(st);
   }

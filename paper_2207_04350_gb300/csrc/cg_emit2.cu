@@ -10,14 +10,10 @@
 // bases below it, reverses the order of the 2-bit fields of each word and
 // complements them (b -> 3 - b is a bitwise NOT of the field).
 //
-// The warp takes the tile's pieces 32 at a time, one per lane, and flattens
-// every chunk they touch into one work list, one chunk per lane at a time,
-// read with two aligned 16-byte loads (a warp reads contiguous memory). A chunk
-// wholly inside one piece is stored as is. A chunk holding piece boundaries
-// gets bits from consecutive pieces: the piece that covers its first base
-// stores it (zeros elsewhere) and the later ones OR their bits in with
-// atomics, after a warp barrier; pieces are contiguous in the output and the
-// list is in piece order, so that first piece always comes first.
+// The interior chunks of a tile's pieces (all 64 bases inside one piece) are
+// one work list that the warp's lanes walk with forward-only cursors; a chunk
+// with a piece boundary inside is assembled by one lane from every piece
+// overlapping it and stored once (spell_tile_global below).
 #include <cuda_runtime.h>
 
 #include "cg_internal.cuh"
@@ -117,16 +113,216 @@ __device__ __forceinline__ Chunk chunk_bits_aligned(const uint32_t* words, long 
   return c;
 }
 
-constexpr int kWarps = kBlock / 32;
-constexpr int kU = 2;              // chunks per lane in flight
+// Chunks per lane in flight and the blocks per SM the registers must allow.
+// On the 3.1 Gb graph: 2 chunks at 5 blocks (48 registers) 0.361 ms, at 6
+// (40, spilling) 0.367, at 7 (32) 0.405; 3 at 5 0.383; 4 at 4 0.396. The
+// loads wait on memory, and resident warps hide that wait better than more
+// chunks per lane. A variant that staged each tile's input in shared memory
+// with TMA bulk copies (one per piece, on an mbarrier, the next tiles' copies
+// in flight while the current one was spelled) ran 0.45-1.6 ms: the smem
+// buffers left too few warps resident, and the spelling itself, not the
+// loads, then bounds a warp.
+#ifndef CG_EMIT2_U
+#define CG_EMIT2_U 2
+#endif
+#ifndef CG_EMIT2_MIN_BLOCKS
+#define CG_EMIT2_MIN_BLOCKS 5
+#endif
+constexpr int kU = CG_EMIT2_U;     // interior chunks per lane in flight
 
-__global__ void __launch_bounds__(kBlock) k_emit2(Scratch s, const uint8_t* packed, long long packed_bytes,
-                                                  long long readable_words, bool aligned16, uint4* out,
-                                                  long long cap_bytes, int tile_bases, long long t_begin,
-                                                  long long t_end) {
+// Aligned 16-byte loads may serve a piece when its stored bases, widened by
+// one chunk on either side, stay inside the stream's readable words.
+__device__ __forceinline__ bool aligned_ok(bool aligned16, long long src, int rc, long long plen,
+                                           long long readable_words) {
+  const long long low = rc ? src - plen + 1 : src, top = rc ? src : src + plen - 1;
+  return aligned16 && low >= 64 && (top >> 4) + 9 < readable_words;
+}
+
+// The 64 bases whose lowest stored base is p (forward: in stored order;
+// reverse complement: reversed and complemented): five words, four funnel
+// shifts. Unchecked: every word must be readable.
+__device__ __forceinline__ Chunk chunk_at(const uint32_t* words, long long p, int rc) {
+  const uint32_t* q = words + (p >> 4);
+  const unsigned sh = (unsigned)(2 * (p & 15));
+  uint32_t W[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) W[k] = __ldg(q + k);
+  Chunk c;
+  if (rc) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) c.v[k] = revcomp16(__funnelshift_r(W[3 - k], W[4 - k], sh));
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) c.v[k] = __funnelshift_r(W[k], W[k + 1], sh);
+  }
+  return c;
+}
+
+// The same with every word checked against the stream (outside it: 0).
+__device__ __forceinline__ Chunk chunk_at_checked(const uint32_t* words, const uint8_t* bytes, long long full_words,
+                                                  long long packed_bytes, long long p, int rc) {
+  const long long w0 = p >> 4;                  // floor, also for p < 0
+  const unsigned sh = (unsigned)(2 * (p & 15));
+  uint32_t W[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) W[k] = load_word_checked(words, bytes, full_words, packed_bytes, w0 + k);
+  Chunk c;
+  if (rc) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) c.v[k] = revcomp16(__funnelshift_r(W[3 - k], W[4 - k], sh));
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) c.v[k] = __funnelshift_r(W[k], W[k + 1], sh);
+  }
+  return c;
+}
+
+constexpr int kWarps = kBlock / 32;
+
+// Per-warp fields of the group of pieces being spelled.
+struct PieceList {
+  long long oj[32];
+  unsigned long long w[32];
+  int start[33];             // first interior chunk of each piece in the work list; [32] = the total
+  long long ca[32];          // first interior chunk of each piece in the output
+  bool safe[32];
+};
+
+// Spells output tile t from global memory: the tile's pieces 32 at a time, one
+// per lane. The interior chunks of the 32 pieces (chunks whose 64 bases all
+// lie inside one piece) form one work list in piece order, kU chunks per lane
+// in flight; a lane's chunks only move forward through the list, so it finds
+// each chunk's piece by stepping a cursor past the pieces it has left behind
+// (no search), and the piece's address arithmetic is a few operations from
+// the piece's fields in shared memory. A chunk with a piece boundary inside
+// has one owner, the piece that covers its first base (the boundary is that
+// piece's end): the owner's lane gathers the bits of every piece overlapping
+// the chunk (reading their offsets and sources) and stores the chunk once, so
+// no chunk is written twice and nothing needs an atomic. Tiles are whole
+// chunks, so a chunk never spans two tiles.
+__device__ void spell_tile_global(const Scratch& s, const uint8_t* packed, long long packed_bytes,
+                                  long long readable_words, bool aligned16, uint4* out, int tile_bases,
+                                  long long total, long long t, int lane, PieceList& L) {
+  const unsigned full = 0xffffffffu;
+  const uint32_t* words = reinterpret_cast<const uint32_t*>(packed);
+  const long long full_words = packed_bytes >> 2;
+  const int64_t* oo = s.out_off;
+  const unsigned long long* ws = s.wsrc;
+  const int lo = s.tile_seg[t], hi = s.tile_seg[t + 1];
+  const long long tbase = t * (long long)tile_bases;
+  const long long tend = min(tbase + (long long)tile_bases, total);
+  for (int jb = lo; jb <= hi; jb += 32) {
+    const int j = jb + lane;
+    long long oj = 0, oe = 0, a = 0, b = 0;
+    unsigned long long w = 0;
+    if (j <= hi) {
+      oj = oo[j];
+      oe = oo[j + 1];
+      w = ws[j];
+      a = max(oj, tbase);
+      b = min(oe, tend);
+    }
+    const long long ca = (a + 63) >> 6, cb = b >> 6;  // chunks wholly inside [a, b)
+    const int n = a < b && ca < cb ? (int)(cb - ca) : 0;
+    int incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(full, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const int T = __shfl_sync(full, incl, 31);
+    L.oj[lane] = oj;
+    L.w[lane] = w;
+    L.start[lane] = incl - n;
+    if (lane == 31) L.start[32] = T;
+    L.ca[lane] = ca;
+    L.safe[lane] = aligned_ok(aligned16, (long long)(w & ~(1ull << 63)), (int)(w >> 63), oe - oj, readable_words);
+    __syncwarp();
+    // this lane's cursor: the piece of its next chunk, with that piece's fields
+    // kept in registers until the lane's chunks move past it
+    int pc = -1, p_first = 0, p_next = 0, p_rc = 0;
+    long long p_base = 0;                             // stored base at chunk offset 0: x0-independent part
+    bool p_safe = false;
+    for (int f0 = 0; f0 < T; f0 += 32 * kU) {         // warp-uniform trip count
+      Chunk v[kU];
+      long long ci[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int f = f0 + 32 * u + lane;
+        ci[u] = -1;
+        if (f < T) {
+          if (f >= p_next) {                          // chunks only move forward
+            do {
+              ++pc;
+              p_next = L.start[pc + 1];
+            } while (p_next <= f);
+            p_first = L.start[pc];
+            const unsigned long long wl = L.w[pc];
+            p_rc = (int)(wl >> 63);
+            const long long src = (long long)(wl & ~(1ull << 63));
+            const long long x_first = L.ca[pc] << 6, oj = L.oj[pc];
+            // lowest stored base of the piece's first interior chunk; later chunks move 64 bases up (forward)
+            // or down (reverse complement)
+            p_base = p_rc ? src - (x_first - oj) - 63 : src + (x_first - oj);
+            p_safe = L.safe[pc];
+            ci[u] = L.ca[pc] - p_first;               // output chunk = ci + f
+          } else {
+            ci[u] = L.ca[pc] - p_first;
+          }
+          const long long k = f - p_first;
+          const long long p = p_rc ? p_base - 64 * k : p_base + 64 * k;
+          v[u] = p_safe ? chunk_at(words, p, p_rc) : chunk_at_checked(words, packed, full_words, packed_bytes, p, p_rc);
+          ci[u] += f;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u)
+        if (ci[u] >= 0) store_chunk(out, ci[u], v[u]);
+    }
+    // the chunk at this piece's end, when a boundary falls inside it and this
+    // piece covers its first base
+    if (j <= hi && a < b && (b & 63) != 0) {
+      const long long x0 = ((b - 1) >> 6) << 6;
+      if (a <= x0) {
+        Chunk acc;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc.v[k] = 0u;
+        long long pj = j, po = oj, pe = oe;
+        unsigned long long pw = w;
+        for (;;) {
+          const long long lo2 = max(po, x0), hi2 = min(pe, x0 + 64);
+          if (lo2 < hi2) {
+            const int rc = (int)(pw >> 63);
+            const long long src = (long long)(pw & ~(1ull << 63));
+            Chunk v = aligned_ok(aligned16, src, rc, pe - po, readable_words)
+                          ? chunk_bits_aligned(words, x0, po, src, rc)
+                          : chunk_bits<true>(words, packed, full_words, packed_bytes, x0, po, src, rc);
+            keep(v, x0, lo2, hi2);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc.v[k] |= v.v[k];
+          }
+          if (pe >= x0 + 64 || pe >= total) break;          // the chunk (or the stream) ends in this piece
+          ++pj;
+          po = pe;
+          pe = oo[pj + 1];
+          pw = ws[pj];
+        }
+        store_chunk(out, x0 >> 6, acc);
+      }
+    }
+    __syncwarp();                                     // the group's fields are reused by the next group
+  }
+}
+
+// One warp per output tile, persistent grid (spell_tile_global).
+__global__ void __launch_bounds__(kBlock, CG_EMIT2_MIN_BLOCKS) k_emit2(Scratch s, const uint8_t* packed,
+                                                                       long long packed_bytes,
+                                                                       long long readable_words, bool aligned16,
+                                                                       uint4* out, long long cap_bytes,
+                                                                       int tile_bases, long long t_begin,
+                                                                       long long t_end) {
   pdl_enter();
-  __shared__ long long s_oj[kWarps][32], s_w[kWarps][32], s_a[kWarps][32], s_b[kWarps][32];
-  __shared__ int s_start[kWarps][32];
+  __shared__ PieceList lists[kWarps];
   const Counters* c = s.ctr;
   const long long total = *(const volatile long long*)&c->total_bases;
   const long long need = 16 * ((total + 63) / 64);
@@ -134,105 +330,21 @@ __global__ void __launch_bounds__(kBlock) k_emit2(Scratch s, const uint8_t* pack
     if (grid_tid() == 0) set_error(s.derr, DERR_CAPACITY, K_EMIT, need);
     return;
   }
-  const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
-  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
   const long long ntiles = (total + tile_bases - 1) / tile_bases;
-  const uint32_t* words = reinterpret_cast<const uint32_t*>(packed);
-  uint32_t* out_words = reinterpret_cast<uint32_t*>(out);
-  const long long full_words = packed_bytes >> 2;
   const long long t_stop = min(ntiles, t_end);          // the tiles [t_begin, t_end) of this launch
-  for (long long t = t_begin + (grid_tid() >> 5); t < t_stop; t += grid_threads() >> 5) {
-    const int lo = s.tile_seg[t], hi = s.tile_seg[t + 1];
-    const long long tbase = t * (long long)tile_bases;
-    const long long tend = min(tbase + (long long)tile_bases, total);
-    for (int jb = lo; jb <= hi; jb += 32) {
-      const int j = jb + lane;
-      long long oj = 0, a = 0, b = 0;
-      unsigned long long w = 0;
-      int plen = 0;
-      if (j <= hi) {
-        oj = s.out_off[j];
-        const long long oe = s.out_off[j + 1];
-        w = s.wsrc[j];
-        plen = (int)(oe - oj);
-        a = max(oj, tbase);
-        b = min(oe, tend);
-      }
-      const bool valid = a < b;
-      const int rc = (int)(w >> 63);
-      const long long src = (long long)(w & ~(1ull << 63));
-      // chunks the piece touches: [a >> 6, (b - 1) >> 6]
-      const int n = valid ? (int)(((b - 1) >> 6) - (a >> 6) + 1) : 0;
-      // aligned loads are safe for the group when every piece's stored bases
-      // stay 64 bases above the stream start and 9 words below the readable end
-      const long long low = rc ? src - plen + 1 : src, top = rc ? src : src + plen - 1;
-      const bool safe = aligned16 && __all_sync(full, !valid || (low >= 64 && (top >> 4) + 9 < readable_words));
-      int incl = n;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(full, incl, o);
-        if (lane >= o) incl += v;
-      }
-      const int T = __shfl_sync(full, incl, 31);
-      s_oj[wq][lane] = oj;
-      s_w[wq][lane] = (long long)w;
-      s_a[wq][lane] = a;
-      s_b[wq][lane] = b;
-      s_start[wq][lane] = incl - n;
-      __syncwarp();
-      // warp-uniform trip count: every lane reaches the warp barriers below
-      for (int f0 = 0; f0 < T; f0 += 32 * kU) {
-        Chunk v[kU];
-        long long ci[kU];
-        bool fresh[kU];
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-          const int f = f0 + 32 * u + lane;
-          ci[u] = -1;
-          fresh[u] = false;
-          if (f < T) {
-            // the piece of item f: the last lane whose first item is <= f
-            // (starts are nondecreasing; l + step never exceeds 31)
-            int l = 0;
-#pragma unroll
-            for (int step = 16; step > 0; step >>= 1)
-              if (s_start[wq][l + step] <= f) l += step;
-            const long long al = s_a[wq][l], bl = s_b[wq][l];
-            const long long x0 = ((al >> 6) + (f - s_start[wq][l])) << 6;
-            const unsigned long long wl = (unsigned long long)s_w[wq][l];
-            const long long srcl = (long long)(wl & ~(1ull << 63));
-            const int rcl = (int)(wl >> 63);
-            v[u] = safe ? chunk_bits_aligned(words, x0, s_oj[wq][l], srcl, rcl)
-                        : chunk_bits<true>(words, packed, full_words, packed_bytes, x0, s_oj[wq][l], srcl, rcl);
-            if (al > x0 || bl < x0 + 64) keep(v[u], x0, al, bl);
-            ci[u] = x0 >> 6;
-            fresh[u] = al <= x0;               // this piece covers the chunk's first base
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < kU; ++u)
-          if (ci[u] >= 0 && fresh[u]) store_chunk(out, ci[u], v[u]);
-        __syncwarp();
-#pragma unroll
-        for (int u = 0; u < kU; ++u)
-          if (ci[u] >= 0 && !fresh[u]) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-              if (v[u].v[k]) atomicOr(out_words + 4 * ci[u] + k, v[u].v[k]);
-          }
-        __syncwarp();
-      }
-    }
-  }
+  for (long long t = t_begin + (grid_tid() >> 5); t < t_stop; t += grid_threads() >> 5)
+    spell_tile_global(s, packed, packed_bytes, readable_words, aligned16, out, tile_bases, total, t, lane,
+                      lists[threadIdx.x >> 5]);
 }
 
 }  // namespace
 
 cudaError_t launch_emit2(const DevGraph& g, const Scratch& s, const Tuning& t, uint8_t* out, int64_t cap,
                          const LaunchEnv& env, long long t_begin, long long t_end) {
+  const bool aligned16 = (reinterpret_cast<uintptr_t>(g.packed) & 15) == 0;
   static const int resident = resident_blocks(k_emit2);   // once, safely across threads
   const int per_sm = t.emit_blocks_per_sm < resident ? t.emit_blocks_per_sm : resident;
-  const bool aligned16 = (reinterpret_cast<uintptr_t>(g.packed) & 15) == 0;
   cudaError_t e = launch_k(k_emit2, env.num_sms * per_sm, env, env.pdl_first, s, g.packed,
                            (long long)g.packed_bytes, (long long)(g.packed_readable / 4), aligned16,
                            reinterpret_cast<uint4*>(out), (long long)cap, t.tile_bytes, t_begin, t_end);

@@ -67,6 +67,7 @@ struct DevGraph {
   const uint8_t* packed;
   int64_t packed_bytes;
   int64_t packed_readable;     // bytes of `packed` that may be read (>= packed_bytes: padding of owned copies)
+  bool packed_host = false;    // `packed` is pinned host memory read in place over the host link
 };
 
 // Scratch owned by a loaded graph. Sizes in elements (n reads).

@@ -118,6 +118,25 @@ def test_bad_arguments(ctx):
         g.close()
 
 
+def test_many_contigs_few_parts(ctx):
+    """9,000 and 17,000 contigs of a few read counts (long runs of equal
+    weights, several sort tiles) into 2 to 32 parts."""
+    rng = np.random.default_rng(12)
+    G = structured(6, list(rng.choice([2, 3, 5, 8, 13, 40], size=9000)), lone=10)
+    check(ctx, G, [2, 7, 8, 9, 16, 17, 31, 32])
+    G = structured(7, list(rng.choice([2, 3, 4], size=17000)), lone=10)
+    check(ctx, G, [8, 16, 32])
+
+
+def test_one_contig_of_80mb(ctx):
+    """A contig of about 80 Mb with 3 and 32 parts: part sums beyond 32 bits
+    once shifted above the part index, so the assignment takes wide keys."""
+    G = structured(13, [4000, 30, 20, 10, 5, 5, 3, 2, 2, 2], min_len=40000, max_len=40000)
+    orc = oracle.run(G)
+    assert (2 * int(np.diff(orc.contig_off).max()) + 1) << 5 > 2**32
+    check(ctx, G, [3, 32])
+
+
 @pytest.mark.slow
 def test_genome_100mb(ctx):
     G = gen.generate("genome-100Mb", threads=16)
