@@ -32,9 +32,9 @@ METRIC = "contig Gbases/s & ms per graph (plain vs batched) vs HBM roofline; p50
 UNIT = "Gbases/s"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 # DRAM bytes (read + write) per contig base of k_emit from one ncu capture
-# (--set full, the 3.1 Gb recipe on a 450 Mb genome: 551.5 MB for 481,446,585
+# (--set full, the 3.1 Gb recipe on a 450 Mb genome: 552.2 MB for 481,446,585
 # bases), valid only for the emission source it was taken on.
-EMIT_TRAFFIC = {"bytes_per_base": (129.657344e6 + 422.573824e6) / 481446585, "source_sha256_16": "f900c359479bfcf8"}
+EMIT_TRAFFIC = {"bytes_per_base": (129.649152e6 + 422.524672e6) / 481446585, "source_sha256_16": "d79cb01e93ba0316"}
 
 
 def _reduce(x: float, world: int, op: str) -> float:

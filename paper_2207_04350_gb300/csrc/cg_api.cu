@@ -13,6 +13,7 @@
 
 #include "cg.h"
 #include "cg_fault.h"
+#include <nvtx3/nvToolsExt.h>
 #include "cg_internal.cuh"
 
 struct cg_ctx {
@@ -180,12 +181,25 @@ cg_status check_ctx(cg_ctx* c) {
   return CG_OK;
 }
 
-// Brackets one stage with CUDA events when timing is on.
+// An NVTX range around a host-side call (shown by profilers on the host
+// timeline; without a tool attached it costs a few nanoseconds).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
+
+// Brackets one stage with an NVTX range and, when timing is on, CUDA events.
 struct StageTimer {
   cg_ctx* c;
   int k;
   bool on;
-  StageTimer(cg_ctx* c_, int k_) : c(c_), k(k_), on(c_->timing && (!c_->timing_emit_only || k_ == 3)) {
+  Range range;
+  static const char* name(int k) {
+    static const char* const n[4] = {"cg.mask", "cg.chains", "cg.offsets", "cg.emit"};
+    return n[k & 3];
+  }
+  StageTimer(cg_ctx* c_, int k_)
+      : c(c_), k(k_), on(c_->timing && (!c_->timing_emit_only || k_ == 3)), range(name(k_)) {
     if (on) cudaEventRecord(c->ev[2 * k], c->stream);
   }
   ~StageTimer() {
@@ -680,6 +694,7 @@ cg_status cg_free_graph(cg_graph* g) {
 }
 
 cg_status cg_load_graph(cg_ctx* c, const cg_graph_desc* d, uint32_t flags, cg_graph** out) {
+  Range range("cg.load_graph");
   cg_status st = check_ctx(c);
   if (st != CG_OK) return st;
   if (!d || !out) return fail(c, CG_EINVAL, "null argument");
@@ -776,6 +791,7 @@ cg_status cg_load_graph(cg_ctx* c, const cg_graph_desc* d, uint32_t flags, cg_gr
 }
 
 cg_status cg_load_batch(cg_ctx* c, const cg_graph_desc* d, int k, uint32_t flags, cg_graph** out) {
+  Range range("cg.load_batch");
   cg_status st = check_ctx(c);
   if (st != CG_OK) return st;
   if (!d || !out || k < 1) return fail(c, CG_EINVAL, "null argument or empty batch");
@@ -1379,6 +1395,7 @@ cg_status cg_emit_contigs_2bit(cg_graph* g, int64_t* contig_off, int64_t contig_
 
 cg_status cg_transitive_reduction(cg_ctx* c, const cg_graph_desc* d, int32_t fuzz, int64_t* row_ptr, int32_t* col,
                                   uint8_t* code, int32_t* suf, int64_t cap_entries, int mem, int64_t* n_entries) {
+  Range range("cg.transitive_reduction");
   cg_status st = check_ctx(c);
   if (st != CG_OK) return st;
   if (!d) return fail(c, CG_EINVAL, "null argument");
@@ -1487,6 +1504,7 @@ static_assert(cg::kMaxParts == CG_MAX_PARTS, "part limit");
 
 cg_status cg_partition_contigs(cg_graph* g, int32_t n_parts, int32_t weight, int32_t* part, int64_t part_cap,
                                int64_t* part_weight, int mem, int64_t* n_contigs) {
+  Range range("cg.partition_contigs");
   if (!g) return CG_EINVAL;
   cg_ctx* c = g->ctx;
   cg_status st = check_ctx(c);

@@ -20,6 +20,7 @@
 
 #include "cg.h"
 #include "cg_fault.h"
+#include <nvtx3/nvToolsExt.h>
 
 namespace {
 
@@ -219,6 +220,7 @@ cg_status run_union(cg_server* s, Worker& w, std::vector<Request*>& batch) {
 }
 
 void run_batch(cg_server* s, Worker& w, std::vector<Request*>& batch) {
+  nvtxRangePushA("cg.server.batch");
   const int k = (int)batch.size();
   const int64_t t0 = now_ns();
   for (Request* r : batch) {
@@ -253,6 +255,7 @@ void run_batch(cg_server* s, Worker& w, std::vector<Request*>& batch) {
   admit_locked(s);
   s->cv_done.notify_all();
   s->cv_work.notify_all();
+  nvtxRangePop();
 }
 
 void worker_main(cg_server* s, int index) {
