@@ -151,6 +151,9 @@ __global__ void k_validate_entries(DevGraph g, DevError* c) {
 // shared-memory buffers and reach the global lists with one reservation per
 // block at the end (a warp flushes early only when a pass would overflow its
 // buffer): returning atomics on one counter, one per pass, would serialise.
+#ifndef CG_MASK_MIN_BLOCKS
+#define CG_MASK_MIN_BLOCKS 4                   // resident blocks per SM the registers must allow
+#endif
 constexpr int kMaskLane = 8;                  // reads per lane per pass
 constexpr int kMaskSpan = 32 * kMaskLane;     // reads per warp per pass
 constexpr int kMaskWarps = kBlock / 32;
@@ -215,7 +218,7 @@ __device__ __forceinline__ void flush_cands(const Scratch& s, const int32_t* buf
 }
 
 template <typename RP, bool kAligned>
-__global__ void __launch_bounds__(kBlock) k_mask(DevGraph g, Scratch s) {
+__global__ void __launch_bounds__(kBlock, CG_MASK_MIN_BLOCKS) k_mask(DevGraph g, Scratch s) {
   pdl_enter();
   __shared__ int64_t q_row[kMaskWarps][kMaskSpan];   // queued reads: row start
   __shared__ uint16_t q_pos[kMaskWarps][kMaskSpan];  //   and position in the pass | (degree == 2) << 8
@@ -231,20 +234,30 @@ __global__ void __launch_bounds__(kBlock) k_mask(DevGraph g, Scratch s) {
   int32_t* const bl = b_lone[wib];
   unsigned nc = 0, nl = 0;                           // buffered entries (warp-uniform)
   const long long stride = (long long)gridDim.x * kMaskWarps * kMaskSpan;
-  for (long long wbase = ((long long)blockIdx.x * kMaskWarps + wib) * kMaskSpan; wbase < g.n; wbase += stride) {
+  // The row starts of a pass (and, on lane 31, the start after its last read).
+  // They are loaded one pass ahead, so that the next pass's stream of row_ptr
+  // is in flight while this pass resolves its queued reads.
+  const int p0 = kMaskLane * lane;
+  auto load_pass = [&](long long wb, int64_t (&r)[kMaskLane], int64_t& e31) {
+    const int cnt = (int)min((long long)kMaskSpan, g.n - wb);
+    const bool full = cnt == kMaskSpan;
+    if (kAligned && full) {
+      load_rows<RP>(rp + wb + p0, r);
+    } else {
+#pragma unroll
+      for (int j = 0; j < kMaskLane; ++j) r[j] = p0 + j <= cnt ? (int64_t)rp[wb + p0 + j] : 0;
+    }
+    e31 = lane == 31 && full ? (int64_t)rp[wb + kMaskSpan] : 0;
+  };
+  long long wbase = ((long long)blockIdx.x * kMaskWarps + wib) * kMaskSpan;
+  int64_t r[kMaskLane], e31 = 0;
+  if (wbase < g.n) load_pass(wbase, r, e31);
+  for (; wbase < g.n; wbase += stride) {
     // warp-uniform trip count; row_ptr holds n + 1 entries
     const int cnt = (int)min((long long)kMaskSpan, g.n - wbase);
     const bool full = cnt == kMaskSpan;
-    const int p0 = kMaskLane * lane;
-    int64_t r[kMaskLane];
-    if (kAligned && full) {
-      load_rows<RP>(rp + wbase + p0, r);
-    } else {
-#pragma unroll
-      for (int j = 0; j < kMaskLane; ++j) r[j] = p0 + j <= cnt ? (int64_t)rp[wbase + p0 + j] : 0;
-    }
     int64_t e = __shfl_down_sync(0xffffffffu, r[0], 1);
-    if (lane == 31) e = full ? (int64_t)rp[wbase + kMaskSpan] : 0;
+    if (lane == 31) e = e31;
     uint32_t br[2] = {0u, 0u};
     unsigned pend = 0, two = 0, lone = 0;
 #pragma unroll
@@ -257,6 +270,8 @@ __global__ void __launch_bounds__(kBlock) k_mask(DevGraph g, Scratch s) {
       }
     }
     if (g.min_chain > 1) lone = 0;
+    int64_t rn[kMaskLane], en31 = 0;                   // the next pass's row starts, in flight from here
+    if (wbase + stride < g.n) load_pass(wbase + stride, rn, en31);
     if (full) {
       *reinterpret_cast<uint2*>(s.branch + wbase + p0) = make_uint2(br[0], br[1]);
     } else {
@@ -334,6 +349,9 @@ __global__ void __launch_bounds__(kBlock) k_mask(DevGraph g, Scratch s) {
       nc += __popc(cm);
     }
     __syncwarp();                                      // queue and buffers reused next pass
+#pragma unroll
+    for (int j = 0; j < kMaskLane; ++j) r[j] = rn[j];
+    e31 = en31;
   }
   // one reservation per block for the entries the warps still hold
   __syncthreads();
