@@ -972,7 +972,83 @@ def sharded_on_one_gpu(args, ctx, stream, dg, flush, total, whole_ms, n_ranks=8,
                      "gbases_per_s_n_ranks": total / (mx * 1e-3) / 1e9}
     out["lpt"]["weight"] = "bases (cg_partition_contigs, recomputed by every rank every step)"
     out["tiles"]["split"] = "equal runs of 32 KiB output tiles (cg_emit_share)"
+    out["exchange"] = exchange_on_one_gpu(ctx, stream, dg, flush, n_ranks, steps, args.min_chain_reads)
     return out
+
+
+def exchange_on_one_gpu(ctx, stream, dg, flush, n_ranks, steps, mcr):
+    """The same 8-way tile split with each rank holding only its slice of the
+    reads (reads in equal id ranges): per rank, the device time of its side of
+    the read exchange -- mask, chains, layout and packing the pieces every share
+    needs from its reads, then spelling its share from what it received -- each
+    timed alone on this GPU, and the bytes it sends and receives. The all-to-all
+    itself needs several GPUs and is not timed; the received buffers are
+    assembled here from the senders' buffers. Each rank's own reads are read in
+    place from the whole stream (my_off = the graph's offsets of its reads)."""
+    import numpy as np
+    import torch
+
+    from paper_2207_04350_gb300 import cg
+    n = int(dg.len.numel())
+    rf = np.array([n * r // n_ranks for r in range(n_ranks + 1)], dtype=np.int64)
+    nr = type("NR", (), {})()
+    for k in ("row_ptr", "col", "code", "suf", "len", "off"):
+        setattr(nr, k, getattr(dg, k))
+    nr.packed, nr.packed_bytes = None, int(dg.packed.numel())
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    graphs = [cg.cg_load_graph(ctx, nr, flags=cg.BORROW_DEVICE | cg.NO_READS, min_chain_reads=mcr)
+              for _ in range(n_ranks)]
+    try:
+        sizes = [cg.cg_exchange_sizes(graphs[r], n_ranks, rf, r) for r in range(n_ranks)]
+        sends = [torch.empty(max(16, int(sizes[r][0].sum())), dtype=torch.uint8, device="cuda") for r in range(n_ranks)]
+        send_ms, recv_ms = [], []
+        for r in range(n_ranks):
+            my_off = dg.off[int(rf[r]):int(rf[r + 1])]
+            ts = []
+            for i in range(steps + 1):
+                with torch.cuda.stream(stream):
+                    flush.fill_(12)
+                ev0.record(stream)
+                cg.cg_mask_branches(graphs[r], want_count=False)
+                cg.cg_chains(graphs[r], want_counts=False)
+                cg.cg_exchange_pack(graphs[r], n_ranks, rf, r, dg.packed, my_off, sends[r])
+                ev1.record(stream)
+                ev1.synchronize()
+                if i:
+                    ts.append(ev0.elapsed_time(ev1))
+            send_ms.append(statistics.median(ts))
+        for r in range(n_ranks):
+            segs = []
+            for s_ in range(n_ranks):
+                a = int(sizes[s_][0][:r].sum())
+                segs.append(sends[s_][a:a + int(sizes[s_][0][r])])
+            recv = torch.cat(segs)
+            n_contigs, _ = cg.cg_emit_contigs(graphs[r])
+            _, nb = cg.cg_emit_share(graphs[r], r, n_ranks)
+            off = torch.empty(n_contigs + 1, dtype=torch.int64, device="cuda")
+            bases = torch.empty(max(16, (nb + 15) // 16 * 16), dtype=torch.uint8, device="cuda")
+            ts = []
+            for i in range(steps + 1):
+                with torch.cuda.stream(stream):
+                    flush.fill_(13)
+                ev0.record(stream)
+                cg.cg_emit_share_received(graphs[r], n_ranks, rf, r, recv, off, bases)
+                ev1.record(stream)
+                ev1.synchronize()
+                if i:
+                    ts.append(ev0.elapsed_time(ev1))
+            recv_ms.append(statistics.median(ts))
+            del recv
+        total_ms = [a + b for a, b in zip(send_ms, recv_ms)]
+        return {"rank_send_side_ms": send_ms, "rank_receive_side_ms": recv_ms, "max_rank_ms_without_all_to_all":
+                max(total_ms), "rank_send_bytes": [int(x[0].sum()) for x in sizes],
+                "rank_recv_bytes": [int(x[1].sum()) for x in sizes],
+                "note": "reads in 8 equal id ranges; per rank: mask + chains + layout + pack (send side), then the "
+                        "layout again + spelling its share from the received pieces (receive side); the all-to-all "
+                        "between them needs several GPUs and is not timed"}
+    finally:
+        for g in graphs:
+            g.close()
 
 
 def run_sharded(args, rank, world, local_rank):

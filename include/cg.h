@@ -71,10 +71,16 @@ enum { CG_MEM_HOST = 0, CG_MEM_DEVICE = 1 };
 enum {
   CG_BORROW_DEVICE = 1u, /* desc pointers are device memory used in place (must outlive the graph) */
   CG_NO_VALIDATE = 2u,   /* skip the input checks (only for graphs known to be valid) */
-  CG_HOST_READS = 4u     /* host inputs whose packed reads are pinned host memory: the reads stay
+  CG_HOST_READS = 4u,    /* host inputs whose packed reads are pinned host memory: the reads stay
                             there (used in place, must outlive the graph) and the spelling reads
                             only the bases it spells, over the host link; the other arrays are
                             copied. CG_EINVAL when packed is not pinned host memory. */
+  CG_NO_READS = 8u       /* the graph without its reads, for a run split over ranks that each
+                            hold a slice of them (cg_exchange_*): packed must be NULL, off still
+                            places every read in one virtual 2-bit stream of packed_bytes bytes
+                            (any layout; the input checks hold reads to it). The mask, chain and
+                            layout steps run as usual; the spelling calls other than
+                            cg_emit_share_received refuse bases outputs with CG_EINVAL. */
 };
 
 typedef struct cg_ctx cg_ctx;
@@ -294,6 +300,44 @@ CG_API cg_status cg_emit_part(cg_graph* g, const int32_t* part, int64_t part_cap
 CG_API cg_status cg_emit_share(cg_graph* g, int32_t share, int32_t n_shares, int64_t* contig_off,
                                int64_t contig_off_cap, uint8_t* bases, int64_t bases_cap, int mem,
                                int64_t* first_base, int64_t* n_bases);
+
+/* The read exchange of a run split over ranks that each hold only a slice of
+ * the reads: the paper's read exchange (Sec. 4.3), for the split of
+ * cg_emit_share. Rank r owns reads [read_first[r], read_first[r+1]) (host
+ * array of n_shares + 1 entries, from 0 to n, never decreasing) and holds
+ * their bases in a 2-bit stream of its own layout. Every rank loads the whole
+ * graph with CG_NO_READS (its `off` placing reads in a virtual stream, the same
+ * on every rank). For every share p, the pieces of p's output range whose reads
+ * rank r owns travel from r to p, in walk order: each as the 32-bit words that
+ * cover its stored bases in the virtual stream (from its lowest base / 16 to
+ * its highest base / 16 + 1), so the receiver reads them exactly as it would
+ * read the virtual stream. Per rank and step:
+ *   1. cg_exchange_sizes: send_bytes[p] (to share p) and recv_bytes[r] (from
+ *      rank r), host arrays of n_shares entries. Runs the earlier steps first
+ *      and waits for the GPU.
+ *   2. cg_exchange_pack: fills send_buf (device, 4-byte aligned, send_cap >=
+ *      the sum of send_bytes) with the segments for shares 0, 1, ... in order,
+ *      each send_bytes[p] long. my_packed (device, my_packed_bytes) holds this
+ *      rank's reads; my_off[i] (device) is the first base of read
+ *      read_first[rank] + i in it. Waits for the GPU.
+ *   3. an all-to-all (outside the library) that delivers every rank's segment
+ *      for this rank, laid end to end by source rank;
+ *   4. cg_emit_share_received: with recv_buf (device, 4-byte aligned,
+ *      recv_bytes = the sum of recv_bytes of step 1), spells this rank's share
+ *      exactly as cg_emit_share(g, rank, n_shares, ...) spells it from the
+ *      whole stream: bases[0 .. n_bases) = stream bytes [first_base, first_base
+ *      + n_bases); contig_off (optional) gets the whole stream's offsets.
+ *      Device outputs; bases 16-byte aligned; waits for the GPU.
+ * CG_EINVAL for a graph not loaded with CG_NO_READS, bad bounds or sizes. */
+CG_API cg_status cg_exchange_sizes(cg_graph* g, int32_t n_shares, const int64_t* read_first, int32_t rank,
+                                   int64_t* send_bytes, int64_t* recv_bytes);
+CG_API cg_status cg_exchange_pack(cg_graph* g, int32_t n_shares, const int64_t* read_first, int32_t rank,
+                                  const uint8_t* my_packed, int64_t my_packed_bytes, const int64_t* my_off,
+                                  uint8_t* send_buf, int64_t send_cap);
+CG_API cg_status cg_emit_share_received(cg_graph* g, int32_t n_shares, const int64_t* read_first, int32_t rank,
+                                        const uint8_t* recv_buf, int64_t recv_bytes, int64_t* contig_off,
+                                        int64_t contig_off_cap, uint8_t* bases, int64_t bases_cap,
+                                        int64_t* first_base, int64_t* n_bases);
 
 /* Launch parameters of a context's kernels. None changes any output. */
 typedef struct {

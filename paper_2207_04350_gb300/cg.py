@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libcg.so")
 
 CG_OK, CG_EINVAL, CG_ENOMEM, CG_ECUDA, CG_EGRAPH, CG_ETIMEOUT, CG_EBUSY, CG_EKERNEL = range(8)
 MEM_HOST, MEM_DEVICE = 0, 1
-BORROW_DEVICE, NO_VALIDATE, HOST_READS = 1, 2, 4
+BORROW_DEVICE, NO_VALIDATE, HOST_READS, NO_READS = 1, 2, 4, 8
 
 _lock = threading.Lock()
 _lib = None
@@ -75,6 +75,13 @@ API = {
     "cg_emit_share": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64,
                       ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
                       ctypes.POINTER(ctypes.c_int64)],
+    "cg_exchange_sizes": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                          ctypes.c_void_p],
+    "cg_exchange_pack": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                         ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64],
+    "cg_emit_share_received": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                               ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                               ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
     "cg_emit_contigs_2bit": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
                              ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
     "cg_transitive_reduction": [ctypes.c_void_p, ctypes.POINTER(GraphDesc), ctypes.c_int32, ctypes.c_void_p,
@@ -253,7 +260,8 @@ def _desc(graph, min_chain_reads):
     d.col, d.code, d.suf = _ptr(graph.col), _ptr(graph.code), _ptr(suf)
     d.pre, d.post = _ptr(pre), _ptr(post)
     d.len, d.off, d.packed = _ptr(graph.len), _ptr(graph.off), _ptr(graph.packed)
-    d.packed_bytes = _nbytes(graph.packed)
+    # a graph without its reads (NO_READS) gives the size of its virtual stream instead
+    d.packed_bytes = _nbytes(graph.packed) if graph.packed is not None else int(getattr(graph, "packed_bytes", 0))
     d.min_chain_reads = int(min_chain_reads)
     return d
 
@@ -417,6 +425,51 @@ def cg_emit_share(g: Graph, share: int, n_shares: int, contig_off=None, bases=No
                                           mem, ctypes.byref(fb) if want_range else None,
                                           ctypes.byref(nb) if want_range else None))
     return (fb.value, nb.value) if want_range else None
+
+
+def _read_first(read_first, n_shares):
+    rf = np.ascontiguousarray(read_first, dtype=np.int64)
+    if rf.shape != (n_shares + 1,):
+        raise ValueError("read_first needs n_shares + 1 entries")
+    return rf
+
+
+def cg_exchange_sizes(g: Graph, n_shares: int, read_first, rank: int):
+    """Bytes this rank sends to each share and receives from each rank (the read
+    exchange of a split whose ranks hold slices of the reads; graph loaded with
+    NO_READS). Returns (send_bytes, recv_bytes) as host int64 arrays."""
+    rf = _read_first(read_first, n_shares)
+    send = np.zeros(n_shares, np.int64)
+    recv = np.zeros(n_shares, np.int64)
+    _check(g.ctx.ptr, lib().cg_exchange_sizes(g.ptr, int(n_shares), _ptr(rf), int(rank), _ptr(send), _ptr(recv)))
+    return send, recv
+
+
+def cg_exchange_pack(g: Graph, n_shares: int, read_first, rank: int, my_packed, my_off, send_buf):
+    """This rank's segments for every share into send_buf (device uint8): the
+    pieces of each share whose reads this rank owns, from my_packed (device, this
+    rank's reads; my_off[i] = first base of read read_first[rank] + i in it)."""
+    rf = _read_first(read_first, n_shares)
+    for name, t in (("my_packed", my_packed), ("my_off", my_off), ("send_buf", send_buf)):
+        if t is not None and not (_is_torch(t) and t.is_cuda):
+            raise ValueError(f"{name} must be a CUDA tensor")
+    _check(g.ctx.ptr, lib().cg_exchange_pack(g.ptr, int(n_shares), _ptr(rf), int(rank), _ptr(my_packed),
+                                             _nbytes(my_packed) if my_packed is not None else 0, _ptr(my_off),
+                                             _ptr(send_buf), _nbytes(send_buf)))
+
+
+def cg_emit_share_received(g: Graph, n_shares: int, read_first, rank: int, recv_buf, contig_off=None, bases=None):
+    """Spells this rank's share from recv_buf (device uint8: every rank's segment for
+    this rank, by source rank); outputs device tensors as for cg_emit_share.
+    Returns (first_base, n_bases)."""
+    rf = _read_first(read_first, n_shares)
+    fb, nb = ctypes.c_int64(-1), ctypes.c_int64(-1)
+    ocap = len(contig_off) if contig_off is not None else 0
+    bcap = _nbytes(bases) if bases is not None else 0
+    _check(g.ctx.ptr, lib().cg_emit_share_received(g.ptr, int(n_shares), _ptr(rf), int(rank), _ptr(recv_buf),
+                                                   _nbytes(recv_buf) if recv_buf is not None else 0, _ptr(contig_off),
+                                                   ocap, _ptr(bases), bcap, ctypes.byref(fb), ctypes.byref(nb)))
+    return fb.value, nb.value
 
 
 def contigs_part_host(g: Graph, part, p: int):

@@ -411,6 +411,7 @@ cg_status finish_load(cg_graph* g, uint32_t flags) {
   S.wlen = galloc<int32_t>(g, N, &st);
   S.out_off = galloc<int64_t>(g, N + 1, &st);
   S.wfirst = galloc<int32_t>(g, N, &st);
+  if (G.no_reads) S.wread = galloc<int32_t>(g, N, &st);
   S.contig_off = galloc<int64_t>(g, N + 1, &st);
   S.scan_tiles_cap = (int64_t)(N + 2047) / 2048 + 1;
   S.scan_state[0] = galloc<unsigned long long>(g, 3 * ((size_t)S.scan_tiles_cap + 1), &st);
@@ -705,8 +706,11 @@ cg_status cg_load_graph(cg_ctx* c, const cg_graph_desc* d, uint32_t flags, cg_gr
   if (d->row_ptr_bytes != 4 && d->row_ptr_bytes != 8) return fail(c, CG_EINVAL, "row_ptr_bytes must be 4 or 8");
   if (d->mem != CG_MEM_HOST && d->mem != CG_MEM_DEVICE) return fail(c, CG_EINVAL, "bad mem");
   const bool xdrop = d->pre && d->post;
+  const bool no_reads = (flags & CG_NO_READS) != 0;
+  if (no_reads && (d->packed || (flags & CG_HOST_READS)))
+    return fail(c, CG_EINVAL, "CG_NO_READS takes no packed reads (packed_bytes gives the virtual stream's size)");
   if (!d->row_ptr || (m > 0 && (!d->col || !d->code || (!xdrop && !d->suf))) || (n > 0 && (!d->len || !d->off)) ||
-      d->packed_bytes < 0 || (d->packed_bytes > 0 && !d->packed))
+      d->packed_bytes < 0 || (d->packed_bytes > 0 && !d->packed && !no_reads))
     return fail(c, CG_EINVAL, "missing input array");
   const bool borrow = (flags & CG_BORROW_DEVICE) != 0;
   if (borrow && d->mem != CG_MEM_DEVICE) return fail(c, CG_EINVAL, "CG_BORROW_DEVICE needs device inputs");
@@ -718,7 +722,7 @@ cg_status cg_load_graph(cg_ctx* c, const cg_graph_desc* d, uint32_t flags, cg_gr
     if (d->packed_bytes > 0 && !host_packed_dev)
       return fail(c, CG_EINVAL, "CG_HOST_READS needs the packed reads in pinned host memory");
   }
-  if (borrow && (!aligned(d->packed, 16) || !aligned(d->row_ptr, d->row_ptr_bytes) || !aligned(d->col, 4) ||
+  if (borrow && ((!no_reads && !aligned(d->packed, 16)) || !aligned(d->row_ptr, d->row_ptr_bytes) || !aligned(d->col, 4) ||
                  (!xdrop && !aligned(d->suf, 4)) || (xdrop && (!aligned(d->pre, 4) || !aligned(d->post, 4))) ||
                  !aligned(d->len, 4) || !aligned(d->off, 8)))
     return fail(c, CG_EINVAL, "borrowed device inputs are misaligned");
@@ -739,6 +743,8 @@ cg_status cg_load_graph(cg_ctx* c, const cg_graph_desc* d, uint32_t flags, cg_gr
   G.min_chain = d->min_chain_reads <= 0 ? 2 : d->min_chain_reads;
   G.packed_bytes = d->packed_bytes;
   G.packed_readable = borrow || host_reads ? d->packed_bytes : d->packed_bytes + 16;   // owned copies: 16 zero bytes
+  G.no_reads = no_reads;
+  if (no_reads) G.packed_readable = 0;
   if (borrow) {
     G.row_ptr = d->row_ptr;
     G.col = d->col;
@@ -779,8 +785,11 @@ cg_status cg_load_graph(cg_ctx* c, const cg_graph_desc* d, uint32_t flags, cg_gr
     if (host_reads) {
       G.packed = host_packed_dev;
       G.packed_host = true;
+    } else if (no_reads) {
+      G.packed = nullptr;
+    } else if (st == CG_OK) {
+      G.packed = (const uint8_t*)copy_in(d->packed, (size_t)d->packed_bytes, 16);
     }
-    else if (st == CG_OK) G.packed = (const uint8_t*)copy_in(d->packed, (size_t)d->packed_bytes, 16);
     if (st != CG_OK) return bail(st);
   }
 
@@ -797,6 +806,7 @@ cg_status cg_load_batch(cg_ctx* c, const cg_graph_desc* d, int k, uint32_t flags
   if (!d || !out || k < 1) return fail(c, CG_EINVAL, "null argument or empty batch");
   *out = nullptr;
   if (flags & CG_BORROW_DEVICE) return fail(c, CG_EINVAL, "a batch is always copied into one union graph");
+  if (flags & CG_NO_READS) return fail(c, CG_EINVAL, "a batch takes its graphs' reads");
   const bool host_reads = (flags & CG_HOST_READS) != 0;
   std::vector<const uint8_t*> alias(host_reads ? k : 0, nullptr);
   std::vector<int64_t> gbytes(host_reads ? k : 0, 0);
@@ -1008,6 +1018,8 @@ cg_status cg_emit_contigs(cg_graph* g, int64_t* contig_off, int64_t contig_off_c
   cg_ctx* c = g->ctx;
   cg_status st = check_ctx(c);
   if (st != CG_OK) return st;
+  if (g->g.no_reads && bases)
+    return fail(c, CG_EINVAL, "the graph was loaded without its reads: spell a share with cg_emit_share_received");
   if (mem != CG_MEM_HOST && mem != CG_MEM_DEVICE) return fail(c, CG_EINVAL, "bad mem");
   if ((bases && bases_cap < 0) || (contig_off && contig_off_cap < 1)) return fail(c, CG_EINVAL, "bad capacity");
   if (mem == CG_MEM_DEVICE && bases && !g->host_batch) {
@@ -1164,6 +1176,8 @@ cg_status cg_emit_part(cg_graph* g, const int32_t* part, int64_t part_cap, int32
   cg_ctx* c = g->ctx;
   cg_status st = check_ctx(c);
   if (st != CG_OK) return st;
+  if (g->g.no_reads && bases)
+    return fail(c, CG_EINVAL, "the graph was loaded without its reads: spell a share with cg_emit_share_received");
   if (mem != CG_MEM_HOST && mem != CG_MEM_DEVICE) return fail(c, CG_EINVAL, "bad mem");
   if (g->host_batch) return fail(c, CG_EINVAL, "cg_emit_part: not for a batch with host-resident reads");
   if (g->stage < 2) {                  // the contig count: lone reads and chain heads
@@ -1202,6 +1216,8 @@ cg_status cg_emit_share(cg_graph* g, int32_t share, int32_t n_shares, int64_t* c
   cg_ctx* c = g->ctx;
   cg_status st = check_ctx(c);
   if (st != CG_OK) return st;
+  if (g->g.no_reads && bases)
+    return fail(c, CG_EINVAL, "the graph was loaded without its reads: spell a share with cg_emit_share_received");
   if (mem != CG_MEM_HOST && mem != CG_MEM_DEVICE) return fail(c, CG_EINVAL, "bad mem");
   if (n_shares < 1 || share < 0 || share >= n_shares)
     return fail(c, CG_EINVAL, "share %d of %d shares", (int)share, (int)n_shares);
@@ -1282,12 +1298,234 @@ cg_status cg_emit_share(cg_graph* g, int32_t share, int32_t n_shares, int64_t* c
   return CG_OK;
 }
 
+// ------------------------------------------------------------ read exchange
+// Device state of one exchange call: the read bounds, the shares' walk
+// ranges, the first pair of each share's range.
+struct Xchg {
+  cg::XchgArgs x{};
+  std::vector<long long> range, pair0;   // host copies
+  long long n_pairs = 0;
+  void* mem[3] = {nullptr, nullptr, nullptr};
+};
+
+static void x_release(cg_ctx* c, Xchg& X) {
+  for (void*& p : X.mem) {
+    dfree(c, p);
+    p = nullptr;
+  }
+}
+
+// Checks the arguments, lays out the graph if needed and fills X (waits).
+static cg_status x_prepare(cg_graph* g, int32_t n_shares, const int64_t* read_first, int32_t rank, Xchg& X) {
+  cg_ctx* c = g->ctx;
+  if (!g->g.no_reads) return fail(c, CG_EINVAL, "the read exchange is for graphs loaded with CG_NO_READS");
+  if (n_shares < 1 || n_shares > CG_MAX_PARTS || rank < 0 || rank >= n_shares || !read_first)
+    return fail(c, CG_EINVAL, "rank %d of %d shares", (int)rank, (int)n_shares);
+  if (read_first[0] != 0 || read_first[n_shares] != g->g.n) return fail(c, CG_EINVAL, "read_first must run from 0 to n");
+  for (int r = 0; r < n_shares; ++r)
+    if (read_first[r + 1] < read_first[r]) return fail(c, CG_EINVAL, "read_first must not decrease");
+  cg_status st = run_offsets(g);
+  if (st != CG_OK) return st;
+  const int N = n_shares;
+  int64_t* rf = (int64_t*)dalloc(c, (size_t)(N + 1) * 8, &st);
+  long long* range = st == CG_OK ? (long long*)dalloc(c, (size_t)2 * N * 8, &st) : nullptr;
+  long long* pair0 = st == CG_OK ? (long long*)dalloc(c, (size_t)(N + 1) * 8, &st) : nullptr;
+  X.mem[0] = rf;
+  X.mem[1] = range;
+  X.mem[2] = pair0;
+  if (st != CG_OK) return st;
+  CK(cudaMemcpyAsync(rf, read_first, (size_t)(N + 1) * 8, cudaMemcpyHostToDevice, c->stream), "copy read bounds");
+  CK(cg::launch_x_ranges(g->s, N, c->tune.tile_bytes, range, c->env), "share ranges");
+  X.range.assign((size_t)2 * N, 0);
+  CK(cudaMemcpyAsync(X.range.data(), range, (size_t)2 * N * 8, cudaMemcpyDeviceToHost, c->stream), "read ranges");
+  st = wait_and_read(g);
+  if (st != CG_OK) return st;
+  X.pair0.assign((size_t)N + 1, 0);
+  for (int p = 0; p < N; ++p)
+    X.pair0[p + 1] = X.pair0[p] + std::max(0ll, X.range[2 * p + 1] - X.range[2 * p] + 1);
+  X.n_pairs = X.pair0[N];
+  CK(cudaMemcpyAsync(pair0, X.pair0.data(), (size_t)(N + 1) * 8, cudaMemcpyHostToDevice, c->stream), "copy pairs");
+  X.x.rf = rf;
+  X.x.n_shares = N;
+  X.x.rank = rank;
+  X.x.range = range;
+  X.x.pair0 = pair0;
+  return CG_OK;
+}
+
+// Words sent to each share and received from each rank (host vectors; waits).
+static cg_status x_sizes(cg_graph* g, Xchg& X, std::vector<unsigned long long>& send_w,
+                         std::vector<unsigned long long>& recv_w) {
+  cg_ctx* c = g->ctx;
+  const int N = X.x.n_shares;
+  cg_status st = CG_OK;
+  unsigned long long* d = (unsigned long long*)dalloc(c, (size_t)2 * N * 8, &st);
+  if (!d) return st;
+  send_w.assign((size_t)N, 0);
+  recv_w.assign((size_t)N, 0);
+  cudaError_t e = cg::launch_x_sizes(g->s, X.x, d, d + N, X.n_pairs, c->env);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(send_w.data(), d, (size_t)N * 8, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(recv_w.data(), d + N, (size_t)N * 8, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) st = wait_and_read(g);
+  dfree(c, d);
+  if (e != cudaSuccess) return cuda_fail(c, e, "exchange sizes");
+  return st;
+}
+
+// Per-owner exclusive scans over walk ranges: slot arrays of `count` entries.
+static cg_status x_scan(cg_graph* g, Xchg& X, long long j0, long long count, int who, long long* slot) {
+  cg_ctx* c = g->ctx;
+  if (count <= 0) return CG_OK;
+  cg_status st = CG_OK;
+  const long long cap = (count + 2047) / 2048 + 1;
+  unsigned long long* state = (unsigned long long*)dalloc(c, (size_t)(cap + 1) * 8, &st);
+  if (!state) return st;
+  cudaError_t e = cg::launch_x_scan(g->s, X.x, j0, count, who, slot, state, cap, c->env);
+  dfree(c, state);                    // stream-ordered: freed after the scan
+  if (e != cudaSuccess) return cuda_fail(c, e, "exchange scan");
+  return CG_OK;
+}
+
+cg_status cg_exchange_sizes(cg_graph* g, int32_t n_shares, const int64_t* read_first, int32_t rank,
+                            int64_t* send_bytes, int64_t* recv_bytes) {
+  if (!g) return CG_EINVAL;
+  cg_ctx* c = g->ctx;
+  Range range("cg.exchange_sizes");
+  cg_status st = check_ctx(c);
+  if (st != CG_OK) return st;
+  Xchg X;
+  st = x_prepare(g, n_shares, read_first, rank, X);
+  std::vector<unsigned long long> sw, rw;
+  if (st == CG_OK) st = x_sizes(g, X, sw, rw);
+  x_release(c, X);
+  if (st != CG_OK) return st;
+  for (int p = 0; p < n_shares; ++p) {
+    if (send_bytes) send_bytes[p] = (int64_t)(4 * sw[p]);
+    if (recv_bytes) recv_bytes[p] = (int64_t)(4 * rw[p]);
+  }
+  return CG_OK;
+}
+
+cg_status cg_exchange_pack(cg_graph* g, int32_t n_shares, const int64_t* read_first, int32_t rank,
+                           const uint8_t* my_packed, int64_t my_packed_bytes, const int64_t* my_off, uint8_t* send_buf,
+                           int64_t send_cap) {
+  if (!g) return CG_EINVAL;
+  cg_ctx* c = g->ctx;
+  Range range("cg.exchange_pack");
+  cg_status st = check_ctx(c);
+  if (st != CG_OK) return st;
+  if (my_packed_bytes < 0 || (my_packed_bytes > 0 && !my_packed) || send_cap < 0 || !aligned(send_buf, 4) ||
+      !aligned(my_off, 8))
+    return fail(c, CG_EINVAL, "bad exchange buffers");
+  Xchg X;
+  st = x_prepare(g, n_shares, read_first, rank, X);
+  std::vector<unsigned long long> sw, rw;
+  if (st == CG_OK) st = x_sizes(g, X, sw, rw);
+  long long* seg = nullptr;
+  long long* slot = nullptr;
+  if (st == CG_OK) {
+    std::vector<long long> seg_h((size_t)n_shares + 1, 0);
+    for (int p = 0; p < n_shares; ++p) seg_h[p + 1] = seg_h[p] + (long long)sw[p];
+    if (4 * seg_h[n_shares] > send_cap)
+      st = fail(c, CG_EINVAL, "send capacity %lld < %lld", (long long)send_cap, 4 * seg_h[n_shares]);
+    const long long my_reads = read_first[rank + 1] - read_first[rank];
+    if (st == CG_OK && my_reads > 0 && !my_off) st = fail(c, CG_EINVAL, "my_off is required");
+    if (st == CG_OK) seg = (long long*)dalloc(c, (size_t)(n_shares + 1) * 8, &st);
+    if (st == CG_OK) slot = (long long*)dalloc(c, (size_t)std::max(1ll, X.n_pairs) * 8, &st);
+    if (st == CG_OK && seg_h[n_shares] > 0) {
+      cudaError_t e = cudaMemcpyAsync(seg, seg_h.data(), (size_t)(n_shares + 1) * 8, cudaMemcpyHostToDevice, c->stream);
+      if (e != cudaSuccess) st = cuda_fail(c, e, "copy segments");
+      for (int p = 0; p < n_shares && st == CG_OK; ++p)
+        st = x_scan(g, X, X.range[2 * p], X.pair0[p + 1] - X.pair0[p], rank, slot + X.pair0[p]);
+      if (st == CG_OK) {
+        e = cg::launch_x_pack(g->g, g->s, X.x, my_packed, my_packed_bytes, my_off, seg, slot,
+                              reinterpret_cast<uint32_t*>(send_buf), X.n_pairs, c->env);
+        if (e != cudaSuccess) st = cuda_fail(c, e, "exchange pack");
+      }
+      if (st == CG_OK) st = wait_and_read(g);
+    }
+  }
+  dfree(c, seg);
+  dfree(c, slot);
+  x_release(c, X);
+  return st;
+}
+
+cg_status cg_emit_share_received(cg_graph* g, int32_t n_shares, const int64_t* read_first, int32_t rank,
+                                 const uint8_t* recv_buf, int64_t recv_bytes, int64_t* contig_off,
+                                 int64_t contig_off_cap, uint8_t* bases, int64_t bases_cap, int64_t* first_base,
+                                 int64_t* n_bases) {
+  if (!g) return CG_EINVAL;
+  cg_ctx* c = g->ctx;
+  Range range("cg.emit_share_received");
+  cg_status st = check_ctx(c);
+  if (st != CG_OK) return st;
+  if (recv_bytes < 0 || (recv_bytes > 0 && !recv_buf) || !aligned(recv_buf, 4) || (bases && !aligned(bases, 16)) ||
+      (bases && bases_cap < 0) || (contig_off && contig_off_cap < 1))
+    return fail(c, CG_EINVAL, "bad receive or output buffers");
+  Xchg X;
+  st = x_prepare(g, n_shares, read_first, rank, X);
+  std::vector<unsigned long long> sw, rw;
+  if (st == CG_OK) st = x_sizes(g, X, sw, rw);
+  long long* seg = nullptr;
+  long long* slot = nullptr;
+  const long long j0 = X.range.empty() ? 0 : X.range[2 * rank];
+  const long long count = st == CG_OK ? X.pair0[rank + 1] - X.pair0[rank] : 0;
+  if (st == CG_OK) {
+    std::vector<long long> seg_h((size_t)n_shares + 1, 0);
+    for (int r = 0; r < n_shares; ++r) seg_h[r + 1] = seg_h[r] + (long long)rw[r];
+    if (4 * seg_h[n_shares] != recv_bytes)
+      st = fail(c, CG_EINVAL, "received %lld bytes, the layout needs %lld", (long long)recv_bytes, 4 * seg_h[n_shares]);
+    if (st == CG_OK) seg = (long long*)dalloc(c, (size_t)(n_shares + 1) * 8, &st);
+    if (st == CG_OK) slot = (long long*)dalloc(c, (size_t)std::max(1ll, count) * 8, &st);
+    if (st == CG_OK) {
+      cudaError_t e = cudaMemcpyAsync(seg, seg_h.data(), (size_t)(n_shares + 1) * 8, cudaMemcpyHostToDevice, c->stream);
+      if (e != cudaSuccess) st = cuda_fail(c, e, "copy segments");
+    }
+    for (int r = 0; r < n_shares && st == CG_OK; ++r) st = x_scan(g, X, j0, count, r, slot);
+    if (st == CG_OK && count > 0) {
+      cudaError_t e = cg::launch_x_rewrite(g->s, X.x, seg, slot, c->env);
+      if (e != cudaSuccess) st = cuda_fail(c, e, "exchange rewrite");
+    }
+  }
+  if (st == CG_OK) {
+    g->stage = 2;                       // the sources now point into recv_buf: a later call lays out again
+    cg::DevGraph ge = g->g;
+    ge.packed = recv_buf;
+    ge.packed_bytes = recv_bytes;
+    ge.packed_readable = recv_bytes;
+    if (bases) {
+      StageTimer tm(c, 3);
+      cudaError_t e = cg::launch_emit(ge, g->s, c->tune, bases, bases_cap, c->env, 0, 1ll << 62, rank, n_shares);
+      if (e != cudaSuccess) st = cuda_fail(c, e, "emission kernel (received share)");
+    }
+    if (st == CG_OK && contig_off) {
+      cudaError_t e = cg::launch_export_contig_off(g->s, contig_off, contig_off_cap, c->env);
+      if (e != cudaSuccess) st = cuda_fail(c, e, "export contig_off");
+    }
+    if (st == CG_OK) st = wait_and_read(g);
+    if (st == CG_OK) {
+      const int64_t tb = c->tune.tile_bytes, total = c->h_ctr->total_bases;
+      const int64_t T = (total + tb - 1) / tb;
+      const int64_t t0 = (int64_t)rank * T / n_shares, t1 = (int64_t)(rank + 1) * T / n_shares;
+      if (first_base) *first_base = t0 * tb;
+      if (n_bases) *n_bases = std::max<int64_t>(0, std::min(total, t1 * tb) - t0 * tb);
+    }
+  }
+  dfree(c, seg);
+  dfree(c, slot);
+  x_release(c, X);
+  return st;
+}
+
 cg_status cg_emit_contigs_2bit(cg_graph* g, int64_t* contig_off, int64_t contig_off_cap, uint8_t* packed_out,
                                int64_t packed_cap, int mem, int64_t* n_contigs, int64_t* total_bases) {
   if (!g) return CG_EINVAL;
   cg_ctx* c = g->ctx;
   cg_status st = check_ctx(c);
   if (st != CG_OK) return st;
+  if (g->g.no_reads && packed_out)
+    return fail(c, CG_EINVAL, "the graph was loaded without its reads: spell a share with cg_emit_share_received");
   if (mem != CG_MEM_HOST && mem != CG_MEM_DEVICE) return fail(c, CG_EINVAL, "bad mem");
   if ((packed_out && packed_cap < 0) || (contig_off && contig_off_cap < 1)) return fail(c, CG_EINVAL, "bad capacity");
   st = run_offsets(g);

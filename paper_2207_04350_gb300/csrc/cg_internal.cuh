@@ -68,6 +68,7 @@ struct DevGraph {
   int64_t packed_bytes;
   int64_t packed_readable;     // bytes of `packed` that may be read (>= packed_bytes: padding of owned copies)
   bool packed_host = false;    // `packed` is pinned host memory read in place over the host link
+  bool no_reads = false;       // loaded without its reads: `off` places reads in a virtual stream
 };
 
 // Scratch owned by a loaded graph. Sizes in elements (n reads).
@@ -113,6 +114,7 @@ struct Scratch {
   int32_t* wlen;        // n: piece length
   int64_t* out_off;     // n+1
   int32_t* wfirst;      // n: per walk position, the contig whose first read it holds, or -1
+  int32_t* wread;       // n, graphs loaded without their reads only: the read at each walk position
   int64_t* contig_off;  // n+1
   int32_t* tile_seg;    // tiles_cap+1: walk position holding the first byte of each emission tile
   int64_t tiles_cap;
@@ -238,6 +240,32 @@ constexpr int kMaxParts = 1024;
 cudaError_t launch_partition(const Scratch& s, long long C, int weight, long long max_weight, int P,
                              const SortBuffers& b, int32_t* part, int64_t* psum, const LaunchEnv& env);
 int coop_blocks_for_grid_kernels(int num_sms);
+// The read exchange of a run split over ranks that each hold a slice of the
+// reads (cg_exchange_*). rf: device, n_shares + 1 read-id bounds (rank r owns
+// reads [rf[r], rf[r+1])). A share's pieces are the walk positions
+// [range[2p], range[2p+1]] (inclusive; range[2p] > range[2p+1] when empty).
+struct XchgArgs {
+  const int64_t* rf;
+  int n_shares;
+  int rank;
+  const long long* range;       // 2 x n_shares
+  const long long* pair0;       // n_shares + 1: first pair index of each share's range
+};
+// share ranges from the tile map (needs the layout's counters)
+cudaError_t launch_x_ranges(const Scratch& s, int n_shares, int tile_bytes, long long* range, const LaunchEnv& env);
+// words (4 bytes) this rank sends to each share and receives from each rank
+cudaError_t launch_x_sizes(const Scratch& s, const XchgArgs& x, unsigned long long* send_words,
+                           unsigned long long* recv_words, long long n_pairs, const LaunchEnv& env);
+// one exclusive scan over a share's walk positions [j0, j0 + count): for the
+// pieces whose read `who` owns, their word offset among those pieces (slot[i])
+cudaError_t launch_x_scan(const Scratch& s, const XchgArgs& x, long long j0, long long count, int who,
+                          long long* slot, unsigned long long* state, long long state_cap, const LaunchEnv& env);
+cudaError_t launch_x_pack(const DevGraph& g, const Scratch& s, const XchgArgs& x, const uint8_t* my_packed,
+                          long long my_bytes, const int64_t* my_off, const long long* seg, const long long* slot,
+                          uint32_t* send, long long n_pairs, const LaunchEnv& env);
+// the receiver: every piece's source moved into the receive buffer
+cudaError_t launch_x_rewrite(const Scratch& s, const XchgArgs& x, const long long* seg, const long long* slot,
+                             const LaunchEnv& env);
 // Self-test of the look-back scan's bounded wait: scans `tiles` tiles of
 // zeros with `state` (tiles descriptors + the ticket word) prepared by the
 // caller; a ticket that starts at 1 withholds tile 0, so the later tiles'

@@ -203,6 +203,7 @@ __global__ void k_scatter(DevGraph g, Scratch s) {
       s.wsrc[pos[j]] = src;
       s.wlen[pos[j]] = s.part && s.part[cidx[j]] != s.part_p ? 0 : cb;   // another part's contig: empty
       s.wfirst[pos[j]] = rk == 0 ? (int32_t)cidx[j] : -1;
+      if (s.wread) s.wread[pos[j]] = v[j];           // a graph without its reads: for the read exchange
     }
   }
 }

@@ -3,13 +3,15 @@ GPU) holds the whole graph and its reads, runs BranchRemoval and the chain
 stage itself, and spells its own share of the contigs (Alg. 2: the ranks'
 LocalAssembly of the contigs assigned to them, Sec. 4.3-4.4).
 
-The reads are replicated (the 3.1 Gb graph's 23 GB of packed reads fit in
-every GPU's HBM), so the data path has no collective: the paper's induced-
-subgraph redistribution and read exchange only moved data between address
-spaces that here all hold it already. Every rank computes the same chains,
-as the path is deterministic.
+With the reads replicated (ShardedRun; the 3.1 Gb graph's 23 GB of packed
+reads fit in every GPU's HBM) the data path has no collective: the paper's
+induced-subgraph redistribution and read exchange only moved data between
+address spaces that here all hold it already. With each rank holding a slice
+of the reads (ExchangeRun), one all-to-all moves to every rank the bases of
+the pieces it spells: the paper's read exchange. Every rank computes the same
+chains, as the path is deterministic.
 
-Two splits of the spelling work:
+Two splits of the spelling work (ShardedRun; ExchangeRun spells tiles):
 - "tiles" (cg_emit_share): the output stream is cut into `world` runs of
   whole output tiles, so every rank spells the same number of bytes whatever
   the contig sizes; a contig may span two ranks.
@@ -85,6 +87,69 @@ class ShardedRun:
         bases = self.bases[: self.n_bases].cpu().numpy()
         part = self.part[: self.n_contigs].cpu().numpy() if self.part is not None else None
         return off, bases, self.first_base, part
+
+    def close(self):
+        self.g.close()
+
+
+class ExchangeRun:
+    """One rank's share of one graph when every rank holds only a slice of the
+    reads: reads [read_first[rank], read_first[rank + 1]) are this rank's, in
+    my_packed (a device 2-bit stream of this rank's own layout; my_off[i] = the
+    first base of read read_first[rank] + i in it). The rank loads the whole
+    graph without its reads (`graph` with packed None and packed_bytes = the size
+    of the virtual stream its `off` places the reads in), runs the mask, chain
+    and layout steps, sends every share the bases of the pieces it needs from
+    this rank's reads and receives those of its own share from every rank (one
+    all-to-all: the paper's read exchange, Sec. 4.3), then spells its share of
+    the output tiles, as ShardedRun's "tiles" mode does from the whole stream."""
+
+    def __init__(self, ctx: cg.Context, graph, my_packed, my_off, read_first, rank: int, world: int,
+                 min_chain_reads: int = 2, group=None):
+        import torch
+        self.ctx, self.rank, self.world, self.group = ctx, rank, world, group
+        self.read_first = np.ascontiguousarray(read_first, dtype=np.int64)
+        self.my_packed, self.my_off = my_packed, my_off
+        self.g = cg.cg_load_graph(ctx, graph, flags=cg.NO_READS, min_chain_reads=min_chain_reads)
+        self.n_contigs, self.total = cg.cg_emit_contigs(self.g)
+        self.send_bytes, self.recv_bytes = cg.cg_exchange_sizes(self.g, world, self.read_first, rank)
+        self.send = torch.empty(max(16, int(self.send_bytes.sum())), dtype=torch.uint8, device="cuda")
+        self.recv = torch.empty(max(16, int(self.recv_bytes.sum())), dtype=torch.uint8, device="cuda")
+        self.first_base, self.n_bases = cg.cg_emit_share(self.g, rank, world)
+        self.bases = torch.empty(max(16, (self.n_bases + 15) // 16 * 16), dtype=torch.uint8, device="cuda")
+        self.contig_off = torch.empty(self.n_contigs + 1, dtype=torch.int64, device="cuda")
+
+    def _all_to_all(self):
+        import torch
+        import torch.distributed as dist
+        ins, outs = [int(x) for x in self.send_bytes], [int(x) for x in self.recv_bytes]
+        send = self.send[: sum(ins)]
+        recv = self.recv[: sum(outs)]
+        if self.world == 1:
+            recv.copy_(send)
+            return
+        if dist.get_backend(self.group) == "nccl":
+            dist.all_to_all_single(recv, send, outs, ins, group=self.group)
+        else:                                   # gloo moves host tensors
+            r = torch.empty(sum(outs), dtype=torch.uint8)
+            dist.all_to_all_single(r, send.cpu(), outs, ins, group=self.group)
+            recv.copy_(r)
+        torch.cuda.synchronize()                # the library reads recv on its own stream
+
+    def step(self):
+        """One pass: mask, chains, layout, the exchange, then this rank's share."""
+        g = self.g
+        cg.cg_mask_branches(g, want_count=False)
+        cg.cg_chains(g, want_counts=False)
+        cg.cg_exchange_pack(g, self.world, self.read_first, self.rank, self.my_packed, self.my_off, self.send)
+        self._all_to_all()
+        cg.cg_emit_share_received(g, self.world, self.read_first, self.rank, self.recv[: int(self.recv_bytes.sum())],
+                                  self.contig_off, self.bases)
+
+    def result(self):
+        """(contig_off of the whole stream, this share's bases, first_base) as host arrays."""
+        cg.cg_sync(self.ctx)
+        return self.contig_off.cpu().numpy(), self.bases[: self.n_bases].cpu().numpy(), self.first_base
 
     def close(self):
         self.g.close()
