@@ -1035,16 +1035,20 @@ cg_status cg_emit_contigs(cg_graph* g, int64_t* contig_off, int64_t contig_off_c
                            (uint64_t)c->tune.emit_blocks_per_sm);
     key = mix_key(mix_key(mix_key(key, (uint64_t)(uintptr_t)contig_off), (uint64_t)contig_off_cap),
                   stages ? 3 : (timing ? 5 : 4));
+    // the caller's contig offsets come from the piece scan itself (no copy kernel)
+    const bool fold_off = contig_off && g->g.n > 0;
     st = run_stage(g, 6, key, [&]() -> cg_status {
       if (stages) record_stage_event(c, 4);
-      CK(cg::launch_offsets(g->g, g->s, c->tune, c->env), "offset kernels");
+      CK(cg::launch_offsets(g->g, g->s, c->tune, c->env, fold_off ? contig_off : nullptr,
+                            fold_off ? contig_off_cap : 0), "offset kernels");
       if (stages) record_stage_event(c, 5);
       if (timing) record_stage_event(c, 6);
       cg::LaunchEnv env = c->env;
       env.pdl_first = !timing;           // no event node between these kernels and the ones before
       CK(cg::launch_emit(g->g, g->s, c->tune, bases, bases_cap, env), "emission kernel");
       if (timing) record_stage_event(c, 7);
-      if (contig_off) CK(cg::launch_export_contig_off(g->s, contig_off, contig_off_cap, env), "export contig_off");
+      if (contig_off && !fold_off)
+        CK(cg::launch_export_contig_off(g->s, contig_off, contig_off_cap, env), "export contig_off");
       return CG_OK;
     });
     if (st != CG_OK) return st;

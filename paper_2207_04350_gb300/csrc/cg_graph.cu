@@ -871,17 +871,25 @@ __global__ void k_sum_len(DevGraph g, unsigned long long* out) {
 
 // Cooperative launch (all blocks co-resident, as the grid barrier needs);
 // expressed as a launch attribute so that stream capture can record it.
-cudaError_t coop(const void* fn, int blocks, void** args, const LaunchEnv& env) {
+// A cooperative launch (every block resident at once, for the grid barrier).
+// Directly after another kernel of the stage it also carries programmatic
+// dependent launch, like launch_k: no kernel signals its dependents early, so
+// the grid is launched only once every block of the kernel before it has
+// exited (the SMs are free for all of its blocks), and each block waits for
+// that kernel's completion before it touches memory.
+cudaError_t coop(const void* fn, int blocks, void** args, const LaunchEnv& env, bool chained) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(blocks);
   cfg.blockDim = dim3(kBlock);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = env.stream;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = chained && env.pdl && !(env.marks && env.marks->on) ? 2 : 1;
   return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
@@ -941,7 +949,7 @@ cudaError_t launch_chains(const DevGraph& g, const Scratch& s, const Tuning& t, 
   mark(env, "k_listwalk");
   Scratch sc = s;
   void* args[] = {&sc};
-  e = coop((const void*)k_jump, env.coop_blocks, args, env);
+  e = coop((const void*)k_jump, env.coop_blocks, args, env, true);
   if (e != cudaSuccess) return e;
   mark(env, "k_jump");
   DevGraph gg = g;
@@ -949,7 +957,7 @@ cudaError_t launch_chains(const DevGraph& g, const Scratch& s, const Tuning& t, 
   if (e != cudaSuccess) return e;
   mark(env, "k_final");
   void* args2[] = {&gg, &sc};
-  e = coop((const void*)k_cycles, env.coop_blocks, args2, env);
+  e = coop((const void*)k_cycles, env.coop_blocks, args2, env, true);
   if (e != cudaSuccess) return e;
   mark(env, "k_cycles");
   return cudaGetLastError();

@@ -176,7 +176,10 @@ inline void mark(const LaunchEnv& env, const char* name) {
 cudaError_t launch_validate(const DevGraph& g, DevError* derr, const LaunchEnv& env);
 cudaError_t launch_mask(const DevGraph& g, const Scratch& s, const LaunchEnv& env);
 cudaError_t launch_chains(const DevGraph& g, const Scratch& s, const Tuning& t, const LaunchEnv& env);
-cudaError_t launch_offsets(const DevGraph& g, const Scratch& s, const Tuning& t, const LaunchEnv& env);
+// With user_off, the piece scan also writes the caller's contig offsets
+// (user_cap entries; a capacity error and nothing written when too small).
+cudaError_t launch_offsets(const DevGraph& g, const Scratch& s, const Tuning& t, const LaunchEnv& env,
+                           int64_t* user_off = nullptr, long long user_cap = 0);
 // Spells the output tiles [t_begin, t_end) (all of them by default); with
 // n_shares > 1, share `share` of the tiles cut into n_shares equal runs,
 // written from out[0] on (out and cap hold that share only).

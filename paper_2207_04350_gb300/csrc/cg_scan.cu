@@ -68,6 +68,8 @@ struct HeadWordStore {
   int32_t* qd;
   unsigned long long* cbase;
   int64_t* contig_off;
+  int64_t* user_off;           // the caller's contig offsets, written by the piece scan (or nullptr)
+  long long user_cap;
   Counters* c;
   __device__ void item(long long w, unsigned long long e, const int2& it) const {
     unsigned k = (unsigned)(e >> kHeadShift);
@@ -93,6 +95,7 @@ struct HeadWordStore {
     c->n_walk = (unsigned)(total & kHeadLow);
     if (C == 0) {                      // no contigs: the piece scan has nothing to scan
       contig_off[0] = 0;
+      if (user_off && user_cap >= 1) user_off[0] = 0;
       c->total_bases = 0;
       c->n_tiles = 0;
     }
@@ -116,10 +119,21 @@ struct PieceStore {
   long long tile_bytes;
   Counters* c;
   DevError* derr;
+  // The caller's contig offsets, when the offsets are spelled for a caller
+  // buffer in the same replayed stage: written here instead of by a copy kernel
+  // afterwards, and only when all n_contigs + 1 fit (else a capacity error).
+  int64_t* user_off;
+  long long user_cap;
+  __device__ bool user_fits() const {
+    return user_off && (long long)*(const volatile unsigned*)&c->n_contigs + 1 <= user_cap;
+  }
   __device__ void item(long long j, unsigned long long e, const int2& it) const {
     long long o = (long long)e, L = it.x;
     out_off[j] = o;
-    if (it.y >= 0) contig_off[it.y] = o;
+    if (it.y >= 0) {
+      contig_off[it.y] = o;
+      if (user_fits()) user_off[it.y] = o;
+    }
     long long t0 = (o + tile_bytes - 1) / tile_bytes, t1 = (o + L + tile_bytes - 1) / tile_bytes;
     for (long long t = t0; t < t1; ++t) {
       if (t < tiles_cap) tile_seg[t] = (int32_t)j;
@@ -129,6 +143,10 @@ struct PieceStore {
   __device__ void last(long long count, unsigned long long total) const {
     out_off[count] = (long long)total;
     contig_off[c->n_contigs] = (long long)total;
+    if (user_off) {
+      if (user_fits()) user_off[c->n_contigs] = (long long)total;
+      else set_error(derr, DERR_CAPACITY, K_CONTIG_OFF, (long long)c->n_contigs + 1);
+    }
     c->total_bases = (long long)total;
     long long nt = ((long long)total + tile_bytes - 1) / tile_bytes;
     c->n_tiles = (unsigned)nt;
@@ -233,7 +251,8 @@ __global__ void k_export_contig_off(Scratch s, int64_t* out, long long cap) {
 
 }  // namespace
 
-cudaError_t launch_offsets(const DevGraph& g, const Scratch& s, const Tuning& t, const LaunchEnv& env) {
+cudaError_t launch_offsets(const DevGraph& g, const Scratch& s, const Tuning& t, const LaunchEnv& env,
+                           int64_t* user_off, long long user_cap) {
   // No memset: the scans' last steps assign every counter of this stage, and
   // each scan zeroes the other one's descriptors (the heads scan the piece
   // scan's, the piece scan the heads scan's, for the next run); the graph
@@ -249,7 +268,7 @@ cudaError_t launch_offsets(const DevGraph& g, const Scratch& s, const Tuning& t,
     return cudaGetLastError();
   }
   HeadWordLoad hl{s.hb, s.headq};
-  HeadWordStore hs{s.wp, s.headq, s.qd, s.cbase, s.contig_off, s.ctr};
+  HeadWordStore hs{s.wp, s.headq, s.qd, s.cbase, s.contig_off, user_off, user_cap, s.ctr};
   cudaError_t e = launch_k(k_scan<HeadWordLoad, HeadWordStore>, scan_grid(tiles_w, env), env, env.pdl_first, hl, hs,
                            words, (const unsigned*)nullptr, s.scan_state[0], s.scan_tiles_cap, s.derr,
                            (int)K_SCAN_HEADS, s.scan_state[2], state_words);
@@ -260,7 +279,7 @@ cudaError_t launch_offsets(const DevGraph& g, const Scratch& s, const Tuning& t,
   if (e != cudaSuccess) return e;
   mark(env, "k_scatter");
   PieceLoad pl{s.wlen, s.wfirst};
-  PieceStore ps{s.out_off, s.contig_off, s.tile_seg, s.tiles_cap, t.tile_bytes, s.ctr, s.derr};
+  PieceStore ps{s.out_off, s.contig_off, s.tile_seg, s.tiles_cap, t.tile_bytes, s.ctr, s.derr, user_off, user_cap};
   e = launch_k(k_scan<PieceLoad, PieceStore>, scan_grid(tiles_n, env), env, true, pl, ps, 0ll,
                (const unsigned*)&s.ctr->n_walk, s.scan_state[2], s.scan_tiles_cap, s.derr, (int)K_SCAN_OFFSETS,
                s.scan_state[0], state_words);

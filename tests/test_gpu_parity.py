@@ -215,10 +215,23 @@ def test_small_capacity_rejected(ctx):
     with pytest.raises(cg.CgError) as e:
         cg.cg_sync(ctx)
     assert e.value.status == cg.CG_EINVAL
+    # device contig offsets one entry short, spelled in the same replayed stage as
+    # the bases: the piece scan writes none of them and the next wait reports it
+    full = torch.empty((total + 15) // 16 * 16, dtype=torch.uint8, device="cuda")
+    short = torch.full((n_contigs,), -5, dtype=torch.int64, device="cuda")
+    cg.cg_emit_contigs(g, short, full, want_counts=False)
+    with pytest.raises(cg.CgError) as e:
+        cg.cg_sync(ctx)
+    assert e.value.status == cg.CG_EINVAL
+    assert (short.cpu().numpy() == -5).all()
+    off_d = torch.full((n_contigs + 1,), -5, dtype=torch.int64, device="cuda")
+    cg.cg_emit_contigs(g, off_d, full, want_counts=False)
+    cg.cg_sync(ctx)
     off, bases = cg.contigs_host(g)          # still usable
     g.close()
     orc = oracle.run(G)
     assert np.array_equal(bases, orc.bases)
+    assert np.array_equal(off_d.cpu().numpy(), orc.contig_off)
 
 
 @pytest.mark.parametrize("ruler_log2,tile_bytes,bps", [(1, 4096, 1), (2, 8192, 2), (4, 16384, 8), (7, 32768, 4),
