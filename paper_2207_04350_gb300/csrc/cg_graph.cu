@@ -545,9 +545,16 @@ __global__ void k_walk(Scratch s, int ruler_log2, int64_t limit) {
   }
 }
 
-// One thread per list head: walk the list of sublists for the total length,
-// the tail and the smallest read, then again to give each sublist its
-// distance to the tail. Longer lists are left to pointer jumping.
+// One thread per list head, one walk over the list of sublists: each sublist
+// gets the reads before it and its list's head (pj[0][r] = (kViaHead, reads
+// before r, head, 0)), and the list's head the totals (pj[1][head] = (total
+// reads, smallest read, last oriented read, 0)); the finals turn the pair into
+// the reads from r to the tail. Longer lists are left to pointer jumping,
+// which rewrites every record in the direct form (-1, reads to the tail,
+// smallest read, last read) into both buffers, so the finals read that form
+// whenever it ran.
+constexpr int kViaHead = -3;                  // pj x-field of a sublist the list walk resolved
+
 __global__ void k_listwalk(Scratch s) {
   pdl_enter();
   Counters* c = s.ctr;
@@ -559,6 +566,7 @@ __global__ void k_listwalk(Scratch s) {
     bool ok = true;
     for (;;) {
       const int4 rc = s.rec[r];
+      s.pj[0][r] = make_int4(kViaHead, (int32_t)min(total, 0x7fffffffll), r0, 0);
       total += rc.y;
       mn = min(mn, rc.z);
       if (rc.x < 0) {
@@ -572,15 +580,7 @@ __global__ void k_listwalk(Scratch s) {
       atomicOr(&c->need_jump, 1u);
       continue;
     }
-    long long acc = total;
-    r = r0;
-    for (;;) {
-      s.pj[0][r] = make_int4(-1, (int32_t)acc, mn, tail);
-      const int4 rc = s.rec[r];
-      acc -= rc.y;
-      if (rc.x < 0) break;
-      r = rc.x;
-    }
+    s.pj[1][r0] = make_int4((int32_t)total, mn, tail, 0);
   }
 }
 
@@ -689,6 +689,20 @@ __global__ void k_final(DevGraph g, Scratch s) {
     for (int j = 0; j < kFinalItems; ++j) {
       p0[j] = r01[j].x >= 0 ? pj[r01[j].x] : make_int4(0, 0, 0, 0);
       p1[j] = r01[j].z >= 0 ? pj[r01[j].z] : make_int4(0, 0, 0, 0);
+    }
+    // a sublist resolved by the list walk: its list's totals sit at the head
+    // (in the other buffer), and the reads from it to the tail are the total
+    // less the reads before it
+    int4 t0[kFinalItems], t1[kFinalItems];
+#pragma unroll
+    for (int j = 0; j < kFinalItems; ++j) {
+      t0[j] = p0[j].x == kViaHead ? s.pj[fb ^ 1][p0[j].z] : make_int4(0, 0, 0, 0);
+      t1[j] = p1[j].x == kViaHead ? s.pj[fb ^ 1][p1[j].z] : make_int4(0, 0, 0, 0);
+    }
+#pragma unroll
+    for (int j = 0; j < kFinalItems; ++j) {
+      if (p0[j].x == kViaHead) p0[j] = make_int4(-1, t0[j].x - p0[j].y, t0[j].y, t0[j].z);
+      if (p1[j].x == kViaHead) p1[j] = make_int4(-1, t1[j].x - p1[j].y, t1[j].y, t1[j].z);
     }
     bool cyc[kFinalItems], ok[kFinalItems];
     int32_t m[kFinalItems], q[kFinalItems], rk[kFinalItems], o[kFinalItems], L[kFinalItems], sin[kFinalItems],
