@@ -42,6 +42,7 @@ struct cg_ctx {
   cudaStream_t copy_stream = nullptr;  // device-to-host copies overlapping the spelling (created on first use)
   cudaEvent_t copy_ev = nullptr;       //   a chunk spelled / the copies done
   cg::FaultPlan fault;                 // host-side fault injection (tests)
+  bool tile_auto = true;               // tile size chosen per graph until cg_set_tuning sets one
 };
 
 // A captured stage: the instantiated graph and what its capture recorded.
@@ -81,6 +82,8 @@ struct cg_graph {
   uint32_t* hb_dst = nullptr;
   int64_t hb_dst_words = 0;
   cg::DevGraph g_emit{};               // the graph as the spelling sees it (gathered reads)
+  int auto_tile = 32768;               // output tile when the context's tile size is left automatic
+  cg::Tuning tune{};                   // the context's launch parameters as this graph uses them
 };
 
 namespace {
@@ -223,6 +226,15 @@ void record_stage_event(cg_ctx* c, int i) {
 
 uint64_t mix_key(uint64_t h, uint64_t v) { return (h ^ (v + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2))); }
 
+// The launch parameters a graph's stages use: the context's, with the output
+// tile chosen per graph (from the graph's total read length) unless the caller
+// set one. Smaller outputs get smaller tiles, so that more warps share them.
+const cg::Tuning& gt(cg_graph* g) {
+  g->tune = g->ctx->tune;
+  if (g->ctx->tile_auto) g->tune.tile_bytes = g->auto_tile;
+  return g->tune;
+}
+
 // Runs one stage's launches. With graphs on, the launches are captured once
 // into a CUDA graph per (stage, key) and replayed with a single launch; the
 // key covers every host-side value the launches bake in (buffers, sizes,
@@ -292,8 +304,8 @@ cg_status run_chains(cg_graph* g) {
     if (st0 != CG_OK) return st0;
   }
   StageTimer tm(c, 1);
-  cg_status st = run_stage(g, 1, (uint64_t)c->tune.ruler_log2, [&]() -> cg_status {
-    CK(cg::launch_chains(g->g, g->s, c->tune, c->env), "chain kernels");
+  cg_status st = run_stage(g, 1, (uint64_t)gt(g).ruler_log2, [&]() -> cg_status {
+    CK(cg::launch_chains(g->g, g->s, gt(g), c->env), "chain kernels");
     return CG_OK;
   });
   if (st != CG_OK) return st;
@@ -308,8 +320,8 @@ cg_status run_offsets(cg_graph* g) {
     if (st0 != CG_OK) return st0;
   }
   StageTimer tm(c, 2);
-  cg_status st = run_stage(g, 2, (uint64_t)c->tune.tile_bytes, [&]() -> cg_status {
-    CK(cg::launch_offsets(g->g, g->s, c->tune, c->env), "offset kernels");
+  cg_status st = run_stage(g, 2, (uint64_t)gt(g).tile_bytes, [&]() -> cg_status {
+    CK(cg::launch_offsets(g->g, g->s, gt(g), c->env), "offset kernels");
     return CG_OK;
   });
   if (st != CG_OK) return st;
@@ -436,6 +448,9 @@ cg_status finish_load(cg_graph* g, uint32_t flags) {
   if (st != CG_OK) return st;
   if (c->fault.hit("bad_graph")) return fail(c, CG_EGRAPH, "injected: invalid string graph");
   g->sum_len = (int64_t)*c->h_u64;
+  // automatic output tile: 4 KiB below 128 Mbases of reads, doubling per doubling, 32 KiB from 1 Gbase
+  g->auto_tile = 4096;
+  while (g->auto_tile < 32768 && g->sum_len >= ((int64_t)1 << 27) * (g->auto_tile / 4096)) g->auto_tile *= 2;
   // the longest possible output is every read spelled whole; tiles of at least 4 KiB
   S.tiles_cap = g->sum_len / 4096 + 2;
   S.tile_seg = galloc<int32_t>(g, (size_t)S.tiles_cap + 1, &st);
@@ -553,16 +568,19 @@ cg_status cg_set_tuning(cg_ctx* c, const cg_tuning* t) {
     if (t->ruler_log2 > 12) return fail(c, CG_EINVAL, "ruler_log2 must be in 1..12");
     n.ruler_log2 = t->ruler_log2;
   }
+  bool tile_set = false;
   if (t->tile_bytes > 0) {
     if (t->tile_bytes < 4096 || t->tile_bytes > 131072 || (t->tile_bytes & (t->tile_bytes - 1)))
       return fail(c, CG_EINVAL, "tile_bytes must be a power of two from 4096 to 131072");
     n.tile_bytes = t->tile_bytes;
+    tile_set = true;
   }
   if (t->emit_blocks_per_sm > 0) {
     if (t->emit_blocks_per_sm > 8) return fail(c, CG_EINVAL, "emit_blocks_per_sm must be in 1..8");
     n.emit_blocks_per_sm = t->emit_blocks_per_sm;
   }
   c->tune = n;
+  if (tile_set) c->tile_auto = false;
   return CG_OK;
 }
 
@@ -1031,21 +1049,21 @@ cg_status cg_emit_contigs(cg_graph* g, int64_t* contig_off, int64_t contig_off_c
     }
     const bool timing = c->timing != 0, stages = timing && !c->timing_emit_only;
     uint64_t key = mix_key(mix_key(mix_key(mix_key((uint64_t)(uintptr_t)bases, (uint64_t)bases_cap),
-                                           (uint64_t)(uintptr_t)g->g.packed), (uint64_t)c->tune.tile_bytes),
-                           (uint64_t)c->tune.emit_blocks_per_sm);
+                                           (uint64_t)(uintptr_t)g->g.packed), (uint64_t)gt(g).tile_bytes),
+                           (uint64_t)gt(g).emit_blocks_per_sm);
     key = mix_key(mix_key(mix_key(key, (uint64_t)(uintptr_t)contig_off), (uint64_t)contig_off_cap),
                   stages ? 3 : (timing ? 5 : 4));
     // the caller's contig offsets come from the piece scan itself (no copy kernel)
     const bool fold_off = contig_off && g->g.n > 0;
     st = run_stage(g, 6, key, [&]() -> cg_status {
       if (stages) record_stage_event(c, 4);
-      CK(cg::launch_offsets(g->g, g->s, c->tune, c->env, fold_off ? contig_off : nullptr,
+      CK(cg::launch_offsets(g->g, g->s, gt(g), c->env, fold_off ? contig_off : nullptr,
                             fold_off ? contig_off_cap : 0), "offset kernels");
       if (stages) record_stage_event(c, 5);
       if (timing) record_stage_event(c, 6);
       cg::LaunchEnv env = c->env;
       env.pdl_first = !timing;           // no event node between these kernels and the ones before
-      CK(cg::launch_emit(g->g, g->s, c->tune, bases, bases_cap, env), "emission kernel");
+      CK(cg::launch_emit(g->g, g->s, gt(g), bases, bases_cap, env), "emission kernel");
       if (timing) record_stage_event(c, 7);
       if (contig_off && !fold_off)
         CK(cg::launch_export_contig_off(g->s, contig_off, contig_off_cap, env), "export contig_off");
@@ -1074,10 +1092,10 @@ cg_status cg_emit_contigs(cg_graph* g, int64_t* contig_off, int64_t contig_off_c
       if (!aligned(bases, 16)) return fail(c, CG_EINVAL, "device bases buffer must be 16-byte aligned");
       StageTimer tm(c, 3);
       uint64_t key = mix_key(mix_key(mix_key(mix_key((uint64_t)(uintptr_t)bases, (uint64_t)bases_cap),
-                                             (uint64_t)(uintptr_t)emit_graph(g).packed), (uint64_t)c->tune.tile_bytes),
-                             (uint64_t)c->tune.emit_blocks_per_sm);
+                                             (uint64_t)(uintptr_t)emit_graph(g).packed), (uint64_t)gt(g).tile_bytes),
+                             (uint64_t)gt(g).emit_blocks_per_sm);
       st = run_stage(g, 3, key, [&]() -> cg_status {
-        CK(cg::launch_emit(emit_graph(g), g->s, c->tune, bases, bases_cap, c->env), "emission kernel");
+        CK(cg::launch_emit(emit_graph(g), g->s, gt(g), bases, bases_cap, c->env), "emission kernel");
         return CG_OK;
       });
       if (st != CG_OK) return st;
@@ -1120,12 +1138,12 @@ cg_status cg_emit_contigs(cg_graph* g, int64_t* contig_off, int64_t contig_off_c
         CK(cudaEventCreateWithFlags(&c->copy_ev, cudaEventDisableTiming), "copy event");
       }
       StageTimer tm(c, 3);
-      const int64_t tb = c->tune.tile_bytes;
+      const int64_t tb = gt(g).tile_bytes;
       const int64_t tiles = (total + tb - 1) / tb, per = std::max<int64_t>(1, kChunk / tb);
       for (int64_t t0 = 0; t0 < tiles; t0 += per) {
         const int64_t t1 = std::min(tiles, t0 + per);
         const int64_t b0 = t0 * tb, b1 = std::min(total, t1 * tb);
-        CK(cg::launch_emit(emit_graph(g), g->s, c->tune, g->stage_bases, g->stage_bases_cap, c->env, t0, t1),
+        CK(cg::launch_emit(emit_graph(g), g->s, gt(g), g->stage_bases, g->stage_bases_cap, c->env, t0, t1),
            "emission kernel");
         CK(cudaEventRecord(c->copy_ev, c->stream), "chunk event");
         CK(cudaStreamWaitEvent(c->copy_stream, c->copy_ev, 0), "copy stream wait");
@@ -1151,9 +1169,9 @@ cg_status cg_emit_contigs(cg_graph* g, int64_t* contig_off, int64_t contig_off_c
         StageTimer tm(c, 3);
         uint64_t key = mix_key(mix_key(mix_key(mix_key((uint64_t)(uintptr_t)dst, (uint64_t)dcap),
                                            (uint64_t)(uintptr_t)emit_graph(g).packed),
-                                       (uint64_t)c->tune.tile_bytes), (uint64_t)c->tune.emit_blocks_per_sm);
+                                       (uint64_t)gt(g).tile_bytes), (uint64_t)gt(g).emit_blocks_per_sm);
         st = run_stage(g, 3, key, [&]() -> cg_status {
-          CK(cg::launch_emit(emit_graph(g), g->s, c->tune, dst, dcap, c->env), "emission kernel");
+          CK(cg::launch_emit(emit_graph(g), g->s, gt(g), dst, dcap, c->env), "emission kernel");
           return CG_OK;
         });
         if (st != CG_OK) return st;
@@ -1233,7 +1251,7 @@ cg_status cg_emit_share(cg_graph* g, int32_t share, int32_t n_shares, int64_t* c
     if (st != CG_OK) return st;
   }
   // the share's stream range, from the stream's size (known on the host after a wait)
-  const int64_t tb = c->tune.tile_bytes;
+  const int64_t tb = gt(g).tile_bytes;
   auto range = [&](int64_t total, int64_t* fb, int64_t* nb) {
     const int64_t T = (total + tb - 1) / tb;
     const int64_t t0 = (int64_t)share * T / n_shares, t1 = (int64_t)(share + 1) * T / n_shares;
@@ -1244,10 +1262,10 @@ cg_status cg_emit_share(cg_graph* g, int32_t share, int32_t n_shares, int64_t* c
     StageTimer tm(c, 3);
     uint64_t key = mix_key(mix_key(mix_key(mix_key((uint64_t)(uintptr_t)dst, (uint64_t)cap),
                                            (uint64_t)(uintptr_t)emit_graph(g).packed), (uint64_t)tb),
-                           (uint64_t)c->tune.emit_blocks_per_sm);
+                           (uint64_t)gt(g).emit_blocks_per_sm);
     key = mix_key(mix_key(key, (uint64_t)share), (uint64_t)n_shares);
     return run_stage(g, 3, key, [&]() -> cg_status {
-      CK(cg::launch_emit(emit_graph(g), g->s, c->tune, dst, cap, c->env, 0, 1ll << 62, share, n_shares),
+      CK(cg::launch_emit(emit_graph(g), g->s, gt(g), dst, cap, c->env, 0, 1ll << 62, share, n_shares),
          "emission kernel (one share)");
       return CG_OK;
     });
@@ -1339,7 +1357,7 @@ static cg_status x_prepare(cg_graph* g, int32_t n_shares, const int64_t* read_fi
   X.mem[2] = pair0;
   if (st != CG_OK) return st;
   CK(cudaMemcpyAsync(rf, read_first, (size_t)(N + 1) * 8, cudaMemcpyHostToDevice, c->stream), "copy read bounds");
-  CK(cg::launch_x_ranges(g->s, N, c->tune.tile_bytes, range, c->env), "share ranges");
+  CK(cg::launch_x_ranges(g->s, N, gt(g).tile_bytes, range, c->env), "share ranges");
   X.range.assign((size_t)2 * N, 0);
   CK(cudaMemcpyAsync(X.range.data(), range, (size_t)2 * N * 8, cudaMemcpyDeviceToHost, c->stream), "read ranges");
   st = wait_and_read(g);
@@ -1500,7 +1518,7 @@ cg_status cg_emit_share_received(cg_graph* g, int32_t n_shares, const int64_t* r
     ge.packed_readable = recv_bytes;
     if (bases) {
       StageTimer tm(c, 3);
-      cudaError_t e = cg::launch_emit(ge, g->s, c->tune, bases, bases_cap, c->env, 0, 1ll << 62, rank, n_shares);
+      cudaError_t e = cg::launch_emit(ge, g->s, gt(g), bases, bases_cap, c->env, 0, 1ll << 62, rank, n_shares);
       if (e != cudaSuccess) st = cuda_fail(c, e, "emission kernel (received share)");
     }
     if (st == CG_OK && contig_off) {
@@ -1509,7 +1527,7 @@ cg_status cg_emit_share_received(cg_graph* g, int32_t n_shares, const int64_t* r
     }
     if (st == CG_OK) st = wait_and_read(g);
     if (st == CG_OK) {
-      const int64_t tb = c->tune.tile_bytes, total = c->h_ctr->total_bases;
+      const int64_t tb = gt(g).tile_bytes, total = c->h_ctr->total_bases;
       const int64_t T = (total + tb - 1) / tb;
       const int64_t t0 = (int64_t)rank * T / n_shares, t1 = (int64_t)(rank + 1) * T / n_shares;
       if (first_base) *first_base = t0 * tb;
@@ -1541,10 +1559,10 @@ cg_status cg_emit_contigs_2bit(cg_graph* g, int64_t* contig_off, int64_t contig_
   auto emit = [&](uint8_t* dst, int64_t cap) -> cg_status {
     StageTimer tm(c, 3);
     uint64_t key = mix_key(mix_key(mix_key(mix_key((uint64_t)(uintptr_t)dst, (uint64_t)cap),
-                                           (uint64_t)(uintptr_t)emit_graph(g).packed), (uint64_t)c->tune.tile_bytes),
-                           (uint64_t)c->tune.emit_blocks_per_sm);
+                                           (uint64_t)(uintptr_t)emit_graph(g).packed), (uint64_t)gt(g).tile_bytes),
+                           (uint64_t)gt(g).emit_blocks_per_sm);
     return run_stage(g, 5, key, [&]() -> cg_status {
-      CK(cg::launch_emit2(emit_graph(g), g->s, c->tune, dst, cap, c->env), "2-bit emission kernel");
+      CK(cg::launch_emit2(emit_graph(g), g->s, gt(g), dst, cap, c->env), "2-bit emission kernel");
       return CG_OK;
     });
   };
@@ -1591,12 +1609,12 @@ cg_status cg_emit_contigs_2bit(cg_graph* g, int64_t* contig_off, int64_t contig_
         CK(cudaEventCreateWithFlags(&c->copy_ev, cudaEventDisableTiming), "copy event");
       }
       StageTimer tm(c, 3);
-      const int64_t tb = c->tune.tile_bytes, tile_out = tb / 4;   // a tile holds tb bases, tb / 4 bytes
+      const int64_t tb = gt(g).tile_bytes, tile_out = tb / 4;   // a tile holds tb bases, tb / 4 bytes
       const int64_t tiles = (total + tb - 1) / tb, per = std::max<int64_t>(1, kChunk / tile_out);
       for (int64_t t0 = 0; t0 < tiles; t0 += per) {
         const int64_t t1 = std::min(tiles, t0 + per);
         const int64_t b0 = t0 * tile_out, b1 = std::min(need, t1 * tile_out);
-        CK(cg::launch_emit2(emit_graph(g), g->s, c->tune, g->stage_bases, g->stage_bases_cap, c->env, t0, t1),
+        CK(cg::launch_emit2(emit_graph(g), g->s, gt(g), g->stage_bases, g->stage_bases_cap, c->env, t0, t1),
            "2-bit emission kernel");
         CK(cudaEventRecord(c->copy_ev, c->stream), "chunk event");
         CK(cudaStreamWaitEvent(c->copy_stream, c->copy_ev, 0), "copy stream wait");
