@@ -1346,8 +1346,11 @@ static cg_status x_prepare(cg_graph* g, int32_t n_shares, const int64_t* read_fi
   if (read_first[0] != 0 || read_first[n_shares] != g->g.n) return fail(c, CG_EINVAL, "read_first must run from 0 to n");
   for (int r = 0; r < n_shares; ++r)
     if (read_first[r + 1] < read_first[r]) return fail(c, CG_EINVAL, "read_first must not decrease");
-  cg_status st = run_offsets(g);
-  if (st != CG_OK) return st;
+  cg_status st = CG_OK;
+  if (g->stage < 3) {                  // the layout of the last call stands unless a later step changed it
+    st = run_offsets(g);
+    if (st != CG_OK) return st;
+  }
   const int N = n_shares;
   int64_t* rf = (int64_t*)dalloc(c, (size_t)(N + 1) * 8, &st);
   long long* range = st == CG_OK ? (long long*)dalloc(c, (size_t)2 * N * 8, &st) : nullptr;
@@ -1457,8 +1460,15 @@ cg_status cg_exchange_pack(cg_graph* g, int32_t n_shares, const int64_t* read_fi
     if (st == CG_OK && seg_h[n_shares] > 0) {
       cudaError_t e = cudaMemcpyAsync(seg, seg_h.data(), (size_t)(n_shares + 1) * 8, cudaMemcpyHostToDevice, c->stream);
       if (e != cudaSuccess) st = cuda_fail(c, e, "copy segments");
-      for (int p = 0; p < n_shares && st == CG_OK; ++p)
-        st = x_scan(g, X, X.range[2 * p], X.pair0[p + 1] - X.pair0[p], rank, slot + X.pair0[p]);
+      if (st == CG_OK) {               // one scan over every share's pairs
+        const long long cap = (X.n_pairs + 2047) / 2048 + 1;
+        unsigned long long* state = (unsigned long long*)dalloc(c, (size_t)(cap + 1) * 8, &st);
+        if (state) {
+          e = cg::launch_x_scan_pairs(g->s, X.x, X.n_pairs, slot, state, cap, c->env);
+          dfree(c, state);
+          if (e != cudaSuccess) st = cuda_fail(c, e, "exchange scan");
+        }
+      }
       if (st == CG_OK) {
         e = cg::launch_x_pack(g->g, g->s, X.x, my_packed, my_packed_bytes, my_off, seg, slot,
                               reinterpret_cast<uint32_t*>(send_buf), X.n_pairs, c->env);

@@ -140,6 +140,25 @@ struct XStore {
   __device__ void last(long long, unsigned long long) const {}
 };
 
+// Scan over all pairs (the shares' ranges end to end): the words of the
+// pieces this rank owns; every pair gets its exclusive prefix, so that a
+// piece's offset in its share's segment is its prefix less the prefix at the
+// share's first pair.
+struct XPairLoad {
+  Scratch s;
+  XchgArgs x;
+  __device__ unsigned long long operator()(long long i) const {
+    const int p = share_of_pair(x, i);
+    const XPiece q = x_piece(s, x, x.range[2 * p] + (i - x.pair0[p]));
+    return q.owner == x.rank ? (unsigned long long)q.words : 0ull;
+  }
+};
+struct XPairStore {
+  long long* slot;
+  __device__ void item(long long i, unsigned long long e) const { slot[i] = (long long)e; }
+  __device__ void last(long long, unsigned long long) const {}
+};
+
 __device__ __forceinline__ uint32_t word_checked(const uint32_t* words, const uint8_t* bytes, long long n_bytes,
                                                  long long w) {
   if (w < 0) return 0u;
@@ -169,7 +188,7 @@ __global__ void k_x_pack(DevGraph g, Scratch s, XchgArgs x, const uint8_t* my_pa
     if (q.owner != x.rank || q.words == 0) continue;        // uniform across the warp
     const long long v = s.wread[j];
     const long long delta = my_off[v - my_first] - g.off[v];
-    uint32_t* dst = send + seg[p] + slot[i];
+    uint32_t* dst = send + seg[p] + (slot[i] - slot[x.pair0[p]]);
     for (long long k = lane; k < q.words; k += 32) {
       const long long b = 16 * (q.W0 + k) + delta;          // the word's first base in this rank's stream
       const long long w = b >> 4;                            // floor, also below 0
@@ -228,6 +247,18 @@ cudaError_t launch_x_rewrite(const Scratch& s, const XchgArgs& x, const long lon
                              const LaunchEnv& env) {
   k_x_rewrite<<<env.num_sms * 4, kBlock, 0, env.stream>>>(s, x, seg, slot);
   mark(env, "k_x_rewrite");
+  return cudaGetLastError();
+}
+
+cudaError_t launch_x_scan_pairs(const Scratch& s, const XchgArgs& x, long long n_pairs, long long* slot,
+                                unsigned long long* state, long long state_cap, const LaunchEnv& env) {
+  if (n_pairs <= 0) return cudaSuccess;
+  const long long tiles = (n_pairs + kTileItems - 1) / kTileItems;
+  if (tiles > state_cap) return cudaErrorInvalidValue;
+  cudaMemsetAsync(state, 0, (size_t)(state_cap + 1) * sizeof(unsigned long long), env.stream);
+  k_scan<<<scan_grid(tiles, env), kBlock, 0, env.stream>>>(XPairLoad{s, x}, XPairStore{slot}, n_pairs, nullptr, state,
+                                                           state_cap, s.derr, (int)K_SCAN_OFFSETS);
+  mark(env, "k_scan_exchange_pairs");
   return cudaGetLastError();
 }
 

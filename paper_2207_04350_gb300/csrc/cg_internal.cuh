@@ -263,6 +263,11 @@ cudaError_t launch_x_sizes(const Scratch& s, const XchgArgs& x, unsigned long lo
 // pieces whose read `who` owns, their word offset among those pieces (slot[i])
 cudaError_t launch_x_scan(const Scratch& s, const XchgArgs& x, long long j0, long long count, int who,
                           long long* slot, unsigned long long* state, long long state_cap, const LaunchEnv& env);
+// the sender: one exclusive scan over all pairs of the words of the pieces it
+// owns (slot[i] for every pair; a piece's offset in its share's segment is
+// slot[i] - slot[first pair of that share])
+cudaError_t launch_x_scan_pairs(const Scratch& s, const XchgArgs& x, long long n_pairs, long long* slot,
+                                unsigned long long* state, long long state_cap, const LaunchEnv& env);
 cudaError_t launch_x_pack(const DevGraph& g, const Scratch& s, const XchgArgs& x, const uint8_t* my_packed,
                           long long my_bytes, const int64_t* my_off, const long long* seg, const long long* slot,
                           uint32_t* send, long long n_pairs, const LaunchEnv& env);
