@@ -114,12 +114,15 @@ __device__ __forceinline__ Chunk chunk_bits_aligned(const uint32_t* words, long 
 }
 
 // Chunks per lane in flight and the blocks per SM the registers must allow.
-// On the 3.1 Gb graph: 2 chunks at 5 blocks (48 registers) 0.361 ms, at 6
-// (40, spilling) 0.367, at 7 (32) 0.405; 3 at 5 0.383; 4 at 4 0.396. The
-// loads wait on memory, and resident warps hide that wait better than more
-// chunks per lane. A variant that staged each tile's input in shared memory
-// with TMA bulk copies (one per piece, on an mbarrier, the next tiles' copies
-// in flight while the current one was spelled) ran 0.45-1.6 ms: the smem
+// On the 3.1 Gb graph, with each tile's sources prefetched to L2: 2 chunks at
+// 5 blocks (48 registers) 0.335 ms, at 6 0.360; 1 at 6 0.346, at 8 0.387; 3
+// at 5 0.354, at 4 0.346; 4 at 4 0.345. The loads wait on memory, and
+// resident warps hide that wait better than more chunks per lane. Keeping
+// more chunks in flight without registers, through a per-lane ring in shared
+// memory filled by 4-byte cp.async copies (2 to 4 chunks ahead), ran 0.367-
+// 0.383 ms. A variant that staged each tile's input in shared memory with
+// TMA bulk copies (one per piece, on an mbarrier, the next tiles' copies in
+// flight while the current one was spelled) ran 0.45-1.6 ms: the smem
 // buffers left too few warps resident, and the spelling itself, not the
 // loads, then bounds a warp.
 #ifndef CG_EMIT2_U
@@ -138,12 +141,10 @@ __device__ __forceinline__ bool aligned_ok(bool aligned16, long long src, int rc
   return aligned16 && low >= 64 && (top >> 4) + 9 < readable_words;
 }
 
-// The 64 bases whose lowest stored base is p (forward: in stored order;
-// reverse complement: reversed and complemented): five words, four funnel
-// shifts. Unchecked: every word must be readable.
-__device__ __forceinline__ Chunk chunk_at(const uint32_t* words, long long p, int rc) {
-  const uint32_t* q = words + (p >> 4);
-  const unsigned sh = (unsigned)(2 * (p & 15));
+// The 64 bases whose lowest stored base is base sh / 2 of word q[0] (forward:
+// in stored order; reverse complement: reversed and complemented): five
+// words, four funnel shifts. Unchecked: every word must be readable.
+__device__ __forceinline__ Chunk chunk_words(const uint32_t* q, unsigned sh, int rc) {
   uint32_t W[5];
 #pragma unroll
   for (int k = 0; k < 5; ++k) W[k] = __ldg(q + k);
@@ -178,6 +179,44 @@ __device__ __forceinline__ Chunk chunk_at_checked(const uint32_t* words, const u
 }
 
 constexpr int kWarps = kBlock / 32;
+
+// Asks L2 for the packed bytes that the pieces of output tile t (tiles of
+// tile_bases bases, pieces [tile_seg[t], tile_seg[t+1]] of the walk) read:
+// one bulk prefetch per piece, by the warp's lanes, rounded out to 16 bytes
+// (and past the last chunk's fifth word) and kept inside the first
+// readable_words words of `packed` (16-byte aligned). The tile's loads then
+// find their lines in L2 or on their way instead of each waiting on DRAM in
+// turn: the pieces of a tile lie at unrelated places of the read stream. On
+// the 3.1 Gb graph (tiles of 32768 bases) k_emit2 went from 0.361 to 0.335
+// ms with it. Prefetching the warp's next tile instead (0.441 ms), or the
+// first 32 pieces of the next tile with the rest of the current one (0.435),
+// was slower, and so was the same prefetch in the ASCII kernel (0.696 to
+// 0.758 ms), whose time the output writes set.
+__device__ __forceinline__ void prefetch_tile_sources(const Scratch& s, const uint8_t* packed,
+                                                      long long readable_words, int tile_bases, long long total,
+                                                      long long t, int lane) {
+  const int64_t* oo = s.out_off;
+  const unsigned long long* ws = s.wsrc;
+  const int lo = s.tile_seg[t], hi = s.tile_seg[t + 1];
+  const long long tbase = t * (long long)tile_bases;
+  const long long tend = min(tbase + (long long)tile_bases, total);
+  const long long top = (readable_words * 4) & ~15ll;
+  for (int j = lo + lane; j <= hi; j += 32) {
+    const long long oj = oo[j], oe = oo[j + 1];
+    const unsigned long long w = ws[j];
+    const long long a = max(oj, tbase), b = min(oe, tend);    // the piece's bases in this tile
+    if (a >= b) continue;
+    const int rc = (int)(w >> 63);
+    const long long src = (long long)(w & ~(1ull << 63));
+    const long long lo_base = rc ? src - (b - 1 - oj) : src + (a - oj);   // stored bases [lo_base, hi_base]
+    const long long hi_base = rc ? src - (a - oj) : src + (b - 1 - oj);
+    const long long b0 = max((lo_base >> 2) & ~15ll, 0ll);
+    const long long b1 = min(((hi_base >> 2) + 32) & ~15ll, top);
+    if (b1 > b0)
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(packed + b0), "r"((unsigned)(b1 - b0))
+                   : "memory");
+  }
+}
 
 // Per-warp fields of the group of pieces being spelled.
 struct PieceList {
@@ -239,45 +278,48 @@ __device__ void spell_tile_global(const Scratch& s, const uint8_t* packed, long 
     L.safe[lane] = aligned_ok(aligned16, (long long)(w & ~(1ull << 63)), (int)(w >> 63), oe - oj, readable_words);
     __syncwarp();
     // this lane's cursor: the piece of its next chunk, with that piece's fields
-    // kept in registers until the lane's chunks move past it
-    int pc = -1, p_first = 0, p_next = 0, p_rc = 0;
-    long long p_base = 0;                             // stored base at chunk offset 0: x0-independent part
+    // kept in registers until the lane's chunks move past it. Inside a piece
+    // the lowest stored base of chunk f moves by 64 per chunk (up forward, down
+    // reverse-complemented): its first word by 4, its shift not at all.
+    int pc = -1, p_next = 0, p_rc = 0;
+    unsigned p_sh = 0;
+    long long p_w = 0;                                // first word of chunk f = 0 of the piece's progression
+    uint4* p_o = out;                                 // chunk f goes to p_o[f]
     bool p_safe = false;
     for (int f0 = 0; f0 < T; f0 += 32 * kU) {         // warp-uniform trip count
       Chunk v[kU];
-      long long ci[kU];
+      uint4* dst[kU];
 #pragma unroll
       for (int u = 0; u < kU; ++u) {
         const int f = f0 + 32 * u + lane;
-        ci[u] = -1;
+        dst[u] = nullptr;
         if (f < T) {
           if (f >= p_next) {                          // chunks only move forward
             do {
               ++pc;
               p_next = L.start[pc + 1];
             } while (p_next <= f);
-            p_first = L.start[pc];
+            const int p_first = L.start[pc];
             const unsigned long long wl = L.w[pc];
             p_rc = (int)(wl >> 63);
             const long long src = (long long)(wl & ~(1ull << 63));
             const long long x_first = L.ca[pc] << 6, oj = L.oj[pc];
-            // lowest stored base of the piece's first interior chunk; later chunks move 64 bases up (forward)
-            // or down (reverse complement)
-            p_base = p_rc ? src - (x_first - oj) - 63 : src + (x_first - oj);
+            // lowest stored base of the piece's first interior chunk
+            const long long p0 = p_rc ? src - (x_first - oj) - 63 : src + (x_first - oj);
+            p_sh = (unsigned)(2 * (p0 & 15));
+            p_w = p_rc ? (p0 >> 4) + 4ll * p_first : (p0 >> 4) - 4ll * p_first;
+            p_o = out + (L.ca[pc] - p_first);
             p_safe = L.safe[pc];
-            ci[u] = L.ca[pc] - p_first;               // output chunk = ci + f
-          } else {
-            ci[u] = L.ca[pc] - p_first;
           }
-          const long long k = f - p_first;
-          const long long p = p_rc ? p_base - 64 * k : p_base + 64 * k;
-          v[u] = p_safe ? chunk_at(words, p, p_rc) : chunk_at_checked(words, packed, full_words, packed_bytes, p, p_rc);
-          ci[u] += f;
+          const long long wq = p_rc ? p_w - 4ll * f : p_w + 4ll * f;
+          v[u] = p_safe ? chunk_words(words + wq, p_sh, p_rc)
+                        : chunk_at_checked(words, packed, full_words, packed_bytes, (wq << 4) | (p_sh >> 1), p_rc);
+          dst[u] = p_o + f;
         }
       }
 #pragma unroll
       for (int u = 0; u < kU; ++u)
-        if (ci[u] >= 0) store_chunk(out, ci[u], v[u]);
+        if (dst[u] != nullptr) __stcs(dst[u], make_uint4(v[u].v[0], v[u].v[1], v[u].v[2], v[u].v[3]));
     }
     // the chunk at this piece's end, when a boundary falls inside it and this
     // piece covers its first base
@@ -333,9 +375,12 @@ __global__ void __launch_bounds__(kBlock, CG_EMIT2_MIN_BLOCKS) k_emit2(Scratch s
   const int lane = threadIdx.x & 31;
   const long long ntiles = (total + tile_bases - 1) / tile_bases;
   const long long t_stop = min(ntiles, t_end);          // the tiles [t_begin, t_end) of this launch
-  for (long long t = t_begin + (grid_tid() >> 5); t < t_stop; t += grid_threads() >> 5)
+  const long long stride = grid_threads() >> 5;
+  for (long long t = t_begin + (grid_tid() >> 5); t < t_stop; t += stride) {
+    if (aligned16) prefetch_tile_sources(s, packed, readable_words, tile_bases, total, t, lane);
     spell_tile_global(s, packed, packed_bytes, readable_words, aligned16, out, tile_bases, total, t, lane,
                       lists[threadIdx.x >> 5]);
+  }
 }
 
 }  // namespace
