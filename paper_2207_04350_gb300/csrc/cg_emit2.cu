@@ -220,7 +220,8 @@ __device__ __forceinline__ void prefetch_tile_sources(const Scratch& s, const ui
 
 // Per-warp fields of the group of pieces being spelled.
 struct PieceList {
-  long long oj[32];
+  long long oj[32];          // output offset of each piece and of its end
+  long long oe[32];
   unsigned long long w[32];
   int start[33];             // first interior chunk of each piece in the work list; [32] = the total
   long long ca[32];          // first interior chunk of each piece in the output
@@ -252,30 +253,34 @@ __device__ void spell_tile_global(const Scratch& s, const uint8_t* packed, long 
   const long long tend = min(tbase + (long long)tile_bases, total);
   for (int jb = lo; jb <= hi; jb += 32) {
     const int j = jb + lane;
-    long long oj = 0, oe = 0, a = 0, b = 0;
-    unsigned long long w = 0;
-    if (j <= hi) {
-      oj = oo[j];
-      oe = oo[j + 1];
-      w = ws[j];
-      a = max(oj, tbase);
-      b = min(oe, tend);
-    }
-    const long long ca = (a + 63) >> 6, cb = b >> 6;  // chunks wholly inside [a, b)
-    const int n = a < b && ca < cb ? (int)(cb - ca) : 0;
-    int incl = n;
+    int T;
+    {
+      long long oj = 0, oe = 0, a = 0, b = 0;
+      unsigned long long w = 0;
+      if (j <= hi) {
+        oj = oo[j];
+        oe = oo[j + 1];
+        w = ws[j];
+        a = max(oj, tbase);
+        b = min(oe, tend);
+      }
+      const long long ca = (a + 63) >> 6, cb = b >> 6;  // chunks wholly inside [a, b)
+      const int n = a < b && ca < cb ? (int)(cb - ca) : 0;
+      int incl = n;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int v = __shfl_up_sync(full, incl, o);
-      if (lane >= o) incl += v;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(full, incl, o);
+        if (lane >= o) incl += v;
+      }
+      T = __shfl_sync(full, incl, 31);
+      L.oj[lane] = oj;
+      L.oe[lane] = oe;
+      L.w[lane] = w;
+      L.start[lane] = incl - n;
+      if (lane == 31) L.start[32] = T;
+      L.ca[lane] = ca;
+      L.safe[lane] = aligned_ok(aligned16, (long long)(w & ~(1ull << 63)), (int)(w >> 63), oe - oj, readable_words);
     }
-    const int T = __shfl_sync(full, incl, 31);
-    L.oj[lane] = oj;
-    L.w[lane] = w;
-    L.start[lane] = incl - n;
-    if (lane == 31) L.start[32] = T;
-    L.ca[lane] = ca;
-    L.safe[lane] = aligned_ok(aligned16, (long long)(w & ~(1ull << 63)), (int)(w >> 63), oe - oj, readable_words);
     __syncwarp();
     // this lane's cursor: the piece of its next chunk, with that piece's fields
     // kept in registers until the lane's chunks move past it. Inside a piece
@@ -322,34 +327,77 @@ __device__ void spell_tile_global(const Scratch& s, const uint8_t* packed, long 
         if (dst[u] != nullptr) __stcs(dst[u], make_uint4(v[u].v[0], v[u].v[1], v[u].v[2], v[u].v[3]));
     }
     // the chunk at this piece's end, when a boundary falls inside it and this
-    // piece covers its first base
+    // piece covers its first base. Mostly the next piece covers the rest of
+    // the chunk (pieces are longer than a chunk): both pieces' words are
+    // loaded at once and the two parts merged under one mask. Otherwise every
+    // piece overlapping the chunk adds its part in turn.
+    // (this lane's piece fields come back from shared memory: registers are
+    // what limits the resident warps)
+    const long long oj = L.oj[lane], oe = L.oe[lane];
+    const unsigned long long w = L.w[lane];
+    const long long a = max(oj, tbase), b = min(oe, tend);
+    long long oe_next = __shfl_down_sync(full, oe, 1);   // the next piece's end and source, from the next lane
+    unsigned long long w_next = __shfl_down_sync(full, w, 1);
     if (j <= hi && a < b && (b & 63) != 0) {
       const long long x0 = ((b - 1) >> 6) << 6;
       if (a <= x0) {
-        Chunk acc;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) acc.v[k] = 0u;
-        long long pj = j, po = oj, pe = oe;
-        unsigned long long pw = w;
-        for (;;) {
-          const long long lo2 = max(po, x0), hi2 = min(pe, x0 + 64);
-          if (lo2 < hi2) {
-            const int rc = (int)(pw >> 63);
-            const long long src = (long long)(pw & ~(1ull << 63));
-            Chunk v = aligned_ok(aligned16, src, rc, pe - po, readable_words)
-                          ? chunk_bits_aligned(words, x0, po, src, rc)
-                          : chunk_bits<true>(words, packed, full_words, packed_bytes, x0, po, src, rc);
-            keep(v, x0, lo2, hi2);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) acc.v[k] |= v.v[k];
-          }
-          if (pe >= x0 + 64 || pe >= total) break;          // the chunk (or the stream) ends in this piece
-          ++pj;
-          po = pe;
-          pe = oo[pj + 1];
-          pw = ws[pj];
+        const bool last = oe >= total;                // the stream ends in this chunk, inside this piece
+        if (!last && (lane == 31 || j + 1 > hi)) {
+          oe_next = oo[j + 2];
+          w_next = ws[j + 1];
         }
-        store_chunk(out, x0 >> 6, acc);
+        if (last || oe_next >= x0 + 64 || oe_next >= total) {
+          const int rc = (int)(w >> 63);
+          const long long src = (long long)(w & ~(1ull << 63));
+          Chunk va = aligned_ok(aligned16, src, rc, oe - oj, readable_words)
+                         ? chunk_bits_aligned(words, x0, oj, src, rc)
+                         : chunk_bits<true>(words, packed, full_words, packed_bytes, x0, oj, src, rc);
+          Chunk vb;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) vb.v[k] = 0u;
+          if (!last) {
+            const int rc2 = (int)(w_next >> 63);
+            const long long src2 = (long long)(w_next & ~(1ull << 63));
+            vb = aligned_ok(aligned16, src2, rc2, oe_next - oe, readable_words)
+                     ? chunk_bits_aligned(words, x0, oe, src2, rc2)
+                     : chunk_bits<true>(words, packed, full_words, packed_bytes, x0, oe, src2, rc2);
+          }
+          // bases [0, m) of the chunk from this piece, [m, m2) from the next
+          const int m = (int)(oe - x0), m2 = last ? m : (int)(min(oe_next, x0 + 64) - x0);
+          Chunk acc;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const uint32_t lo_k = field_mask(0, min(max(m - 16 * k, 0), 16));
+            const uint32_t hi_k = field_mask(0, min(max(m2 - 16 * k, 0), 16));
+            acc.v[k] = (va.v[k] & lo_k) | (vb.v[k] & hi_k & ~lo_k);
+          }
+          store_chunk(out, x0 >> 6, acc);
+        } else {
+          Chunk acc;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) acc.v[k] = 0u;
+          long long pj = j, po = oj, pe = oe;
+          unsigned long long pw = w;
+          for (;;) {
+            const long long lo2 = max(po, x0), hi2 = min(pe, x0 + 64);
+            if (lo2 < hi2) {
+              const int rc = (int)(pw >> 63);
+              const long long src = (long long)(pw & ~(1ull << 63));
+              Chunk v = aligned_ok(aligned16, src, rc, pe - po, readable_words)
+                            ? chunk_bits_aligned(words, x0, po, src, rc)
+                            : chunk_bits<true>(words, packed, full_words, packed_bytes, x0, po, src, rc);
+              keep(v, x0, lo2, hi2);
+#pragma unroll
+              for (int k = 0; k < 4; ++k) acc.v[k] |= v.v[k];
+            }
+            if (pe >= x0 + 64 || pe >= total) break;        // the chunk (or the stream) ends in this piece
+            ++pj;
+            po = pe;
+            pe = oo[pj + 1];
+            pw = ws[pj];
+          }
+          store_chunk(out, x0 >> 6, acc);
+        }
       }
     }
     __syncwarp();                                     // the group's fields are reused by the next group
