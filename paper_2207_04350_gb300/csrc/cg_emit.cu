@@ -66,15 +66,6 @@ __device__ __forceinline__ uint8_t base_at(const uint8_t* packed, unsigned long 
 // n_shares runs of whole tiles (tiles [share * T / n_shares, (share + 1) * T /
 // n_shares) of the T tiles), written from out[0] on: out and cap then hold
 // that share only.
-//
-// Measured alternatives on the 3.1 Gb graph (this kernel: 0.695 ms): the
-// 2-bit kernel's design (the interior chunks of 32 pieces as one work list
-// walked by per-lane cursors, boundary chunks merged from two pieces' fields
-// and stored once) ran 0.99-1.13 ms at 2-8 chunks per lane and 4-5 blocks per
-// SM; an L2 bulk prefetch of each tile's piece sources at the tile's start
-// ran 0.758 ms. With pieces of ~33 chunks a whole warp per piece keeps the
-// per-chunk work at a few operations, and the output writes, not the reads,
-// set the time.
 template <int U>
 __global__ void __launch_bounds__(kBlock, 4) k_emit(Scratch s, const uint8_t* packed, long long packed_bytes,
                                                  long long readable_words, uint8_t* out, long long cap,
