@@ -34,7 +34,7 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 # DRAM bytes (read + write) per contig base of k_emit from one ncu capture
 # (--set full, the 3.1 Gb recipe on a 450 Mb genome: 552.2 MB for 481,446,585
 # bases), valid only for the emission source it was taken on.
-EMIT_TRAFFIC = {"bytes_per_base": (129.649152e6 + 422.524672e6) / 481446585, "source_sha256_16": "d79cb01e93ba0316"}
+EMIT_TRAFFIC = {"bytes_per_base": (129.660416e6 + 422.298880e6) / 481446585, "source_sha256_16": "4997eb2682d1320e"}
 
 
 def _reduce(x: float, world: int, op: str) -> float:
@@ -102,6 +102,7 @@ def parse():
     p.add_argument("--ruler-log2", type=int, default=0)
     p.add_argument("--tile-bytes", type=int, default=0)
     p.add_argument("--emit-blocks-per-sm", type=int, default=0)
+    p.add_argument("--emit-block-threads", type=int, default=0, help="spelling CTA size: 128, 256 or 512")
     p.add_argument("--partition-parts", type=int, nargs="*", default=[8, 18, 72, 128],
                    help="part counts for the GreedyPartitioning measurement (none: skip)")
     return p.parse_args()
@@ -225,7 +226,7 @@ def run_batched(args, rank, world, local_rank):
     t_gen = time.time() - t_gen
     stream = torch.cuda.Stream()
     ctx = cg.cg_create(local_rank, stream=stream)
-    cg.cg_set_tuning(ctx, args.ruler_log2, args.tile_bytes, args.emit_blocks_per_sm)
+    cg.cg_set_tuning(ctx, args.ruler_log2, args.tile_bytes, args.emit_blocks_per_sm, args.emit_block_threads)
     mcr = args.min_chain_reads
     # plain: every graph loaded on its own (untimed), outputs sized by a size query
     plain = []
@@ -579,7 +580,7 @@ def run_ours(args, rank, world, local_rank):
 
     stream = torch.cuda.Stream()
     ctx = cg.cg_create(local_rank, stream=stream)
-    cg.cg_set_tuning(ctx, args.ruler_log2, args.tile_bytes, args.emit_blocks_per_sm)
+    cg.cg_set_tuning(ctx, args.ruler_log2, args.tile_bytes, args.emit_blocks_per_sm, args.emit_block_threads)
     names = ("row_ptr", "col", "code", "suf", "len", "off", "packed")
     with torch.cuda.stream(stream):
         dev = {k: torch.from_numpy(getattr(G, k)).to("cuda", non_blocking=True) for k in names}

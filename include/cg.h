@@ -345,8 +345,8 @@ typedef struct {
   int32_t tile_bytes;         /* spelling: output tile per warp iteration, a power of two from 4096 to 131072;
                                  until it is set, each graph takes its own from its total read length
                                  (4 KiB below 2^27 bases, doubling per doubling, 32 KiB from 2^29) */
-  int32_t emit_blocks_per_sm; /* spelling: resident blocks per SM, 1..8 */
-  int32_t reserved;
+  int32_t emit_blocks_per_sm; /* spelling: resident blocks per SM, 1..16 (at most what fits) */
+  int32_t emit_block_threads; /* spelling: threads per block (the CTA size), 128, 256 or 512 */
 } cg_tuning;
 
 /* Sets the launch parameters (a field <= 0 keeps its value); CG_EINVAL for

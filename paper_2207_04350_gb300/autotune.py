@@ -1,8 +1,9 @@
 """Launch-parameter autotuning for the contig path, with a JSON cache.
 
 The parameters (cg_tuning: the sublist sampling 2^-ruler_log2, the emission
-tile size, resident emission blocks per SM) never change an output byte; they
-only move time between the chain stage and the spelling. This module times a
+tile size, resident emission blocks per SM and the emission CTA size) never
+change an output byte; they only move time between the chain stage and the
+spelling. This module times a
 small grid of them on a loaded graph (the whole step: cg_mask_branches ->
 cg_chains -> cg_emit_contigs into device buffers, waited for), keeps the
 fastest by median, and caches the choice per size class of the input
@@ -20,8 +21,12 @@ import threading
 
 from . import cg
 
-GRID = [dict(ruler_log2=r, tile_bytes=t, emit_blocks_per_sm=b)
-        for r in (3, 4, 5) for t in (16384, 32768, 65536) for b in (4, 8)]
+# (resident blocks per SM, threads per block) of the spelling kernels: half
+# occupancy, and full occupancy with CTAs of 256, 128 and 512 threads (the
+# blocks per SM are capped at what fits)
+LAUNCH = ((4, 256), (8, 256), (16, 128), (2, 512))
+GRID = [dict(ruler_log2=r, tile_bytes=t, emit_blocks_per_sm=b, emit_block_threads=bt)
+        for r in (3, 4, 5) for t in (16384, 32768, 65536) for b, bt in LAUNCH]
 
 
 def size_class(n_reads: int, n_entries: int, packed_bytes: int) -> str:

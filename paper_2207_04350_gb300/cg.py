@@ -497,18 +497,20 @@ def cg_selftest_wait_timeout(ctx: Context, tiles: int = 2) -> int:
 
 class Tuning(ctypes.Structure):
     _fields_ = [("ruler_log2", ctypes.c_int32), ("tile_bytes", ctypes.c_int32), ("emit_blocks_per_sm", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("emit_block_threads", ctypes.c_int32)]
 
 
-def cg_set_tuning(ctx: Context, ruler_log2: int = 0, tile_bytes: int = 0, emit_blocks_per_sm: int = 0):
-    t = Tuning(int(ruler_log2), int(tile_bytes), int(emit_blocks_per_sm), 0)
+def cg_set_tuning(ctx: Context, ruler_log2: int = 0, tile_bytes: int = 0, emit_blocks_per_sm: int = 0,
+                  emit_block_threads: int = 0):
+    t = Tuning(int(ruler_log2), int(tile_bytes), int(emit_blocks_per_sm), int(emit_block_threads))
     _check(ctx.ptr, lib().cg_set_tuning(ctx.ptr, ctypes.byref(t)))
 
 
 def cg_get_tuning(ctx: Context) -> dict:
     t = Tuning()
     _check(ctx.ptr, lib().cg_get_tuning(ctx.ptr, ctypes.byref(t)))
-    return {"ruler_log2": t.ruler_log2, "tile_bytes": t.tile_bytes, "emit_blocks_per_sm": t.emit_blocks_per_sm}
+    return {"ruler_log2": t.ruler_log2, "tile_bytes": t.tile_bytes, "emit_blocks_per_sm": t.emit_blocks_per_sm,
+            "emit_block_threads": t.emit_block_threads}
 
 
 class Stats(ctypes.Structure):

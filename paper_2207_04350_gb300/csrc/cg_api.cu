@@ -576,8 +576,13 @@ cg_status cg_set_tuning(cg_ctx* c, const cg_tuning* t) {
     tile_set = true;
   }
   if (t->emit_blocks_per_sm > 0) {
-    if (t->emit_blocks_per_sm > 8) return fail(c, CG_EINVAL, "emit_blocks_per_sm must be in 1..8");
+    if (t->emit_blocks_per_sm > 16) return fail(c, CG_EINVAL, "emit_blocks_per_sm must be in 1..16");
     n.emit_blocks_per_sm = t->emit_blocks_per_sm;
+  }
+  if (t->emit_block_threads > 0) {
+    if (t->emit_block_threads != 128 && t->emit_block_threads != 256 && t->emit_block_threads != 512)
+      return fail(c, CG_EINVAL, "emit_block_threads must be 128, 256 or 512");
+    n.emit_block_threads = t->emit_block_threads;
   }
   c->tune = n;
   if (tile_set) c->tile_auto = false;
@@ -589,7 +594,7 @@ cg_status cg_get_tuning(cg_ctx* c, cg_tuning* out) {
   out->ruler_log2 = c->tune.ruler_log2;
   out->tile_bytes = c->tune.tile_bytes;
   out->emit_blocks_per_sm = c->tune.emit_blocks_per_sm;
-  out->reserved = 0;
+  out->emit_block_threads = c->tune.emit_block_threads;
   return CG_OK;
 }
 
@@ -1050,7 +1055,7 @@ cg_status cg_emit_contigs(cg_graph* g, int64_t* contig_off, int64_t contig_off_c
     const bool timing = c->timing != 0, stages = timing && !c->timing_emit_only;
     uint64_t key = mix_key(mix_key(mix_key(mix_key((uint64_t)(uintptr_t)bases, (uint64_t)bases_cap),
                                            (uint64_t)(uintptr_t)g->g.packed), (uint64_t)gt(g).tile_bytes),
-                           (uint64_t)gt(g).emit_blocks_per_sm);
+                           (uint64_t)cg::emit_launch_key(gt(g)));
     key = mix_key(mix_key(mix_key(key, (uint64_t)(uintptr_t)contig_off), (uint64_t)contig_off_cap),
                   stages ? 3 : (timing ? 5 : 4));
     // the caller's contig offsets come from the piece scan itself (no copy kernel)
@@ -1093,7 +1098,7 @@ cg_status cg_emit_contigs(cg_graph* g, int64_t* contig_off, int64_t contig_off_c
       StageTimer tm(c, 3);
       uint64_t key = mix_key(mix_key(mix_key(mix_key((uint64_t)(uintptr_t)bases, (uint64_t)bases_cap),
                                              (uint64_t)(uintptr_t)emit_graph(g).packed), (uint64_t)gt(g).tile_bytes),
-                             (uint64_t)gt(g).emit_blocks_per_sm);
+                             (uint64_t)cg::emit_launch_key(gt(g)));
       st = run_stage(g, 3, key, [&]() -> cg_status {
         CK(cg::launch_emit(emit_graph(g), g->s, gt(g), bases, bases_cap, c->env), "emission kernel");
         return CG_OK;
@@ -1169,7 +1174,7 @@ cg_status cg_emit_contigs(cg_graph* g, int64_t* contig_off, int64_t contig_off_c
         StageTimer tm(c, 3);
         uint64_t key = mix_key(mix_key(mix_key(mix_key((uint64_t)(uintptr_t)dst, (uint64_t)dcap),
                                            (uint64_t)(uintptr_t)emit_graph(g).packed),
-                                       (uint64_t)gt(g).tile_bytes), (uint64_t)gt(g).emit_blocks_per_sm);
+                                       (uint64_t)gt(g).tile_bytes), (uint64_t)cg::emit_launch_key(gt(g)));
         st = run_stage(g, 3, key, [&]() -> cg_status {
           CK(cg::launch_emit(emit_graph(g), g->s, gt(g), dst, dcap, c->env), "emission kernel");
           return CG_OK;
@@ -1262,7 +1267,7 @@ cg_status cg_emit_share(cg_graph* g, int32_t share, int32_t n_shares, int64_t* c
     StageTimer tm(c, 3);
     uint64_t key = mix_key(mix_key(mix_key(mix_key((uint64_t)(uintptr_t)dst, (uint64_t)cap),
                                            (uint64_t)(uintptr_t)emit_graph(g).packed), (uint64_t)tb),
-                           (uint64_t)gt(g).emit_blocks_per_sm);
+                           (uint64_t)cg::emit_launch_key(gt(g)));
     key = mix_key(mix_key(key, (uint64_t)share), (uint64_t)n_shares);
     return run_stage(g, 3, key, [&]() -> cg_status {
       CK(cg::launch_emit(emit_graph(g), g->s, gt(g), dst, cap, c->env, 0, 1ll << 62, share, n_shares),
@@ -1570,7 +1575,7 @@ cg_status cg_emit_contigs_2bit(cg_graph* g, int64_t* contig_off, int64_t contig_
     StageTimer tm(c, 3);
     uint64_t key = mix_key(mix_key(mix_key(mix_key((uint64_t)(uintptr_t)dst, (uint64_t)cap),
                                            (uint64_t)(uintptr_t)emit_graph(g).packed), (uint64_t)gt(g).tile_bytes),
-                           (uint64_t)gt(g).emit_blocks_per_sm);
+                           (uint64_t)cg::emit_launch_key(gt(g)));
     return run_stage(g, 5, key, [&]() -> cg_status {
       CK(cg::launch_emit2(emit_graph(g), g->s, gt(g), dst, cap, c->env), "2-bit emission kernel");
       return CG_OK;

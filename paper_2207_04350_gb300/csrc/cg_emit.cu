@@ -66,8 +66,8 @@ __device__ __forceinline__ uint8_t base_at(const uint8_t* packed, unsigned long 
 // n_shares runs of whole tiles (tiles [share * T / n_shares, (share + 1) * T /
 // n_shares) of the T tiles), written from out[0] on: out and cap then hold
 // that share only.
-template <int U>
-__global__ void __launch_bounds__(kBlock, 4) k_emit(Scratch s, const uint8_t* packed, long long packed_bytes,
+template <int U, int BT>
+__global__ void __launch_bounds__(BT, 1024 / BT) k_emit(Scratch s, const uint8_t* packed, long long packed_bytes,
                                                  long long readable_words, uint8_t* out, long long cap,
                                                  int tile_bytes, long long t_begin, long long t_end, int share,
                                                  int n_shares) {
@@ -205,16 +205,29 @@ __global__ void __launch_bounds__(kBlock, 4) k_emit(Scratch s, const uint8_t* pa
 
 }  // namespace
 
+namespace {
+
+// One block size: a persistent grid of at most the blocks that can be resident
+// at once (the function-local static is initialised once, safely across threads).
+template <int BT>
+cudaError_t launch_emit_bt(const DevGraph& g, const Scratch& s, const Tuning& t, uint8_t* out, int64_t cap,
+                           const LaunchEnv& env, long long t_begin, long long t_end, int share, int n_shares) {
+  static const int resident = resident_blocks(k_emit<4, BT>, BT);
+  const int per_sm = t.emit_blocks_per_sm < resident ? t.emit_blocks_per_sm : resident;
+  return launch_kb(k_emit<4, BT>, env.num_sms * per_sm, BT, env, env.pdl_first, s, g.packed,
+                   (long long)g.packed_bytes, (long long)(g.packed_readable / 4), out, (long long)cap, t.tile_bytes,
+                   t_begin, t_end, share, n_shares);
+}
+
+}  // namespace
+
 cudaError_t launch_emit(const DevGraph& g, const Scratch& s, const Tuning& t, uint8_t* out, int64_t cap,
                         const LaunchEnv& env, long long t_begin, long long t_end, int share, int n_shares) {
-  // a persistent grid: never more blocks than can be resident at once (a
-  // function-local static is initialised once, safely across threads)
-  static const int resident = resident_blocks(k_emit<4>);
-  int per_sm = t.emit_blocks_per_sm < resident ? t.emit_blocks_per_sm : resident;
-  int blocks = env.num_sms * per_sm;
-  cudaError_t e = launch_k(k_emit<4>, blocks, env, env.pdl_first, s, g.packed, (long long)g.packed_bytes,
-                           (long long)(g.packed_readable / 4), out, (long long)cap, t.tile_bytes, t_begin, t_end,
-                           share, n_shares);
+  cudaError_t e = t.emit_block_threads == 128
+                      ? launch_emit_bt<128>(g, s, t, out, cap, env, t_begin, t_end, share, n_shares)
+                  : t.emit_block_threads == 512
+                      ? launch_emit_bt<512>(g, s, t, out, cap, env, t_begin, t_end, share, n_shares)
+                      : launch_emit_bt<256>(g, s, t, out, cap, env, t_begin, t_end, share, n_shares);
   if (e != cudaSuccess) return e;
   mark(env, "k_emit");
   return cudaGetLastError();

@@ -178,8 +178,6 @@ __device__ __forceinline__ Chunk chunk_at_checked(const uint32_t* words, const u
   return c;
 }
 
-constexpr int kWarps = kBlock / 32;
-
 // Asks L2 for the packed bytes that the pieces of output tile t (tiles of
 // tile_bases bases, pieces [tile_seg[t], tile_seg[t+1]] of the walk) read:
 // one bulk prefetch per piece, by the warp's lanes, rounded out to 16 bytes
@@ -404,15 +402,15 @@ __device__ void spell_tile_global(const Scratch& s, const uint8_t* packed, long 
   }
 }
 
-// One warp per output tile, persistent grid (spell_tile_global).
-__global__ void __launch_bounds__(kBlock, CG_EMIT2_MIN_BLOCKS) k_emit2(Scratch s, const uint8_t* packed,
-                                                                       long long packed_bytes,
-                                                                       long long readable_words, bool aligned16,
-                                                                       uint4* out, long long cap_bytes,
-                                                                       int tile_bases, long long t_begin,
-                                                                       long long t_end) {
+// One warp per output tile, persistent grid (spell_tile_global). Blocks of BT
+// threads; the launch bounds keep CG_EMIT2_MIN_BLOCKS blocks of 256 threads'
+// worth of warps resident (two blocks of 512).
+template <int BT>
+__global__ void __launch_bounds__(BT, BT >= 512 ? 2 : CG_EMIT2_MIN_BLOCKS * 256 / BT)
+    k_emit2(Scratch s, const uint8_t* packed, long long packed_bytes, long long readable_words, bool aligned16,
+            uint4* out, long long cap_bytes, int tile_bases, long long t_begin, long long t_end) {
   pdl_enter();
-  __shared__ PieceList lists[kWarps];
+  __shared__ PieceList lists[BT / 32];
   const Counters* c = s.ctr;
   const long long total = *(const volatile long long*)&c->total_bases;
   const long long need = 16 * ((total + 63) / 64);
@@ -433,14 +431,26 @@ __global__ void __launch_bounds__(kBlock, CG_EMIT2_MIN_BLOCKS) k_emit2(Scratch s
 
 }  // namespace
 
+namespace {
+
+template <int BT>
+cudaError_t launch_emit2_bt(const DevGraph& g, const Scratch& s, const Tuning& t, uint8_t* out, int64_t cap,
+                            const LaunchEnv& env, long long t_begin, long long t_end) {
+  const bool aligned16 = (reinterpret_cast<uintptr_t>(g.packed) & 15) == 0;
+  static const int resident = resident_blocks(k_emit2<BT>, BT);   // once, safely across threads
+  const int per_sm = t.emit_blocks_per_sm < resident ? t.emit_blocks_per_sm : resident;
+  return launch_kb(k_emit2<BT>, env.num_sms * per_sm, BT, env, env.pdl_first, s, g.packed,
+                   (long long)g.packed_bytes, (long long)(g.packed_readable / 4), aligned16,
+                   reinterpret_cast<uint4*>(out), (long long)cap, t.tile_bytes, t_begin, t_end);
+}
+
+}  // namespace
+
 cudaError_t launch_emit2(const DevGraph& g, const Scratch& s, const Tuning& t, uint8_t* out, int64_t cap,
                          const LaunchEnv& env, long long t_begin, long long t_end) {
-  const bool aligned16 = (reinterpret_cast<uintptr_t>(g.packed) & 15) == 0;
-  static const int resident = resident_blocks(k_emit2);   // once, safely across threads
-  const int per_sm = t.emit_blocks_per_sm < resident ? t.emit_blocks_per_sm : resident;
-  cudaError_t e = launch_k(k_emit2, env.num_sms * per_sm, env, env.pdl_first, s, g.packed,
-                           (long long)g.packed_bytes, (long long)(g.packed_readable / 4), aligned16,
-                           reinterpret_cast<uint4*>(out), (long long)cap, t.tile_bytes, t_begin, t_end);
+  cudaError_t e = t.emit_block_threads == 128 ? launch_emit2_bt<128>(g, s, t, out, cap, env, t_begin, t_end)
+                  : t.emit_block_threads == 512 ? launch_emit2_bt<512>(g, s, t, out, cap, env, t_begin, t_end)
+                                                : launch_emit2_bt<256>(g, s, t, out, cap, env, t_begin, t_end);
   if (e != cudaSuccess) return e;
   mark(env, "k_emit2");
   return cudaGetLastError();

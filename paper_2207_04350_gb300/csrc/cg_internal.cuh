@@ -133,8 +133,14 @@ struct Tuning {
   int ruler_log2 = 3;      // a read starts a sublist with probability 2^-ruler_log2
   int tile_bytes = 32768;  // emission tile: 4, 8, 16 or 32 KiB
   int emit_blocks_per_sm = 8;
+  int emit_block_threads = 256;   // CTA size of the spelling kernels: 128, 256 or 512
   int grid_blocks_per_sm = 8;
 };
+
+// The spelling launch parameters as one value, for the keys of captured stages.
+inline unsigned long long emit_launch_key(const Tuning& t) {
+  return (unsigned long long)t.emit_blocks_per_sm | ((unsigned long long)t.emit_block_threads << 16);
+}
 
 // CUDA events recorded after each kernel when timing is on.
 struct KernelMarks {
@@ -309,11 +315,11 @@ enum KernelId {
   K_SELFTEST_WAIT
 };
 
-// Blocks of kBlock threads of `kernel` that fit on one SM at once.
+// Blocks of `threads` threads (kBlock by default) of `kernel` that fit on one SM at once.
 template <typename Kernel>
-inline int resident_blocks(Kernel kernel) {
+inline int resident_blocks(Kernel kernel, int threads = kBlock) {
   int r = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, kernel, kBlock, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, kernel, threads, 0);
   return r > 0 ? r : 1;
 }
 
@@ -325,10 +331,11 @@ inline int resident_blocks(Kernel kernel) {
 // pdl_enter() for that completion. Per-kernel timing events sit between every two
 // kernels, so they turn the attribute off.
 template <typename... P, typename... A>
-inline cudaError_t launch_k(void (*kernel)(P...), int grid, const LaunchEnv& env, bool chained, A&&... args) {
+inline cudaError_t launch_kb(void (*kernel)(P...), int grid, int threads, const LaunchEnv& env, bool chained,
+                             A&&... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid);
-  cfg.blockDim = dim3(kBlock);
+  cfg.blockDim = dim3((unsigned)threads);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = env.stream;
   cudaLaunchAttribute attr[1];
@@ -337,6 +344,11 @@ inline cudaError_t launch_k(void (*kernel)(P...), int grid, const LaunchEnv& env
   cfg.attrs = attr;
   cfg.numAttrs = chained && env.pdl && !(env.marks && env.marks->on) ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, kernel, static_cast<A&&>(args)...);
+}
+
+template <typename... P, typename... A>
+inline cudaError_t launch_k(void (*kernel)(P...), int grid, const LaunchEnv& env, bool chained, A&&... args) {
+  return launch_kb(kernel, grid, kBlock, env, chained, static_cast<A&&>(args)...);
 }
 
 inline int grid_for(long long n, const LaunchEnv& env, int per_sm = 8) {

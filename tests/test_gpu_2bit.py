@@ -92,6 +92,21 @@ def test_short_pieces(ctx, align):
     check(ctx, G, 2, device=True)
 
 
+@pytest.mark.parametrize("bt,bps", [(128, 16), (128, 3), (512, 2), (512, 1)])
+def test_block_sizes(bt, bps):
+    """The spelling CTA size and blocks per SM change no byte of either form."""
+    c = cg.cg_create(0)
+    try:
+        cg.cg_set_tuning(c, tile_bytes=4096, emit_blocks_per_sm=bps, emit_block_threads=bt)
+        rng = np.random.default_rng(bt + bps)
+        G = structured(60 + bps, list(rng.integers(1, 60, size=2000)) + [3000] * 3, lone=50, align=1)
+        for mcr in (1, 2):
+            check(c, G, mcr)
+        check(c, gen.generate("tiny-1Mb", threads=8, off_align=4), 2, device=True)
+    finally:
+        c.close()
+
+
 def test_long_reads_and_cycles(ctx):
     sizes = [30_000, 3, 4, 5, 7, 16, 33, 100] + [2] * 200
     closed = [False] + [True] * 7 + [False] * 200

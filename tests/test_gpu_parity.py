@@ -234,14 +234,16 @@ def test_small_capacity_rejected(ctx):
     assert np.array_equal(off_d.cpu().numpy(), orc.contig_off)
 
 
-@pytest.mark.parametrize("ruler_log2,tile_bytes,bps", [(1, 4096, 1), (2, 8192, 2), (4, 16384, 8), (7, 32768, 4),
-                                                       (12, 32768, 3), (3, 65536, 8), (5, 131072, 6)])
-def test_tuning_does_not_change_output(ruler_log2, tile_bytes, bps):
+@pytest.mark.parametrize("ruler_log2,tile_bytes,bps,bt", [(1, 4096, 1, 256), (2, 8192, 2, 128), (4, 16384, 8, 512),
+                                                          (7, 32768, 4, 128), (12, 32768, 3, 256), (3, 65536, 8, 256),
+                                                          (5, 131072, 6, 512), (3, 32768, 16, 128), (3, 32768, 2, 512)])
+def test_tuning_does_not_change_output(ruler_log2, tile_bytes, bps, bt):
     """Launch parameters chosen by the autotuner never change a byte."""
     c = cg.cg_create(0)
     try:
-        cg.cg_set_tuning(c, ruler_log2=ruler_log2, tile_bytes=tile_bytes, emit_blocks_per_sm=bps)
-        assert cg.cg_get_tuning(c) == {"ruler_log2": ruler_log2, "tile_bytes": tile_bytes, "emit_blocks_per_sm": bps}
+        cg.cg_set_tuning(c, ruler_log2=ruler_log2, tile_bytes=tile_bytes, emit_blocks_per_sm=bps, emit_block_threads=bt)
+        assert cg.cg_get_tuning(c) == {"ruler_log2": ruler_log2, "tile_bytes": tile_bytes, "emit_blocks_per_sm": bps,
+                                       "emit_block_threads": bt}
         check(c, structured(21, [50_000, 3, 4, 17] + [2] * 40 + [6] * 30, [False, True, True, True] + [False] * 70,
                             lone=50, align=1), 1)
         check(c, gen.generate(gen.batched_graph(11), threads=8), 2)
