@@ -365,6 +365,7 @@ cg_status prepare_emit(cg_graph* g) {
   g->g_emit.packed = reinterpret_cast<const uint8_t*>(g->hb_dst);
   g->g_emit.packed_bytes = 4 * g->hb_dst_words;
   g->g_emit.packed_readable = 4 * g->hb_dst_words;
+  g->g_emit.packed_host = false;
   return CG_OK;
 }
 

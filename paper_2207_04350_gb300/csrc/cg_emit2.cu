@@ -408,7 +408,7 @@ __device__ void spell_tile_global(const Scratch& s, const uint8_t* packed, long 
 template <int BT>
 __global__ void __launch_bounds__(BT, BT >= 512 ? 2 : CG_EMIT2_MIN_BLOCKS * 256 / BT)
     k_emit2(Scratch s, const uint8_t* packed, long long packed_bytes, long long readable_words, bool aligned16,
-            uint4* out, long long cap_bytes, int tile_bases, long long t_begin, long long t_end) {
+            bool prefetch, uint4* out, long long cap_bytes, int tile_bases, long long t_begin, long long t_end) {
   pdl_enter();
   __shared__ PieceList lists[BT / 32];
   const Counters* c = s.ctr;
@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(BT, BT >= 512 ? 2 : CG_EMIT2_MIN_BLOCKS * 256 
   const long long t_stop = min(ntiles, t_end);          // the tiles [t_begin, t_end) of this launch
   const long long stride = grid_threads() >> 5;
   for (long long t = t_begin + (grid_tid() >> 5); t < t_stop; t += stride) {
-    if (aligned16) prefetch_tile_sources(s, packed, readable_words, tile_bases, total, t, lane);
+    if (prefetch) prefetch_tile_sources(s, packed, readable_words, tile_bases, total, t, lane);
     spell_tile_global(s, packed, packed_bytes, readable_words, aligned16, out, tile_bases, total, t, lane,
                       lists[threadIdx.x >> 5]);
   }
@@ -437,10 +437,14 @@ template <int BT>
 cudaError_t launch_emit2_bt(const DevGraph& g, const Scratch& s, const Tuning& t, uint8_t* out, int64_t cap,
                             const LaunchEnv& env, long long t_begin, long long t_end) {
   const bool aligned16 = (reinterpret_cast<uintptr_t>(g.packed) & 15) == 0;
+  // the L2 prefetch pays for HBM-resident reads only: with the reads in pinned
+  // host memory it did not help (the 3.1 Gb end-to-end 2-bit step took 10.7 ms
+  // with it, 9.9-10.6 ms without)
+  const bool prefetch = aligned16 && !g.packed_host;
   static const int resident = resident_blocks(k_emit2<BT>, BT);   // once, safely across threads
   const int per_sm = t.emit_blocks_per_sm < resident ? t.emit_blocks_per_sm : resident;
   return launch_kb(k_emit2<BT>, env.num_sms * per_sm, BT, env, env.pdl_first, s, g.packed,
-                   (long long)g.packed_bytes, (long long)(g.packed_readable / 4), aligned16,
+                   (long long)g.packed_bytes, (long long)(g.packed_readable / 4), aligned16, prefetch,
                    reinterpret_cast<uint4*>(out), (long long)cap, t.tile_bytes, t_begin, t_end);
 }
 
