@@ -10,10 +10,12 @@
 // bases below it, reverses the order of the 2-bit fields of each word and
 // complements them (b -> 3 - b is a bitwise NOT of the field).
 //
-// The interior chunks of a tile's pieces (all 64 bases inside one piece) are
-// one work list that the warp's lanes walk with forward-only cursors; a chunk
-// with a piece boundary inside is assembled by one lane from every piece
-// overlapping it and stored once (spell_tile_global below).
+// At a tile's start the warp asks L2 for the source bytes of all the tile's
+// pieces (they lie at unrelated places of the read stream). The interior
+// chunks of the tile's pieces (all 64 bases inside one piece) are one work
+// list that the warp's lanes walk with forward-only cursors; a chunk with a
+// piece boundary inside is assembled by one lane from the pieces overlapping
+// it and stored once (spell_tile_global below).
 #include <cuda_runtime.h>
 
 #include "cg_internal.cuh"
@@ -113,9 +115,9 @@ __device__ __forceinline__ Chunk chunk_bits_aligned(const uint32_t* words, long 
   return c;
 }
 
-// Chunks per lane in flight and the blocks per SM the registers must allow.
-// On the 3.1 Gb graph, with each tile's sources prefetched to L2: 2 chunks at
-// 5 blocks (48 registers) 0.335 ms, at 6 0.360; 1 at 6 0.346, at 8 0.387; 3
+// Chunks per lane in flight and the blocks (of 256 threads) per SM the
+// registers must allow. On the 3.1 Gb graph, with each tile's sources
+// prefetched to L2: 2 chunks at 5 blocks (48 registers) 0.335 ms, at 6 0.360; 1 at 6 0.346, at 8 0.387; 3
 // at 5 0.354, at 4 0.346; 4 at 4 0.345. The loads wait on memory, and
 // resident warps hide that wait better than more chunks per lane. Keeping
 // more chunks in flight without registers, through a per-lane ring in shared
