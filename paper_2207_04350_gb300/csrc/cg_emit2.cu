@@ -122,7 +122,9 @@ __device__ __forceinline__ Chunk chunk_bits_aligned(const uint32_t* words, long 
 // resident warps hide that wait better than more chunks per lane. Keeping
 // more chunks in flight without registers, through a per-lane ring in shared
 // memory filled by 4-byte cp.async copies (2 to 4 chunks ahead), ran 0.367-
-// 0.383 ms. A variant that staged each tile's input in shared memory with
+// 0.383 ms; two aligned 16-byte loads per chunk instead of five 4-byte ones
+// (fewer L1 wavefronts, eight words selected down to five) 0.333 ms against
+// 0.325-0.328, and slower from pinned host reads too. A variant that staged each tile's input in shared memory with
 // TMA bulk copies (one per piece, on an mbarrier, the next tiles' copies in
 // flight while the current one was spelled) ran 0.45-1.6 ms: the smem
 // buffers left too few warps resident, and the spelling itself, not the
