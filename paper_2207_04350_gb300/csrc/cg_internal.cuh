@@ -49,6 +49,8 @@ struct Counters {
   unsigned int n_tiles;        // emission tiles
   unsigned int pad;
   long long total_bases;
+  // spelling
+  unsigned long long emit_ticket;  // output tiles handed out by a spelling launch (zeroed before each)
 };
 
 // The graph as kernels see it (all device pointers).
