@@ -436,6 +436,7 @@ cg_status finish_load(cg_graph* g, uint32_t flags) {
                        c->stream), "clear scan descriptors");
   }
   S.ctr = galloc<cg::Counters>(g, 1, &st);
+  S.tickets = galloc<unsigned long long>(g, cg::kTicketSets * cg::kTicketStride, &st);
   g->d_sum = galloc<unsigned long long>(g, 1, &st);
   S.derr = c->derr;
   if (st != CG_OK) return st;

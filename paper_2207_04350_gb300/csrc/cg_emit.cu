@@ -4,11 +4,11 @@
 // The output is one byte stream holding every contig back to back; each read
 // of a contig owns one piece [out_off[j], out_off[j+1]) of it (walk position
 // j). The kernel tiles the OUTPUT: the warps of a persistent grid take
-// fixed-size tiles one at a time from a counter, and inside a tile every
+// fixed-size tiles one at a time (TileQueue), and inside a tile every
 // thread produces aligned 16-byte chunks, so stores are full 128-bit,
 // coalesced and independent of piece lengths (a long contig spreads over many
-// warps, short pieces share a chunk). Taking tiles from a counter rather than
-// in a fixed stride lets the warps end together whatever each tile holds: on
+// warps, short pieces share a chunk). Taking tiles as the warps free up rather
+// than in a fixed stride lets them end together whatever each tile holds: on
 // the 3.1 Gb graph 0.682 ms against 0.695.
 //
 // A chunk inside one piece is read with two 32-bit words of the packed
@@ -54,8 +54,8 @@ __device__ __forceinline__ uint8_t base_at(const uint8_t* packed, unsigned long 
   return (uint8_t)(0x54474341u >> (8 * b));
 }
 
-// One warp per output tile (persistent grid; tiles from the counter
-// s.ctr->emit_ticket, zeroed before the launch). The warp takes the pieces of its
+// One warp per output tile (persistent grid; tiles from a TileQueue, its
+// counters zeroed before the launch). The warp takes the pieces of its
 // tile, [tile_seg[t], tile_seg[t+1]], in order; of each piece it writes the
 // 16-byte-aligned interior inside the tile with full chunks, and the at most
 // 30 bytes at its two ragged ends byte by byte (chunks shared by two pieces
@@ -110,15 +110,10 @@ __global__ void __launch_bounds__(BT, 1024 / BT) k_emit(Scratch s, const uint8_t
   const int64_t* oo = s.out_off;
   const unsigned long long* ws = s.wsrc;
   const long long t_stop = min(ntiles, t_end);          // the tiles [t_begin, t_end) of this launch
-  // tiles handed out one at a time from a counter: a warp takes its next tile
-  // when it finishes one, so the warps end together whatever each tile holds
-  // (the next ticket is asked for while the current tile is spelled)
-  unsigned long long* ticket = &s.ctr->emit_ticket;
-  unsigned long long tk = 0;
-  if (lane == 0) tk = atomicAdd(ticket, 1ull);
-  long long t = t_begin + (long long)__shfl_sync(0xffffffffu, tk, 0);
-  for (; t < t_stop;) {
-    if (lane == 0) tk = atomicAdd(ticket, 1ull);
+  TileQueue q(t_begin);                                 // the warp's tiles, from counters after the first
+  for (; q.t < t_stop; q.next(t_begin, t_stop)) {
+    q.ask(s.tickets, t_begin, t_stop, lane);
+    const long long t = q.t;
     const int lo = s.tile_seg[t], hi = s.tile_seg[t + 1];
     const long long tbase = t * (long long)tile_bytes;
     const long long tend = min(tbase + (long long)tile_bytes, total);
@@ -212,7 +207,6 @@ __global__ void __launch_bounds__(BT, 1024 / BT) k_emit(Scratch s, const uint8_t
         if (A < B && B + lane < b) out[B + lane] = base_at(packed, w, oj, B + lane);
       }
     }
-    t = t_begin + (long long)__shfl_sync(0xffffffffu, tk, 0);
   }
 }
 
@@ -227,7 +221,7 @@ cudaError_t launch_emit_bt(const DevGraph& g, const Scratch& s, const Tuning& t,
                            const LaunchEnv& env, long long t_begin, long long t_end, int share, int n_shares) {
   static const int resident = resident_blocks(k_emit<4, BT>, BT);
   const int per_sm = t.emit_blocks_per_sm < resident ? t.emit_blocks_per_sm : resident;
-  cudaError_t e = cudaMemsetAsync(&s.ctr->emit_ticket, 0, sizeof(unsigned long long), env.stream);
+  cudaError_t e = cudaMemsetAsync(s.tickets, 0, kTicketSets * kTicketStride * sizeof(unsigned long long), env.stream);
   if (e != cudaSuccess) return e;
   const bool chained = false;                     // a memset, not a kernel, comes right before
   return launch_kb(k_emit<4, BT>, env.num_sms * per_sm, BT, env, chained, s, g.packed,

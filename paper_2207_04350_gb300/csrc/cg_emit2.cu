@@ -4,8 +4,9 @@
 // convention of the packed reads), a quarter of the bytes.
 //
 // The output is tiled like the ASCII form (tiles of tile_bytes bases, one warp
-// per tile, persistent grid, tiles taken from a counter: 0.309 ms on the 3.1
-// Gb graph against 0.326 in a fixed stride) and written in 16-byte chunks of
+// per tile, persistent grid, tiles taken as the warps free up (TileQueue):
+// 0.309 ms on the 3.1 Gb graph against 0.326 in a fixed stride) and written
+// in 16-byte chunks of
 // 64 bases. A
 // forward piece is a bit-granular copy of the packed read: five words and four
 // funnel shifts per chunk. A reverse-complement piece takes the 64 stored
@@ -427,18 +428,11 @@ __global__ void __launch_bounds__(BT, BT >= 512 ? 2 : CG_EMIT2_MIN_BLOCKS * 256 
   const int lane = threadIdx.x & 31;
   const long long ntiles = (total + tile_bases - 1) / tile_bases;
   const long long t_stop = min(ntiles, t_end);          // the tiles [t_begin, t_end) of this launch
-  // tiles handed out one at a time from a counter (zeroed before the launch):
-  // a warp takes its next tile when it finishes one, asking for it while the
-  // current one is spelled
-  unsigned long long* ticket = &s.ctr->emit_ticket;
-  unsigned long long tk = 0;
-  if (lane == 0) tk = atomicAdd(ticket, 1ull);
-  for (long long t = t_begin + (long long)__shfl_sync(0xffffffffu, tk, 0); t < t_stop;) {
-    if (lane == 0) tk = atomicAdd(ticket, 1ull);
-    if (prefetch) prefetch_tile_sources(s, packed, readable_words, tile_bases, total, t, lane);
-    spell_tile_global(s, packed, packed_bytes, readable_words, aligned16, out, tile_bases, total, t, lane,
+  for (TileQueue q(t_begin); q.t < t_stop; q.next(t_begin, t_stop)) {   // tiles as the warp frees up
+    q.ask(s.tickets, t_begin, t_stop, lane);
+    if (prefetch) prefetch_tile_sources(s, packed, readable_words, tile_bases, total, q.t, lane);
+    spell_tile_global(s, packed, packed_bytes, readable_words, aligned16, out, tile_bases, total, q.t, lane,
                       lists[threadIdx.x >> 5]);
-    t = t_begin + (long long)__shfl_sync(0xffffffffu, tk, 0);
   }
 }
 
@@ -456,7 +450,7 @@ cudaError_t launch_emit2_bt(const DevGraph& g, const Scratch& s, const Tuning& t
   const bool prefetch = aligned16 && !g.packed_host;
   static const int resident = resident_blocks(k_emit2<BT>, BT);   // once, safely across threads
   const int per_sm = t.emit_blocks_per_sm < resident ? t.emit_blocks_per_sm : resident;
-  cudaError_t e = cudaMemsetAsync(&s.ctr->emit_ticket, 0, sizeof(unsigned long long), env.stream);
+  cudaError_t e = cudaMemsetAsync(s.tickets, 0, kTicketSets * kTicketStride * sizeof(unsigned long long), env.stream);
   if (e != cudaSuccess) return e;
   const bool chained = false;                     // a memset, not a kernel, comes right before
   return launch_kb(k_emit2<BT>, env.num_sms * per_sm, BT, env, chained, s, g.packed,

@@ -49,8 +49,6 @@ struct Counters {
   unsigned int n_tiles;        // emission tiles
   unsigned int pad;
   long long total_bases;
-  // spelling
-  unsigned long long emit_ticket;  // output tiles handed out by a spelling launch (zeroed before each)
 };
 
 // The graph as kernels see it (all device pointers).
@@ -128,6 +126,40 @@ struct Scratch {
   int64_t scan_tiles_cap;
   Counters* ctr;
   DevError* derr;
+  unsigned long long* tickets;  // kTicketSets counters, one 128-byte line each: a spelling launch's tiles
+};
+
+// Output tiles [t_begin, t_stop) for the W warps of a persistent grid: warp gw
+// spells tile t_begin + gw first; the tiles from t_begin + W on go out one at a
+// time, the tiles t_begin + W + c + kTicketSets * k from counter c (zeroed
+// before the launch) to the warps gw = c mod kTicketSets, each warp asking for
+// its next ticket while it spells its current tile. A warp thus takes its next
+// tile when it finishes one, and the warps end together whatever each tile
+// holds; no launch starts with every warp on one counter, and a launch with no
+// more tiles than warps touches no counter.
+constexpr int kTicketSets = 8, kTicketStride = 16;
+
+struct TileQueue {
+  long long t;                 // the warp's current tile (past t_stop: done)
+  unsigned long long tk;
+  __device__ static long long warp_id() {
+    return (long long)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
+  }
+  __device__ static long long warps() { return (long long)gridDim.x * (blockDim.x >> 5); }
+  __device__ TileQueue(long long t_begin) : t(t_begin + warp_id()), tk(0) {}
+  // The warp's current tile is t while t < t_stop; call ask() as the tile is
+  // started and next() when it is done (warp-uniform calls, with the launch's
+  // counters and tile range; the queue keeps no copy, to spare registers). A
+  // grid with no fewer warps than tiles takes no ticket.
+  __device__ void ask(unsigned long long* tickets, long long t_begin, long long t_stop, int lane) {
+    if (t_begin + warps() < t_stop && lane == 0)
+      tk = atomicAdd(tickets + kTicketStride * (int)(warp_id() % kTicketSets), 1ull);
+  }
+  __device__ void next(long long t_begin, long long t_stop) {
+    const long long k = (long long)__shfl_sync(0xffffffffu, tk, 0);
+    t = t_begin + warps() < t_stop ? t_begin + warps() + warp_id() % kTicketSets + (long long)kTicketSets * k
+                                   : 0x7fffffffffffffffll;
+  }
 };
 
 // Tuning knobs (chosen by the autotuner per size class).
