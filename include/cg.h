@@ -165,7 +165,7 @@ CG_API cg_status cg_batch_ranges(cg_graph* g, int64_t* first_contig, int64_t* fi
 typedef struct cg_server cg_server;
 typedef struct {
   int32_t max_batch;          /* requests per batch, >= 1 */
-  int32_t workers;            /* batches in flight, 1..8 */
+  int32_t workers;            /* batches in flight, 1..16 */
   uint64_t hbm_budget_bytes;  /* admission budget, > 0 */
 } cg_server_opts;
 typedef struct {

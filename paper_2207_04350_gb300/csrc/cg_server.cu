@@ -2,10 +2,11 @@
 // path. Requests (one string graph each, host inputs) are admitted against a
 // device-memory budget, grouped by continuous batching -- every admitted
 // request waiting when a worker becomes free joins its batch -- and run as
-// one union graph per batch. Two workers, each with its own context and
-// stream, keep two batches in flight so that one batch's host-to-device copy
-// overlaps the other's kernels; each request's contigs are copied from the
-// batch's device output straight into the request's result. Host code only.
+// one union graph per batch. Several workers, each with its own context and
+// stream, keep as many batches in flight, so that one batch's host-to-device
+// copy or host-link reads overlap the others' kernels and copies back; each
+// request's contigs are copied from the batch's device output straight into
+// the request's result. Host code only.
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -291,7 +292,7 @@ void worker_main(cg_server* s, int index) {
 extern "C" {
 
 cg_status cg_server_start(int device, const cg_server_opts* opts, cg_server** out) {
-  if (!opts || !out || opts->max_batch < 1 || opts->workers < 1 || opts->workers > 8 || opts->hbm_budget_bytes == 0)
+  if (!opts || !out || opts->max_batch < 1 || opts->workers < 1 || opts->workers > 16 || opts->hbm_budget_bytes == 0)
     return CG_EINVAL;
   *out = nullptr;
   cg_server* s = new (std::nothrow) cg_server();
