@@ -79,9 +79,10 @@ def test_batched_512_full(ctx):
 def test_served_pool_full(ctx):
     """Every one of the 200 graphs of the served pool through the server, against
     the oracle: once alone (one request per batch, one worker) and once mixed
-    into batches (two workers, up to 64 requests per batch) by a seeded
-    Poisson-order submission in which every graph appears at least once and
-    some several times, so that each result is checked alone and in the mix."""
+    into batches (eight workers, as the bench serves, up to 64 requests per
+    batch) by a seeded Poisson-order submission in which every graph appears at
+    least once and some several times, so that each result is checked alone and
+    in the mix."""
     import time
     keep = []
     alloc = _pinned_alloc(keep)
@@ -110,7 +111,7 @@ def test_served_pool_full(ctx):
     rng = np.random.default_rng(gen.SEED0 + 4)
     order = np.concatenate([rng.permutation(P), rng.integers(0, P, size=P)])
     gaps = rng.exponential(2e-4, size=len(order))
-    mixed = cg.Server(0, hbm_budget_bytes=150 << 30, max_batch=64, workers=2)
+    mixed = cg.Server(0, hbm_budget_bytes=150 << 30, max_batch=64, workers=8)
     try:
         ids = []
         for j, gap in zip(order.tolist(), gaps.tolist()):
