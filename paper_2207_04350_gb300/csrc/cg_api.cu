@@ -2,6 +2,7 @@
 // stage sequence mask -> chains -> offsets -> emission on one CUDA stream.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -896,7 +897,45 @@ cg_status cg_load_batch(cg_ctx* c, const cg_graph_desc* d, int k, uint32_t flags
   g->batch_k = k;
   g->batch_R = tab;
   if (!host_reads) CK(cudaMemsetAsync(packed, 0, (size_t)PB[k] + 16, c->stream), "clear packed");
-  for (int j = 0; j < k; ++j) {
+  // Host inputs all in pinned memory: one kernel reads them in place (a copy
+  // call per graph and array costs a few microseconds of host time each, which
+  // dominates a batch of hundreds of small graphs); otherwise a copy per array.
+  std::vector<cg::CopySeg> segs;
+  bool in_place = mem == CG_MEM_HOST;
+  for (int j = 0; j < k && in_place; ++j) {
+    const cg_graph_desc& q = d[j];
+    auto add = [&](void* dst, const void* src, long long bytes) {
+      if (!in_place || bytes <= 0) return;
+      const uint8_t* a = (const uint8_t*)pinned_device_alias(src);
+      if (!a) { in_place = false; return; }
+      const long long kPiece = 256 << 10;               // long arrays in pieces, to spread them over warps
+      for (long long o = 0; o < bytes; o += kPiece)
+        segs.push_back({a + o, (uint8_t*)dst + o, std::min(kPiece, bytes - o)});
+    };
+    add((char*)stage_rp + (size_t)SR[j] * rpb, q.row_ptr, (q.n_reads + 1) * (long long)rpb);
+    add(col + E[j], q.col, q.n_entries * 4ll);
+    add(code + E[j], q.code, q.n_entries);
+    if (!xdrop) add(suf + E[j], q.suf, q.n_entries * 4ll);
+    if (xdrop) add(pre + E[j], q.pre, q.n_entries * 4ll);
+    if (xdrop) add(post + E[j], q.post, q.n_entries * 4ll);
+    add(len + R[j], q.len, q.n_reads * 4ll);
+    add(off + R[j], q.off, q.n_reads * 8ll);
+    if (!host_reads) add(packed + PB[j], q.packed, q.packed_bytes);
+  }
+  cg::CopySeg* d_segs = nullptr;
+  if (in_place && !segs.empty()) {
+    d_segs = (cg::CopySeg*)dalloc(c, segs.size() * sizeof(cg::CopySeg), &st);
+    if (!d_segs) { dfree(c, stage_rp); return bail(st); }
+    cudaError_t e = cudaMemcpyAsync(d_segs, segs.data(), segs.size() * sizeof(cg::CopySeg), cudaMemcpyHostToDevice,
+                                    c->stream);
+    if (e == cudaSuccess) e = cg::launch_batch_copy(d_segs, (int)segs.size(), c->env);
+    if (e != cudaSuccess) {
+      dfree(c, d_segs);
+      dfree(c, stage_rp);
+      return bail(cuda_fail(c, e, "copy batch input"));
+    }
+  }
+  for (int j = 0; j < k && !in_place; ++j) {
     const cg_graph_desc& q = d[j];
     auto cp = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
       return bytes ? cudaMemcpyAsync(dst, src, bytes, kind, c->stream) : cudaSuccess;
@@ -926,8 +965,9 @@ cg_status cg_load_batch(cg_ctx* c, const cg_graph_desc* d, int k, uint32_t flags
   }
   CK(cg::launch_batch_fixup(k, tab, tab + (k + 1), tab + 2 * (k + 1), tab + 3 * (k + 1), stage_rp, rpb, rp, col, off,
                             n, m, c->env), "batch fixup");
-  CK(cudaStreamSynchronize(c->stream), "stream synchronize");   // host_tab is read by the copy above
+  CK(cudaStreamSynchronize(c->stream), "stream synchronize");   // host_tab and segs are read by the copies above
   dfree(c, stage_rp);
+  if (d_segs) dfree(c, d_segs);
   G.row_ptr = rp;
   G.col = col;
   G.code = code;

@@ -234,6 +234,15 @@ cudaError_t launch_emit2(const DevGraph& g, const Scratch& s, const Tuning& t, u
                          const LaunchEnv& env, long long t_begin = 0, long long t_end = 1ll << 62);
 cudaError_t launch_export_contig_off(const Scratch& s, int64_t* out, int64_t cap, const LaunchEnv& env);
 cudaError_t launch_sum_len(const DevGraph& g, unsigned long long* out, const LaunchEnv& env);
+// One copy of a batched load: `bytes` bytes from src (device memory, or the
+// device alias of pinned host memory) to dst.
+struct CopySeg {
+  const uint8_t* src;
+  uint8_t* dst;
+  long long bytes;
+};
+// Every segment of seg[0, n) (device memory), a warp per segment.
+cudaError_t launch_batch_copy(const CopySeg* seg, int n, const LaunchEnv& env);
 cudaError_t launch_batch_fixup(int k, const int64_t* R, const int64_t* E, const int64_t* PB, const int64_t* SR,
                                const void* stage_rp, int rp_bytes, int64_t* rp, int32_t* col, int64_t* off,
                                long long N, long long M, const LaunchEnv& env);
