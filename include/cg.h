@@ -139,7 +139,9 @@ CG_API cg_status cg_free_graph(cg_graph* g);
  * packed reads are pinned host memory, 4-byte aligned, keep them there, and
  * each spelling call first gathers the words of the pieces it spells from the
  * owning graph's stream over the host link (CG_EINVAL when a graph's reads
- * are not pinned). Chains never cross graphs, so the union's
+ * are not pinned). Host inputs that are all pinned memory are read in place
+ * by one copy kernel; other host inputs are copied array by array. Chains
+ * never cross graphs, so the union's
  * contigs are those of graph 0, then graph 1, ... in each graph's own order,
  * and read r of graph j is read R_j + r of the union (R_j = reads of graphs
  * before j). Waits for the GPU. */
