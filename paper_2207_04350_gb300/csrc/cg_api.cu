@@ -339,7 +339,9 @@ const cg::DevGraph& emit_graph(const cg_graph* g) { return g->host_batch ? g->g_
 // For a batch with host-resident reads, after the offsets stage: the words of
 // every piece, gathered from its graph's pinned host stream into one device
 // buffer (at most total/16 + 3 W words), and the pieces' sources moved there.
-cg_status prepare_emit(cg_graph* g) {
+// With gather_all false only the slots are laid out: the caller gathers the
+// pieces range by range (gather_range) before spelling each range of tiles.
+cg_status prepare_emit(cg_graph* g, bool gather_all = true) {
   if (!g->host_batch) return CG_OK;
   cg_ctx* c = g->ctx;
   cg_status st = wait_and_read(g);                  // the walk positions and bases of this layout
@@ -360,8 +362,9 @@ cg_status prepare_emit(cg_graph* g) {
     if (st != CG_OK) return st;
   }
   CK(cg::launch_gather_slots(g->s, W, g->hb_slot, g->hb_state, g->hb_state_cap, c->env), "gather slots");
-  CK(cg::launch_gather_pieces(g->s, g->batch_k, g->hb_PB, g->hb_base, g->hb_bytes, g->hb_slot, g->hb_dst,
-                              g->hb_dst_words, W, c->env), "gather pieces");
+  if (gather_all)
+    CK(cg::launch_gather_pieces(g->s, g->batch_k, g->hb_PB, g->hb_base, g->hb_bytes, g->hb_slot, g->hb_dst,
+                                g->hb_dst_words, W, c->env), "gather pieces");
   g->g_emit = g->g;
   g->g_emit.packed = reinterpret_cast<const uint8_t*>(g->hb_dst);
   g->g_emit.packed_bytes = 4 * g->hb_dst_words;
@@ -1130,8 +1133,19 @@ cg_status cg_emit_contigs(cg_graph* g, int64_t* contig_off, int64_t contig_off_c
   }
   st = run_offsets(g);
   if (st != CG_OK) return st;
+  // Large outputs into host memory are spelled and copied in chunks of tiles
+  // (below); a batch with host-resident reads then gathers each chunk's
+  // pieces just before spelling it, so that the gathers, which read the host
+  // link, overlap the copies of earlier chunks, which write it.
+  const int64_t kPipelineMin = 64ll << 20, kChunk = 128ll << 20;
+  bool chunk_gather = false;
   if (bases) {
-    st = prepare_emit(g);
+    if (g->host_batch && mem == CG_MEM_HOST) {
+      st = wait_and_read(g);
+      if (st != CG_OK) return st;
+      chunk_gather = c->h_ctr->total_bases >= kPipelineMin;
+    }
+    st = prepare_emit(g, !chunk_gather);
     if (st != CG_OK) return st;
   }
   if (mem == CG_MEM_DEVICE) {
@@ -1169,7 +1183,6 @@ cg_status cg_emit_contigs(cg_graph* g, int64_t* contig_off, int64_t contig_off_c
     // link, not the spelling, bounds the step). Smaller ones, when pinned: the
     // kernel writes them over the host link in place; otherwise staged and
     // copied once.
-    const int64_t kPipelineMin = 64ll << 20, kChunk = 128ll << 20;
     const bool pipelined = bases && total >= kPipelineMin;
     uint8_t* direct = c->host_direct && !pipelined ? (uint8_t*)pinned_device_alias(bases) : nullptr;
     if (direct && !aligned(direct, 16)) direct = nullptr;
@@ -1190,6 +1203,9 @@ cg_status cg_emit_contigs(cg_graph* g, int64_t* contig_off, int64_t contig_off_c
       for (int64_t t0 = 0; t0 < tiles; t0 += per) {
         const int64_t t1 = std::min(tiles, t0 + per);
         const int64_t b0 = t0 * tb, b1 = std::min(total, t1 * tb);
+        if (chunk_gather)
+          CK(cg::launch_gather_pieces(g->s, g->batch_k, g->hb_PB, g->hb_base, g->hb_bytes, g->hb_slot, g->hb_dst,
+                                      g->hb_dst_words, c->h_ctr->n_walk, c->env, t0, t1), "gather pieces");
         CK(cg::launch_emit(emit_graph(g), g->s, gt(g), g->stage_bases, g->stage_bases_cap, c->env, t0, t1),
            "emission kernel");
         CK(cudaEventRecord(c->copy_ev, c->stream), "chunk event");

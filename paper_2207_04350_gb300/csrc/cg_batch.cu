@@ -161,13 +161,21 @@ struct SlotStore {
 // One warp per piece: the graph holding its first word, the words copied
 // with that graph's bounds (words past its stream read as 0), the source
 // moved into the slot.
+// With t_end > 0 only the pieces that output tiles [t_begin, t_end) need and
+// that no earlier range took: (tile_seg[t_begin], tile_seg[t_end]] (from
+// piece 0 when t_begin is 0), each piece once, as its source is moved.
 __global__ void __launch_bounds__(kBlock) k_gather_pieces(Scratch s, int k, const int64_t* PB,
                                                           const uint8_t* const* base, const int64_t* bytes,
                                                           const unsigned long long* slot, uint32_t* dst,
-                                                          long long cap_words) {
-  const long long W = *(const volatile unsigned*)&s.ctr->n_walk;
+                                                          long long cap_words, long long t_begin, long long t_end) {
+  long long j_begin = 0, W = *(const volatile unsigned*)&s.ctr->n_walk;
+  if (t_end > 0) {
+    const long long nt = *(const volatile unsigned*)&s.ctr->n_tiles;
+    j_begin = t_begin > 0 ? (long long)s.tile_seg[min(t_begin, nt)] + 1 : 0;
+    W = min(W, (long long)s.tile_seg[min(t_end, nt)] + 1);
+  }
   const int lane = threadIdx.x & 31;
-  for (long long j = grid_tid() >> 5; j < W; j += grid_threads() >> 5) {
+  for (long long j = j_begin + (grid_tid() >> 5); j < W; j += grid_threads() >> 5) {
     const unsigned long long w = s.wsrc[j];
     long long w0, nw;
     piece_words(w, s.wlen[j], &w0, &nw);
@@ -219,9 +227,10 @@ cudaError_t launch_gather_slots(const Scratch& s, long long W, unsigned long lon
 
 cudaError_t launch_gather_pieces(const Scratch& s, int k, const int64_t* PB, const uint8_t* const* base,
                                  const int64_t* bytes, const unsigned long long* slot, uint32_t* dst,
-                                 long long cap_words, long long W, const LaunchEnv& env) {
+                                 long long cap_words, long long W, const LaunchEnv& env, long long t_begin,
+                                 long long t_end) {
   k_gather_pieces<<<grid_for(32 * (W > 0 ? W : 1), env), kBlock, 0, env.stream>>>(s, k, PB, base, bytes, slot, dst,
-                                                                                 cap_words);
+                                                                                 cap_words, t_begin, t_end);
   mark(env, "k_gather_pieces");
   return cudaGetLastError();
 }

@@ -253,9 +253,12 @@ cudaError_t launch_batch_ranges(const Scratch& s, int k, const int64_t* R, long 
 // buffer, which rewrites every piece's source into it.
 cudaError_t launch_gather_slots(const Scratch& s, long long W, unsigned long long* slot, unsigned long long* state,
                                 long long state_cap, const LaunchEnv& env);
+// With t_end > 0: only the pieces output tiles [t_begin, t_end) need that no
+// earlier range of an increasing sequence took.
 cudaError_t launch_gather_pieces(const Scratch& s, int k, const int64_t* PB, const uint8_t* const* base,
                                  const int64_t* bytes, const unsigned long long* slot, uint32_t* dst,
-                                 long long cap_words, long long W, const LaunchEnv& env);
+                                 long long cap_words, long long W, const LaunchEnv& env, long long t_begin = 0,
+                                 long long t_end = 0);
 // Buffers of the contig-weight sort (capacity: the number of contigs).
 struct SortBuffers {
   unsigned long long* key[2];
