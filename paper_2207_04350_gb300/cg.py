@@ -577,9 +577,10 @@ def cg_get_stats(ctx: Context) -> dict:
 
 
 class Server:
-    """cg_server: continuous batching over the batched form (host inputs and outputs)."""
+    """cg_server: continuous batching over the batched form (host inputs and outputs).
+    `workers` batches are in flight at once, each on its own context and stream."""
 
-    def __init__(self, device: int = 0, hbm_budget_bytes: int = 150 << 30, max_batch: int = 64, workers: int = 2):
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 150 << 30, max_batch: int = 64, workers: int = 8):
         self.ptr = ctypes.c_void_p()
         opts = ServerOpts(int(max_batch), int(workers), int(hbm_budget_bytes))
         st = lib().cg_server_start(int(device), ctypes.byref(opts), ctypes.byref(self.ptr))
