@@ -77,3 +77,45 @@ def test_batch_one_graph_equals_plain(ctx):
     finally:
         b.close()
         p.close()
+
+
+def _pinned_at(a, offset, keep):
+    """a's values in pinned host memory, `offset` bytes into a pinned buffer (so
+    that the copy may start at any alignment)."""
+    import torch
+    buf = torch.empty(a.nbytes + offset + 16, dtype=torch.uint8, pin_memory=True)
+    keep.append(buf)
+    v = buf.numpy()[offset: offset + a.nbytes].view(a.dtype)
+    v[...] = a
+    return v
+
+
+def test_batch_from_pinned_memory_in_place(ctx):
+    """Every input array of every graph in pinned memory: the batch is read in
+    place by the copy kernel, at 16-byte, 4-byte and byte alignments (arrays
+    placed at offsets 0..7 into their buffers), with the reads in pinned
+    memory too (copied into the union, or read in place with HOST_READS)."""
+    keep = []
+    graphs = [gen.generate(gen.batched_graph(j), threads=8) for j in range(12)]
+    graphs.append(structured(5, [300, 4, 5, 2, 2, 1], [False, True, True, False, False, False], lone=7))
+    graphs[-1].row_ptr = graphs[-1].row_ptr.astype(np.int32)
+    want = [oracle.run(G, min_chain_reads=2) for G in graphs]
+    pinned = []
+    for j, G in enumerate(graphs):
+        P = type("P", (), {})()
+        for i, k in enumerate(("row_ptr", "col", "code", "suf", "len", "off")):
+            setattr(P, k, _pinned_at(getattr(G, k), (j + 3 * i) % 8, keep))
+        P.packed = _pinned_at(G.packed, 0, keep)           # HOST_READS wants the reads 4-byte aligned
+        pinned.append(P)
+    for flags in (0, cg.HOST_READS):
+        g = cg.cg_load_batch(ctx, pinned, flags=flags, min_chain_reads=2)
+        try:
+            off, bases = cg.contigs_host(g)
+            fc, fb = cg.cg_batch_ranges(g)
+        finally:
+            g.close()
+        for j, w in enumerate(want):
+            c0, c1 = int(fc[j]), int(fc[j + 1])
+            assert c1 - c0 == w.n_contigs, j
+            assert np.array_equal(off[c0:c1 + 1] - off[c0], w.contig_off), j
+            assert np.array_equal(bases[int(fb[j]):int(fb[j + 1])], w.bases), j
