@@ -344,9 +344,9 @@ CG_API cg_status cg_emit_share_received(cg_graph* g, int32_t n_shares, const int
 /* Launch parameters of a context's kernels. None changes any output. */
 typedef struct {
   int32_t ruler_log2;         /* list ranking: a read starts a sublist with probability 2^-ruler_log2, 1..12 */
-  int32_t tile_bytes;         /* spelling: output tile per warp iteration, a power of two from 4096 to 131072;
-                                 until it is set, each graph takes its own from its total read length
-                                 (4 KiB below 2^27 bases, doubling per doubling, 32 KiB from 2^29) */
+  int32_t tile_bytes;         /* spelling: output a warp spells at a time, a power of two from 4096 to
+                                 131072; 0 (the default): each launch chooses 4, 8, 16 or 32 KiB from
+                                 its output, the largest that leaves every warp at least 8 of them */
   int32_t emit_blocks_per_sm; /* spelling: resident blocks per SM, 1..16 (at most what fits) */
   int32_t emit_block_threads; /* spelling: threads per block (the CTA size), 128, 256 or 512 */
 } cg_tuning;

@@ -25,8 +25,9 @@ from . import cg
 # occupancy, and full occupancy with CTAs of 256, 128 and 512 threads (the
 # blocks per SM are capped at what fits)
 LAUNCH = ((4, 256), (8, 256), (16, 128), (2, 512))
+# spelling tile: 0 lets each launch choose from its output size
 GRID = [dict(ruler_log2=r, tile_bytes=t, emit_blocks_per_sm=b, emit_block_threads=bt)
-        for r in (3, 4, 5) for t in (16384, 32768, 65536) for b, bt in LAUNCH]
+        for r in (3, 4, 5) for t in (0, 16384, 32768, 65536) for b, bt in LAUNCH]
 
 
 def size_class(n_reads: int, n_entries: int, packed_bytes: int) -> str:

@@ -43,7 +43,6 @@ struct cg_ctx {
   cudaStream_t copy_stream = nullptr;  // device-to-host copies overlapping the spelling (created on first use)
   cudaEvent_t copy_ev = nullptr;       //   a chunk spelled / the copies done
   cg::FaultPlan fault;                 // host-side fault injection (tests)
-  bool tile_auto = true;               // tile size chosen per graph until cg_set_tuning sets one
 };
 
 // A captured stage: the instantiated graph and what its capture recorded.
@@ -61,6 +60,7 @@ struct cg_graph {
   std::vector<void*> owned;
   int stage = 0;                  // 0 loaded, 1 masked, 2 chained, 3 offsets
   int64_t sum_len = 0;
+  int layout_tile = 4096;         // output layout tile (gt)
   uint8_t* stage_bases = nullptr; // device staging for host outputs
   int64_t stage_bases_cap = 0;
   void* stage_reads = nullptr;
@@ -83,7 +83,6 @@ struct cg_graph {
   uint32_t* hb_dst = nullptr;
   int64_t hb_dst_words = 0;
   cg::DevGraph g_emit{};               // the graph as the spelling sees it (gathered reads)
-  int auto_tile = 32768;               // output tile when the context's tile size is left automatic
   cg::Tuning tune{};                   // the context's launch parameters as this graph uses them
 };
 
@@ -227,12 +226,15 @@ void record_stage_event(cg_ctx* c, int i) {
 
 uint64_t mix_key(uint64_t h, uint64_t v) { return (h ^ (v + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2))); }
 
-// The launch parameters a graph's stages use: the context's, with the output
-// tile chosen per graph (from the graph's total read length) unless the caller
-// set one. Smaller outputs get smaller tiles, so that more warps share them.
+// The launch parameters a graph's stages use: the context's, with the graph's
+// own layout tile (the granularity of its tile map, shares and copy chunks:
+// 4 KiB below 2^31 bases of reads, else 8 KiB, where the finer map costs the
+// offsets stage more than it gives the spelling). Each spelling launch groups
+// layout tiles into spans of emit_tile bytes, or of a size it chooses from the
+// output when emit_tile is 0.
 const cg::Tuning& gt(cg_graph* g) {
   g->tune = g->ctx->tune;
-  if (g->ctx->tile_auto) g->tune.tile_bytes = g->auto_tile;
+  g->tune.tile_bytes = g->layout_tile;
   return g->tune;
 }
 
@@ -454,10 +456,8 @@ cg_status finish_load(cg_graph* g, uint32_t flags) {
   if (st != CG_OK) return st;
   if (c->fault.hit("bad_graph")) return fail(c, CG_EGRAPH, "injected: invalid string graph");
   g->sum_len = (int64_t)*c->h_u64;
-  // automatic output tile: 4 KiB below 128 Mbases of reads, doubling per doubling, 32 KiB from 1 Gbase
-  g->auto_tile = 4096;
-  while (g->auto_tile < 32768 && g->sum_len >= ((int64_t)1 << 27) * (g->auto_tile / 4096)) g->auto_tile *= 2;
-  // the longest possible output is every read spelled whole; tiles of at least 4 KiB
+  g->layout_tile = g->sum_len < ((int64_t)1 << 31) ? 4096 : 8192;
+  // the longest possible output is every read spelled whole, in tiles of at least 4 KiB
   S.tiles_cap = g->sum_len / 4096 + 2;
   S.tile_seg = galloc<int32_t>(g, (size_t)S.tiles_cap + 1, &st);
   return st;
@@ -574,12 +574,10 @@ cg_status cg_set_tuning(cg_ctx* c, const cg_tuning* t) {
     if (t->ruler_log2 > 12) return fail(c, CG_EINVAL, "ruler_log2 must be in 1..12");
     n.ruler_log2 = t->ruler_log2;
   }
-  bool tile_set = false;
   if (t->tile_bytes > 0) {
     if (t->tile_bytes < 4096 || t->tile_bytes > 131072 || (t->tile_bytes & (t->tile_bytes - 1)))
       return fail(c, CG_EINVAL, "tile_bytes must be a power of two from 4096 to 131072");
-    n.tile_bytes = t->tile_bytes;
-    tile_set = true;
+    n.emit_tile = t->tile_bytes;
   }
   if (t->emit_blocks_per_sm > 0) {
     if (t->emit_blocks_per_sm > 16) return fail(c, CG_EINVAL, "emit_blocks_per_sm must be in 1..16");
@@ -591,14 +589,13 @@ cg_status cg_set_tuning(cg_ctx* c, const cg_tuning* t) {
     n.emit_block_threads = t->emit_block_threads;
   }
   c->tune = n;
-  if (tile_set) c->tile_auto = false;
   return CG_OK;
 }
 
 cg_status cg_get_tuning(cg_ctx* c, cg_tuning* out) {
   if (!c || !out) return CG_EINVAL;
   out->ruler_log2 = c->tune.ruler_log2;
-  out->tile_bytes = c->tune.tile_bytes;
+  out->tile_bytes = c->tune.emit_tile;
   out->emit_blocks_per_sm = c->tune.emit_blocks_per_sm;
   out->emit_block_threads = c->tune.emit_block_threads;
   return CG_OK;

@@ -73,8 +73,8 @@ __device__ __forceinline__ uint8_t base_at(const uint8_t* packed, unsigned long 
 template <int U, int BT>
 __global__ void __launch_bounds__(BT, 1024 / BT) k_emit(Scratch s, const uint8_t* packed, long long packed_bytes,
                                                  long long readable_words, uint8_t* out, long long cap,
-                                                 int tile_bytes, long long t_begin, long long t_end, int share,
-                                                 int n_shares) {
+                                                 int tile_bytes, int emit_tile, long long t_begin, long long t_end,
+                                                 int share, int n_shares) {
   __shared__ uint32_t lut[2][256];
   for (int i = threadIdx.x; i < 256; i += blockDim.x) {
     uint32_t f = 0, r = 0;
@@ -109,14 +109,17 @@ __global__ void __launch_bounds__(BT, 1024 / BT) k_emit(Scratch s, const uint8_t
   const long long full_words = packed_bytes >> 2;
   const int64_t* oo = s.out_off;
   const unsigned long long* ws = s.wsrc;
-  const long long t_stop = min(ntiles, t_end);          // the tiles [t_begin, t_end) of this launch
-  TileQueue q(t_begin);                                 // the warp's tiles, from counters after the first
-  for (; q.t < t_stop; q.next(t_begin, t_stop)) {
-    q.ask(s.tickets, t_begin, t_stop, lane);
-    const long long t = q.t;
-    const int lo = s.tile_seg[t], hi = s.tile_seg[t + 1];
+  const long long t_stop = min(ntiles, t_end);          // the layout tiles [t_begin, t_end) of this launch
+  // a warp spells `span` consecutive layout tiles at a time
+  const int span = emit_span(t_stop - t_begin, grid_threads() >> 5, emit_tile, tile_bytes);
+  const long long n_spans = (t_stop - t_begin + span - 1) / span;
+  TileQueue q(0);                                       // the warp's spans, from counters after the first
+  for (; q.t < n_spans; q.next(0, n_spans)) {
+    q.ask(s.tickets, 0, n_spans, lane);
+    const long long t = t_begin + q.t * span, t_hi = min(t + span, t_stop);
+    const int lo = s.tile_seg[t], hi = s.tile_seg[t_hi];
     const long long tbase = t * (long long)tile_bytes;
-    const long long tend = min(tbase + (long long)tile_bytes, total);
+    const long long tend = min(t_hi * (long long)tile_bytes, total);
     for (int jb = lo; jb <= hi; jb += 32) {
       int jl = jb + lane;
       long long my_o = jl <= hi ? oo[jl] : 0, my_e = jl <= hi ? oo[jl + 1] : 0;
@@ -226,7 +229,7 @@ cudaError_t launch_emit_bt(const DevGraph& g, const Scratch& s, const Tuning& t,
   const bool chained = false;                     // a memset, not a kernel, comes right before
   return launch_kb(k_emit<4, BT>, env.num_sms * per_sm, BT, env, chained, s, g.packed,
                    (long long)g.packed_bytes, (long long)(g.packed_readable / 4), out, (long long)cap, t.tile_bytes,
-                   t_begin, t_end, share, n_shares);
+                   t.emit_tile, t_begin, t_end, share, n_shares);
 }
 
 }  // namespace

@@ -199,12 +199,12 @@ __device__ __forceinline__ Chunk chunk_at_checked(const uint32_t* words, const u
 // 0.758 ms), whose time the output writes set.
 __device__ __forceinline__ void prefetch_tile_sources(const Scratch& s, const uint8_t* packed,
                                                       long long readable_words, int tile_bases, long long total,
-                                                      long long t, int lane) {
+                                                      long long t, long long t_hi, int lane) {
   const int64_t* oo = s.out_off;
   const unsigned long long* ws = s.wsrc;
-  const int lo = s.tile_seg[t], hi = s.tile_seg[t + 1];
+  const int lo = s.tile_seg[t], hi = s.tile_seg[t_hi];
   const long long tbase = t * (long long)tile_bases;
-  const long long tend = min(tbase + (long long)tile_bases, total);
+  const long long tend = min(t_hi * (long long)tile_bases, total);
   const long long top = (readable_words * 4) & ~15ll;
   for (int j = lo + lane; j <= hi; j += 32) {
     const long long oj = oo[j], oe = oo[j + 1];
@@ -247,15 +247,15 @@ struct PieceList {
 // chunks, so a chunk never spans two tiles.
 __device__ void spell_tile_global(const Scratch& s, const uint8_t* packed, long long packed_bytes,
                                   long long readable_words, bool aligned16, uint4* out, int tile_bases,
-                                  long long total, long long t, int lane, PieceList& L) {
+                                  long long total, long long t, long long t_hi, int lane, PieceList& L) {
   const unsigned full = 0xffffffffu;
   const uint32_t* words = reinterpret_cast<const uint32_t*>(packed);
   const long long full_words = packed_bytes >> 2;
   const int64_t* oo = s.out_off;
   const unsigned long long* ws = s.wsrc;
-  const int lo = s.tile_seg[t], hi = s.tile_seg[t + 1];
+  const int lo = s.tile_seg[t], hi = s.tile_seg[t_hi];
   const long long tbase = t * (long long)tile_bases;
-  const long long tend = min(tbase + (long long)tile_bases, total);
+  const long long tend = min(t_hi * (long long)tile_bases, total);
   for (int jb = lo; jb <= hi; jb += 32) {
     const int j = jb + lane;
     int T;
@@ -415,7 +415,8 @@ __device__ void spell_tile_global(const Scratch& s, const uint8_t* packed, long 
 template <int BT>
 __global__ void __launch_bounds__(BT, BT >= 512 ? 2 : CG_EMIT2_MIN_BLOCKS * 256 / BT)
     k_emit2(Scratch s, const uint8_t* packed, long long packed_bytes, long long readable_words, bool aligned16,
-            bool prefetch, uint4* out, long long cap_bytes, int tile_bases, long long t_begin, long long t_end) {
+            bool prefetch, uint4* out, long long cap_bytes, int tile_bases, int emit_tile, long long t_begin,
+            long long t_end) {
   pdl_enter();
   __shared__ PieceList lists[BT / 32];
   const Counters* c = s.ctr;
@@ -428,10 +429,14 @@ __global__ void __launch_bounds__(BT, BT >= 512 ? 2 : CG_EMIT2_MIN_BLOCKS * 256 
   const int lane = threadIdx.x & 31;
   const long long ntiles = (total + tile_bases - 1) / tile_bases;
   const long long t_stop = min(ntiles, t_end);          // the tiles [t_begin, t_end) of this launch
-  for (TileQueue q(t_begin); q.t < t_stop; q.next(t_begin, t_stop)) {   // tiles as the warp frees up
-    q.ask(s.tickets, t_begin, t_stop, lane);
-    if (prefetch) prefetch_tile_sources(s, packed, readable_words, tile_bases, total, q.t, lane);
-    spell_tile_global(s, packed, packed_bytes, readable_words, aligned16, out, tile_bases, total, q.t, lane,
+  // a warp spells `span` consecutive layout tiles at a time, spans taken as the warp frees up
+  const int span = emit_span(t_stop - t_begin, grid_threads() >> 5, emit_tile, tile_bases);
+  const long long n_spans = (t_stop - t_begin + span - 1) / span;
+  for (TileQueue q(0); q.t < n_spans; q.next(0, n_spans)) {
+    q.ask(s.tickets, 0, n_spans, lane);
+    const long long t = t_begin + q.t * span, t_hi = min(t + span, t_stop);
+    if (prefetch) prefetch_tile_sources(s, packed, readable_words, tile_bases, total, t, t_hi, lane);
+    spell_tile_global(s, packed, packed_bytes, readable_words, aligned16, out, tile_bases, total, t, t_hi, lane,
                       lists[threadIdx.x >> 5]);
   }
 }
@@ -455,7 +460,7 @@ cudaError_t launch_emit2_bt(const DevGraph& g, const Scratch& s, const Tuning& t
   const bool chained = false;                     // a memset, not a kernel, comes right before
   return launch_kb(k_emit2<BT>, env.num_sms * per_sm, BT, env, chained, s, g.packed,
                    (long long)g.packed_bytes, (long long)(g.packed_readable / 4), aligned16, prefetch,
-                   reinterpret_cast<uint4*>(out), (long long)cap, t.tile_bytes, t_begin, t_end);
+                   reinterpret_cast<uint4*>(out), (long long)cap, t.tile_bytes, t.emit_tile, t_begin, t_end);
 }
 
 }  // namespace

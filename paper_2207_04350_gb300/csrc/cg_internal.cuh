@@ -165,7 +165,8 @@ struct TileQueue {
 // Tuning knobs (chosen by the autotuner per size class).
 struct Tuning {
   int ruler_log2 = 3;      // a read starts a sublist with probability 2^-ruler_log2
-  int tile_bytes = 32768;  // emission tile: 4, 8, 16 or 32 KiB
+  int tile_bytes = 4096;   // layout tile of the output (tile_seg, shares, chunks): set per graph
+  int emit_tile = 0;       // spelling tile, a multiple of tile_bytes; 0: chosen per launch (emit_span)
   int emit_blocks_per_sm = 8;
   int emit_block_threads = 256;   // CTA size of the spelling kernels: 128, 256 or 512
   int grid_blocks_per_sm = 8;
@@ -173,7 +174,20 @@ struct Tuning {
 
 // The spelling launch parameters as one value, for the keys of captured stages.
 inline unsigned long long emit_launch_key(const Tuning& t) {
-  return (unsigned long long)t.emit_blocks_per_sm | ((unsigned long long)t.emit_block_threads << 16);
+  return (unsigned long long)t.emit_blocks_per_sm | ((unsigned long long)t.emit_block_threads << 16) |
+         ((unsigned long long)t.emit_tile << 32);
+}
+
+// Layout tiles a spelling warp takes at once: emit_tile / layout tile when the
+// caller set one (at least one tile), else the largest span of at most 32 KiB
+// that leaves every one of the launch's warps at least 8 spans of the n layout
+// tiles (big outputs: 32 KiB spans, few per-span overheads; small ones: one
+// layout tile, enough spans to balance).
+__host__ __device__ inline int emit_span(long long n_tiles, long long warps, int emit_tile, int layout_tile) {
+  if (emit_tile > 0) return emit_tile > layout_tile ? emit_tile / layout_tile : 1;
+  int span = 1;
+  while (2 * span * layout_tile <= 32768 && n_tiles / (2 * span) >= 8 * warps) span *= 2;
+  return span;
 }
 
 // CUDA events recorded after each kernel when timing is on.

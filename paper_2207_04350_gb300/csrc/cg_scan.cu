@@ -134,7 +134,9 @@ struct PieceStore {
       contig_off[it.y] = o;
       if (user_fits()) user_off[it.y] = o;
     }
-    long long t0 = (o + tile_bytes - 1) / tile_bytes, t1 = (o + L + tile_bytes - 1) / tile_bytes;
+    // tile_bytes is a power of two: the first tile starting at or after o, and after o + L
+    const int sh = __ffsll(tile_bytes) - 1;
+    long long t0 = (o + tile_bytes - 1) >> sh, t1 = (o + L + tile_bytes - 1) >> sh;
     for (long long t = t0; t < t1; ++t) {
       if (t < tiles_cap) tile_seg[t] = (int32_t)j;
       else set_error(derr, DERR_KERNEL, K_SCAN_OFFSETS, t);

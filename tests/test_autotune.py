@@ -36,7 +36,7 @@ def test_cache_round_trip_and_apply_uses_it(tmp_path, monkeypatch):
         return 2.0 - 0.1 * cand["emit_blocks_per_sm"] - 0.01 * cand["ruler_log2"]
     r1 = autotune.apply(None, None, (1000, 854, 2_500_000), cache=c, device="GB300", time_it=timer)
     assert not r1["cached"] and len(timer_calls) == len(autotune.GRID)
-    assert r1["tuning"] == {"ruler_log2": 5, "tile_bytes": 16384, "emit_blocks_per_sm": 16, "emit_block_threads": 128}
+    assert r1["tuning"] == {"ruler_log2": 5, "tile_bytes": 0, "emit_blocks_per_sm": 16, "emit_block_threads": 128}
     data = json.load(open(path))
     assert data["GB300"][r1["size_class"]]["tuning"] == r1["tuning"]
     # a new process reads the file; no timing happens for a known class

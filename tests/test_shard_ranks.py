@@ -3,7 +3,7 @@ on CPU: two gloo ranks. Each rank's share is made here from the oracle's
 contigs (test input), then the module's collectives bring the shares to
 rank 0, which must get the oracle's whole stream back:
 
-- "tiles": the stream cut into two runs of whole 32 KiB output tiles;
+- "tiles": the stream cut into two runs of whole 4 KiB layout tiles;
 - "lpt": whole contigs split by GreedyPartitioning (the oracle's LPT, weights
   = bases); two ranks that computed different partitions are refused.
 """
@@ -13,7 +13,7 @@ import socket
 import numpy as np
 import torch.multiprocessing as mp
 
-TILE = 32768
+TILE = 4096                                          # the library's layout tile
 
 
 def _free_port() -> int:
