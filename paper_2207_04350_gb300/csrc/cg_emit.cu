@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(BT, 1024 / BT) k_emit(Scratch s, const uint8_t
   const unsigned long long* ws = s.wsrc;
   const long long t_stop = min(ntiles, t_end);          // the layout tiles [t_begin, t_end) of this launch
   // a warp spells `span` consecutive layout tiles at a time
-  const int span = emit_span(t_stop - t_begin, grid_threads() >> 5, emit_tile, tile_bytes);
+  const int span = emit_span(t_stop - t_begin, grid_threads() >> 5, emit_tile, tile_bytes, 8);
   const long long n_spans = (t_stop - t_begin + span - 1) / span;
   TileQueue q(0);                                       // the warp's spans, from counters after the first
   for (; q.t < n_spans; q.next(0, n_spans)) {

@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(BT, BT >= 512 ? 2 : CG_EMIT2_MIN_BLOCKS * 256 
   const long long ntiles = (total + tile_bases - 1) / tile_bases;
   const long long t_stop = min(ntiles, t_end);          // the tiles [t_begin, t_end) of this launch
   // a warp spells `span` consecutive layout tiles at a time, spans taken as the warp frees up
-  const int span = emit_span(t_stop - t_begin, grid_threads() >> 5, emit_tile, tile_bases);
+  const int span = emit_span(t_stop - t_begin, grid_threads() >> 5, emit_tile, tile_bases, 2);
   const long long n_spans = (t_stop - t_begin + span - 1) / span;
   for (TileQueue q(0); q.t < n_spans; q.next(0, n_spans)) {
     q.ask(s.tickets, 0, n_spans, lane);

@@ -180,13 +180,16 @@ inline unsigned long long emit_launch_key(const Tuning& t) {
 
 // Layout tiles a spelling warp takes at once: emit_tile / layout tile when the
 // caller set one (at least one tile), else the largest span of at most 32 KiB
-// that leaves every one of the launch's warps at least 8 spans of the n layout
-// tiles (big outputs: 32 KiB spans, few per-span overheads; small ones: one
-// layout tile, enough spans to balance).
-__host__ __device__ inline int emit_span(long long n_tiles, long long warps, int emit_tile, int layout_tile) {
+// that leaves every one of the launch's warps at least per_warp spans of the n
+// layout tiles (big outputs: 32 KiB spans, few per-span overheads; small ones:
+// one layout tile, enough spans to balance). The ASCII kernel asks for 8 per
+// warp; the 2-bit one, whose fixed cost per span weighs four times more
+// against its bytes, for 2.
+__host__ __device__ inline int emit_span(long long n_tiles, long long warps, int emit_tile, int layout_tile,
+                                         int per_warp) {
   if (emit_tile > 0) return emit_tile > layout_tile ? emit_tile / layout_tile : 1;
   int span = 1;
-  while (2 * span * layout_tile <= 32768 && n_tiles / (2 * span) >= 8 * warps) span *= 2;
+  while (2 * span * layout_tile <= 32768 && n_tiles / (2 * span) >= per_warp * warps) span *= 2;
   return span;
 }
 
