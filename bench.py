@@ -34,7 +34,7 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 # DRAM bytes (read + write) per contig base of k_emit from one ncu capture
 # (--set full, the 3.1 Gb recipe on a 450 Mb genome: 552.2 MB for 481,446,585
 # bases), valid only for the emission source it was taken on.
-EMIT_TRAFFIC = {"bytes_per_base": (129.703680e6 + 422.134528e6) / 481446585, "source_sha256_16": "d9d165b66b4d0c1f"}
+EMIT_TRAFFIC = {"bytes_per_base": (128.766464e6 + 421.409280e6) / 481446585, "source_sha256_16": "81bd7d9611aecfe5"}
 
 
 def _reduce(x: float, world: int, op: str) -> float:
