@@ -978,7 +978,7 @@ def sharded_on_one_gpu(args, ctx, stream, dg, flush, total, whole_ms, n_ranks=8,
                      "speedup_over_one_gpu": whole_ms / mx,
                      "gbases_per_s_n_ranks": total / (mx * 1e-3) / 1e9}
     out["lpt"]["weight"] = "bases (cg_partition_contigs, recomputed by every rank every step)"
-    out["tiles"]["split"] = "equal runs of 32 KiB output tiles (cg_emit_share)"
+    out["tiles"]["split"] = "equal runs of the graph's layout tiles, 8 KiB here (cg_emit_share)"
     out["exchange"] = exchange_on_one_gpu(ctx, stream, dg, flush, n_ranks, steps, args.min_chain_reads)
     return out
 
