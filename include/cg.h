@@ -287,15 +287,16 @@ CG_API cg_status cg_emit_part(cg_graph* g, const int32_t* part, int64_t part_cap
  * that each hold the whole graph and its reads and split the LocalAssembly
  * work among themselves (Sec. 4.3-4.4). Where the paper gives each process
  * whole contigs (cg_partition_contigs + cg_emit_part), this call cuts the
- * output stream of cg_emit_contigs itself into n_shares runs of whole output
- * tiles (tiles of the context's tuning.tile_bytes; runs as equal as the tiles
- * allow) and spells share `share` only, so every share is the same work
- * whatever the contig sizes, and a contig may span two shares. Output:
- * bases[0 .. n_bases) = stream bytes [first_base, first_base + n_bases);
- * concatenating the shares 0..n_shares-1 gives the stream of
+ * output stream of cg_emit_contigs itself into n_shares runs of whole layout
+ * tiles (the graph's: 4 KiB below 2^31 bases of reads, else 8 KiB; runs as
+ * equal as the tiles allow) and spells share `share` only, so every share is
+ * the same work whatever the contig sizes, and a contig may span two shares.
+ * Output: bases[0 .. n_bases) = stream bytes [first_base, first_base +
+ * n_bases); concatenating the shares 0..n_shares-1 gives the stream of
  * cg_emit_contigs. contig_off (optional, n_contigs + 1 entries) gets the
- * whole stream's contig offsets. Every share of one split must use the same
- * tile_bytes. bases: NULL (sizes only) or bases_cap >= the share's size,
+ * whole stream's contig offsets. Every share of one split must come from
+ * graphs of the same reads (the same layout tile). bases: NULL (sizes only)
+ * or bases_cap >= the share's size,
  * 16-byte aligned in device memory; first_base and n_bases are optional
  * (asking for them waits for the GPU). 0 <= share < n_shares, else
  * CG_EINVAL. Runs the earlier steps first. */
