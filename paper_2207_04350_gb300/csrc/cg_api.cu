@@ -897,9 +897,11 @@ cg_status cg_load_batch(cg_ctx* c, const cg_graph_desc* d, int k, uint32_t flags
   g->batch_k = k;
   g->batch_R = tab;
   if (!host_reads) CK(cudaMemsetAsync(packed, 0, (size_t)PB[k] + 16, c->stream), "clear packed");
-  // Host inputs all in pinned memory: one kernel reads them in place (a copy
-  // call per graph and array costs a few microseconds of host time each, which
-  // dominates a batch of hundreds of small graphs); otherwise a copy per array.
+  // Host inputs all in pinned memory: one kernel reads the graph arrays in place
+  // (a copy call per graph and array costs a few microseconds of host time
+  // each, which dominates a batch of hundreds of small graphs); the packed
+  // reads, when copied, go by the copy engines, which move large arrays over
+  // the host link faster than the kernel. Otherwise a copy per array.
   std::vector<cg::CopySeg> segs;
   bool in_place = mem == CG_MEM_HOST;
   for (int j = 0; j < k && in_place; ++j) {
@@ -920,17 +922,21 @@ cg_status cg_load_batch(cg_ctx* c, const cg_graph_desc* d, int k, uint32_t flags
     if (xdrop) add(post + E[j], q.post, q.n_entries * 4ll);
     add(len + R[j], q.len, q.n_reads * 4ll);
     add(off + R[j], q.off, q.n_reads * 8ll);
-    if (!host_reads) add(packed + PB[j], q.packed, q.packed_bytes);
   }
   cg::CopySeg* d_segs = nullptr;
-  if (in_place && !segs.empty()) {
-    d_segs = (cg::CopySeg*)dalloc(c, segs.size() * sizeof(cg::CopySeg), &st);
-    if (!d_segs) { dfree(c, stage_rp); return bail(st); }
-    cudaError_t e = cudaMemcpyAsync(d_segs, segs.data(), segs.size() * sizeof(cg::CopySeg), cudaMemcpyHostToDevice,
-                                    c->stream);
-    if (e == cudaSuccess) e = cg::launch_batch_copy(d_segs, (int)segs.size(), c->env);
+  if (in_place) {
+    cudaError_t e = cudaSuccess;
+    if (!segs.empty()) {
+      d_segs = (cg::CopySeg*)dalloc(c, segs.size() * sizeof(cg::CopySeg), &st);
+      if (!d_segs) { dfree(c, stage_rp); return bail(st); }
+      e = cudaMemcpyAsync(d_segs, segs.data(), segs.size() * sizeof(cg::CopySeg), cudaMemcpyHostToDevice, c->stream);
+      if (e == cudaSuccess) e = cg::launch_batch_copy(d_segs, (int)segs.size(), c->env);
+    }
+    for (int j = 0; j < k && e == cudaSuccess && !host_reads; ++j)
+      if (d[j].packed_bytes > 0)
+        e = cudaMemcpyAsync(packed + PB[j], d[j].packed, (size_t)d[j].packed_bytes, kind, c->stream);
     if (e != cudaSuccess) {
-      dfree(c, d_segs);
+      if (d_segs) dfree(c, d_segs);
       dfree(c, stage_rp);
       return bail(cuda_fail(c, e, "copy batch input"));
     }
