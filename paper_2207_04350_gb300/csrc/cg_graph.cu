@@ -953,7 +953,13 @@ cudaError_t launch_chains(const DevGraph& g, const Scratch& s, const Tuning& t, 
   cudaMemsetAsync(&s.ctr->n_rulers, 0, offsetof(Counters, n_contigs) - offsetof(Counters, n_rulers), env.stream);
   static const int succ_resident = resident_blocks(k_succ);   // persistent grids
   static const int final_resident = resident_blocks(k_final);
-  k_succ<<<env.num_sms * succ_resident, kBlock, 0, env.stream>>>(g, s, t.ruler_log2);
+  // a persistent grid, but no more blocks than the reads can use (a small
+  // graph's launches would otherwise spend their time starting idle blocks)
+  auto cap = [&](long long resident_grid, long long items_per_block) {
+    const long long need = (g.n + items_per_block - 1) / items_per_block;
+    return (int)std::max(1LL, std::min(resident_grid, need));
+  };
+  k_succ<<<cap((long long)env.num_sms * succ_resident, kBlock), kBlock, 0, env.stream>>>(g, s, t.ruler_log2);
   mark(env, "k_succ");
   cudaError_t e = launch_k(k_walk, grid_for(2 * g.n, env), env, true, s, t.ruler_log2, (int64_t)(2 * g.n + 1));
   if (e != cudaSuccess) return e;
@@ -963,15 +969,17 @@ cudaError_t launch_chains(const DevGraph& g, const Scratch& s, const Tuning& t, 
   mark(env, "k_listwalk");
   Scratch sc = s;
   void* args[] = {&sc};
-  e = coop((const void*)k_jump, env.coop_blocks, args, env, true);
+  const int coop_grid = cap(env.coop_blocks, kBlock / 2);   // up to 2 rulers or candidates per read
+  e = coop((const void*)k_jump, coop_grid, args, env, true);
   if (e != cudaSuccess) return e;
   mark(env, "k_jump");
   DevGraph gg = g;
-  e = launch_k(k_final, env.num_sms * final_resident, env, true, gg, s);
+  e = launch_k(k_final, cap((long long)env.num_sms * final_resident, (long long)kBlock * kFinalItems), env, true, gg,
+               s);
   if (e != cudaSuccess) return e;
   mark(env, "k_final");
   void* args2[] = {&gg, &sc};
-  e = coop((const void*)k_cycles, env.coop_blocks, args2, env, true);
+  e = coop((const void*)k_cycles, coop_grid, args2, env, true);
   if (e != cudaSuccess) return e;
   mark(env, "k_cycles");
   return cudaGetLastError();

@@ -277,7 +277,9 @@ cudaError_t launch_offsets(const DevGraph& g, const Scratch& s, const Tuning& t,
   if (e != cudaSuccess) return e;
   mark(env, "k_scan_heads");
   static const int scatter_resident = resident_blocks(k_scatter);   // a persistent grid
-  e = launch_k(k_scatter, env.num_sms * scatter_resident, env, true, g, s);
+  const long long scatter_need = (g.n + (long long)kBlock * kScatterItems - 1) / ((long long)kBlock * kScatterItems);
+  e = launch_k(k_scatter, (int)std::max(1LL, std::min((long long)env.num_sms * scatter_resident, scatter_need)), env,
+               true, g, s);
   if (e != cudaSuccess) return e;
   mark(env, "k_scatter");
   PieceLoad pl{s.wlen, s.wfirst};
