@@ -199,7 +199,11 @@ CG_API cg_status cg_server_contexts_replaced(cg_server* s, uint64_t* replaced);
 CG_API cg_status cg_server_stop(cg_server* s);
 
 /* BranchRemoval (Alg. 2; Sec. 4.2). is_branch: NULL or n bytes (1 = branch),
- * in `mem`. n_branch: NULL or receives the count (waits for the GPU). */
+ * in `mem`. n_branch: NULL or receives the count (waits for the GPU).
+ * Asked for neither (and with CUDA graphs on, no per-kernel timing), the call
+ * only records that the step is due: its kernels are launched by the next call
+ * on the graph, in one CUDA graph with that call's own stages when it spells
+ * into device buffers. The same holds for cg_chains asked for nothing. */
 CG_API cg_status cg_mask_branches(cg_graph* g, uint8_t* is_branch, int mem, int64_t* n_branch);
 
 /* ConnectedComponent + the walk order of every chain (Alg. 2; Sec. 4.2, 4.4).

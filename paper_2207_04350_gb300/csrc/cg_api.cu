@@ -58,7 +58,8 @@ struct cg_graph {
   cg::DevGraph g{};
   cg::Scratch s{};
   std::vector<void*> owned;
-  int stage = 0;                  // 0 loaded, 1 masked, 2 chained, 3 offsets
+  int stage = 0;                  // 0 loaded, 1 masked, 2 chained, 3 offsets (launches issued)
+  int want = 0;                   // a later stage asked for with nothing to return, not yet launched
   int64_t sum_len = 0;
   int layout_tile = 4096;         // output layout tile (gt)
   uint8_t* stage_bases = nullptr; // device staging for host outputs
@@ -67,8 +68,8 @@ struct cg_graph {
   int32_t* part_buf = nullptr;         // device copy of a host part assignment (cg_emit_part)
   int64_t part_buf_cap = 0;
   unsigned long long* d_sum = nullptr;
-  StageExec execs[7];                  // mask, chains, offsets, emission, contig_off export, 2-bit emission,
-                                       // offsets + emission + export in one graph
+  StageExec execs[8];                  // mask, chains, offsets, emission, contig_off export, 2-bit emission,
+                                       // offsets + emission + export in one graph, all stages in one graph
   int batch_k = 0;                     // graphs of a batch (0: a single graph)
   int64_t* batch_R = nullptr;          // device: first read of each graph, batch_k + 1 entries
   // a batch whose reads stay in pinned host memory: per graph its stream's
@@ -155,8 +156,14 @@ T* galloc(cg_graph* g, size_t count, cg_status* st) {
 }
 
 // Reads the context error word and the graph counters (waits for the stream).
+cg_status flush(cg_graph* g);
+
 cg_status wait_and_read(cg_graph* g) {
   cg_ctx* c = g->ctx;
+  if (g->want) {                          // launches that still wait go first
+    cg_status st0 = flush(g);
+    if (st0 != CG_OK) return st0;
+  }
   CK(cudaMemcpyAsync(c->h_err, c->derr, sizeof(cg::DevError), cudaMemcpyDeviceToHost, c->stream), "read error word");
   if (g->s.ctr)
     CK(cudaMemcpyAsync(c->h_ctr, g->s.ctr, sizeof(cg::Counters), cudaMemcpyDeviceToHost, c->stream), "read counters");
@@ -316,8 +323,29 @@ cg_status run_chains(cg_graph* g) {
   return CG_OK;
 }
 
+// The mask and chain calls return nothing when asked for no outputs or
+// counts; then, with graphs on and no per-kernel marks or per-stage events,
+// their launches wait for the next call, so that a spelling into device
+// buffers replays all four stages as one CUDA graph (each graph launch of its
+// own costs the GPU a few microseconds between stages). flush() issues what
+// waits; every call that uses the graph's device state does that first.
+bool defer_ok(const cg_ctx* c) {
+  return c->graphs && !c->marks.on && (!c->timing || c->timing_emit_only);
+}
+
+cg_status flush(cg_graph* g) {
+  const int want = g->want;
+  g->want = 0;
+  if (want > g->stage) return want >= 2 ? run_chains(g) : run_mask(g);
+  return CG_OK;
+}
+
 cg_status run_offsets(cg_graph* g) {
   cg_ctx* c = g->ctx;
+  if (g->want) {
+    cg_status st0 = flush(g);
+    if (st0 != CG_OK) return st0;
+  }
   if (g->stage < 2) {
     cg_status st0 = run_chains(g);
     if (st0 != CG_OK) return st0;
@@ -1031,6 +1059,12 @@ cg_status cg_mask_branches(cg_graph* g, uint8_t* is_branch, int mem, int64_t* n_
   cg_status st = check_ctx(c);
   if (st != CG_OK) return st;
   if (mem != CG_MEM_HOST && mem != CG_MEM_DEVICE) return fail(c, CG_EINVAL, "bad mem");
+  if (!is_branch && !n_branch && defer_ok(c)) {   // nothing to return: launched with the next call
+    g->stage = 0;
+    g->want = 1;
+    return CG_OK;
+  }
+  g->want = 0;
   st = run_mask(g);
   if (st != CG_OK) return st;
   if (is_branch && g->g.n > 0)
@@ -1052,6 +1086,15 @@ cg_status cg_chains(cg_graph* g, int32_t* chain_id, int32_t* rank, uint8_t* orie
   cg_status st = check_ctx(c);
   if (st != CG_OK) return st;
   if (mem != CG_MEM_HOST && mem != CG_MEM_DEVICE) return fail(c, CG_EINVAL, "bad mem");
+  if (!chain_id && !rank && !orient && !n_contigs && !n_cycles && defer_ok(c)) {
+    if (g->stage > 1) g->stage = 1;        // nothing to return: launched with the next call
+    g->want = 2;
+    return CG_OK;
+  }
+  if (g->want) {
+    st = flush(g);
+    if (st != CG_OK) return st;
+  }
   st = run_chains(g);
   if (st != CG_OK) return st;
   const int64_t n = g->g.n;
@@ -1094,21 +1137,35 @@ cg_status cg_emit_contigs(cg_graph* g, int64_t* contig_off, int64_t contig_off_c
   if (mem != CG_MEM_HOST && mem != CG_MEM_DEVICE) return fail(c, CG_EINVAL, "bad mem");
   if ((bases && bases_cap < 0) || (contig_off && contig_off_cap < 1)) return fail(c, CG_EINVAL, "bad capacity");
   if (mem == CG_MEM_DEVICE && bases && !g->host_batch) {
-    // the layout, the spelling and the offsets export replayed as one graph
+    // the layout, the spelling and the offsets export replayed as one graph;
+    // with the mask and chain launches too when both wait (a whole step in one)
     if (!aligned(bases, 16)) return fail(c, CG_EINVAL, "device bases buffer must be 16-byte aligned");
-    if (g->stage < 2) {
-      st = run_chains(g);
-      if (st != CG_OK) return st;
+    const bool whole = g->want == 2 && g->stage == 0 && defer_ok(c);
+    if (!whole) {
+      if (g->want) {
+        st = flush(g);
+        if (st != CG_OK) return st;
+      }
+      if (g->stage < 2) {
+        st = run_chains(g);
+        if (st != CG_OK) return st;
+      }
     }
+    g->want = 0;
     const bool timing = c->timing != 0, stages = timing && !c->timing_emit_only;
     uint64_t key = mix_key(mix_key(mix_key(mix_key((uint64_t)(uintptr_t)bases, (uint64_t)bases_cap),
                                            (uint64_t)(uintptr_t)g->g.packed), (uint64_t)gt(g).tile_bytes),
                            (uint64_t)cg::emit_launch_key(gt(g)));
     key = mix_key(mix_key(mix_key(key, (uint64_t)(uintptr_t)contig_off), (uint64_t)contig_off_cap),
                   stages ? 3 : (timing ? 5 : 4));
+    if (whole) key = mix_key(key, (uint64_t)gt(g).ruler_log2);
     // the caller's contig offsets come from the piece scan itself (no copy kernel)
     const bool fold_off = contig_off && g->g.n > 0;
-    st = run_stage(g, 6, key, [&]() -> cg_status {
+    st = run_stage(g, whole ? 7 : 6, key, [&]() -> cg_status {
+      if (whole) {
+        CK(cg::launch_mask(g->g, g->s, c->env), "mask kernels");
+        CK(cg::launch_chains(g->g, g->s, gt(g), c->env), "chain kernels");
+      }
       if (stages) record_stage_event(c, 4);
       CK(cg::launch_offsets(g->g, g->s, gt(g), c->env, fold_off ? contig_off : nullptr,
                             fold_off ? contig_off_cap : 0), "offset kernels");
