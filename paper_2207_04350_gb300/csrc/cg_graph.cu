@@ -391,8 +391,8 @@ void launch_mask_kernel(const DevGraph& g, const Scratch& s, const LaunchEnv& en
 // candidate indexes (-1: a branch read) are loaded before any store. The
 // start lists gather in per-warp shared-memory buffers and reach the global
 // lists with one reservation per block at the end (a warp flushes early only
-// when its buffer runs full); a start learns its sublist id, rr[u] = (id, 0),
-// when it is written out.
+// when its buffer runs full); a start learns its sublist id (kept in the
+// successor record's last field for (c,0)) when it is written out.
 constexpr int kSuccWarps = kBlock / 32;
 constexpr int kSuccStarts = 256;    // sublist starts per warp: oriented candidate | list head << 31
 
@@ -410,7 +410,9 @@ __device__ __forceinline__ void put_starts(const Scratch& s, const uint32_t* buf
       const int32_t u = (int32_t)(e & 0x7fffffffu);
       head = (e >> 31) != 0;
       s.rlist[rbase + i] = u;
-      s.rr[u] = make_int2((int32_t)(rbase + i), 0);
+      // a sampled read's two copies are consecutive starts, (c,0) first: its
+      // record keeps the first id, for the walks that end there
+      if ((u & 1) == 0) s.succ[u >> 1].w = (int32_t)(rbase + i);
     }
     const unsigned hm = __ballot_sync(0xffffffffu, head);
     if (head) s.hlist[hbase + h + __popc(hm & lt)] = (int32_t)(rbase + i);
@@ -525,7 +527,7 @@ __global__ void k_walk(Scratch s, int ruler_log2, int64_t limit) {
   for (long long r = grid_tid(); r < R; r += grid_threads()) {
     const int32_t x = s.rlist[r];
     const int4 sv = s.succ[x >> 1];
-    int32_t y = x, z = (x & 1) ? sv.y : sv.x, vy = sv.z, mn = sv.z, next_start = -1;
+    int32_t y = x, z = (x & 1) ? sv.y : sv.x, vy = sv.z, mn = sv.z, next = -1;
     int32_t cnt = 0;
     for (;;) {
       s.rr[y] = make_int2((int32_t)r, cnt);
@@ -533,14 +535,13 @@ __global__ void k_walk(Scratch s, int ruler_log2, int64_t limit) {
       mn = min(mn, vy);
       if (z < 0) break;
       const int4 sz = s.succ[z >> 1];
-      if (sampled(sz.z, ruler_log2)) { next_start = z; break; }
+      if (sampled(sz.z, ruler_log2)) { next = sz.w + (z & 1); break; }   // the sublist z starts
       y = z;
       vy = sz.z;
       z = (z & 1) ? sz.y : sz.x;
       if (cnt > limit) { set_error(s.derr, DERR_KERNEL, K_WALK, y); break; }
     }
-    // the next sublist's id, written by k_succ for every sublist start
-    s.rec[r] = make_int4(next_start >= 0 ? s.rr[next_start].x : -1, cnt, mn, 2 * vy + (y & 1));
+    s.rec[r] = make_int4(next, cnt, mn, 2 * vy + (y & 1));
     s.pj[0][r].x = kUnresolved;
   }
 }

@@ -82,7 +82,8 @@ struct Scratch {
   // The chain stage indexes candidates, c = cidx[v], and their oriented
   // copies u = 2c + o: its records sit together in candidate order instead
   // of spreading over arrays of n reads.
-  int4* succ;           // n: (successor of (c,fwd), successor of (c,rc) as oriented candidates, or -1; read id; 0)
+  int4* succ;           // n: (successor of (c,fwd), successor of (c,rc) as oriented candidates, or -1; read id;
+                        //     the sublist (c,fwd) starts, when it starts one)
   int32_t* sufin;       // 2n: suffix (x-drop form: post) of the overlap entering oriented candidate u
   int32_t* preout;      // 2n, x-drop form only: pre of the overlap leaving oriented candidate u
   int32_t* pfirst;      // n, x-drop form only: per candidate, stored index of the piece's first base

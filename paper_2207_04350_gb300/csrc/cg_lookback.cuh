@@ -156,8 +156,10 @@ __global__ void __launch_bounds__(kBlock) k_scan(Load ld, Store st, long long co
         long long i = base + k * kBlock + tid;
         if (i < count) {
           unsigned long long e = sm[k * kBlock + tid];
+          // the total before the item's store: a store may reuse its load's inputs
+          const unsigned long long tot = i == count - 1 ? e + ld.value(i, it[k]) : 0ull;
           st.item(i, e, it[k]);
-          if (i == count - 1) st.last(count, e + ld.value(i, it[k]));
+          if (i == count - 1) st.last(count, tot);
         }
       }
     } else {
@@ -165,8 +167,9 @@ __global__ void __launch_bounds__(kBlock) k_scan(Load ld, Store st, long long co
         long long i = base + k * kBlock + tid;
         if (i < count) {
           unsigned long long e = sm[k * kBlock + tid];
+          const unsigned long long tot = i == count - 1 ? e + ld(i) : 0ull;
           st.item(i, e);
-          if (i == count - 1) st.last(count, e + ld(i));
+          if (i == count - 1) st.last(count, tot);
         }
       }
     }
