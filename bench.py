@@ -1242,7 +1242,7 @@ def form_records(args, local_rank):
     the main line: the tiny and 100 Mb plain graphs, the 512-graph batch (one
     union pass against the same graphs one by one) and the 2000-request
     served stream (continuous batching against one request at a time), each
-    with its oracle leg's bit-exact verdict."""
+    with its oracle leg's bit-exact result."""
     import copy
 
     import torch
@@ -1313,7 +1313,7 @@ def cpu_baseline(args, cfg, steps=None, warmup=0, budget_s=None):
     workload: the workload's recipe on a smaller genome. Without budget_s the
     genome is 20 Mb and the oracle repeats for about `cpu_seconds`; with it,
     the genome is the largest (up to the workload's own) whose warmup + steps
-    runs fit budget_s, judged from one run on 200 Mb."""
+    runs fit budget_s, estimated from one run on 200 Mb."""
     import gen
     import oracle
     G0 = cfg["genome_len"]
